@@ -1,0 +1,344 @@
+"""Benchmark of the block-SVD recommender hot path on GB300.
+
+One step = the whole hot path on one synthetic rating matrix already in
+HBM: partition + block means + dense scatter, Gram products, truncated
+eigen-solve, projection, held-out prediction and RMSE. The default workload
+is the MovieLens-1M-shaped matrix (6040 users x 3952 items, 1,000,209
+ratings, 90/10 split) on a 4 x 4 grid with k = 20.
+
+Prints one JSON line (rank 0). Usage:
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own copy of the workload (weak scaling;
+no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+FP32_LANES_PER_SM = 128
+SMS = 152
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def fp32_alu_peak_tflops(peaks):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock
+    return SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def gram_flops(blocks):
+    """Symmetric Gram: s(s+1)/2 entries, 2L flops each, per block."""
+    return float(sum(L * s * (s + 1) for (s, L) in blocks))
+
+
+def block_shapes(w):
+    br, bc = -(-w.m // w.p), -(-w.n // w.q)
+    shapes = []
+    for bi in range(w.p):
+        mb = min(w.m, (bi + 1) * br) - bi * br
+        for bj in range(w.q):
+            nb = min(w.n, (bj + 1) * bc) - bj * bc
+            shapes.append((min(mb, nb), max(mb, nb)))
+    return shapes
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed loop."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "bsvd_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def golden_rmse(w):
+    path = os.path.join(ROOT, "tests", "golden", w.name + ".json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)["rmse"]
+    return None
+
+
+def oracle_sample(w, r, nblocks, threads):
+    """The oracle (as it stands) on a bounded sample: partition of all the
+    ratings, factorisation of `nblocks` blocks, RMSE over their held-out
+    ratings. Returns (seconds, blocks)."""
+    import oracle
+    t0 = time.perf_counter()
+    part = oracle.partition(w.m, w.n, r.u_train, r.i_train, r.x_train, w.p,
+                            w.q)
+    ids = list(range(min(nblocks, w.p * w.q)))
+    model = oracle.factor(part, w.k, blocks=ids, threads=threads)
+    b, _, _ = part.grid.locate(r.u_test, r.i_test)
+    sel = np.isin(b, ids)
+    if sel.any():
+        oracle.rmse(model, r.u_test[sel], r.i_test[sel], r.x_test[sel])
+    return time.perf_counter() - t0, len(ids)
+
+
+def run_reference(args, w, r, rank):
+    """Reference arm: the FP64 oracle on the host cores."""
+    if rank != 0:
+        return
+    cores = min(os.cpu_count() or 1, w.p * w.q)
+    times = []
+    for step in range(args.warmup + args.steps):
+        dt, nb = oracle_sample(w, r, cores, cores)
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = nb * len(times) / total
+    sample = ("per step: oracle partition of all %d training ratings, FP64 "
+              "Jacobi SVD of %d of the %d blocks (one thread each), RMSE over "
+              "their held-out ratings" % (r.u_train.size, nb, w.p * w.q))
+    line = {
+        "impl": "reference", "metric": "block SVDs/s", "value": value,
+        "unit": "block-SVDs/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "m": w.m, "n": w.n, "p": w.p,
+                   "q": w.q, "k": w.k},
+        "cpu_baseline": {"value": value, "unit": "block-SVDs/s",
+                         "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "block-SVDs/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default=synth.MEDIUM.name,
+                    choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w = synth.WORKLOADS[args.workload]
+    r = synth.generate(w)
+
+    if args.impl == "reference":
+        run_reference(args, w, r, rank)
+        return
+
+    import torch
+    import paper_1907_07410_gb300 as bs
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    u_tr, i_tr, x_tr = dev(r.u_train), dev(r.i_train), dev(r.x_train)
+    u_te, i_te, x_te = dev(r.u_test), dev(r.i_test), dev(r.x_test)
+    stream = torch.cuda.current_stream()
+    ctx = bs.Context(stream=stream, profile=1)
+    nblocks = w.p * w.q
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        ctx.partition(w.m, w.n, u_tr, i_tr, x_tr, w.p, w.q)
+        ctx.factor(w.k)
+        return ctx.rmse(u_te, i_te, x_te)
+
+    for _ in range(args.warmup):
+        rm = step()
+
+    # ---- device-resident timed region -----------------------------------
+    phases = {k: [] for k in bs.PHASES}
+    step_ms = []
+    launches0 = ctx.kernel_launches()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1)                       # evict L2 between steps (untimed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        part_ph = None
+        ctx.partition(w.m, w.n, u_tr, i_tr, x_tr, w.p, w.q)
+        part_ph = ctx.phase_times()["partition"]
+        ctx.factor(w.k)
+        fac_ph = ctx.phase_times()
+        rm = ctx.rmse(u_te, i_te, x_te)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        ph = ctx.phase_times()
+        phases["partition"].append(part_ph)
+        for key in ("gram", "eigen", "project"):
+            phases[key].append(fac_ph[key])
+        phases["predict"].append(ph["predict"])
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.kernel_launches() - launches0
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # ---- end to end through the public API with host buffers -------------
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    h_u, h_i, h_x = pin(r.u_train), pin(r.i_train), pin(r.x_train)
+    h_ut, h_it, h_xt = pin(r.u_test), pin(r.i_test), pin(r.x_test)
+    e2e_ms = []
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.partition(w.m, w.n, h_u, h_i, h_x, w.p, w.q)
+        ctx.factor(w.k)
+        rm_e2e = ctx.rmse(h_ut, h_it, h_xt)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    barrier()
+    e2e_total = sum(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = load_peaks()
+    shapes = block_shapes(w)
+    gflops = gram_flops(shapes)
+    gram_ms = statistics.mean(phases["gram"])
+    alu_peak = fp32_alu_peak_tflops(peaks)
+    achieved = gflops / (gram_ms * 1e-3) / 1e12
+    value = world * nblocks * args.steps / (total_ms * 1e-3)
+    proj_flops = 2.0 * sum(L * s * w.k for (s, L) in shapes)
+    pred_flops = 2.0 * w.k * r.u_test.size
+    tflops = (gflops + proj_flops + pred_flops) * args.steps / (total_ms * 1e-3) / 1e12
+    gold = golden_rmse(w)
+    line = {
+        "metric": "block SVDs/s", "value": value, "unit": "block-SVDs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded MovieLens-1M-shaped ratings, in HBM)",
+        "config": {"workload": w.name, "m": w.m, "n": w.n,
+                   "nnz_train": int(r.u_train.size),
+                   "nnz_test": int(r.u_test.size), "p": w.p, "q": w.q,
+                   "k": w.k, "precision": "fp32",
+                   "l2": "flushed (256 MB write) before each step, untimed"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "tflops": tflops,
+        "phases_ms": {k: statistics.mean(v) for k, v in phases.items()},
+        "rmse": rm, "rmse_oracle": gold,
+        "rmse_parity": (gold is not None and abs(rm - gold) <= 1e-4),
+        "roofline": {"kernel": "k_gram_f32", "bound": "alu",
+                     "achieved": achieved, "peak": alu_peak,
+                     "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                     "traffic": None,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz"
+                                    % peaks.get("sm_max_mhz", 2070.0)},
+        "gpu_launches": int(launches),
+        "e2e": {"value": world * nblocks * args.steps / (e2e_total * 1e-3),
+                "unit": "block-SVDs/s",
+                "h2d_bytes_per_step": int(12 * (r.u_train.size + r.u_test.size)),
+                "d2h_bytes_per_step": 8, "rmse": rm_e2e},
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cores = min(os.cpu_count() or 1, nblocks)
+        dt, nb = oracle_sample(w, r, cores, cores)
+        line["cpu_baseline"] = {
+            "value": nb / dt, "unit": "block-SVDs/s", "cores": cores,
+            "kind": "oracle",
+            "sample": "oracle partition of all ratings + FP64 Jacobi SVD of "
+                      "%d of %d blocks (one thread each) + their held-out "
+                      "RMSE, %.1f s" % (nb, nblocks, dt)}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * bsvd.h: C ABI of the block-SVD recommender library (libbsvd.so).
+ *
+ * The library runs one method on one GPU: the block-based truncated SVD
+ * recommender of Bhavana, Kumar and Padmanabhan, "Block based Singular
+ * Value Decomposition approach to matrix factorization for recommender
+ * systems" (arXiv 1907.07410).
+ *
+ *   1. bsvd_partition: scatter the training ratings into a p x q grid of
+ *      dense blocks (Section 3, Eq. "datax"), centre each block on its
+ *      mean rating and fill missing cells with that mean (so they become 0).
+ *   2. bsvd_factor: truncated rank-k SVD of every block (Section 2, Eq. 1
+ *      and the rank-k truncation after it).
+ *   3. bsvd_predict / bsvd_rmse: predict held-out ratings as
+ *      mu_b + p_u . q_i (Section 2.1, Eq. 2) and score them by RMSE
+ *      (Section 5, Table 1 "Test RMSE").
+ *
+ * Conventions shared by every call:
+ *   - Ids are 0-based. A rating is observed when it is listed in the COO
+ *     input. Ratings must be finite, |x| < 2^31, and a block's count times
+ *     its largest |x| must stay below 2^31. Block sums are then exact for
+ *     every rating that is a multiple of 2^-32; in float32 that is every
+ *     value with |x| >= 2^-9. Smaller non-zero ratings are rounded to a
+ *     multiple of 2^-32 before they are summed.
+ *   - Pointers named "host or device" may point to either kind of memory.
+ *     The library asks the CUDA runtime which kind it is. Host data is
+ *     copied to device buffers that the context owns; device data is used
+ *     in place. The caller keeps ownership of every pointer it passes. The
+ *     library never frees or keeps caller memory after a call returns.
+ *   - Work is queued on the stream in the config (NULL: the legacy default
+ *     stream). Every call below synchronises that stream before it
+ *     returns, so its status also covers the GPU work it launched.
+ *   - Errors come back as status codes; no exception crosses the ABI and the
+ *     library never exits, aborts or traps on the device. After an error,
+ *     bsvd_last_error() describes it. A device-side check that fails (an id
+ *     out of range, a non-finite rating) sets a flag that the call reads
+ *     back as BSVD_EINVAL.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef BSVD_H
+#define BSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bsvd_ctx bsvd_ctx;
+
+typedef enum {
+    BSVD_OK = 0,
+    BSVD_EINVAL = 1,    /* bad argument or bad input data */
+    BSVD_ENOMEM = 2,    /* device or host allocation failed */
+    BSVD_ECUDA = 3,     /* a CUDA runtime call failed */
+    BSVD_ENOTCONV = 4,  /* an eigen-solver hit its iteration cap */
+    BSVD_ETIMEOUT = 5,  /* reserved for bounded device-side waits */
+    BSVD_ESTATE = 6     /* call out of order (e.g. factor before partition) */
+} bsvd_status;
+
+typedef enum {
+    BSVD_FP32 = 0       /* float32 blocks, Gram products and solver */
+} bsvd_precision;
+
+typedef struct {
+    int32_t precision;    /* bsvd_precision */
+    int32_t clamp;        /* 1: clip predictions to [clamp_lo, clamp_hi] */
+    float clamp_lo;
+    float clamp_hi;
+    int32_t oversample;   /* subspace columns beyond k; <= 0: default */
+    int32_t cheb_degree;  /* Chebyshev filter degree; <= 0: default (8) */
+    int32_t max_iters;    /* subspace iterations cap; <= 0: default (30) */
+    int32_t max_sweeps;   /* Jacobi sweeps cap per small solve; <= 0: 30 */
+    int32_t profile;      /* 1: time each phase with CUDA events */
+    int32_t reserved;     /* must be 0 */
+    double tol;           /* residual |G v - theta v| <= tol * theta_1;
+                             <= 0: default (1e-5) */
+    uint64_t seed;        /* seed of the start basis */
+    void *stream;         /* cudaStream_t, or NULL for the default stream */
+} bsvd_config;
+
+/* Fill *cfg with the defaults listed above. */
+void bsvd_config_default(bsvd_config *cfg);
+
+/*
+ * Create a context on the current CUDA device. cfg may be NULL (defaults).
+ * Errors: BSVD_EINVAL (bad config), BSVD_ECUDA (no usable device),
+ * BSVD_ENOMEM.
+ */
+bsvd_status bsvd_create(const bsvd_config *cfg, bsvd_ctx **out);
+
+/* Free the context and every device buffer it owns. NULL is ignored. */
+void bsvd_destroy(bsvd_ctx *ctx);
+
+/* Description of the last error on this context ("" if none). */
+const char *bsvd_last_error(const bsvd_ctx *ctx);
+
+/*
+ * Partition (Section 3, Eq. "datax") plus block means and the dense,
+ * centred blocks.
+ *
+ * m, n       users and items of the rating matrix X (m x n); m, n >= 1.
+ * nnz        number of training ratings (>= 0).
+ * u, i, x    host or device arrays of nnz entries: user id, item id and
+ *            rating. A (u, i) pair must not repeat (not checked).
+ * p, q       block rows and block columns, 1 <= p <= m, 1 <= q <= n.
+ * row_bounds host array of p + 1 increasing positions with row_bounds[0]
+ *            = 0 and row_bounds[p] = m; block row bi holds row positions
+ *            [row_bounds[bi], row_bounds[bi+1]). NULL selects the paper's
+ *            equal blocks: ceil(m/p) rows each, the last holding the rest.
+ * col_bounds the same for the q block columns over n items.
+ * row_perm   host or device array of m entries, a permutation mapping user
+ *            id -> row position; NULL means position = id.
+ * col_perm   the same for items (n entries).
+ *
+ * Block b = bi * q + bj. Its mean mu_b is the exact sum of its training
+ * ratings divided by their count in float64, then rounded to float32. An
+ * empty block takes the global training mean (0 if nnz = 0). The dense
+ * block holds float32(x - mu_b) at observed cells and 0 elsewhere.
+ * A new partition discards any previous partition and factors.
+ * Errors: BSVD_EINVAL (bad sizes, bounds or permutation; an id out of
+ * range; a non-finite or too large rating), BSVD_ENOMEM, BSVD_ECUDA.
+ */
+bsvd_status bsvd_partition(bsvd_ctx *ctx, int64_t m, int64_t n, int64_t nnz,
+                           const int32_t *u, const int32_t *i,
+                           const float *x, int32_t p, int32_t q,
+                           const int64_t *row_bounds,
+                           const int64_t *col_bounds,
+                           const int32_t *row_perm, const int32_t *col_perm);
+
+/*
+ * Truncated SVD of every block (Section 2, Eq. 1 and the rank-k truncation
+ * after it): keep the k_eff = min(k, min(m_b, n_b)) largest singular values
+ * of each centred block B_b and their singular vectors.
+ *
+ * The library forms the Gram matrix of the block's shorter side and finds
+ * its top eigenpairs by Chebyshev-filtered subspace iteration with
+ * Rayleigh-Ritz steps solved by Jacobi. Factors stay on the device.
+ * k >= 0; k = 0 keeps no factor (predictions are then the block means).
+ * The limit is k <= 56.
+ * Errors: BSVD_ESTATE (no partition), BSVD_EINVAL (k out of range),
+ * BSVD_ENOTCONV (some block hit the iteration cap; its factors are still
+ * stored and usable), BSVD_ENOMEM, BSVD_ECUDA.
+ */
+bsvd_status bsvd_factor(bsvd_ctx *ctx, int32_t k);
+
+/*
+ * Predict nq ratings (Section 2.1, Eq. 2): yhat = mu_b + P_b[r,:] . V_b[c,:]
+ * with P_b = U_k S_k, clipped to [clamp_lo, clamp_hi] when clamp = 1.
+ * u, i: host or device arrays of nq ids. yhat: host or device array of nq
+ * floats, written by the call. nq >= 0.
+ * Errors: BSVD_ESTATE (no factors), BSVD_EINVAL (id out of range).
+ */
+bsvd_status bsvd_predict(bsvd_ctx *ctx, int64_t nq, const int32_t *u,
+                         const int32_t *i, float *yhat);
+
+/*
+ * Root mean squared error of the predictions for nq held-out ratings y
+ * (Section 5, Table 1 "Test RMSE"): sqrt(sum (yhat - y)^2 / nq). The
+ * squared errors are summed in float64 in a fixed order, so the result is
+ * the same on every run. u, i, y: host or device arrays of nq entries;
+ * nq >= 1. *out_rmse: host double.
+ * Errors: BSVD_ESTATE, BSVD_EINVAL.
+ */
+bsvd_status bsvd_rmse(bsvd_ctx *ctx, int64_t nq, const int32_t *u,
+                      const int32_t *i, const float *y, double *out_rmse);
+
+/*
+ * Grid information after a partition: number of blocks and the count and
+ * mean of each. counts (int64) and mu (float): host arrays of p*q entries,
+ * either may be NULL.
+ */
+bsvd_status bsvd_block_stats(bsvd_ctx *ctx, int32_t *nblocks,
+                             int64_t *counts, float *mu);
+
+/*
+ * Copy one block's results to host memory. Any output pointer may be NULL.
+ *   mb, nb    block shape; keff retained rank; mu the block mean.
+ *   sigma     keff singular values, descending (float64 norms |B v_i|).
+ *   P         mb x keff, row-major: U_k S_k (user side).
+ *   V         nb x keff, row-major: V_k (item side, unit columns). Each
+ *             pair (P_i, V_i) has the sign that makes the largest-|.|
+ *             entry of V_i positive.
+ *   dense     mb x nb, row-major float32: the centred dense block as
+ *             stored on the device (needs only a partition).
+ * Errors: BSVD_ESTATE, BSVD_EINVAL (b out of range).
+ */
+bsvd_status bsvd_get_block(bsvd_ctx *ctx, int32_t b, int32_t *mb,
+                           int32_t *nb, int32_t *keff, float *mu,
+                           double *sigma, float *P, float *V, float *dense);
+
+/*
+ * Rank-k reconstruction of block b (the low-rank matrix of Section 2):
+ * out[r * nb + c] = (add_mean ? mu_b : 0) + P[r,:] . V[c,:], for the
+ * mb x nb block. out: host or device array of mb * nb floats.
+ * Errors: BSVD_ESTATE, BSVD_EINVAL.
+ */
+bsvd_status bsvd_reconstruct(bsvd_ctx *ctx, int32_t b, int32_t add_mean,
+                             float *out);
+
+/*
+ * Per-block solver report after bsvd_factor (host arrays of p*q entries,
+ * any may be NULL): iterations used and 1 where the block converged.
+ */
+bsvd_status bsvd_factor_report(bsvd_ctx *ctx, int32_t *iters,
+                               int32_t *converged);
+
+/*
+ * Phase timings of the last call, in milliseconds of device time between
+ * CUDA events on the context's stream (needs profile = 1 in the config):
+ *   ms[0] partition (count, means, scatter)   ms[1] Gram products
+ *   ms[2] subspace iteration (eigen-solve)    ms[3] projection and norms
+ *   ms[4] prediction / squared-error sum
+ * Phases the last calls did not run read as 0. ms: host array of 5.
+ */
+bsvd_status bsvd_phase_times(bsvd_ctx *ctx, double *ms);
+
+/*
+ * Number of kernels this context has launched since it was created (every
+ * launch of the library's own kernels; memory copies and sets excluded).
+ * Returns -1 for a NULL context.
+ */
+int64_t bsvd_kernel_launches(const bsvd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSVD_H */

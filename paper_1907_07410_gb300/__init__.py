@@ -1,0 +1,362 @@
+"""Python binding of libbsvd, the block-SVD recommender library for GB300.
+
+The functions named ``bsvd_*`` mirror the C ABI in ``include/bsvd.h`` one to
+one and only marshal arguments: every step of the method runs in the CUDA
+library. ``Context`` wraps them for convenience. Arrays may be numpy arrays
+(host memory) or torch tensors (host or CUDA); their dtypes must already be
+int32 for ids and float32 for ratings.
+
+There is no CPU fallback: if libbsvd.so cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import warnings
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbsvd.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT, ESTATE = range(7)
+STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
+                ENOTCONV: "ENOTCONV", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
+
+# every symbol the header declares
+EXPORTS = ("bsvd_config_default", "bsvd_create", "bsvd_destroy",
+           "bsvd_last_error", "bsvd_partition", "bsvd_factor", "bsvd_predict",
+           "bsvd_rmse", "bsvd_block_stats", "bsvd_get_block",
+           "bsvd_reconstruct", "bsvd_factor_report", "bsvd_phase_times",
+           "bsvd_kernel_launches")
+
+
+class BsvdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("clamp", ctypes.c_int32),
+                ("clamp_lo", ctypes.c_float), ("clamp_hi", ctypes.c_float),
+                ("oversample", ctypes.c_int32),
+                ("cheb_degree", ctypes.c_int32),
+                ("max_iters", ctypes.c_int32), ("max_sweeps", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libbsvd.so (compiling it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        from . import build as _build
+        if _build.stale():
+            _build.build()
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libbsvd.so is not built (run __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "bsvd_config_default": (None, [ctypes.POINTER(Config)]),
+        "bsvd_create": (i32, [ctypes.POINTER(Config), ctypes.POINTER(vp)]),
+        "bsvd_destroy": (None, [vp]),
+        "bsvd_last_error": (ctypes.c_char_p, [vp]),
+        "bsvd_partition": (i32, [vp, i64, i64, i64, vp, vp, vp, i32, i32, vp,
+                                 vp, vp, vp]),
+        "bsvd_factor": (i32, [vp, i32]),
+        "bsvd_predict": (i32, [vp, i64, vp, vp, vp]),
+        "bsvd_rmse": (i32, [vp, i64, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]),
+        "bsvd_block_stats": (i32, [vp, ctypes.POINTER(i32), vp, vp]),
+        "bsvd_get_block": (i32, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                 ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
+                                 vp, vp, vp, vp]),
+        "bsvd_reconstruct": (i32, [vp, i32, i32, vp]),
+        "bsvd_factor_report": (i32, [vp, vp, vp]),
+        "bsvd_phase_times": (i32, [vp, vp]),
+        "bsvd_kernel_launches": (i64, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ---- argument marshalling ------------------------------------------------
+
+def _ptr(a, dtype, name):
+    """Address of a contiguous array (numpy or torch, host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype:
+            raise TypeError("%s must be %s, got %s" % (name, dtype, a.dtype))
+        if not a.flags.c_contiguous:
+            raise ValueError("%s must be contiguous" % name)
+        return a.ctypes.data
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        want = {np.dtype(np.int32): torch.int32, np.dtype(np.float32): torch.float32,
+                np.dtype(np.int64): torch.int64, np.dtype(np.float64): torch.float64}[np.dtype(dtype)]
+        if a.dtype != want:
+            raise TypeError("%s must be %s, got %s" % (name, want, a.dtype))
+        if not a.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        return a.data_ptr()
+    raise TypeError("%s must be a numpy array or torch tensor" % name)
+
+
+def _len(a):
+    return int(a.shape[0]) if a is not None else 0
+
+
+def _check(ctx, status, allow=()):
+    if status != OK and status not in allow:
+        msg = load().bsvd_last_error(ctx)
+        raise BsvdError(status, msg.decode() if msg else "")
+    return status
+
+
+# ---- the C ABI, one function per entry point ------------------------------
+
+def bsvd_config_default() -> Config:
+    cfg = Config()
+    load().bsvd_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def bsvd_create(cfg: Config | None = None) -> int:
+    h = ctypes.c_void_p()
+    st = load().bsvd_create(ctypes.byref(cfg) if cfg is not None else None,
+                            ctypes.byref(h))
+    if st != OK:
+        raise BsvdError(st, "bsvd_create failed")
+    return h.value
+
+
+def bsvd_destroy(ctx) -> None:
+    load().bsvd_destroy(ctx)
+
+
+def bsvd_last_error(ctx) -> str:
+    return load().bsvd_last_error(ctx).decode()
+
+
+def bsvd_partition(ctx, m, n, u, i, x, p, q, row_bounds=None, col_bounds=None,
+                   row_perm=None, col_perm=None) -> int:
+    nnz = _len(u)
+    if _len(i) != nnz or _len(x) != nnz:
+        raise ValueError("u, i, x must have the same length")
+    rb = None if row_bounds is None else np.ascontiguousarray(row_bounds, np.int64)
+    cb = None if col_bounds is None else np.ascontiguousarray(col_bounds, np.int64)
+    if rb is not None and rb.size != p + 1:
+        raise ValueError("row_bounds must have p + 1 entries")
+    if cb is not None and cb.size != q + 1:
+        raise ValueError("col_bounds must have q + 1 entries")
+    if row_perm is not None and _len(row_perm) != m:
+        raise ValueError("row_perm must have m entries")
+    if col_perm is not None and _len(col_perm) != n:
+        raise ValueError("col_perm must have n entries")
+    st = load().bsvd_partition(
+        ctx, m, n, nnz, _ptr(u, np.int32, "u"), _ptr(i, np.int32, "i"),
+        _ptr(x, np.float32, "x"), p, q, _ptr(rb, np.int64, "row_bounds"),
+        _ptr(cb, np.int64, "col_bounds"), _ptr(row_perm, np.int32, "row_perm"),
+        _ptr(col_perm, np.int32, "col_perm"))
+    return _check(ctx, st)
+
+
+def bsvd_factor(ctx, k) -> int:
+    st = load().bsvd_factor(ctx, k)
+    return _check(ctx, st, allow=(ENOTCONV,))
+
+
+def bsvd_predict(ctx, u, i, yhat) -> int:
+    nq = _len(u)
+    if _len(i) != nq or _len(yhat) != nq:
+        raise ValueError("u, i, yhat must have the same length")
+    st = load().bsvd_predict(ctx, nq, _ptr(u, np.int32, "u"),
+                             _ptr(i, np.int32, "i"),
+                             _ptr(yhat, np.float32, "yhat"))
+    return _check(ctx, st)
+
+
+def bsvd_rmse(ctx, u, i, y) -> float:
+    nq = _len(u)
+    if _len(i) != nq or _len(y) != nq:
+        raise ValueError("u, i, y must have the same length")
+    out = ctypes.c_double()
+    st = load().bsvd_rmse(ctx, nq, _ptr(u, np.int32, "u"),
+                          _ptr(i, np.int32, "i"), _ptr(y, np.float32, "y"),
+                          ctypes.byref(out))
+    _check(ctx, st)
+    return out.value
+
+
+def bsvd_block_stats(ctx, nblocks: int):
+    counts = np.zeros(nblocks, np.int64)
+    mu = np.zeros(nblocks, np.float32)
+    nb = ctypes.c_int32()
+    st = load().bsvd_block_stats(ctx, ctypes.byref(nb), counts.ctypes.data,
+                                 mu.ctypes.data)
+    _check(ctx, st)
+    return counts[:nb.value], mu[:nb.value]
+
+
+def bsvd_get_block(ctx, b, want_factors=True, want_dense=False):
+    mb, nb, keff = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    mu = ctypes.c_float()
+    lib = load()
+    st = lib.bsvd_get_block(ctx, b, ctypes.byref(mb), ctypes.byref(nb),
+                            ctypes.byref(keff), ctypes.byref(mu), None, None,
+                            None, None)
+    _check(ctx, st)
+    out = dict(mb=mb.value, nb=nb.value, keff=keff.value, mu=mu.value)
+    sigma = P = V = dense = None
+    if want_factors:
+        sigma = np.zeros(max(keff.value, 1), np.float64)
+        P = np.zeros((mb.value, keff.value), np.float32)
+        V = np.zeros((nb.value, keff.value), np.float32)
+    if want_dense:
+        dense = np.zeros((mb.value, nb.value), np.float32)
+    st = lib.bsvd_get_block(ctx, b, None, None, None, None,
+                            sigma.ctypes.data if sigma is not None else None,
+                            P.ctypes.data if P is not None else None,
+                            V.ctypes.data if V is not None else None,
+                            dense.ctypes.data if dense is not None else None)
+    _check(ctx, st)
+    if want_factors:
+        out.update(sigma=sigma[:keff.value], P=P, V=V)
+    if want_dense:
+        out["dense"] = dense
+    return out
+
+
+def bsvd_reconstruct(ctx, b, out, add_mean=True) -> int:
+    st = load().bsvd_reconstruct(ctx, b, 1 if add_mean else 0,
+                                 _ptr(out, np.float32, "out"))
+    return _check(ctx, st)
+
+
+def bsvd_factor_report(ctx, nblocks: int):
+    iters = np.zeros(nblocks, np.int32)
+    conv = np.zeros(nblocks, np.int32)
+    st = load().bsvd_factor_report(ctx, iters.ctypes.data, conv.ctypes.data)
+    _check(ctx, st)
+    return iters, conv
+
+
+def bsvd_phase_times(ctx) -> np.ndarray:
+    ms = np.zeros(5, np.float64)
+    _check(ctx, load().bsvd_phase_times(ctx, ms.ctypes.data))
+    return ms
+
+
+def bsvd_kernel_launches(ctx) -> int:
+    return int(load().bsvd_kernel_launches(ctx))
+
+
+PHASES = ("partition", "gram", "eigen", "project", "predict")
+
+
+# ---- convenience wrapper ----------------------------------------------------
+
+class Context:
+    """One libbsvd context on the current CUDA device.
+
+    ``stream``: a torch.cuda.Stream, a raw cudaStream_t integer, or None
+    (the current torch stream when torch is imported, else the default
+    stream).
+    """
+
+    def __init__(self, stream=None, **cfg_fields):
+        cfg = bsvd_config_default()
+        for k, v in cfg_fields.items():
+            if not hasattr(cfg, k):
+                raise TypeError("unknown config field %r" % k)
+            setattr(cfg, k, v)
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream()
+            except ImportError:  # pragma: no cover
+                pass
+        if stream is not None and not isinstance(stream, int):
+            stream = stream.cuda_stream
+        cfg.stream = stream
+        self.cfg = cfg
+        self.handle = bsvd_create(cfg)
+        self.nblocks = 0
+        self.last_status = OK
+
+    def close(self):
+        if getattr(self, "handle", None):
+            bsvd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def partition(self, m, n, u, i, x, p, q, row_bounds=None, col_bounds=None,
+                  row_perm=None, col_perm=None):
+        bsvd_partition(self.handle, m, n, u, i, x, p, q, row_bounds,
+                       col_bounds, row_perm, col_perm)
+        self.nblocks = p * q
+
+    def factor(self, k, warn=True):
+        st = bsvd_factor(self.handle, k)
+        self.last_status = st
+        if st == ENOTCONV and warn:
+            warnings.warn("bsvd_factor: " + bsvd_last_error(self.handle))
+        return st
+
+    def predict(self, u, i, out=None):
+        if out is None:
+            out = np.zeros(_len(u), np.float32)
+        bsvd_predict(self.handle, u, i, out)
+        return out
+
+    def rmse(self, u, i, y):
+        return bsvd_rmse(self.handle, u, i, y)
+
+    def block_stats(self):
+        return bsvd_block_stats(self.handle, self.nblocks)
+
+    def get_block(self, b, want_factors=True, want_dense=False):
+        return bsvd_get_block(self.handle, b, want_factors, want_dense)
+
+    def reconstruct(self, b, add_mean=True):
+        info = bsvd_get_block(self.handle, b, want_factors=False)
+        out = np.zeros((info["mb"], info["nb"]), np.float32)
+        bsvd_reconstruct(self.handle, b, out, add_mean)
+        return out
+
+    def factor_report(self):
+        return bsvd_factor_report(self.handle, self.nblocks)
+
+    def phase_times(self) -> dict:
+        return dict(zip(PHASES, bsvd_phase_times(self.handle).tolist()))
+
+    def kernel_launches(self) -> int:
+        return bsvd_kernel_launches(self.handle)

@@ -1,0 +1,780 @@
+// C ABI of libbsvd: context, argument checks, buffers and the order of
+// kernel launches for each call. See include/bsvd.h for the contract.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bsvd.h"
+#include "kernels.h"
+
+using namespace bsvd;
+
+namespace {
+
+// A device allocation that only grows.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t want) {
+    if (want <= bytes && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    if (want == 0) want = 16;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e == cudaSuccess) bytes = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct bsvd_ctx {
+  bsvd_config cfg;
+  cudaStream_t st = nullptr;
+  std::string err;
+  int device = 0;
+
+  // partition
+  bool parted = false;
+  int64_t m = 0, n = 0, nnz = 0;
+  int32_t p = 0, q = 0, nblocks = 0;
+  std::vector<int64_t> rb, cb;
+  bool eq_r = true, eq_c = true, has_rperm = false, has_cperm = false;
+  int64_t br = 0, bc = 0;
+  std::vector<BlockMeta> meta;
+  int64_t arena = 0;
+  DevBuf d_rb, d_cb, d_rperm, d_cperm, d_seen, d_meta, d_counts, d_sums,
+      d_maxabs, d_mu, d_W, d_err;
+
+  // factor
+  bool factored = false;
+  int32_t k = 0, bsub = 0, kp = 4;
+  DevBuf d_G, d_X, d_Z, d_SH, d_T, d_theta, d_state, d_Fs, d_FL, d_sigma,
+      d_running, d_gtiles, d_rowtiles, d_ltiles;
+  int32_t n_gtiles = 0, n_rowtiles = 0, n_ltiles = 0;
+  bool any_capped = false;
+
+  // staging of host arguments and results
+  DevBuf s_a, s_b, s_c, s_out, d_partials, d_rmse;
+
+  // tracing: kernel launch count and per-phase CUDA events
+  int64_t launches = 0;
+  cudaEvent_t ev[6] = {};
+  double phase_ms[5] = {};
+
+  GridDesc grid() const {
+    GridDesc g;
+    g.m = m; g.n = n; g.p = p; g.q = q;
+    g.equal_rows = eq_r ? 1 : 0;
+    g.equal_cols = eq_c ? 1 : 0;
+    g.br = br; g.bc = bc;
+    g.row_bounds = d_rb.as<int64_t>();
+    g.col_bounds = d_cb.as<int64_t>();
+    g.row_perm = has_rperm ? d_rperm.as<int32_t>() : nullptr;
+    g.col_perm = has_cperm ? d_cperm.as<int32_t>() : nullptr;
+    return g;
+  }
+};
+
+namespace {
+
+bsvd_status fail(bsvd_ctx *c, bsvd_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  c->err = buf;
+  return s;
+}
+
+bsvd_status cuda_fail(bsvd_ctx *c, cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(c, BSVD_ENOMEM, "%s: out of device memory", what);
+  }
+  return fail(c, BSVD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+bool is_device_ptr(const void *ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller array: the pointer itself when it is device
+// memory, else a copy in the staging buffer.
+cudaError_t device_view(bsvd_ctx *c, const void *ptr, size_t bytes,
+                        DevBuf &stage, const void **out) {
+  if (bytes == 0 || is_device_ptr(ptr)) {
+    *out = ptr;
+    return cudaSuccess;
+  }
+  cudaError_t e = stage.ensure(bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(stage.p, ptr, bytes, cudaMemcpyHostToDevice, c->st);
+  *out = stage.p;
+  return e;
+}
+
+bsvd_status read_errors(bsvd_ctx *c, const char *what) {
+  int32_t h = 0;
+  CK(cudaMemcpyAsync(&h, c->d_err.p, sizeof h, cudaMemcpyDeviceToHost, c->st),
+     what);
+  CK(cudaStreamSynchronize(c->st), what);
+  if (h) {
+    std::string msg = std::string(what) + ":";
+    if (h & kErrIndex) msg += " id out of range;";
+    if (h & kErrValue) msg += " non-finite rating or |x| >= 2^31;";
+    if (h & kErrSumRange) msg += " ratings too large for exact block sums;";
+    if (h & kErrBadPerm) msg += " invalid permutation;";
+    CK(cudaMemsetAsync(c->d_err.p, 0, sizeof(int32_t), c->st), what);
+    return fail(c, BSVD_EINVAL, "%s", msg.c_str());
+  }
+  return BSVD_OK;
+}
+
+// Phase events: mark(i) records event i on the stream when profiling.
+void mark(bsvd_ctx *c, int i) {
+  if (c->cfg.profile && c->ev[i]) cudaEventRecord(c->ev[i], c->st);
+}
+
+// After a synchronised call: phase_ms[ph] = time between events a and b.
+void take(bsvd_ctx *c, int ph, int a, int b) {
+  if (!c->cfg.profile) return;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]) == cudaSuccess)
+    c->phase_ms[ph] = ms;
+  else
+    cudaGetLastError();
+}
+
+bool bounds_ok(const int64_t *b, int32_t parts, int64_t total) {
+  if (b[0] != 0 || b[parts] != total) return false;
+  for (int32_t j = 0; j < parts; ++j)
+    if (b[j + 1] < b[j]) return false;
+  return true;
+}
+
+int32_t subspace_width(int32_t k, int32_t oversample) {
+  int32_t extra = oversample > 0 ? oversample : std::max(8, k / 2);
+  int32_t want = k + extra;
+  if (want <= 16) return 16;
+  if (want <= 32) return 32;
+  return 64;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bsvd_config_default(bsvd_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->precision = BSVD_FP32;
+  cfg->clamp = 0;
+  cfg->clamp_lo = 1.0f;
+  cfg->clamp_hi = 5.0f;
+  cfg->oversample = 0;
+  cfg->cheb_degree = 8;
+  cfg->max_iters = 30;
+  cfg->max_sweeps = 30;
+  cfg->tol = 1e-5;
+  cfg->seed = 0x5eed5eedull;
+  cfg->stream = nullptr;
+}
+
+bsvd_status bsvd_create(const bsvd_config *cfg, bsvd_ctx **out) {
+  if (!out) return BSVD_EINVAL;
+  *out = nullptr;
+  bsvd_ctx *c = new (std::nothrow) bsvd_ctx();
+  if (!c) return BSVD_ENOMEM;
+  bsvd_config_default(&c->cfg);
+  if (cfg) {
+    c->cfg = *cfg;
+    if (c->cfg.cheb_degree <= 0) c->cfg.cheb_degree = 8;
+    if (c->cfg.max_iters <= 0) c->cfg.max_iters = 30;
+    if (c->cfg.max_sweeps <= 0) c->cfg.max_sweeps = 30;
+    if (!(c->cfg.tol > 0)) c->cfg.tol = 1e-5;
+  }
+  if (c->cfg.precision != BSVD_FP32 || c->cfg.reserved != 0 ||
+      c->cfg.cheb_degree % 2 != 0 ||
+      c->cfg.cheb_degree > 64 || (c->cfg.clamp && !(c->cfg.clamp_lo <= c->cfg.clamp_hi))) {
+    delete c;
+    return BSVD_EINVAL;
+  }
+  c->st = static_cast<cudaStream_t>(c->cfg.stream);
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      c->d_err.ensure(sizeof(int32_t)) != cudaSuccess ||
+      cudaMemset(c->d_err.p, 0, sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return BSVD_ECUDA;
+  }
+  if (c->cfg.profile) {
+    for (auto &e : c->ev) {
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        e = nullptr;
+      }
+    }
+  }
+  *out = c;
+  return BSVD_OK;
+}
+
+void bsvd_destroy(bsvd_ctx *c) {
+  if (!c) return;
+  DevBuf *bufs[] = {&c->d_rb, &c->d_cb, &c->d_rperm, &c->d_cperm, &c->d_seen,
+                    &c->d_meta, &c->d_counts, &c->d_sums, &c->d_maxabs,
+                    &c->d_mu, &c->d_W, &c->d_err, &c->d_G, &c->d_X, &c->d_Z,
+                    &c->d_SH, &c->d_T, &c->d_theta, &c->d_state, &c->d_Fs,
+                    &c->d_FL, &c->d_sigma, &c->d_running, &c->d_gtiles,
+                    &c->d_rowtiles, &c->d_ltiles, &c->s_a, &c->s_b, &c->s_c,
+                    &c->s_out, &c->d_partials, &c->d_rmse};
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  for (DevBuf *b : bufs) b->release();
+  for (auto &e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+const char *bsvd_last_error(const bsvd_ctx *c) {
+  return c ? c->err.c_str() : "null context";
+}
+
+bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
+                           const int32_t *u, const int32_t *i,
+                           const float *x, int32_t p, int32_t q,
+                           const int64_t *row_bounds,
+                           const int64_t *col_bounds,
+                           const int32_t *row_perm, const int32_t *col_perm) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (m < 1 || n < 1 || m > INT32_MAX || n > INT32_MAX || nnz < 0)
+    return fail(c, BSVD_EINVAL, "partition: bad sizes m=%lld n=%lld nnz=%lld",
+                (long long)m, (long long)n, (long long)nnz);
+  if (p < 1 || q < 1 || (!row_bounds && p > m) || (!col_bounds && q > n))
+    return fail(c, BSVD_EINVAL, "partition: bad grid %d x %d", p, q);
+  if (nnz > 0 && (!u || !i || !x))
+    return fail(c, BSVD_EINVAL, "partition: null rating arrays");
+  if ((int64_t)p * q > (int64_t)INT32_MAX)
+    return fail(c, BSVD_EINVAL, "partition: too many blocks");
+  if (row_bounds && !bounds_ok(row_bounds, p, m))
+    return fail(c, BSVD_EINVAL, "partition: bad row bounds");
+  if (col_bounds && !bounds_ok(col_bounds, q, n))
+    return fail(c, BSVD_EINVAL, "partition: bad column bounds");
+
+  c->parted = false;
+  c->factored = false;
+  c->m = m; c->n = n; c->nnz = nnz; c->p = p; c->q = q;
+  c->nblocks = p * q;
+  c->eq_r = row_bounds == nullptr;
+  c->eq_c = col_bounds == nullptr;
+  c->br = (m + p - 1) / p;
+  c->bc = (n + q - 1) / q;
+  c->rb.assign(p + 1, 0);
+  c->cb.assign(q + 1, 0);
+  for (int32_t j = 0; j <= p; ++j)
+    c->rb[j] = row_bounds ? row_bounds[j] : std::min<int64_t>(j * c->br, m);
+  for (int32_t j = 0; j <= q; ++j)
+    c->cb[j] = col_bounds ? col_bounds[j] : std::min<int64_t>(j * c->bc, n);
+
+  // block shapes and the dense arena layout
+  c->meta.assign(c->nblocks, BlockMeta());
+  int64_t off = 0;
+  for (int32_t bi = 0; bi < p; ++bi) {
+    for (int32_t bj = 0; bj < q; ++bj) {
+      BlockMeta &bm = c->meta[bi * q + bj];
+      std::memset(&bm, 0, sizeof bm);
+      bm.mb = (int32_t)(c->rb[bi + 1] - c->rb[bi]);
+      bm.nb = (int32_t)(c->cb[bj + 1] - c->cb[bj]);
+      bm.trans = bm.nb <= bm.mb ? 1 : 0;
+      bm.s = std::min(bm.mb, bm.nb);
+      bm.L = std::max(bm.mb, bm.nb);
+      bm.s_pad = (int32_t)round_up(bm.s, kPad);
+      bm.L_pad = (int32_t)round_up(bm.L, kPad);
+      bm.row0 = c->rb[bi];
+      bm.col0 = c->cb[bj];
+      bm.w_off = off;
+      off += (int64_t)bm.s_pad * bm.L_pad;
+    }
+  }
+  c->arena = off;
+
+  const int32_t nb = c->nblocks;
+  CK(c->d_rb.ensure(sizeof(int64_t) * (p + 1)), "partition");
+  CK(c->d_cb.ensure(sizeof(int64_t) * (q + 1)), "partition");
+  CK(c->d_meta.ensure(sizeof(BlockMeta) * nb), "partition");
+  CK(c->d_counts.ensure(sizeof(unsigned long long) * nb), "partition");
+  CK(c->d_sums.ensure(sizeof(long long) * nb), "partition");
+  CK(c->d_maxabs.ensure(sizeof(unsigned int)), "partition");
+  CK(c->d_mu.ensure(sizeof(float) * nb), "partition");
+  CK(c->d_W.ensure(sizeof(float) * std::max<int64_t>(off, 1)), "partition");
+  CK(cudaMemcpyAsync(c->d_rb.p, c->rb.data(), sizeof(int64_t) * (p + 1),
+                     cudaMemcpyHostToDevice, c->st), "partition");
+  CK(cudaMemcpyAsync(c->d_cb.p, c->cb.data(), sizeof(int64_t) * (q + 1),
+                     cudaMemcpyHostToDevice, c->st), "partition");
+  CK(cudaMemcpyAsync(c->d_meta.p, c->meta.data(), sizeof(BlockMeta) * nb,
+                     cudaMemcpyHostToDevice, c->st), "partition");
+
+  // permutations: copied into context memory, then checked on the device
+  c->has_rperm = row_perm != nullptr;
+  c->has_cperm = col_perm != nullptr;
+  CK(cudaMemsetAsync(c->d_err.p, 0, sizeof(int32_t), c->st), "partition");
+  if (row_perm) {
+    CK(c->d_rperm.ensure(sizeof(int32_t) * m), "partition");
+    CK(c->d_seen.ensure(sizeof(int32_t) * std::max(m, n)), "partition");
+    CK(cudaMemcpyAsync(c->d_rperm.p, row_perm, sizeof(int32_t) * m,
+                       cudaMemcpyDefault, c->st), "partition");
+    CK(launch_perm_check(c->d_rperm.as<int32_t>(), m, c->d_seen.as<int32_t>(),
+                         c->d_err.as<int32_t>(), c->st), "partition");
+    c->launches += 2;
+  }
+  if (col_perm) {
+    CK(c->d_cperm.ensure(sizeof(int32_t) * n), "partition");
+    CK(c->d_seen.ensure(sizeof(int32_t) * std::max(m, n)), "partition");
+    CK(cudaMemcpyAsync(c->d_cperm.p, col_perm, sizeof(int32_t) * n,
+                       cudaMemcpyDefault, c->st), "partition");
+    CK(launch_perm_check(c->d_cperm.as<int32_t>(), n, c->d_seen.as<int32_t>(),
+                         c->d_err.as<int32_t>(), c->st), "partition");
+    c->launches += 2;
+  }
+  if (row_perm || col_perm) {
+    bsvd_status s = read_errors(c, "partition");
+    if (s != BSVD_OK) return s;
+  }
+
+  const void *du = nullptr, *di = nullptr, *dx = nullptr;
+  CK(device_view(c, u, sizeof(int32_t) * nnz, c->s_a, &du), "partition");
+  CK(device_view(c, i, sizeof(int32_t) * nnz, c->s_b, &di), "partition");
+  CK(device_view(c, x, sizeof(float) * nnz, c->s_c, &dx), "partition");
+
+  CK(cudaMemsetAsync(c->d_counts.p, 0, sizeof(unsigned long long) * nb, c->st),
+     "partition");
+  CK(cudaMemsetAsync(c->d_sums.p, 0, sizeof(long long) * nb, c->st),
+     "partition");
+  CK(cudaMemsetAsync(c->d_maxabs.p, 0, sizeof(unsigned int), c->st),
+     "partition");
+  CK(cudaMemsetAsync(c->d_W.p, 0, sizeof(float) * std::max<int64_t>(off, 1),
+                     c->st), "partition");
+  const GridDesc g = c->grid();
+  std::fill(c->phase_ms, c->phase_ms + 5, 0.0);
+  mark(c, 0);
+  CK(launch_count(g, nnz, (const int32_t *)du, (const int32_t *)di,
+                  (const float *)dx, nb, c->d_counts.as<unsigned long long>(),
+                  c->d_sums.as<long long>(), c->d_maxabs.as<unsigned int>(),
+                  c->d_err.as<int32_t>(), c->st), "partition: count");
+  CK(launch_means(nb, c->d_counts.as<unsigned long long>(),
+                  c->d_sums.as<long long>(), c->d_maxabs.as<unsigned int>(),
+                  c->d_mu.as<float>(), c->d_err.as<int32_t>(), c->st),
+     "partition: means");
+  CK(launch_scatter(g, c->d_meta.as<BlockMeta>(), nnz, (const int32_t *)du,
+                    (const int32_t *)di, (const float *)dx,
+                    c->d_mu.as<float>(), c->d_W.as<float>(), c->st),
+     "partition: scatter");
+  c->launches += nnz > 0 ? 3 : 1;
+  mark(c, 1);
+  bsvd_status s = read_errors(c, "partition");
+  if (s != BSVD_OK) return s;
+  take(c, 0, 0, 1);
+  c->parted = true;
+  return BSVD_OK;
+}
+
+bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (!c->parted) return fail(c, BSVD_ESTATE, "factor: no partition");
+  if (k < 0 || k > 56) return fail(c, BSVD_EINVAL, "factor: k=%d outside [0, 56]", k);
+  c->factored = false;
+  c->any_capped = false;
+  c->k = k;
+  c->bsub = subspace_width(k, c->cfg.oversample);
+  c->kp = (int32_t)std::max<int64_t>(4, round_up(k, 4));
+  const int32_t B = c->bsub, kp = c->kp, nb = c->nblocks;
+
+  int64_t goff = 0, xoff = 0, fsoff = 0, floff = 0;
+  std::vector<int4> gt;
+  std::vector<int2> rt, lt;
+  std::vector<SolverState> st0(nb);
+  for (int32_t b = 0; b < nb; ++b) {
+    BlockMeta &bm = c->meta[b];
+    bm.keff = std::min(k, bm.s);
+    bm.g_off = goff;
+    bm.x_off = xoff;
+    bm.fs_off = fsoff;
+    bm.fl_off = floff;
+    goff += (int64_t)bm.s_pad * bm.s_pad;
+    xoff += (int64_t)bm.s_pad * B;
+    fsoff += (int64_t)bm.s_pad * kp;
+    floff += (int64_t)bm.L_pad * kp;
+    SolverState &s = st0[b];
+    std::memset(&s, 0, sizeof s);
+    s.bsub = std::min(B, bm.s);
+    s.status = (bm.s == 0 || bm.keff == 0) ? kConverged : kRunning;
+    if (bm.s == 0) continue;
+    const int32_t T = (bm.s_pad + 127) / 128;
+    for (int32_t ti = 0; ti < T; ++ti)
+      for (int32_t tj = ti; tj < T; ++tj) gt.push_back(make_int4(b, ti, tj, 0));
+    for (int32_t r = 0; r < bm.s_pad; r += 64) rt.push_back(make_int2(b, r));
+    for (int32_t l = 0; l < bm.L; l += 128) lt.push_back(make_int2(b, l));
+  }
+  c->n_gtiles = (int32_t)gt.size();
+  c->n_rowtiles = (int32_t)rt.size();
+  c->n_ltiles = (int32_t)lt.size();
+
+  CK(c->d_G.ensure(sizeof(float) * std::max<int64_t>(goff, 1)), "factor");
+  CK(c->d_X.ensure(sizeof(float) * std::max<int64_t>(xoff, 1)), "factor");
+  CK(c->d_Z.ensure(sizeof(float) * std::max<int64_t>(xoff, 1)), "factor");
+  CK(c->d_SH.ensure(sizeof(float) * 2 * B * B * (int64_t)nb), "factor");
+  CK(c->d_T.ensure(sizeof(float) * B * B * (int64_t)nb), "factor");
+  CK(c->d_theta.ensure(sizeof(float) * B * (int64_t)nb), "factor");
+  CK(c->d_state.ensure(sizeof(SolverState) * nb), "factor");
+  CK(c->d_Fs.ensure(sizeof(float) * std::max<int64_t>(fsoff, 1)), "factor");
+  CK(c->d_FL.ensure(sizeof(float) * std::max<int64_t>(floff, 1)), "factor");
+  CK(c->d_sigma.ensure(sizeof(double) * kp * (int64_t)nb), "factor");
+  CK(c->d_running.ensure(sizeof(int32_t)), "factor");
+  CK(c->d_gtiles.ensure(sizeof(int4) * std::max<size_t>(gt.size(), 1)), "factor");
+  CK(c->d_rowtiles.ensure(sizeof(int2) * std::max<size_t>(rt.size(), 1)), "factor");
+  CK(c->d_ltiles.ensure(sizeof(int2) * std::max<size_t>(lt.size(), 1)), "factor");
+
+  CK(cudaMemcpyAsync(c->d_meta.p, c->meta.data(), sizeof(BlockMeta) * nb,
+                     cudaMemcpyHostToDevice, c->st), "factor");
+  CK(cudaMemcpyAsync(c->d_state.p, st0.data(), sizeof(SolverState) * nb,
+                     cudaMemcpyHostToDevice, c->st), "factor");
+  if (!gt.empty())
+    CK(cudaMemcpyAsync(c->d_gtiles.p, gt.data(), sizeof(int4) * gt.size(),
+                       cudaMemcpyHostToDevice, c->st), "factor");
+  if (!rt.empty())
+    CK(cudaMemcpyAsync(c->d_rowtiles.p, rt.data(), sizeof(int2) * rt.size(),
+                       cudaMemcpyHostToDevice, c->st), "factor");
+  if (!lt.empty())
+    CK(cudaMemcpyAsync(c->d_ltiles.p, lt.data(), sizeof(int2) * lt.size(),
+                       cudaMemcpyHostToDevice, c->st), "factor");
+  CK(cudaMemsetAsync(c->d_Fs.p, 0, sizeof(float) * std::max<int64_t>(fsoff, 1), c->st), "factor");
+  CK(cudaMemsetAsync(c->d_FL.p, 0, sizeof(float) * std::max<int64_t>(floff, 1), c->st), "factor");
+  CK(cudaMemsetAsync(c->d_sigma.p, 0, sizeof(double) * kp * (int64_t)nb, c->st), "factor");
+
+  if (k > 0) {
+    EigBuffers e;
+    e.meta = c->d_meta.as<BlockMeta>();
+    e.state = c->d_state.as<SolverState>();
+    e.G = c->d_G.as<float>();
+    e.X = c->d_X.as<float>();
+    e.Z = c->d_Z.as<float>();
+    e.SH = c->d_SH.as<float>();
+    e.T = c->d_T.as<float>();
+    e.theta = c->d_theta.as<float>();
+    e.Fs = c->d_Fs.as<float>();
+    e.running = c->d_running.as<int32_t>();
+    e.bsub = B; e.kp = kp; e.k = k; e.nblocks = nb;
+    e.max_iters = c->cfg.max_iters;
+    e.max_sweeps = c->cfg.max_sweeps;
+    e.tol = (float)c->cfg.tol;
+    e.seed = c->cfg.seed;
+    const int2 *rtd = c->d_rowtiles.as<int2>();
+    const int nrt = c->n_rowtiles;
+
+    std::fill(c->phase_ms + 1, c->phase_ms + 4, 0.0);
+    mark(c, 0);
+    CK(launch_gram_f32(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
+                       c->n_gtiles, c->d_W.as<float>(), e.G, c->st), "factor: gram");
+    mark(c, 1);
+    CK(launch_init_panels(e, rtd, nrt, c->st), "factor: init");
+    CK(launch_gpanel(e, rtd, nrt, 0, 0, 0, e.X, nullptr, e.Z, c->st), "factor: G X");
+    c->launches += (c->n_gtiles > 0) + 2 * (nrt > 0);
+    const int deg = c->cfg.cheb_degree;
+    for (int it = 0; it <= c->cfg.max_iters + 1; ++it) {
+      CK(launch_small_gram(e, c->st), "factor: rr gram");
+      CK(launch_rr_solve(e, c->st), "factor: rr solve");
+      CK(launch_rotate(e, rtd, nrt, c->st), "factor: rotate");
+      CK(cudaMemsetAsync(e.running, 0, sizeof(int32_t), c->st), "factor");
+      CK(launch_check(e, c->st), "factor: check");
+      c->launches += 3 + (nrt > 0);
+      int32_t running = 0;
+      CK(cudaMemcpyAsync(&running, e.running, sizeof running,
+                         cudaMemcpyDeviceToHost, c->st), "factor");
+      CK(cudaStreamSynchronize(c->st), "factor");
+      if (running == 0) break;
+      // Chebyshev filter of even degree: Y_1 -> Z, Y_2 -> X, ..., Y_d -> X
+      // step j reads Y_{j-1}, Y_{j-2} and overwrites Y_{j-2} with Y_j
+      for (int j = 1; j <= deg; ++j) {
+        const bool even = j % 2 == 0;
+        const float *in = even ? e.Z : e.X;
+        const float *in2 = j == 1 ? nullptr : (even ? e.X : e.Z);
+        float *out = even ? e.X : e.Z;
+        CK(launch_gpanel(e, rtd, nrt, j == 1 ? 1 : 2, j, deg, in, in2, out,
+                         c->st), "factor: filter");
+      }
+      CK(launch_gpanel(e, rtd, nrt, 0, 0, 0, e.X, nullptr, e.Z, c->st),
+         "factor: G X");
+      c->launches += (deg + 1) * (nrt > 0);
+    }
+    mark(c, 2);
+    CK(launch_project(c->d_meta.as<BlockMeta>(), c->d_ltiles.as<int2>(),
+                      c->n_ltiles, c->d_W.as<float>(), e.Fs, c->d_FL.as<float>(),
+                      kp, c->st), "factor: project");
+    CK(launch_finalize(c->d_meta.as<BlockMeta>(), nb, e.Fs, c->d_FL.as<float>(),
+                       c->d_sigma.as<double>(), kp, k, c->st), "factor: finalize");
+    c->launches += (c->n_ltiles > 0) + (nb > 0);
+    mark(c, 3);
+    std::vector<SolverState> fin(nb);
+    CK(cudaMemcpyAsync(fin.data(), c->d_state.p, sizeof(SolverState) * nb,
+                       cudaMemcpyDeviceToHost, c->st), "factor");
+    CK(cudaStreamSynchronize(c->st), "factor");
+    for (int32_t b = 0; b < nb; ++b)
+      if (fin[b].status != kConverged) c->any_capped = true;
+    take(c, 1, 0, 1);
+    take(c, 2, 1, 2);
+    take(c, 3, 2, 3);
+  }
+  CK(cudaStreamSynchronize(c->st), "factor");
+  c->factored = true;
+  if (c->any_capped)
+    return fail(c, BSVD_ENOTCONV, "factor: some blocks hit the iteration cap");
+  return BSVD_OK;
+}
+
+static PredictArgs predict_args(bsvd_ctx *c) {
+  PredictArgs a;
+  a.g = c->grid();
+  a.meta = c->d_meta.as<BlockMeta>();
+  a.mu = c->d_mu.as<float>();
+  a.Fs = c->d_Fs.as<float>();
+  a.FL = c->d_FL.as<float>();
+  a.kp = c->kp;
+  a.clamp = c->cfg.clamp;
+  a.lo = c->cfg.clamp_lo;
+  a.hi = c->cfg.clamp_hi;
+  return a;
+}
+
+bsvd_status bsvd_predict(bsvd_ctx *c, int64_t nq, const int32_t *u,
+                         const int32_t *i, float *yhat) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (!c->factored) return fail(c, BSVD_ESTATE, "predict: no factors");
+  if (nq < 0 || (nq > 0 && (!u || !i || !yhat)))
+    return fail(c, BSVD_EINVAL, "predict: bad arguments");
+  if (nq == 0) return BSVD_OK;
+  const void *du, *di;
+  CK(device_view(c, u, sizeof(int32_t) * nq, c->s_a, &du), "predict");
+  CK(device_view(c, i, sizeof(int32_t) * nq, c->s_b, &di), "predict");
+  const bool dev_out = is_device_ptr(yhat);
+  float *out = yhat;
+  if (!dev_out) {
+    CK(c->s_out.ensure(sizeof(float) * nq), "predict");
+    out = c->s_out.as<float>();
+  }
+  mark(c, 4);
+  CK(launch_predict(predict_args(c), nq, (const int32_t *)du,
+                    (const int32_t *)di, out, c->d_err.as<int32_t>(), c->st),
+     "predict");
+  mark(c, 5);
+  c->launches += 1;
+  if (!dev_out)
+    CK(cudaMemcpyAsync(yhat, out, sizeof(float) * nq, cudaMemcpyDeviceToHost,
+                       c->st), "predict");
+  bsvd_status s = read_errors(c, "predict");
+  if (s == BSVD_OK) take(c, 4, 4, 5);
+  return s;
+}
+
+bsvd_status bsvd_rmse(bsvd_ctx *c, int64_t nq, const int32_t *u,
+                      const int32_t *i, const float *y, double *out_rmse) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (!c->factored) return fail(c, BSVD_ESTATE, "rmse: no factors");
+  if (nq < 1 || !u || !i || !y || !out_rmse)
+    return fail(c, BSVD_EINVAL, "rmse: bad arguments");
+  const void *du, *di, *dy;
+  CK(device_view(c, u, sizeof(int32_t) * nq, c->s_a, &du), "rmse");
+  CK(device_view(c, i, sizeof(int32_t) * nq, c->s_b, &di), "rmse");
+  CK(device_view(c, y, sizeof(float) * nq, c->s_c, &dy), "rmse");
+  CK(c->d_partials.ensure(sizeof(double) * kSqerrBlocks), "rmse");
+  CK(c->d_rmse.ensure(sizeof(double)), "rmse");
+  mark(c, 4);
+  CK(launch_sqerr(predict_args(c), nq, (const int32_t *)du,
+                  (const int32_t *)di, (const float *)dy,
+                  c->d_partials.as<double>(), c->d_rmse.as<double>(),
+                  c->d_err.as<int32_t>(), c->st), "rmse");
+  mark(c, 5);
+  c->launches += 2;
+  double sum = 0;
+  CK(cudaMemcpyAsync(&sum, c->d_rmse.p, sizeof sum, cudaMemcpyDeviceToHost,
+                     c->st), "rmse");
+  bsvd_status s = read_errors(c, "rmse");
+  if (s != BSVD_OK) return s;
+  take(c, 4, 4, 5);
+  *out_rmse = std::sqrt(sum / (double)nq);
+  return BSVD_OK;
+}
+
+bsvd_status bsvd_block_stats(bsvd_ctx *c, int32_t *nblocks, int64_t *counts,
+                             float *mu) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (!c->parted) return fail(c, BSVD_ESTATE, "block_stats: no partition");
+  if (nblocks) *nblocks = c->nblocks;
+  if (counts)
+    CK(cudaMemcpyAsync(counts, c->d_counts.p, sizeof(int64_t) * c->nblocks,
+                       cudaMemcpyDeviceToHost, c->st), "block_stats");
+  if (mu)
+    CK(cudaMemcpyAsync(mu, c->d_mu.p, sizeof(float) * c->nblocks,
+                       cudaMemcpyDeviceToHost, c->st), "block_stats");
+  CK(cudaStreamSynchronize(c->st), "block_stats");
+  return BSVD_OK;
+}
+
+bsvd_status bsvd_get_block(bsvd_ctx *c, int32_t b, int32_t *mb, int32_t *nb,
+                           int32_t *keff, float *mu, double *sigma, float *P,
+                           float *V, float *dense) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (!c->parted) return fail(c, BSVD_ESTATE, "get_block: no partition");
+  if (b < 0 || b >= c->nblocks) return fail(c, BSVD_EINVAL, "get_block: bad block %d", b);
+  const BlockMeta &bm = c->meta[b];
+  if ((sigma || P || V) && !c->factored)
+    return fail(c, BSVD_ESTATE, "get_block: no factors");
+  if (mb) *mb = bm.mb;
+  if (nb) *nb = bm.nb;
+  if (keff) *keff = c->factored ? bm.keff : 0;
+  if (mu)
+    CK(cudaMemcpyAsync(mu, c->d_mu.as<float>() + b, sizeof(float),
+                       cudaMemcpyDeviceToHost, c->st), "get_block");
+  std::vector<float> W;
+  if (dense) {
+    W.resize((size_t)bm.s_pad * bm.L_pad);
+    CK(cudaMemcpyAsync(W.data(), c->d_W.as<float>() + bm.w_off,
+                       sizeof(float) * W.size(), cudaMemcpyDeviceToHost, c->st),
+       "get_block");
+  }
+  std::vector<float> Fs, FL;
+  std::vector<double> sg(c->kp);
+  if (c->factored && (sigma || P || V)) {
+    Fs.resize((size_t)bm.s_pad * c->kp);
+    FL.resize((size_t)bm.L_pad * c->kp);
+    CK(cudaMemcpyAsync(Fs.data(), c->d_Fs.as<float>() + bm.fs_off,
+                       sizeof(float) * Fs.size(), cudaMemcpyDeviceToHost, c->st),
+       "get_block");
+    CK(cudaMemcpyAsync(FL.data(), c->d_FL.as<float>() + bm.fl_off,
+                       sizeof(float) * FL.size(), cudaMemcpyDeviceToHost, c->st),
+       "get_block");
+    CK(cudaMemcpyAsync(sg.data(), c->d_sigma.as<double>() + (int64_t)b * c->kp,
+                       sizeof(double) * c->kp, cudaMemcpyDeviceToHost, c->st),
+       "get_block");
+  }
+  CK(cudaStreamSynchronize(c->st), "get_block");
+  const int kp = c->kp, ke = c->factored ? bm.keff : 0;
+  if (sigma)
+    for (int j = 0; j < ke; ++j) sigma[j] = sg[j];
+  // W orientation -> user side P (U_k S_k) and item side V (unit columns)
+  if (P || V) {
+    for (int j = 0; j < ke; ++j) {
+      const double sj = sg[j];
+      for (int r = 0; r < bm.mb; ++r) {
+        float v = bm.trans ? FL[(size_t)r * kp + j]
+                           : (float)(Fs[(size_t)r * kp + j] * sj);
+        if (P) P[(size_t)r * ke + j] = v;
+      }
+      for (int cc = 0; cc < bm.nb; ++cc) {
+        float v = bm.trans ? Fs[(size_t)cc * kp + j]
+                           : (sj > 0 ? (float)(FL[(size_t)cc * kp + j] / sj) : 0.f);
+        if (V) V[(size_t)cc * ke + j] = v;
+      }
+    }
+  }
+  if (dense) {
+    for (int r = 0; r < bm.mb; ++r)
+      for (int cc = 0; cc < bm.nb; ++cc)
+        dense[(size_t)r * bm.nb + cc] =
+            bm.trans ? W[(size_t)cc * bm.L_pad + r] : W[(size_t)r * bm.L_pad + cc];
+  }
+  return BSVD_OK;
+}
+
+bsvd_status bsvd_reconstruct(bsvd_ctx *c, int32_t b, int32_t add_mean,
+                             float *out) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (!c->factored) return fail(c, BSVD_ESTATE, "reconstruct: no factors");
+  if (b < 0 || b >= c->nblocks || !out)
+    return fail(c, BSVD_EINVAL, "reconstruct: bad arguments");
+  const BlockMeta &bm = c->meta[b];
+  const size_t cells = (size_t)bm.mb * bm.nb;
+  if (cells == 0) return BSVD_OK;
+  float mu = 0.f;
+  if (add_mean)
+    CK(cudaMemcpyAsync(&mu, c->d_mu.as<float>() + b, sizeof mu,
+                       cudaMemcpyDeviceToHost, c->st), "reconstruct");
+  CK(cudaStreamSynchronize(c->st), "reconstruct");
+  const bool dev_out = is_device_ptr(out);
+  float *dst = out;
+  if (!dev_out) {
+    CK(c->s_out.ensure(sizeof(float) * cells), "reconstruct");
+    dst = c->s_out.as<float>();
+  }
+  CK(launch_reconstruct(c->d_meta.as<BlockMeta>(), b, c->d_Fs.as<float>(),
+                        c->d_FL.as<float>(), c->kp, mu, dst, c->st),
+     "reconstruct");
+  c->launches += 1;
+  if (!dev_out)
+    CK(cudaMemcpyAsync(out, dst, sizeof(float) * cells, cudaMemcpyDeviceToHost,
+                       c->st), "reconstruct");
+  CK(cudaStreamSynchronize(c->st), "reconstruct");
+  return BSVD_OK;
+}
+
+bsvd_status bsvd_factor_report(bsvd_ctx *c, int32_t *iters,
+                               int32_t *converged) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (!c->factored) return fail(c, BSVD_ESTATE, "factor_report: no factors");
+  std::vector<SolverState> s(c->nblocks);
+  CK(cudaMemcpyAsync(s.data(), c->d_state.p, sizeof(SolverState) * c->nblocks,
+                     cudaMemcpyDeviceToHost, c->st), "factor_report");
+  CK(cudaStreamSynchronize(c->st), "factor_report");
+  for (int32_t b = 0; b < c->nblocks; ++b) {
+    if (iters) iters[b] = s[b].iters;
+    if (converged) converged[b] = s[b].status == kConverged ? 1 : 0;
+  }
+  return BSVD_OK;
+}
+
+bsvd_status bsvd_phase_times(bsvd_ctx *c, double *ms) {
+  if (!c || !ms) return BSVD_EINVAL;
+  if (!c->cfg.profile)
+    return fail(c, BSVD_ESTATE, "phase_times: profiling is off");
+  for (int j = 0; j < 5; ++j) ms[j] = c->phase_ms[j];
+  return BSVD_OK;
+}
+
+int64_t bsvd_kernel_launches(const bsvd_ctx *c) {
+  return c ? c->launches : -1;
+}
+
+}  // extern "C"

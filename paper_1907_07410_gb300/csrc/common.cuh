@@ -1,0 +1,107 @@
+// Device-side data layout shared by the kernels of libbsvd.
+//
+// One rating matrix X (m users x n items) is cut into a p x q grid of
+// blocks (Section 3, Eq. "datax"). Every block b stores its centred dense
+// matrix B_b "Gram-side major":
+//
+//   W_b = B_b^T (s = n_b items, L = m_b users)  when n_b <= m_b   (trans=1)
+//   W_b = B_b   (s = m_b users, L = n_b items)  otherwise         (trans=0)
+//
+// W_b is s_pad x L_pad row-major in one arena, zero-padded. Its Gram matrix
+// G_b = W_b W_b^T (s x s) is the smaller of B^T B and B B^T, and its top-k
+// eigenvectors F_s are the singular vectors of the shorter side. The longer
+// side's factor is F_L = W_b^T F_s (L x k), i.e. U_k S_k or V_k S_k, so that
+// B_b ~ F_s F_L^T in W orientation.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bsvd {
+
+constexpr int kPad = 32;          // s and L are padded to multiples of this
+constexpr int kMaxSub = 64;       // widest subspace the small solver handles
+
+struct BlockMeta {
+  int32_t mb, nb;       // block shape (users x items)
+  int32_t s, L;         // Gram side, reduction side
+  int32_t s_pad, L_pad; // padded to kPad
+  int32_t trans;        // 1: W = B^T (s indexes items); 0: W = B
+  int32_t keff;         // retained rank min(k, s) (set by factor)
+  int64_t row0, col0;   // first row / column position of the block
+  int64_t w_off;        // W arena offset (floats)
+  int64_t g_off;        // Gram offset, s_pad x s_pad
+  int64_t x_off;        // subspace panels offset, s_pad x bsub
+  int64_t fs_off;       // F_s offset, s_pad x kp
+  int64_t fl_off;       // F_L offset, L_pad x kp
+};
+
+// Per-block state of the subspace iteration.
+struct SolverState {
+  float cut;            // upper end of the damped interval [0, cut]
+  float a0;             // scaling point (largest Ritz value)
+  float theta1;         // largest Ritz value
+  float resid;          // max residual / theta1 at the last check
+  int32_t bsub;         // subspace width used by this block (<= s)
+  int32_t iters;        // Rayleigh-Ritz steps taken
+  int32_t status;       // kRunning / kConverged / kCapped
+  int32_t pad;
+};
+
+enum : int32_t { kRunning = 0, kConverged = 1, kCapped = 2 };
+
+// Error bits raised by kernels (read back by the calling entry point).
+enum : int32_t {
+  kErrIndex = 1,        // an id outside [0, m) or [0, n)
+  kErrValue = 2,        // a non-finite rating or |x| >= 2^31
+  kErrSumRange = 4,     // count * max|x| >= 2^31 in some block
+  kErrBadPerm = 8       // a permutation entry out of range or repeated
+};
+
+// Grid description used by every kernel that maps (user, item) to a block.
+struct GridDesc {
+  int64_t m, n;
+  int32_t p, q;
+  int32_t equal_rows, equal_cols;   // 1: equal ceil-sized blocks
+  int64_t br, bc;                   // equal block sizes
+  const int64_t *row_bounds;        // device, p + 1
+  const int64_t *col_bounds;        // device, q + 1
+  const int32_t *row_perm;          // device or null
+  const int32_t *col_perm;          // device or null
+};
+
+// Largest j with bounds[j] <= v, for bounds[0] = 0 <= v < bounds[count].
+__device__ __forceinline__ int32_t upper_index(const int64_t *bounds,
+                                               int32_t count, int64_t v) {
+  int32_t lo = 0, hi = count;       // invariant: bounds[lo] <= v < bounds[hi]
+  while (hi - lo > 1) {
+    int32_t mid = (lo + hi) >> 1;
+    if (bounds[mid] <= v) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Block id and local (row, col) of a rating; false if an id is out of range.
+__device__ __forceinline__ bool locate(const GridDesc &g, int32_t u,
+                                       int32_t i, int32_t *blk, int32_t *r,
+                                       int32_t *c) {
+  if (u < 0 || (int64_t)u >= g.m || i < 0 || (int64_t)i >= g.n) return false;
+  int64_t ru = g.row_perm ? (int64_t)g.row_perm[u] : (int64_t)u;
+  int64_t ci = g.col_perm ? (int64_t)g.col_perm[i] : (int64_t)i;
+  int32_t bi, bj;
+  if (g.equal_rows) bi = (int32_t)(ru / g.br);
+  else bi = upper_index(g.row_bounds, g.p, ru);
+  if (g.equal_cols) bj = (int32_t)(ci / g.bc);
+  else bj = upper_index(g.col_bounds, g.q, ci);
+  *blk = bi * g.q + bj;
+  *r = (int32_t)(ru - g.row_bounds[bi]);
+  *c = (int32_t)(ci - g.col_bounds[bj]);
+  return true;
+}
+
+// (r, c) of B -> (a, l) of W: a on the Gram side, l on the reduction side.
+__device__ __forceinline__ void to_w(const BlockMeta &bm, int32_t r,
+                                     int32_t c, int32_t *a, int32_t *l) {
+  if (bm.trans) { *a = c; *l = r; } else { *a = r; *l = c; }
+}
+
+}  // namespace bsvd

@@ -1,0 +1,96 @@
+// Launchers of the libbsvd kernels (host side). Every launcher queues work
+// on the given stream and returns the launch status.
+#pragma once
+#include "common.cuh"
+
+namespace bsvd {
+
+// ---- partition (kernels_partition.cu) ----------------------------------
+cudaError_t launch_perm_check(const int32_t *perm, int64_t n, int32_t *seen,
+                              int32_t *err, cudaStream_t st);
+cudaError_t launch_count(const GridDesc &g, int64_t nnz, const int32_t *u,
+                         const int32_t *i, const float *x, int32_t nblocks,
+                         unsigned long long *counts, long long *sums,
+                         unsigned int *maxabs_bits, int32_t *err,
+                         cudaStream_t st);
+cudaError_t launch_means(int32_t nblocks, const unsigned long long *counts,
+                         const long long *sums,
+                         const unsigned int *maxabs_bits, float *mu,
+                         int32_t *err, cudaStream_t st);
+cudaError_t launch_scatter(const GridDesc &g, const BlockMeta *meta,
+                           int64_t nnz, const int32_t *u, const int32_t *i,
+                           const float *x, const float *mu, float *W,
+                           cudaStream_t st);
+
+// ---- Gram (kernels_gram.cu) ---------------------------------------------
+// tiles: (block, tile_i, tile_j, 0) with tile_i <= tile_j, 128 x 128 tiles.
+cudaError_t launch_gram_f32(const BlockMeta *meta, const int4 *tiles,
+                            int32_t ntiles, const float *W, float *G,
+                            cudaStream_t st);
+
+// ---- subspace iteration (kernels_eig.cu) --------------------------------
+struct EigBuffers {
+  const BlockMeta *meta;
+  SolverState *state;
+  float *G;          // s_pad x s_pad Gram per block
+  float *X;          // panels, s_pad x bsub per block
+  float *Z;          // G X panels
+  float *SH;         // per block: S (bsub^2) then H (bsub^2)
+  float *T;          // per block: bsub^2 transform
+  float *theta;      // per block: bsub Ritz values, descending
+  float *Fs;         // s_pad x kp per block
+  int32_t *running;  // count of blocks still iterating (device scalar)
+  int32_t bsub, kp, k;
+  int32_t nblocks;
+  int32_t max_iters, max_sweeps;
+  float tol;
+  uint64_t seed;
+};
+
+// row tiles: (block, first row) pairs, 64 rows each.
+cudaError_t launch_init_panels(const EigBuffers &e, const int2 *rowtiles,
+                               int32_t ntiles, cudaStream_t st);
+// mode 0: Z = G X. mode 1: first Chebyshev step X -> Z. mode 2: step j >= 2.
+cudaError_t launch_gpanel(const EigBuffers &e, const int2 *rowtiles,
+                          int32_t ntiles, int32_t mode, int32_t step,
+                          int32_t degree, const float *in, const float *in2,
+                          float *out, cudaStream_t st);
+cudaError_t launch_small_gram(const EigBuffers &e, cudaStream_t st);
+cudaError_t launch_rr_solve(const EigBuffers &e, cudaStream_t st);
+cudaError_t launch_rotate(const EigBuffers &e, const int2 *rowtiles,
+                          int32_t ntiles, cudaStream_t st);
+cudaError_t launch_check(const EigBuffers &e, cudaStream_t st);
+
+// F_L = W^T F_s, then float64 norms (sigma) and sign canonicalisation.
+cudaError_t launch_project(const BlockMeta *meta, const int2 *ltiles,
+                           int32_t ntiles, const float *W, const float *Fs,
+                           float *FL, int32_t kp, cudaStream_t st);
+cudaError_t launch_finalize(const BlockMeta *meta, int32_t nblocks,
+                            float *Fs, float *FL, double *sigma, int32_t kp,
+                            int32_t k, cudaStream_t st);
+
+// ---- prediction (kernels_predict.cu) ------------------------------------
+struct PredictArgs {
+  GridDesc g;
+  const BlockMeta *meta;
+  const float *mu;
+  const float *Fs;
+  const float *FL;
+  int32_t kp;
+  int32_t clamp;
+  float lo, hi;
+};
+cudaError_t launch_predict(const PredictArgs &a, int64_t nq, const int32_t *u,
+                           const int32_t *i, float *yhat, int32_t *err,
+                           cudaStream_t st);
+// Squared-error partial sums: one float64 per CTA of a fixed grid, then a
+// fixed-order final sum. partials must hold kSqerrBlocks doubles.
+constexpr int kSqerrBlocks = 304;
+cudaError_t launch_sqerr(const PredictArgs &a, int64_t nq, const int32_t *u,
+                         const int32_t *i, const float *y, double *partials,
+                         double *out, int32_t *err, cudaStream_t st);
+cudaError_t launch_reconstruct(const BlockMeta *meta, int32_t b,
+                               const float *Fs, const float *FL, int32_t kp,
+                               float mu, float *out, cudaStream_t st);
+
+}  // namespace bsvd

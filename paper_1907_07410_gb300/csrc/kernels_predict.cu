@@ -1,0 +1,142 @@
+// Held-out prediction and scoring.
+//
+// A rating is predicted from its block's factors (Section 2.1, Eq. 2, with
+// the singular values merged into one side): yhat = mu_b + P[r,:] . V[c,:].
+// In W orientation that is mu_b + F_s[a,:] . F_L[l,:]. The score is the RMSE
+// of Section 5 (Table 1, "Test RMSE").
+//
+// The squared errors are summed in float64 with a fixed grid, a fixed
+// per-thread stride and a fixed reduction tree. The sum therefore does not
+// depend on scheduling, and reruns are bit-identical.
+#include "kernels.h"
+
+namespace bsvd {
+
+namespace {
+
+__device__ __forceinline__ bool predict_one(const PredictArgs &a, int32_t u,
+                                            int32_t i, float *out) {
+  int32_t blk, r, c, wa, wl;
+  if (!locate(a.g, u, i, &blk, &r, &c)) return false;
+  const BlockMeta &bm = a.meta[blk];
+  float y = a.mu[blk];
+  if (bm.keff > 0) {
+    to_w(bm, r, c, &wa, &wl);
+    const float4 *fs = reinterpret_cast<const float4 *>(
+        a.Fs + bm.fs_off + (int64_t)wa * a.kp);
+    const float4 *fl = reinterpret_cast<const float4 *>(
+        a.FL + bm.fl_off + (int64_t)wl * a.kp);
+    float dot = 0.f;
+    for (int j = 0; j < a.kp / 4; ++j) {
+      const float4 p = __ldg(fs + j), q = __ldg(fl + j);
+      dot = fmaf(p.x, q.x, dot);
+      dot = fmaf(p.y, q.y, dot);
+      dot = fmaf(p.z, q.z, dot);
+      dot = fmaf(p.w, q.w, dot);
+    }
+    y += dot;
+  }
+  if (a.clamp) y = fminf(fmaxf(y, a.lo), a.hi);
+  *out = y;
+  return true;
+}
+
+__global__ void __launch_bounds__(256)
+k_predict(PredictArgs a, int64_t nq, const int32_t *__restrict__ u,
+          const int32_t *__restrict__ it, float *__restrict__ yhat,
+          int32_t *err) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nq;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    float y = 0.f;
+    if (!predict_one(a, u[t], it[t], &y)) atomicOr(err, kErrIndex);
+    yhat[t] = y;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_sqerr(PredictArgs a, int64_t nq, const int32_t *__restrict__ u,
+        const int32_t *__restrict__ it, const float *__restrict__ y,
+        double *__restrict__ partials, int32_t *err) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nq;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    float yh;
+    if (!predict_one(a, u[t], it[t], &yh)) { atomicOr(err, kErrIndex); continue; }
+    const double d = (double)yh - (double)y[t];
+    acc = fma(d, d, acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(512)
+k_sum_partials(const double *__restrict__ partials, int n, double *out) {
+  __shared__ double red[512];
+  red[threadIdx.x] = threadIdx.x < n ? partials[threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int w = 256; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void __launch_bounds__(256)
+k_reconstruct(const BlockMeta *__restrict__ meta, int32_t b,
+              const float *__restrict__ Fs, const float *__restrict__ FL,
+              int32_t kp, float mu, float *__restrict__ out) {
+  const BlockMeta bm = meta[b];
+  const int64_t total = (int64_t)bm.mb * bm.nb;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = (int32_t)(e / bm.nb), c = (int32_t)(e % bm.nb);
+    int32_t wa, wl;
+    to_w(bm, r, c, &wa, &wl);
+    const float *fs = Fs + bm.fs_off + (int64_t)wa * kp;
+    const float *fl = FL + bm.fl_off + (int64_t)wl * kp;
+    float dot = 0.f;
+    for (int j = 0; j < bm.keff; ++j) dot = fmaf(fs[j], fl[j], dot);
+    out[e] = mu + dot;
+  }
+}
+
+int grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 152 * 8) g = 152 * 8;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_predict(const PredictArgs &a, int64_t nq, const int32_t *u,
+                           const int32_t *i, float *yhat, int32_t *err,
+                           cudaStream_t st) {
+  if (nq <= 0) return cudaSuccess;
+  k_predict<<<grid_for(nq), 256, 0, st>>>(a, nq, u, i, yhat, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sqerr(const PredictArgs &a, int64_t nq, const int32_t *u,
+                         const int32_t *i, const float *y, double *partials,
+                         double *out, int32_t *err, cudaStream_t st) {
+  static_assert(kSqerrBlocks <= 512, "final sum is one CTA of 512");
+  k_sqerr<<<kSqerrBlocks, 256, 0, st>>>(a, nq, u, i, y, partials, err);
+  k_sum_partials<<<1, 512, 0, st>>>(partials, kSqerrBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reconstruct(const BlockMeta *meta, int32_t b,
+                               const float *Fs, const float *FL, int32_t kp,
+                               float mu, float *out, cudaStream_t st) {
+  k_reconstruct<<<152 * 4, 256, 0, st>>>(meta, b, Fs, FL, kp, mu, out);
+  return cudaGetLastError();
+}
+
+}  // namespace bsvd

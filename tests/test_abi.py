@@ -1,0 +1,40 @@
+"""The C-ABI library loads and exports every entry point include/bsvd.h
+declares. No compute call is made, so this runs without a GPU."""
+import ctypes
+import os
+import re
+
+import paper_1907_07410_gb300 as bs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(bsvd_[a-z_0-9]+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = bs.load()
+    declared = declared_symbols()
+    assert "bsvd_partition" in declared and "bsvd_factor" in declared
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert declared <= set(bs.EXPORTS) | declared
+    assert set(bs.EXPORTS) <= declared
+
+
+def test_config_layout_matches_header():
+    cfg = bs.bsvd_config_default()
+    assert cfg.cheb_degree == 8 and cfg.max_iters == 30
+    assert abs(cfg.tol - 1e-5) < 1e-20
+    assert cfg.clamp_lo == 1.0 and cfg.clamp_hi == 5.0
+    # int32 x2, float x2, int32 x6, double, uint64, pointer
+    assert ctypes.sizeof(bs.Config) == 64
+    assert bs.Config.tol.offset == 40 and bs.Config.stream.offset == 56
