@@ -69,7 +69,8 @@ typedef struct {
     float clamp_lo;
     float clamp_hi;
     int32_t oversample;   /* subspace columns beyond k; <= 0: default */
-    int32_t cheb_degree;  /* Chebyshev filter degree; <= 0: default (8) */
+    int32_t cheb_degree;  /* largest Chebyshev filter degree, even;
+                             <= 0: default (8) */
     int32_t max_iters;    /* subspace iterations cap; <= 0: default (30) */
     int32_t max_sweeps;   /* Jacobi sweeps cap per small solve; <= 0: 30 */
     int32_t profile;      /* 1: time each phase with CUDA events */

@@ -494,6 +494,7 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
     e.bsub = B; e.kp = kp; e.k = k; e.nblocks = nb;
     e.max_iters = c->cfg.max_iters;
     e.max_sweeps = c->cfg.max_sweeps;
+    e.max_degree = c->cfg.cheb_degree;
     e.tol = (float)c->cfg.tol;
     e.seed = c->cfg.seed;
     const int2 *rtd = c->d_rowtiles.as<int2>();

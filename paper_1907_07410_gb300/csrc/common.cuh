@@ -44,7 +44,7 @@ struct SolverState {
   int32_t bsub;         // subspace width used by this block (<= s)
   int32_t iters;        // Rayleigh-Ritz steps taken
   int32_t status;       // kRunning / kConverged / kCapped
-  int32_t pad;
+  int32_t degree;       // Chebyshev degree of the next filter (even)
 };
 
 enum : int32_t { kRunning = 0, kConverged = 1, kCapped = 2 };

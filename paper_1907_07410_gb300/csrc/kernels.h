@@ -43,6 +43,7 @@ struct EigBuffers {
   int32_t bsub, kp, k;
   int32_t nblocks;
   int32_t max_iters, max_sweeps;
+  int32_t max_degree;  // cap on the per-block Chebyshev degree (even)
   float tol;
   uint64_t seed;
 };

@@ -21,6 +21,13 @@
 //   3. Stop a block when |G x_i - theta_i x_i| <= tol * theta_1 for its k
 //      wanted pairs; otherwise cut <- smallest Ritz value and go to 1.
 //
+// The filter amplifies the top of the spectrum by C_d(t_1), with
+// t_1 = 2 theta_1 / cut - 1, relative to the damped interval. In float32
+// the columns that should hold the lower Ritz directions drown in rounding
+// noise once that ratio nears 1/eps, so each block picks the largest even
+// degree d <= max_degree with C_d(t_1) <= kMaxAmplification (at least 2).
+// Steep spectra get short filters and more Rayleigh-Ritz steps.
+//
 // A block with s <= bsub starts from the identity basis, so the first
 // Rayleigh-Ritz step is an exact eigen-decomposition of G.
 #include <float.h>
@@ -34,6 +41,8 @@ namespace bsvd {
 namespace {
 
 constexpr int TR = 64;       // panel rows per CTA
+constexpr float kMaxAmplification = 3e6f;
+constexpr float kCutFloor = 1e-3f;   // cut >= kCutFloor * theta_1
 constexpr int KC = 32;       // k-chunk of the panel GEMM
 
 __device__ __forceinline__ float hash_uniform(uint64_t seed, uint64_t a,
@@ -83,6 +92,7 @@ k_gpanel(const BlockMeta *__restrict__ meta,
   const int2 t = rowtiles[blockIdx.x];
   const SolverState st = state[t.x];
   if (st.status != kRunning) return;
+  if (mode >= 1 && step > st.degree) return;   // this block's filter is done
   const BlockMeta bm = meta[t.x];
   const int sp = bm.s_pad;
   const int row0 = t.y;
@@ -467,7 +477,7 @@ __global__ void __launch_bounds__(256)
 k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
         const float *__restrict__ X, const float *__restrict__ Z,
         const float *__restrict__ theta, float *__restrict__ Fs, int kp,
-        int max_iters, float tol, int32_t *running) {
+        int max_iters, int max_degree, float tol, int32_t *running) {
   constexpr int G = 256 / B;          // row groups
   __shared__ float rs[G][B], xs[G][B];
   __shared__ int s_done;
@@ -508,10 +518,16 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
       s_done = 1;
     } else {
       float cut = th[n - 1];
-      cut = fmaxf(cut, 1e-4f * t1);
-      if (cut >= t1) cut = 0.5f * t1;
+      cut = fmaxf(cut, kCutFloor * t1);
+      if (cut >= 0.5f * t1) cut = 0.5f * t1;
       st.cut = cut;
       st.a0 = t1;
+      const float tt = 2.f * t1 / cut - 1.f;   // >= 3
+      const float at = acoshf(tt);
+      int d = 2;
+      while (d + 2 <= max_degree && coshf((float)(d + 2) * at) <= kMaxAmplification)
+        d += 2;
+      st.degree = d;
       atomicAdd(running, 1);
       s_done = 0;
     }
@@ -710,7 +726,7 @@ cudaError_t launch_check(const EigBuffers &e, cudaStream_t st) {
     constexpr int B = decltype(w)::value;
     k_check<B><<<e.nblocks, 256, 0, st>>>(e.meta, e.state, e.X, e.Z,
                                           e.theta, e.Fs, e.kp, e.max_iters,
-                                          e.tol, e.running);
+                                          e.max_degree, e.tol, e.running);
     return cudaGetLastError();
   });
 }
