@@ -62,7 +62,7 @@ struct bsvd_ctx {
   // factor
   bool factored = false;
   int32_t k = 0, bsub = 0, kp = 4;
-  DevBuf d_G, d_X, d_Z, d_SH, d_T, d_theta, d_state, d_Fs, d_FL, d_sigma,
+  DevBuf d_G, d_X, d_Z, d_SH, d_RP, d_T, d_theta, d_state, d_Fs, d_FL, d_sigma,
       d_running, d_gtiles, d_rowtiles, d_ltiles;
   int32_t n_gtiles = 0, n_rowtiles = 0, n_ltiles = 0;
   bool any_capped = false;
@@ -250,7 +250,7 @@ void bsvd_destroy(bsvd_ctx *c) {
   DevBuf *bufs[] = {&c->d_rb, &c->d_cb, &c->d_rperm, &c->d_cperm, &c->d_seen,
                     &c->d_meta, &c->d_counts, &c->d_sums, &c->d_maxabs,
                     &c->d_mu, &c->d_W, &c->d_err, &c->d_G, &c->d_X, &c->d_Z,
-                    &c->d_SH, &c->d_T, &c->d_theta, &c->d_state, &c->d_Fs,
+                    &c->d_SH, &c->d_RP, &c->d_T, &c->d_theta, &c->d_state, &c->d_Fs,
                     &c->d_FL, &c->d_sigma, &c->d_running, &c->d_gtiles,
                     &c->d_rowtiles, &c->d_ltiles, &c->s_a, &c->s_b, &c->s_c,
                     &c->s_out, &c->d_partials, &c->d_rmse};
@@ -436,12 +436,15 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
     std::memset(&s, 0, sizeof s);
     s.bsub = std::min(B, bm.s);
     s.status = (bm.s == 0 || bm.keff == 0) ? kConverged : kRunning;
+    bm.t0 = (int32_t)rt.size();
+    bm.nt = 0;
     if (bm.s == 0) continue;
     const int32_t T = (bm.s_pad + 127) / 128;
     for (int32_t ti = 0; ti < T; ++ti)
       for (int32_t tj = ti; tj < T; ++tj) gt.push_back(make_int4(b, ti, tj, 0));
     for (int32_t r = 0; r < bm.s_pad; r += 64) rt.push_back(make_int2(b, r));
-    for (int32_t l = 0; l < bm.L; l += 128) lt.push_back(make_int2(b, l));
+    bm.nt = (int32_t)rt.size() - bm.t0;
+    for (int32_t l = 0; l < bm.L; l += kProjCols) lt.push_back(make_int2(b, l));
   }
   c->n_gtiles = (int32_t)gt.size();
   c->n_rowtiles = (int32_t)rt.size();
@@ -450,7 +453,8 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
   CK(c->d_G.ensure(sizeof(float) * std::max<int64_t>(goff, 1)), "factor");
   CK(c->d_X.ensure(sizeof(float) * std::max<int64_t>(xoff, 1)), "factor");
   CK(c->d_Z.ensure(sizeof(float) * std::max<int64_t>(xoff, 1)), "factor");
-  CK(c->d_SH.ensure(sizeof(float) * 2 * B * B * (int64_t)nb), "factor");
+  CK(c->d_SH.ensure(sizeof(float) * 2 * B * B * std::max<int64_t>(rt.size(), 1)), "factor");
+  CK(c->d_RP.ensure(sizeof(float) * 2 * B * std::max<int64_t>(rt.size(), 1)), "factor");
   CK(c->d_T.ensure(sizeof(float) * B * B * (int64_t)nb), "factor");
   CK(c->d_theta.ensure(sizeof(float) * B * (int64_t)nb), "factor");
   CK(c->d_state.ensure(sizeof(SolverState) * nb), "factor");
@@ -487,6 +491,7 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
     e.X = c->d_X.as<float>();
     e.Z = c->d_Z.as<float>();
     e.SH = c->d_SH.as<float>();
+    e.RP = c->d_RP.as<float>();
     e.T = c->d_T.as<float>();
     e.theta = c->d_theta.as<float>();
     e.Fs = c->d_Fs.as<float>();
@@ -510,12 +515,12 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
     c->launches += (c->n_gtiles > 0) + 2 * (nrt > 0);
     const int deg = c->cfg.cheb_degree;
     for (int it = 0; it <= c->cfg.max_iters + 1; ++it) {
-      CK(launch_small_gram(e, c->st), "factor: rr gram");
+      CK(launch_small_gram(e, rtd, nrt, c->st), "factor: rr gram");
       CK(launch_rr_solve(e, c->st), "factor: rr solve");
       CK(launch_rotate(e, rtd, nrt, c->st), "factor: rotate");
       CK(cudaMemsetAsync(e.running, 0, sizeof(int32_t), c->st), "factor");
       CK(launch_check(e, c->st), "factor: check");
-      c->launches += 3 + (nrt > 0);
+      c->launches += 2 + 2 * (nrt > 0);
       int32_t running = 0;
       CK(cudaMemcpyAsync(&running, e.running, sizeof running,
                          cudaMemcpyDeviceToHost, c->st), "factor");

@@ -27,6 +27,7 @@ struct BlockMeta {
   int32_t s_pad, L_pad; // padded to kPad
   int32_t trans;        // 1: W = B^T (s indexes items); 0: W = B
   int32_t keff;         // retained rank min(k, s) (set by factor)
+  int32_t t0, nt;       // the block's 64-row tiles in the row-tile table
   int64_t row0, col0;   // first row / column position of the block
   int64_t w_off;        // W arena offset (floats)
   int64_t g_off;        // Gram offset, s_pad x s_pad
@@ -45,6 +46,9 @@ struct SolverState {
   int32_t iters;        // Rayleigh-Ritz steps taken
   int32_t status;       // kRunning / kConverged / kCapped
   int32_t degree;       // Chebyshev degree of the next filter (even)
+  uint64_t refill;      // Ritz columns refilled with random vectors
+  int32_t sweeps;       // Jacobi sweeps used so far
+  int32_t pad;
 };
 
 enum : int32_t { kRunning = 0, kConverged = 1, kCapped = 2 };

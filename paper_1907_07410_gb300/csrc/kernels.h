@@ -35,7 +35,8 @@ struct EigBuffers {
   float *G;          // s_pad x s_pad Gram per block
   float *X;          // panels, s_pad x bsub per block
   float *Z;          // G X panels
-  float *SH;         // per block: S (bsub^2) then H (bsub^2)
+  float *SH;         // per row tile: partial S (bsub^2) then H (bsub^2)
+  float *RP;         // per row tile: partial residual^2 and norm^2 (2 bsub)
   float *T;          // per block: bsub^2 transform
   float *theta;      // per block: bsub Ritz values, descending
   float *Fs;         // s_pad x kp per block
@@ -56,13 +57,16 @@ cudaError_t launch_gpanel(const EigBuffers &e, const int2 *rowtiles,
                           int32_t ntiles, int32_t mode, int32_t step,
                           int32_t degree, const float *in, const float *in2,
                           float *out, cudaStream_t st);
-cudaError_t launch_small_gram(const EigBuffers &e, cudaStream_t st);
+cudaError_t launch_small_gram(const EigBuffers &e, const int2 *rowtiles,
+                              int32_t ntiles, cudaStream_t st);
 cudaError_t launch_rr_solve(const EigBuffers &e, cudaStream_t st);
 cudaError_t launch_rotate(const EigBuffers &e, const int2 *rowtiles,
                           int32_t ntiles, cudaStream_t st);
 cudaError_t launch_check(const EigBuffers &e, cudaStream_t st);
 
 // F_L = W^T F_s, then float64 norms (sigma) and sign canonicalisation.
+// ltiles: (block, first column l) pairs, kProjCols columns each.
+constexpr int kProjCols = 32;
 cudaError_t launch_project(const BlockMeta *meta, const int2 *ltiles,
                            int32_t ntiles, const float *W, const float *Fs,
                            float *FL, int32_t kp, cudaStream_t st);

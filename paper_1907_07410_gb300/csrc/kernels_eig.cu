@@ -10,14 +10,16 @@
 //      on the unwanted interval [0, cut] and equals 1 at the largest Ritz
 //      value a0. It uses the scaled three-term recurrence, so values stay
 //      O(1) and float32 cannot overflow.
-//   2. Rayleigh-Ritz with SVQB orthonormalisation (Stathopoulos and Wu,
-//      2002):
-//        S = X^T X, S_n = D^-1 S D^-1 = Q L Q^T,
-//        T1 = D^-1 Q L^-1/2,
+//   2. Rayleigh-Ritz on span(X) with Cholesky-QR orthonormalisation:
+//        S = X^T X, S_n = D^-1 S D^-1 = L L^T (D = diag(S)^1/2),
+//        T1 = D^-1 L^-T, so X T1 has orthonormal columns;
 //        H' = T1^T (X^T G X) T1 = Y Theta Y^T,
-//        X <- X T1 Y.
-//      Both small symmetric eigenproblems are solved by cyclic Jacobi with
-//      parallel (round-robin) ordering in shared memory.
+//        X <- X T1 Y, and G X <- (G X) T1 Y without another product.
+//      The b x b eigenproblem is solved by cyclic Jacobi with parallel
+//      (round-robin) ordering in shared memory. A column whose Cholesky
+//      pivot is below kPivotDrop is numerically inside the span of the
+//      columns before it; it is dropped from the basis and refilled with a
+//      fresh random vector, so the subspace keeps its width.
 //   3. Stop a block when |G x_i - theta_i x_i| <= tol * theta_1 for its k
 //      wanted pairs; otherwise cut <- smallest Ritz value and go to 1.
 //
@@ -43,6 +45,7 @@ namespace {
 constexpr int TR = 64;       // panel rows per CTA
 constexpr float kMaxAmplification = 3e6f;
 constexpr float kCutFloor = 1e-3f;   // cut >= kCutFloor * theta_1
+constexpr float kPivotDrop = 1e-4f;  // squared sine of the angle to the span
 constexpr int KC = 32;       // k-chunk of the panel GEMM
 
 __device__ __forceinline__ float hash_uniform(uint64_t seed, uint64_t a,
@@ -179,87 +182,93 @@ k_gpanel(const BlockMeta *__restrict__ meta,
   }
 }
 
-// S = X^T X and H = X^T Z over the block's s rows (float32 sums).
+// Partial S = X^T X and H = X^T Z over the 64 rows of one row tile, for
+// every tile of every running block; k_rr_solve sums a block's tiles in a
+// fixed order, so the totals do not depend on scheduling.
 template <int B>
 __global__ void __launch_bounds__(256)
 k_small_gram(const BlockMeta *__restrict__ meta,
              const SolverState *__restrict__ state,
-             const float *__restrict__ X, const float *__restrict__ Z,
-             float *__restrict__ SH) {
-  constexpr int CH = 32;
+             const int2 *__restrict__ rowtiles, const float *__restrict__ X,
+             const float *__restrict__ Z, float *__restrict__ SHp) {
   constexpr int PER = (B * B + 255) / 256;
-  __shared__ float Xs[CH][B + 1];
-  __shared__ float Zs[CH][B + 1];
-  const int blk = blockIdx.x;
-  if (state[blk].status != kRunning) return;
-  const BlockMeta bm = meta[blk];
-  const float *Xb = X + bm.x_off;
-  const float *Zb = Z + bm.x_off;
-  float s_acc[PER], h_acc[PER];
-#pragma unroll
-  for (int e = 0; e < PER; ++e) { s_acc[e] = 0.f; h_acc[e] = 0.f; }
-  for (int r0 = 0; r0 < bm.s; r0 += CH) {
-    for (int e = threadIdx.x; e < CH * B; e += 256) {
-      const int rr = e / B, c = e % B;
-      const bool ok = r0 + rr < bm.s;
-      Xs[rr][c] = ok ? Xb[(int64_t)(r0 + rr) * B + c] : 0.f;
-      Zs[rr][c] = ok ? Zb[(int64_t)(r0 + rr) * B + c] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < PER; ++e) {
-      const int idx = threadIdx.x + 256 * e;
-      if (idx < B * B) {
-        const int i = idx / B, j = idx % B;
-        float sa = s_acc[e], ha = h_acc[e];
-#pragma unroll 8
-        for (int rr = 0; rr < CH; ++rr) {
-          const float xi = Xs[rr][i];
-          sa = fmaf(xi, Xs[rr][j], sa);
-          ha = fmaf(xi, Zs[rr][j], ha);
-        }
-        s_acc[e] = sa;
-        h_acc[e] = ha;
-      }
-    }
-    __syncthreads();
+  __shared__ float Xs[TR][B + 1];
+  __shared__ float Zs[TR][B + 1];
+  const int2 t = rowtiles[blockIdx.x];
+  if (state[t.x].status != kRunning) return;
+  const BlockMeta bm = meta[t.x];
+  const int rows = min(TR, bm.s - t.y);
+  const float *Xb = X + bm.x_off + (int64_t)t.y * B;
+  const float *Zb = Z + bm.x_off + (int64_t)t.y * B;
+  for (int e = threadIdx.x; e < TR * B; e += 256) {
+    const int rr = e / B, c = e % B;
+    const bool ok = rr < rows;
+    Xs[rr][c] = ok ? Xb[e] : 0.f;
+    Zs[rr][c] = ok ? Zb[e] : 0.f;
   }
-  float *S = SH + (int64_t)blk * 2 * B * B;
+  __syncthreads();
+  float *S = SHp + (int64_t)blockIdx.x * 2 * B * B;
   float *H = S + B * B;
 #pragma unroll
-  for (int e = 0; e < PER; ++e) {
-    const int idx = threadIdx.x + 256 * e;
-    if (idx < B * B) { S[idx] = s_acc[e]; H[idx] = h_acc[e]; }
+  for (int q = 0; q < PER; ++q) {
+    const int idx = threadIdx.x + 256 * q;
+    if (idx < B * B) {
+      const int i = idx / B, j = idx % B;
+      float sa = 0.f, ha = 0.f;
+#pragma unroll 16
+      for (int rr = 0; rr < TR; ++rr) {
+        const float xi = Xs[rr][i];
+        sa = fmaf(xi, Xs[rr][j], sa);
+        ha = fmaf(xi, Zs[rr][j], ha);
+      }
+      S[idx] = sa;
+      H[idx] = ha;
+    }
+  }
+}
+
+// Round-robin pairings for cyclic Jacobi on ne (even) indices: round r pairs
+// position i with position ne-1-i, where position 0 holds index 0 and
+// position j >= 1 holds 1 + (j - 1 + r) mod (ne - 1). Every pair meets once
+// per sweep of ne - 1 rounds, and the pairs of a round are disjoint.
+__device__ __forceinline__ void build_pairs(int ne, unsigned short *tab) {
+  const int np = ne / 2;
+  for (int e = threadIdx.x; e < (ne - 1) * np; e += blockDim.x) {
+    const int r = e / np, i = e % np;
+    const int pa = i, pb = ne - 1 - i;
+    const int p = pa == 0 ? 0 : 1 + (pa - 1 + r) % (ne - 1);
+    const int q = 1 + (pb - 1 + r) % (ne - 1);
+    tab[e] = (unsigned short)(p | (q << 8));
   }
 }
 
 // Cyclic Jacobi for a symmetric n x n matrix A (n <= B) in shared memory.
-// On return A is diagonal (to the tolerance) and A_in = V diag(A) V^T.
-// Round-robin ordering: n_even - 1 rounds per sweep, n_even / 2 disjoint
-// pairs per round, so all rotations of a round commute.
+// On return A is diagonal to the tolerance and A_in = V diag(A) V^T. A pair
+// (p, q) is rotated when |a_pq| > max(tol sqrt|a_pp a_qq|, 1e-9 max|a_ii|).
 template <int B>
-__device__ void jacobi_eig(float (*A)[B + 1], float (*V)[B + 1], int n,
-                           int max_sweeps, float *rc, float *rs, int *rp,
-                           int *rq, int *flag) {
+__device__ int jacobi_eig(float (*A)[B + 1], float (*V)[B + 1], int n,
+                          int max_sweeps, const unsigned short *pairs,
+                          const unsigned short *tri, float *rc, float *rs,
+                          int *flag) {
   const int tid = threadIdx.x;
   const int ne = n + (n & 1);
   const int np = ne / 2;
+  const int ntri = np * (np + 1) / 2;
   for (int e = tid; e < n * n; e += blockDim.x)
     V[e / n][e % n] = (e / n == e % n) ? 1.f : 0.f;
-  // absolute floor: rotations below it cannot change float32 results
   float dmax = 0.f;
   for (int i = 0; i < n; ++i) dmax = fmaxf(dmax, fabsf(A[i][i]));
-  __syncthreads();
   const float floor_abs = dmax * 1e-9f;
   const float tol = 3e-7f;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+  int sweep = 0;
+  __syncthreads();
+  for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) *flag = 0;
     __syncthreads();
     for (int round = 0; round < ne - 1; ++round) {
+      const unsigned short *pr = pairs + round * np;
       if (tid < np) {
-        const int pa = tid, pb = ne - 1 - tid;
-        const int p = pa == 0 ? 0 : 1 + (pa - 1 + round) % (ne - 1);
-        const int q = 1 + (pb - 1 + round) % (ne - 1);
+        const int p = pr[tid] & 255, q = pr[tid] >> 8;
         float c = 1.f, s = 0.f;
         if (p < n && q < n) {
           const float app = A[p][p], aqq = A[q][q], apq = A[p][q];
@@ -273,27 +282,26 @@ __device__ void jacobi_eig(float (*A)[B + 1], float (*V)[B + 1], int n,
             *flag = 1;
           }
         }
-        rc[tid] = c; rs[tid] = s; rp[tid] = p; rq[tid] = q;
+        rc[tid] = c;
+        rs[tid] = s;
       }
       __syncthreads();
       // A <- J^T A J on the 2 x 2 sub-blocks (pair i, pair j), i <= j; the
       // (j, i) sub-block is written as the transpose so A stays symmetric.
-      for (int e = tid; e < np * np; e += blockDim.x) {
-        const int i = e / np, j = e % np;
-        if (i > j) continue;
+      for (int e = tid; e < ntri; e += blockDim.x) {
+        const int i = tri[e] & 255, j = tri[e] >> 8;
         const float si = rs[i], sj = rs[j];
         if (si == 0.f && sj == 0.f) continue;
         const float ci = rc[i], cj = rc[j];
-        const int pi = rp[i], qi = rq[i], pj = rp[j], qj = rq[j];
+        const int pi = pr[i] & 255, qi = pr[i] >> 8;
+        const int pj = pr[j] & 255, qj = pr[j] >> 8;
         const bool vpi = pi < n, vqi = qi < n, vpj = pj < n, vqj = qj < n;
         const float x00 = (vpi && vpj) ? A[pi][pj] : 0.f;
         const float x01 = (vpi && vqj) ? A[pi][qj] : 0.f;
         const float x10 = (vqi && vpj) ? A[qi][pj] : 0.f;
         const float x11 = (vqi && vqj) ? A[qi][qj] : 0.f;
-        // rows: J^T from the left
         const float y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
         const float y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
-        // columns: J from the right
         float z00 = cj * y00 - sj * y01, z01 = sj * y00 + cj * y01;
         float z10 = cj * y10 - sj * y11, z11 = sj * y10 + cj * y11;
         if (i == j) { z01 = 0.f; z10 = 0.f; }
@@ -308,12 +316,14 @@ __device__ void jacobi_eig(float (*A)[B + 1], float (*V)[B + 1], int n,
           if (vqi && vqj) A[qj][qi] = z11;
         }
       }
+      // V <- V J
       for (int e = tid; e < n * np; e += blockDim.x) {
-        const int x = e / np, j = e % np;
+        const int j = e % np, x = e / np;
         const float sj = rs[j];
         if (sj == 0.f) continue;
         const float cj = rc[j];
-        const int pj = rp[j], qj = rq[j];
+        const int pj = pr[j] & 255, qj = pr[j] >> 8;
+        if (qj >= n || pj >= n) continue;
         const float v0 = V[x][pj], v1 = V[x][qj];
         V[x][pj] = cj * v0 - sj * v1;
         V[x][qj] = sj * v0 + cj * v1;
@@ -324,77 +334,122 @@ __device__ void jacobi_eig(float (*A)[B + 1], float (*V)[B + 1], int n,
     __syncthreads();
     if (!any) break;
   }
+  return sweep;
 }
 
 template <int B>
 struct RRSmem {
+  float S[B][B + 1];      // S_n, then its Cholesky factor L (lower)
+  float Li[B][B + 1];     // L^-1 (lower)
+  float H[B][B + 1];
+  float T1[B][B + 1];
   float A[B][B + 1];
   float V[B][B + 1];
-  float T1[B][B + 1];
-  float Tm[B][B + 1];
   float d[B];
-  float lam[B];
-  float rc[B / 2 + 1], rs[B / 2 + 1];
-  int rp[B / 2 + 1], rq[B / 2 + 1];
+  float key[B];
+  int drop[B];
   int rank[B];
+  float rc[B / 2 + 1], rs[B / 2 + 1];
+  unsigned short pairs[(B - 1) * (B / 2)];
+  unsigned short tri[(B / 2) * (B / 2 + 1) / 2];
   int flag;
 };
 
 template <int B>
 __global__ void __launch_bounds__(256)
-k_rr_solve(const BlockMeta *__restrict__ meta,
-           const SolverState *__restrict__ state,
-           const float *__restrict__ SH, float *__restrict__ Tout,
+k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
+           const float *__restrict__ SHp, float *__restrict__ Tout,
            float *__restrict__ theta, int max_sweeps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RRSmem<B> &sm = *reinterpret_cast<RRSmem<B> *>(smem_raw);
   const int blk = blockIdx.x;
-  const SolverState st = state[blk];
-  if (st.status != kRunning) return;
-  const int n = st.bsub;
+  if (state[blk].status != kRunning) return;
+  const BlockMeta bm = meta[blk];
+  const int n = state[blk].bsub;
   const int tid = threadIdx.x;
-  const float *S = SH + (int64_t)blk * 2 * B * B;
-  const float *H = S + B * B;
-
-  // SVQB: normalise S to unit diagonal, eigen-decompose
+  const int ne = n + (n & 1), np = ne / 2;
+  build_pairs(ne, sm.pairs);
+  for (int e = tid; e < np * np; e += blockDim.x) {
+    const int i = e / np, j = e % np;
+    if (i <= j) sm.tri[i * np - i * (i - 1) / 2 + (j - i)] = (unsigned short)(i | (j << 8));
+  }
+  // 1. sum the row-tile partials in tile order
+  const float *part = SHp + (int64_t)bm.t0 * 2 * B * B;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    float s = 0.f, h = 0.f;
+    for (int t = 0; t < bm.nt; ++t) {
+      s += part[(int64_t)t * 2 * B * B + i * B + j];
+      h += part[(int64_t)t * 2 * B * B + B * B + i * B + j];
+    }
+    sm.S[i][j] = s;
+    sm.H[i][j] = h;
+  }
+  __syncthreads();
+  // 2. unit diagonal
   for (int i = tid; i < n; i += blockDim.x) {
-    const float sii = S[i * B + i];
-    sm.d[i] = sii > 0.f ? sqrtf(sii) : 1.f;
+    const float sii = sm.S[i][i];
+    sm.d[i] = sii > 0.f ? sqrtf(sii) : 0.f;
   }
   __syncthreads();
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
-    sm.A[i][j] = S[i * B + j] / (sm.d[i] * sm.d[j]);
+    const float di = sm.d[i], dj = sm.d[j];
+    sm.S[i][j] = (di > 0.f && dj > 0.f) ? sm.S[i][j] / (di * dj) : (i == j ? 0.f : 0.f);
   }
   __syncthreads();
-  jacobi_eig<B>(sm.A, sm.V, n, max_sweeps, sm.rc, sm.rs, sm.rp, sm.rq,
-                &sm.flag);
-  if (tid == 0) {
-    float lmax = 0.f;
-    for (int i = 0; i < n; ++i) lmax = fmaxf(lmax, sm.A[i][i]);
-    const float lfloor = fmaxf(lmax * 1e-6f, FLT_MIN);
-    for (int i = 0; i < n; ++i) sm.lam[i] = 1.f / sqrtf(fmaxf(sm.A[i][i], lfloor));
+  // 3. Cholesky S_n = L L^T, column by column; weak pivots are dropped
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const float piv = sm.S[j][j];
+      const bool drop = !(piv > kPivotDrop);
+      sm.drop[j] = drop;
+      sm.S[j][j] = drop ? 1.f : sqrtf(piv);
+    }
+    __syncthreads();
+    const float ljj = sm.S[j][j];
+    const bool dj = sm.drop[j];
+    for (int i = j + 1 + tid; i < n; i += blockDim.x)
+      sm.S[i][j] = dj ? 0.f : sm.S[i][j] / ljj;
+    __syncthreads();
+    const int m2 = n - j - 1;
+    for (int e = tid; e < m2 * m2; e += blockDim.x) {
+      const int i = j + 1 + e / m2, l = j + 1 + e % m2;
+      if (l <= i) sm.S[i][l] = fmaf(-sm.S[i][j], sm.S[l][j], sm.S[i][l]);
+    }
+    __syncthreads();
+  }
+  // 4. L^-1 by forward substitution, one column per thread
+  for (int j = tid; j < n; j += blockDim.x) {
+    for (int i = 0; i < j; ++i) sm.Li[i][j] = 0.f;
+    for (int i = j; i < n; ++i) {
+      float acc = (i == j) ? 1.f : 0.f;
+      for (int l = j; l < i; ++l) acc = fmaf(-sm.S[i][l], sm.Li[l][j], acc);
+      sm.Li[i][j] = acc / sm.S[i][i];
+    }
   }
   __syncthreads();
-  // T1 = D^-1 Q L^-1/2
+  // 5. T1 = D^-1 L^-T, dropped basis columns are zero
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
-    sm.T1[i][j] = sm.V[i][j] * sm.lam[j] / sm.d[i];
+    float v = 0.f;
+    if (!sm.drop[j] && sm.d[i] > 0.f) v = sm.Li[j][i] / sm.d[i];
+    sm.T1[i][j] = v;
   }
   __syncthreads();
-  // Tm = H T1, then A = T1^T Tm (symmetrised)
+  // 6. H' = T1^T H T1 (Li reused as scratch for H T1)
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
     float acc = 0.f;
-    for (int l = 0; l < n; ++l) acc = fmaf(H[i * B + l], sm.T1[l][j], acc);
-    sm.Tm[i][j] = acc;
+    for (int l = 0; l < n; ++l) acc = fmaf(sm.H[i][l], sm.T1[l][j], acc);
+    sm.Li[i][j] = acc;
   }
   __syncthreads();
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
     float acc = 0.f;
-    for (int l = 0; l < n; ++l) acc = fmaf(sm.T1[l][i], sm.Tm[l][j], acc);
-    sm.V[i][j] = acc;          // V is free until the next Jacobi call
+    for (int l = 0; l < n; ++l) acc = fmaf(sm.T1[l][i], sm.Li[l][j], acc);
+    sm.V[i][j] = acc;
   }
   __syncthreads();
   for (int e = tid; e < n * n; e += blockDim.x) {
@@ -402,15 +457,19 @@ k_rr_solve(const BlockMeta *__restrict__ meta,
     sm.A[i][j] = 0.5f * (sm.V[i][j] + sm.V[j][i]);
   }
   __syncthreads();
-  jacobi_eig<B>(sm.A, sm.V, n, max_sweeps, sm.rc, sm.rs, sm.rp, sm.rq,
-                &sm.flag);
-  // descending order, ties by index
+  // 7. eigen-decomposition of H'
+  const int sweeps = jacobi_eig<B>(sm.A, sm.V, n, max_sweeps, sm.pairs, sm.tri,
+                                   sm.rc, sm.rs, &sm.flag);
+  // 8. descending order (dropped directions last), T = T1 V
+  for (int i = tid; i < n; i += blockDim.x)
+    sm.key[i] = sm.drop[i] ? -INFINITY : sm.A[i][i];
+  __syncthreads();
   for (int i = tid; i < n; i += blockDim.x) {
-    const float ti = sm.A[i][i];
+    const float ki = sm.key[i];
     int r = 0;
     for (int j = 0; j < n; ++j) {
-      const float tj = sm.A[j][j];
-      r += (tj > ti) || (tj == ti && j < i);
+      const float kj = sm.key[j];
+      r += (kj > ki) || (kj == ki && j < i);
     }
     sm.rank[i] = r;
   }
@@ -418,36 +477,48 @@ k_rr_solve(const BlockMeta *__restrict__ meta,
   float *Tb = Tout + (int64_t)blk * B * B;
   for (int e = tid; e < B * B; e += blockDim.x) {
     const int i = e / B, j = e % B;
-    float acc = 0.f;
     if (i < n && j < n) {
+      float acc = 0.f;
       for (int l = 0; l < n; ++l) acc = fmaf(sm.T1[i][l], sm.V[l][j], acc);
       Tb[i * B + sm.rank[j]] = acc;
     } else {
       Tb[i * B + j] = 0.f;
     }
   }
-  for (int i = tid; i < B; i += blockDim.x)
-    if (i < n) theta[(int64_t)blk * B + sm.rank[i]] = sm.A[i][i];
+  for (int i = tid; i < B; i += blockDim.x) {
+    if (i < n) theta[(int64_t)blk * B + sm.rank[i]] = sm.drop[i] ? 0.f : sm.A[i][i];
     else theta[(int64_t)blk * B + i] = 0.f;
+  }
+  if (tid == 0) {
+    unsigned long long mask = 0ull;
+    for (int i = 0; i < n; ++i)
+      if (sm.drop[i]) mask |= 1ull << sm.rank[i];
+    state[blk].refill = mask;
+    state[blk].sweeps += sweeps;
+  }
 }
 
-// X <- X T and Z <- Z T on rows [row0, row0 + 64), in place.
+// X <- X T and Z <- Z T on one row tile, in place; refilled columns get
+// fresh random values (and Z = 0 until the next product). Writes the tile's
+// partial |Z_j - theta_j X_j|^2 and |X_j|^2 for every column j.
 template <int B>
 __global__ void __launch_bounds__(256)
 k_rotate(const BlockMeta *__restrict__ meta,
          const SolverState *__restrict__ state,
          const int2 *__restrict__ rowtiles, const float *__restrict__ T,
-         float *X, float *Z) {
+         const float *__restrict__ theta, float *X, float *Z,
+         float *__restrict__ RP, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float (*Ts)[B + 1] = reinterpret_cast<float (*)[B + 1]>(smem_raw);
   float (*Xs)[B + 1] = Ts + B;
   float (*Zs)[B + 1] = Xs + TR;
   const int2 t = rowtiles[blockIdx.x];
-  if (state[t.x].status != kRunning) return;
+  const SolverState st = state[t.x];
+  if (st.status != kRunning) return;
   const BlockMeta bm = meta[t.x];
   const int rows = min(TR, bm.s - t.y);
-  if (rows <= 0) return;
   const float *Tb = T + (int64_t)t.x * B * B;
+  const float *th = theta + (int64_t)t.x * B;
   float *Xb = X + bm.x_off + (int64_t)t.y * B;
   float *Zb = Z + bm.x_off + (int64_t)t.y * B;
   for (int e = threadIdx.x; e < B * B; e += blockDim.x)
@@ -457,8 +528,14 @@ k_rotate(const BlockMeta *__restrict__ meta,
     Zs[e / B][e % B] = Zb[e];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < rows * B; e += blockDim.x) {
-    const int r = e / B, j = e % B;
+  // column j handled by threads j, j + B, ... (256 / B row groups)
+  constexpr int G = 256 / B;
+  __shared__ float r2s[G][B], x2s[G][B];
+  const int j = threadIdx.x % B, grp = threadIdx.x / B;
+  const bool refill = (st.refill >> j) & 1ull;
+  const float tj = th[j];
+  float r2 = 0.f, x2 = 0.f;
+  for (int r = grp; r < rows; r += G) {
     float ax = 0.f, az = 0.f;
 #pragma unroll 8
     for (int l = 0; l < B; ++l) {
@@ -466,58 +543,73 @@ k_rotate(const BlockMeta *__restrict__ meta,
       ax = fmaf(Xs[r][l], tl, ax);
       az = fmaf(Zs[r][l], tl, az);
     }
-    Xb[e] = ax;
-    Zb[e] = az;
+    if (refill) {
+      ax = hash_uniform(seed ^ (0x51ED270Bull * (uint64_t)(st.iters + 1)),
+                        (uint64_t)t.x, (uint64_t)(t.y + r) * B + j);
+      az = 0.f;
+    }
+    Xb[(int64_t)r * B + j] = ax;
+    Zb[(int64_t)r * B + j] = az;
+    const float d = az - tj * ax;
+    r2 = fmaf(d, d, r2);
+    x2 = fmaf(ax, ax, x2);
+  }
+  r2s[grp][j] = r2;
+  x2s[grp][j] = x2;
+  __syncthreads();
+  if (threadIdx.x < B) {
+    float a = 0.f, b = 0.f;
+    for (int g = 0; g < G; ++g) { a += r2s[g][threadIdx.x]; b += x2s[g][threadIdx.x]; }
+    float *rp = RP + (int64_t)blockIdx.x * 2 * B;
+    rp[threadIdx.x] = a;
+    rp[B + threadIdx.x] = b;
   }
 }
 
-// Residuals, convergence, next filter interval; copies F_s when done.
+// Residuals, convergence, next filter; copies F_s when a block is done.
 template <int B>
 __global__ void __launch_bounds__(256)
 k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
-        const float *__restrict__ X, const float *__restrict__ Z,
+        const float *__restrict__ X, const float *__restrict__ RP,
         const float *__restrict__ theta, float *__restrict__ Fs, int kp,
         int max_iters, int max_degree, float tol, int32_t *running) {
-  constexpr int G = 256 / B;          // row groups
-  __shared__ float rs[G][B], xs[G][B];
+  __shared__ float r2[B], x2[B];
   __shared__ int s_done;
   const int blk = blockIdx.x;
   SolverState st = state[blk];
   if (st.status != kRunning) return;
   const BlockMeta bm = meta[blk];
   const int n = st.bsub, s = bm.s, keff = bm.keff;
-  const float *Xb = X + bm.x_off;
-  const float *Zb = Z + bm.x_off;
   const float *th = theta + (int64_t)blk * B;
-  const int col = threadIdx.x % B, grp = threadIdx.x / B;
-  float r2 = 0.f, x2 = 0.f;
-  const float tc = th[col];
-  for (int r = grp; r < s; r += G) {
-    const float xv = Xb[(int64_t)r * B + col];
-    const float d = Zb[(int64_t)r * B + col] - tc * xv;
-    r2 = fmaf(d, d, r2);
-    x2 = fmaf(xv, xv, x2);
+  if (threadIdx.x < B) {
+    float a = 0.f, b = 0.f;
+    for (int t = 0; t < bm.nt; ++t) {
+      const float *rp = RP + (int64_t)(bm.t0 + t) * 2 * B;
+      a += rp[threadIdx.x];
+      b += rp[B + threadIdx.x];
+    }
+    r2[threadIdx.x] = a;
+    x2[threadIdx.x] = b;
   }
-  rs[grp][col] = r2;
-  xs[grp][col] = x2;
   __syncthreads();
   if (threadIdx.x == 0) {
     const float t1 = th[0];
     float worst = 0.f;
-    for (int j = 0; j < keff && j < n; ++j) {
-      float a = 0.f;
-      for (int g = 0; g < G; ++g) a += rs[g][j];
-      worst = fmaxf(worst, sqrtf(a));
-    }
+    for (int j = 0; j < keff && j < n; ++j) worst = fmaxf(worst, sqrtf(r2[j]));
+    const unsigned long long wanted =
+        keff >= 64 ? ~0ull : ((1ull << keff) - 1ull);
     st.iters += 1;
     st.theta1 = t1;
     st.resid = t1 > 0.f ? worst / t1 : 0.f;
-    const bool conv = (s <= B) || !(t1 > 1e-30f) || (worst <= tol * t1);
+    const bool refilled_wanted = (st.refill & wanted) != 0ull;
+    const bool conv = !refilled_wanted &&
+                      ((s <= B) || !(t1 > 1e-30f) || (worst <= tol * t1));
     if (conv || st.iters >= max_iters) {
       st.status = conv ? kConverged : kCapped;
       s_done = 1;
     } else {
-      float cut = th[n - 1];
+      const int ndrop = __popcll(st.refill);
+      float cut = th[max(0, n - 1 - ndrop)];
       cut = fmaxf(cut, kCutFloor * t1);
       if (cut >= 0.5f * t1) cut = 0.5f * t1;
       st.cut = cut;
@@ -535,30 +627,34 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   }
   __syncthreads();
   if (!s_done) return;
-  // F_s = normalised first keff Ritz vectors
+  const float *Xb = X + bm.x_off;
   for (int e = threadIdx.x; e < s * kp; e += blockDim.x) {
     const int r = e / kp, j = e % kp;
     float v = 0.f;
     if (j < keff && j < n) {
-      float nn = 0.f;
-      for (int g = 0; g < G; ++g) nn += xs[g][j];
+      const float nn = x2[j];
       v = nn > 0.f ? Xb[(int64_t)r * B + j] / sqrtf(nn) : 0.f;
     }
     Fs[bm.fs_off + (int64_t)r * kp + j] = v;
   }
 }
 
-// F_L[l, :] = sum_a W[a, l] F_s[a, :] for 128 consecutive l.
+// F_L[l, :] = sum_a W[a, l] F_s[a, :] for kProjCols = 32 consecutive l
+// (one per lane). Warp w takes the
+// rows a = w, w + 8, ...; lane = l; the 8 partial sums are added in order.
 template <int KM>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
           const float *__restrict__ W, const float *__restrict__ Fs,
           float *__restrict__ FL, int kp) {
-  constexpr int CH = 32;
+  constexpr int CH = 64;
   __shared__ float Fsh[CH][KM];
+  __shared__ float red[8][32][17];
   const int2 t = ltiles[blockIdx.x];
   const BlockMeta bm = meta[t.x];
-  const int l = t.y + threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = t.y + lane;
+  const bool lv = l < bm.L;
   const float *Wb = W + bm.w_off;
   const float *Fb = Fs + bm.fs_off;
   float acc[KM];
@@ -571,8 +667,8 @@ k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
     }
     __syncthreads();
     const int lim = min(CH, bm.s - a0);
-    if (l < bm.L) {
-      for (int rr = 0; rr < lim; ++rr) {
+    if (lv) {
+      for (int rr = warp; rr < lim; rr += 8) {
         const float w = Wb[(int64_t)(a0 + rr) * bm.L_pad + l];
 #pragma unroll
         for (int j = 0; j < KM; ++j) acc[j] = fmaf(w, Fsh[rr][j], acc[j]);
@@ -580,57 +676,90 @@ k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
     }
     __syncthreads();
   }
-  if (l < bm.L) {
-    float *out = FL + bm.fl_off + (int64_t)l * kp;
+  // add the 8 warps' partial sums in warp order, 16 columns at a time
 #pragma unroll
-    for (int j = 0; j < KM; ++j)
-      if (j < kp) out[j] = acc[j];
+  for (int jc = 0; jc < KM; jc += 16) {
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj)
+      if (jc + jj < KM) red[warp][lane][jj] = acc[jc + jj];
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * 16; e += blockDim.x) {
+      const int ln = e >> 4, jj = e & 15, j = jc + jj;
+      const int ll = t.y + ln;
+      if (ll < bm.L && j < kp && j < KM) {
+        float s = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += red[w][ln][jj];
+        FL[bm.fl_off + (int64_t)ll * kp + j] = s;
+      }
+    }
+    __syncthreads();
   }
 }
 
-// sigma_j = |F_L[:, j]| in float64; flip (F_s_j, F_L_j) so the item-side
-// vector's largest-|.| entry (lowest index on ties) is positive.
+// sigma_j = |F_L[:, j]| (float64 sums); then flip (F_s_j, F_L_j) so the
+// item-side vector's largest-|.| entry (lowest index on ties) is positive.
 __global__ void __launch_bounds__(256)
 k_finalize(const BlockMeta *__restrict__ meta, float *Fs, float *FL,
-           double *sigma, int kp, int k) {
+           double *sigma, int kp) {
+  __shared__ double sq[8][64];
+  __shared__ float bv[8][64];
+  __shared__ int bi[8][64];
+  __shared__ int flip[64];
   const int blk = blockIdx.x;
   const BlockMeta bm = meta[blk];
+  const int keff = bm.keff;
+  if (keff == 0) {
+    for (int j = threadIdx.x; j < kp; j += blockDim.x) sigma[(int64_t)blk * kp + j] = 0.0;
+    return;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float *Fsb = Fs + bm.fs_off;
   float *FLb = FL + bm.fl_off;
-  for (int j = warp; j < kp; j += 8) {
-    if (j >= bm.keff) {
-      if (lane == 0) sigma[(int64_t)blk * kp + j] = 0.0;
-      continue;
-    }
+  const float *vec = bm.trans ? Fsb : FLb;     // item-side vectors
+  const int len = bm.trans ? bm.s : bm.L;
+  // lane -> column j (two passes of 32 when kp > 32); warp -> rows
+  for (int jb = 0; jb < kp; jb += 32) {
+    const int j = jb + lane;
     double acc = 0.0;
-    for (int l = lane; l < bm.L; l += 32) {
-      const double v = FLb[(int64_t)l * kp + j];
-      acc = fma(v, v, acc);
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    // item-side vector: F_s when trans (s indexes items), else F_L
-    const float *vec = bm.trans ? Fsb : FLb;
-    const int len = bm.trans ? bm.s : bm.L;
     float best = -1.f;
     int bidx = 0x7fffffff;
-    for (int a = lane; a < len; a += 32) {
-      const float v = fabsf(vec[(int64_t)a * kp + j]);
-      if (v > best) { best = v; bidx = a; }
+    if (j < keff) {
+      for (int l = warp; l < bm.L; l += 8) {
+        const double v = FLb[(int64_t)l * kp + j];
+        acc = fma(v, v, acc);
+      }
+      for (int a = warp; a < len; a += 8) {
+        const float v = fabsf(vec[(int64_t)a * kp + j]);
+        if (v > best) { best = v; bidx = a; }
+      }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-      if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    sq[warp][lane] = acc;
+    bv[warp][lane] = best;
+    bi[warp][lane] = bidx;
+    __syncthreads();
+    if (warp == 0 && j < keff) {
+      double s = 0.0;
+      float b = -1.f;
+      int ix = 0x7fffffff;
+      for (int w = 0; w < 8; ++w) {
+        s += sq[w][lane];
+        const float ob = bv[w][lane];
+        const int oi = bi[w][lane];
+        if (ob > b || (ob == b && oi < ix)) { b = ob; ix = oi; }
+      }
+      sigma[(int64_t)blk * kp + j] = sqrt(s);
+      flip[j] = (ix < len && vec[(int64_t)ix * kp + j] < 0.f) ? 1 : 0;
+    } else if (warp == 0 && j < kp) {
+      sigma[(int64_t)blk * kp + j] = 0.0;
+      flip[j] = 0;
     }
-    const bool flip = bidx < len && vec[(int64_t)bidx * kp + j] < 0.f;
-    __syncwarp();
-    if (flip) {
-      for (int a = lane; a < bm.s; a += 32) Fsb[(int64_t)a * kp + j] *= -1.f;
-      for (int l = lane; l < bm.L; l += 32) FLb[(int64_t)l * kp + j] *= -1.f;
-    }
-    if (lane == 0) sigma[(int64_t)blk * kp + j] = sqrt(acc);
+    __syncthreads();
   }
+  for (int e = threadIdx.x; e < bm.s * kp; e += blockDim.x)
+    if (flip[e % kp] && e % kp < keff) Fsb[e] = -Fsb[e];
+  for (int e = threadIdx.x; e < bm.L * kp; e += blockDim.x)
+    if (flip[e % kp] && e % kp < keff) FLb[e] = -FLb[e];
 }
 
 template <int B>
@@ -645,10 +774,9 @@ cudaError_t set_attrs() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)rr_smem<B>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_rotate<B>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)rot_smem<B>());
-  return e;
+  return cudaFuncSetAttribute(k_rotate<B>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)rot_smem<B>());
 }
 
 template <typename F>
@@ -688,11 +816,13 @@ cudaError_t launch_gpanel(const EigBuffers &e, const int2 *rowtiles,
   });
 }
 
-cudaError_t launch_small_gram(const EigBuffers &e, cudaStream_t st) {
+cudaError_t launch_small_gram(const EigBuffers &e, const int2 *rowtiles,
+                              int32_t ntiles, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
   return by_width(e.bsub, [&](auto w) {
     constexpr int B = decltype(w)::value;
-    k_small_gram<B><<<e.nblocks, 256, 0, st>>>(e.meta, e.state, e.X, e.Z,
-                                               e.SH);
+    k_small_gram<B><<<ntiles, 256, 0, st>>>(e.meta, e.state, rowtiles, e.X,
+                                            e.Z, e.SH);
     return cudaGetLastError();
   });
 }
@@ -715,8 +845,8 @@ cudaError_t launch_rotate(const EigBuffers &e, const int2 *rowtiles,
     constexpr int B = decltype(w)::value;
     cudaError_t err = set_attrs<B>();
     if (err != cudaSuccess) return err;
-    k_rotate<B><<<ntiles, 256, rot_smem<B>(), st>>>(e.meta, e.state,
-                                                    rowtiles, e.T, e.X, e.Z);
+    k_rotate<B><<<ntiles, 256, rot_smem<B>(), st>>>(
+        e.meta, e.state, rowtiles, e.T, e.theta, e.X, e.Z, e.RP, e.seed);
     return cudaGetLastError();
   });
 }
@@ -724,7 +854,7 @@ cudaError_t launch_rotate(const EigBuffers &e, const int2 *rowtiles,
 cudaError_t launch_check(const EigBuffers &e, cudaStream_t st) {
   return by_width(e.bsub, [&](auto w) {
     constexpr int B = decltype(w)::value;
-    k_check<B><<<e.nblocks, 256, 0, st>>>(e.meta, e.state, e.X, e.Z,
+    k_check<B><<<e.nblocks, 256, 0, st>>>(e.meta, e.state, e.X, e.RP,
                                           e.theta, e.Fs, e.kp, e.max_iters,
                                           e.max_degree, e.tol, e.running);
     return cudaGetLastError();
@@ -735,17 +865,18 @@ cudaError_t launch_project(const BlockMeta *meta, const int2 *ltiles,
                            int32_t ntiles, const float *W, const float *Fs,
                            float *FL, int32_t kp, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
-  if (kp <= 16) k_project<16><<<ntiles, 128, 0, st>>>(meta, ltiles, W, Fs, FL, kp);
-  else if (kp <= 32) k_project<32><<<ntiles, 128, 0, st>>>(meta, ltiles, W, Fs, FL, kp);
-  else k_project<56><<<ntiles, 128, 0, st>>>(meta, ltiles, W, Fs, FL, kp);
+  if (kp <= 16) k_project<16><<<ntiles, 256, 0, st>>>(meta, ltiles, W, Fs, FL, kp);
+  else if (kp <= 32) k_project<32><<<ntiles, 256, 0, st>>>(meta, ltiles, W, Fs, FL, kp);
+  else k_project<56><<<ntiles, 256, 0, st>>>(meta, ltiles, W, Fs, FL, kp);
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const BlockMeta *meta, int32_t nblocks,
                             float *Fs, float *FL, double *sigma, int32_t kp,
                             int32_t k, cudaStream_t st) {
+  (void)k;
   if (nblocks <= 0) return cudaSuccess;
-  k_finalize<<<nblocks, 256, 0, st>>>(meta, Fs, FL, sigma, kp, k);
+  k_finalize<<<nblocks, 256, 0, st>>>(meta, Fs, FL, sigma, kp);
   return cudaGetLastError();
 }
 
