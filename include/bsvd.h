@@ -202,10 +202,14 @@ bsvd_status bsvd_reconstruct(bsvd_ctx *ctx, int32_t b, int32_t add_mean,
 
 /*
  * Per-block solver report after bsvd_factor (host arrays of p*q entries,
- * any may be NULL): iterations used and 1 where the block converged.
+ * any may be NULL): Rayleigh-Ritz steps used, 1 where the block converged,
+ * Jacobi sweeps summed over the steps, and SM clock cycles spent in the
+ * Rayleigh-Ritz kernel (3 per block: partial sums + Cholesky QR + H',
+ * Jacobi, ordering + output), summed over the steps.
  */
 bsvd_status bsvd_factor_report(bsvd_ctx *ctx, int32_t *iters,
-                               int32_t *converged);
+                               int32_t *converged, int32_t *sweeps,
+                               int64_t *cycles);
 
 /*
  * Phase timings of the last call, in milliseconds of device time between

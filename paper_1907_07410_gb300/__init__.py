@@ -79,7 +79,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                  ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
                                  vp, vp, vp, vp]),
         "bsvd_reconstruct": (i32, [vp, i32, i32, vp]),
-        "bsvd_factor_report": (i32, [vp, vp, vp]),
+        "bsvd_factor_report": (i32, [vp, vp, vp, vp, vp]),
         "bsvd_phase_times": (i32, [vp, vp]),
         "bsvd_kernel_launches": (i64, [vp]),
     }
@@ -249,11 +249,16 @@ def bsvd_reconstruct(ctx, b, out, add_mean=True) -> int:
     return _check(ctx, st)
 
 
-def bsvd_factor_report(ctx, nblocks: int):
+def bsvd_factor_report(ctx, nblocks: int, full: bool = False):
     iters = np.zeros(nblocks, np.int32)
     conv = np.zeros(nblocks, np.int32)
-    st = load().bsvd_factor_report(ctx, iters.ctypes.data, conv.ctypes.data)
+    sweeps = np.zeros(nblocks, np.int32)
+    cycles = np.zeros((nblocks, 3), np.int64)
+    st = load().bsvd_factor_report(ctx, iters.ctypes.data, conv.ctypes.data,
+                                   sweeps.ctypes.data, cycles.ctypes.data)
     _check(ctx, st)
+    if full:
+        return dict(iters=iters, converged=conv, sweeps=sweeps, cycles=cycles)
     return iters, conv
 
 
@@ -352,8 +357,8 @@ class Context:
         bsvd_reconstruct(self.handle, b, out, add_mean)
         return out
 
-    def factor_report(self):
-        return bsvd_factor_report(self.handle, self.nblocks)
+    def factor_report(self, full=False):
+        return bsvd_factor_report(self.handle, self.nblocks, full)
 
     def phase_times(self) -> dict:
         return dict(zip(PHASES, bsvd_phase_times(self.handle).tolist()))

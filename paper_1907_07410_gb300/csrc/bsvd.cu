@@ -461,7 +461,7 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
   CK(c->d_Fs.ensure(sizeof(float) * std::max<int64_t>(fsoff, 1)), "factor");
   CK(c->d_FL.ensure(sizeof(float) * std::max<int64_t>(floff, 1)), "factor");
   CK(c->d_sigma.ensure(sizeof(double) * kp * (int64_t)nb), "factor");
-  CK(c->d_running.ensure(sizeof(int32_t)), "factor");
+  CK(c->d_running.ensure(2 * sizeof(int32_t)), "factor");
   CK(c->d_gtiles.ensure(sizeof(int4) * std::max<size_t>(gt.size(), 1)), "factor");
   CK(c->d_rowtiles.ensure(sizeof(int2) * std::max<size_t>(rt.size(), 1)), "factor");
   CK(c->d_ltiles.ensure(sizeof(int2) * std::max<size_t>(lt.size(), 1)), "factor");
@@ -513,19 +513,19 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
     CK(launch_init_panels(e, rtd, nrt, c->st), "factor: init");
     CK(launch_gpanel(e, rtd, nrt, 0, 0, 0, e.X, nullptr, e.Z, c->st), "factor: G X");
     c->launches += (c->n_gtiles > 0) + 2 * (nrt > 0);
-    const int deg = c->cfg.cheb_degree;
     for (int it = 0; it <= c->cfg.max_iters + 1; ++it) {
       CK(launch_small_gram(e, rtd, nrt, c->st), "factor: rr gram");
       CK(launch_rr_solve(e, c->st), "factor: rr solve");
       CK(launch_rotate(e, rtd, nrt, c->st), "factor: rotate");
-      CK(cudaMemsetAsync(e.running, 0, sizeof(int32_t), c->st), "factor");
+      CK(cudaMemsetAsync(e.running, 0, 2 * sizeof(int32_t), c->st), "factor");
       CK(launch_check(e, c->st), "factor: check");
       c->launches += 2 + 2 * (nrt > 0);
-      int32_t running = 0;
-      CK(cudaMemcpyAsync(&running, e.running, sizeof running,
+      int32_t run_deg[2] = {0, 0};
+      CK(cudaMemcpyAsync(run_deg, e.running, sizeof run_deg,
                          cudaMemcpyDeviceToHost, c->st), "factor");
       CK(cudaStreamSynchronize(c->st), "factor");
-      if (running == 0) break;
+      if (run_deg[0] == 0) break;
+      const int deg = std::min(c->cfg.cheb_degree, std::max(2, run_deg[1]));
       // Chebyshev filter of even degree: Y_1 -> Z, Y_2 -> X, ..., Y_d -> X
       // step j reads Y_{j-1}, Y_{j-2} and overwrites Y_{j-2} with Y_j
       for (int j = 1; j <= deg; ++j) {
@@ -756,7 +756,8 @@ bsvd_status bsvd_reconstruct(bsvd_ctx *c, int32_t b, int32_t add_mean,
 }
 
 bsvd_status bsvd_factor_report(bsvd_ctx *c, int32_t *iters,
-                               int32_t *converged) {
+                               int32_t *converged, int32_t *sweeps,
+                               int64_t *cycles) {
   if (!c) return BSVD_EINVAL;
   c->err.clear();
   if (!c->factored) return fail(c, BSVD_ESTATE, "factor_report: no factors");
@@ -767,6 +768,9 @@ bsvd_status bsvd_factor_report(bsvd_ctx *c, int32_t *iters,
   for (int32_t b = 0; b < c->nblocks; ++b) {
     if (iters) iters[b] = s[b].iters;
     if (converged) converged[b] = s[b].status == kConverged ? 1 : 0;
+    if (sweeps) sweeps[b] = s[b].sweeps;
+    if (cycles)
+      for (int j = 0; j < 3; ++j) cycles[3 * b + j] = s[b].cycles[j];
   }
   return BSVD_OK;
 }

@@ -49,6 +49,8 @@ struct SolverState {
   uint64_t refill;      // Ritz columns refilled with random vectors
   int32_t sweeps;       // Jacobi sweeps used so far
   int32_t pad;
+  int64_t cycles[3];    // SM clock cycles in the Rayleigh-Ritz kernel:
+                        // [0] sums + Cholesky QR + H', [1] Jacobi, [2] rest
 };
 
 enum : int32_t { kRunning = 0, kConverged = 1, kCapped = 2 };

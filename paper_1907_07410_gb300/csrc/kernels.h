@@ -40,7 +40,7 @@ struct EigBuffers {
   float *T;          // per block: bsub^2 transform
   float *theta;      // per block: bsub Ritz values, descending
   float *Fs;         // s_pad x kp per block
-  int32_t *running;  // count of blocks still iterating (device scalar)
+  int32_t *running;  // [0] blocks still iterating, [1] their largest degree
   int32_t bsub, kp, k;
   int32_t nblocks;
   int32_t max_iters, max_sweeps;

@@ -242,91 +242,73 @@ __device__ __forceinline__ void build_pairs(int ne, unsigned short *tab) {
   }
 }
 
-// Cyclic Jacobi for a symmetric n x n matrix A (n <= B) in shared memory.
-// On return A is diagonal to the tolerance and A_in = V diag(A) V^T. A pair
-// (p, q) is rotated when |a_pq| > max(tol sqrt|a_pp a_qq|, 1e-9 max|a_ii|).
+// One-sided (Hestenes) Jacobi on a symmetric positive semi-definite n x n
+// matrix held by columns: Ac[j][0..n) is column j of A, Vc[j] column j of V
+// (V = I on entry). Column pairs are rotated until every pair is
+// numerically orthogonal, |a_p.a_q| <= tol |a_p| |a_q|. Then A V = U S with
+// orthonormal U, and for a PSD A the columns of V are its eigenvectors and
+// the column norms |A v_j| its eigenvalues.
+// Round-robin ordering gives np disjoint pairs per round. Warp w takes the
+// pairs w, w + nwarps, ... (one pair per warp when the block has np warps);
+// lane l holds rows l and l + 32 of the two columns. The three dot products
+// are xor-butterfly warp sums: each step adds the same two operands in
+// every lane, so all lanes hold bitwise equal sums and apply the same
+// rotation. One block-wide barrier per round.
 template <int B>
-__device__ int jacobi_eig(float (*A)[B + 1], float (*V)[B + 1], int n,
-                          int max_sweeps, const unsigned short *pairs,
-                          const unsigned short *tri, float *rc, float *rs,
-                          int *flag) {
-  const int tid = threadIdx.x;
-  const int ne = n + (n & 1);
-  const int np = ne / 2;
-  const int ntri = np * (np + 1) / 2;
-  for (int e = tid; e < n * n; e += blockDim.x)
-    V[e / n][e % n] = (e / n == e % n) ? 1.f : 0.f;
-  float dmax = 0.f;
-  for (int i = 0; i < n; ++i) dmax = fmaxf(dmax, fabsf(A[i][i]));
-  const float floor_abs = dmax * 1e-9f;
+__device__ int onesided_jacobi(float (*Ac)[B + 1], float (*Vc)[B + 1], int n,
+                               int max_sweeps, const unsigned short *pairs,
+                               int *flag) {
+  constexpr int RPL = (B + 31) / 32;        // rows per lane
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int ne = n + (n & 1), np = ne / 2;
   const float tol = 3e-7f;
   int sweep = 0;
-  __syncthreads();
   for (; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) *flag = 0;
+    if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
     for (int round = 0; round < ne - 1; ++round) {
       const unsigned short *pr = pairs + round * np;
-      if (tid < np) {
-        const int p = pr[tid] & 255, q = pr[tid] >> 8;
-        float c = 1.f, s = 0.f;
-        if (p < n && q < n) {
-          const float app = A[p][p], aqq = A[q][q], apq = A[p][q];
-          const float thr = fmaxf(tol * sqrtf(fabsf(app) * fabsf(aqq)), floor_abs);
-          if (fabsf(apq) > thr) {
-            const float theta = (aqq - app) / (2.f * apq);
-            const float t = copysignf(1.f, theta) /
-                            (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
-            c = 1.f / sqrtf(fmaf(t, t, 1.f));
-            s = t * c;
-            *flag = 1;
+      for (int i = warp; i < np; i += nwarps) {
+        const int p = pr[i] & 255, q = pr[i] >> 8;
+        if (p >= n || q >= n) continue;
+        float a[RPL], b[RPL];
+        float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+        for (int h = 0; h < RPL; ++h) {
+          const int r = lane + 32 * h;
+          a[h] = r < n ? Ac[p][r] : 0.f;
+          b[h] = r < n ? Ac[q][r] : 0.f;
+          al = fmaf(a[h], a[h], al);
+          be = fmaf(b[h], b[h], be);
+          ga = fmaf(a[h], b[h], ga);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (!(ga * ga > (tol * tol) * (al * be))) continue;
+        const float zeta = (be - al) * __frcp_rn(2.f * ga);
+        const float t = copysignf(__frcp_rn(fabsf(zeta) +
+                                            __fsqrt_rn(fmaf(zeta, zeta, 1.f))),
+                                  zeta);
+        const float c = __frsqrt_rn(fmaf(t, t, 1.f));
+        const float s = t * c;
+        if (s == 0.f) continue;
+        if (lane == 0) *flag = 1;
+#pragma unroll
+        for (int h = 0; h < RPL; ++h) {
+          const int r = lane + 32 * h;
+          if (r < n) {
+            Ac[p][r] = c * a[h] - s * b[h];
+            Ac[q][r] = s * a[h] + c * b[h];
+            const float va = Vc[p][r], vb = Vc[q][r];
+            Vc[p][r] = c * va - s * vb;
+            Vc[q][r] = s * va + c * vb;
           }
         }
-        rc[tid] = c;
-        rs[tid] = s;
-      }
-      __syncthreads();
-      // A <- J^T A J on the 2 x 2 sub-blocks (pair i, pair j), i <= j; the
-      // (j, i) sub-block is written as the transpose so A stays symmetric.
-      for (int e = tid; e < ntri; e += blockDim.x) {
-        const int i = tri[e] & 255, j = tri[e] >> 8;
-        const float si = rs[i], sj = rs[j];
-        if (si == 0.f && sj == 0.f) continue;
-        const float ci = rc[i], cj = rc[j];
-        const int pi = pr[i] & 255, qi = pr[i] >> 8;
-        const int pj = pr[j] & 255, qj = pr[j] >> 8;
-        const bool vpi = pi < n, vqi = qi < n, vpj = pj < n, vqj = qj < n;
-        const float x00 = (vpi && vpj) ? A[pi][pj] : 0.f;
-        const float x01 = (vpi && vqj) ? A[pi][qj] : 0.f;
-        const float x10 = (vqi && vpj) ? A[qi][pj] : 0.f;
-        const float x11 = (vqi && vqj) ? A[qi][qj] : 0.f;
-        const float y00 = ci * x00 - si * x10, y01 = ci * x01 - si * x11;
-        const float y10 = si * x00 + ci * x10, y11 = si * x01 + ci * x11;
-        float z00 = cj * y00 - sj * y01, z01 = sj * y00 + cj * y01;
-        float z10 = cj * y10 - sj * y11, z11 = sj * y10 + cj * y11;
-        if (i == j) { z01 = 0.f; z10 = 0.f; }
-        if (vpi && vpj) A[pi][pj] = z00;
-        if (vpi && vqj) A[pi][qj] = z01;
-        if (vqi && vpj) A[qi][pj] = z10;
-        if (vqi && vqj) A[qi][qj] = z11;
-        if (i != j) {
-          if (vpi && vpj) A[pj][pi] = z00;
-          if (vpi && vqj) A[qj][pi] = z01;
-          if (vqi && vpj) A[pj][qi] = z10;
-          if (vqi && vqj) A[qj][qi] = z11;
-        }
-      }
-      // V <- V J
-      for (int e = tid; e < n * np; e += blockDim.x) {
-        const int j = e % np, x = e / np;
-        const float sj = rs[j];
-        if (sj == 0.f) continue;
-        const float cj = rc[j];
-        const int pj = pr[j] & 255, qj = pr[j] >> 8;
-        if (qj >= n || pj >= n) continue;
-        const float v0 = V[x][pj], v1 = V[x][qj];
-        V[x][pj] = cj * v0 - sj * v1;
-        V[x][qj] = sj * v0 + cj * v1;
       }
       __syncthreads();
     }
@@ -349,14 +331,12 @@ struct RRSmem {
   float key[B];
   int drop[B];
   int rank[B];
-  float rc[B / 2 + 1], rs[B / 2 + 1];
   unsigned short pairs[(B - 1) * (B / 2)];
-  unsigned short tri[(B / 2) * (B / 2 + 1) / 2];
   int flag;
 };
 
 template <int B>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024, 1)
 k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
            const float *__restrict__ SHp, float *__restrict__ Tout,
            float *__restrict__ theta, int max_sweeps) {
@@ -368,11 +348,8 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   const int n = state[blk].bsub;
   const int tid = threadIdx.x;
   const int ne = n + (n & 1), np = ne / 2;
+  const long long c0 = clock64();
   build_pairs(ne, sm.pairs);
-  for (int e = tid; e < np * np; e += blockDim.x) {
-    const int i = e / np, j = e % np;
-    if (i <= j) sm.tri[i * np - i * (i - 1) / 2 + (j - i)] = (unsigned short)(i | (j << 8));
-  }
   // 1. sum the row-tile partials in tile order
   const float *part = SHp + (int64_t)bm.t0 * 2 * B * B;
   for (int e = tid; e < n * n; e += blockDim.x) {
@@ -398,34 +375,35 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
     sm.S[i][j] = (di > 0.f && dj > 0.f) ? sm.S[i][j] / (di * dj) : (i == j ? 0.f : 0.f);
   }
   __syncthreads();
-  // 3. Cholesky S_n = L L^T, column by column; weak pivots are dropped
+  // 3. Cholesky S_n = L L^T, left-looking: column j from columns < j, one
+  // barrier per column. Every thread recomputes the pivot (same operands,
+  // same order), row i's thread writes L[i][j]. Weak pivots are dropped:
+  // the column is treated as zero below its unit diagonal.
   for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      const float piv = sm.S[j][j];
-      const bool drop = !(piv > kPivotDrop);
-      sm.drop[j] = drop;
-      sm.S[j][j] = drop ? 1.f : sqrtf(piv);
+    float piv = sm.S[j][j];
+    for (int l = 0; l < j; ++l) piv = fmaf(-sm.S[j][l], sm.S[j][l], piv);
+    const bool drop = !(piv > kPivotDrop);
+    const float ljj = drop ? 1.f : __fsqrt_rn(piv);
+    const float inv = __frcp_rn(ljj);
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) {
+      float v = sm.S[i][j];
+      for (int l = 0; l < j; ++l) v = fmaf(-sm.S[i][l], sm.S[j][l], v);
+      sm.S[i][j] = drop ? 0.f : v * inv;
     }
-    __syncthreads();
-    const float ljj = sm.S[j][j];
-    const bool dj = sm.drop[j];
-    for (int i = j + 1 + tid; i < n; i += blockDim.x)
-      sm.S[i][j] = dj ? 0.f : sm.S[i][j] / ljj;
-    __syncthreads();
-    const int m2 = n - j - 1;
-    for (int e = tid; e < m2 * m2; e += blockDim.x) {
-      const int i = j + 1 + e / m2, l = j + 1 + e % m2;
-      if (l <= i) sm.S[i][l] = fmaf(-sm.S[i][j], sm.S[l][j], sm.S[i][l]);
+    if (tid == 0) {
+      sm.drop[j] = drop;
+      sm.key[j] = ljj;          // L's diagonal; S[j][j] stays readable
     }
     __syncthreads();
   }
-  // 4. L^-1 by forward substitution, one column per thread
+  // 4. L^-1 by forward substitution, one column per thread (the strict
+  // lower triangle of S holds L, key[] its diagonal)
   for (int j = tid; j < n; j += blockDim.x) {
     for (int i = 0; i < j; ++i) sm.Li[i][j] = 0.f;
     for (int i = j; i < n; ++i) {
       float acc = (i == j) ? 1.f : 0.f;
       for (int l = j; l < i; ++l) acc = fmaf(-sm.S[i][l], sm.Li[l][j], acc);
-      sm.Li[i][j] = acc / sm.S[i][i];
+      sm.Li[i][j] = acc / sm.key[i];
     }
   }
   __syncthreads();
@@ -437,7 +415,8 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
     sm.T1[i][j] = v;
   }
   __syncthreads();
-  // 6. H' = T1^T H T1 (Li reused as scratch for H T1)
+  // 6. H' = T1^T H T1 (Li reused as scratch for H T1); A holds H' by
+  // columns (A[j][i] = H'_ij, symmetrised), V = I
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
     float acc = 0.f;
@@ -454,15 +433,24 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   __syncthreads();
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
-    sm.A[i][j] = 0.5f * (sm.V[i][j] + sm.V[j][i]);
+    sm.A[j][i] = 0.5f * (sm.V[i][j] + sm.V[j][i]);
   }
   __syncthreads();
-  // 7. eigen-decomposition of H'
-  const int sweeps = jacobi_eig<B>(sm.A, sm.V, n, max_sweeps, sm.pairs, sm.tri,
-                                   sm.rc, sm.rs, &sm.flag);
-  // 8. descending order (dropped directions last), T = T1 V
-  for (int i = tid; i < n; i += blockDim.x)
-    sm.key[i] = sm.drop[i] ? -INFINITY : sm.A[i][i];
+  for (int e = tid; e < n * n; e += blockDim.x)
+    sm.V[e / n][e % n] = (e / n == e % n) ? 1.f : 0.f;
+  __syncthreads();
+  // 7. eigen-decomposition of H' (V by columns: V[j] is eigenvector j)
+  const long long c1 = clock64();
+  const int sweeps = onesided_jacobi<B>(sm.A, sm.V, n, max_sweeps, sm.pairs,
+                                        &sm.flag);
+  const long long c2 = clock64();
+  // 8. eigenvalues = column norms; descending order, dropped directions last
+  for (int j = tid; j < n; j += blockDim.x) {
+    float nn = 0.f;
+    for (int r = 0; r < n; ++r) nn = fmaf(sm.A[j][r], sm.A[j][r], nn);
+    sm.d[j] = sqrtf(nn);                  // d is free after step 5
+    sm.key[j] = sm.drop[j] ? -INFINITY : sm.d[j];
+  }
   __syncthreads();
   for (int i = tid; i < n; i += blockDim.x) {
     const float ki = sm.key[i];
@@ -479,14 +467,14 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
     const int i = e / B, j = e % B;
     if (i < n && j < n) {
       float acc = 0.f;
-      for (int l = 0; l < n; ++l) acc = fmaf(sm.T1[i][l], sm.V[l][j], acc);
+      for (int l = 0; l < n; ++l) acc = fmaf(sm.T1[i][l], sm.V[j][l], acc);
       Tb[i * B + sm.rank[j]] = acc;
     } else {
       Tb[i * B + j] = 0.f;
     }
   }
   for (int i = tid; i < B; i += blockDim.x) {
-    if (i < n) theta[(int64_t)blk * B + sm.rank[i]] = sm.drop[i] ? 0.f : sm.A[i][i];
+    if (i < n) theta[(int64_t)blk * B + sm.rank[i]] = sm.drop[i] ? 0.f : sm.d[i];
     else theta[(int64_t)blk * B + i] = 0.f;
   }
   if (tid == 0) {
@@ -495,6 +483,9 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
       if (sm.drop[i]) mask |= 1ull << sm.rank[i];
     state[blk].refill = mask;
     state[blk].sweeps += sweeps;
+    state[blk].cycles[0] += c1 - c0;
+    state[blk].cycles[1] += c2 - c1;
+    state[blk].cycles[2] += clock64() - c2;
   }
 }
 
@@ -621,6 +612,7 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
         d += 2;
       st.degree = d;
       atomicAdd(running, 1);
+      atomicMax(running + 1, d);
       s_done = 0;
     }
     state[blk] = st;
@@ -832,7 +824,8 @@ cudaError_t launch_rr_solve(const EigBuffers &e, cudaStream_t st) {
     constexpr int B = decltype(w)::value;
     cudaError_t err = set_attrs<B>();
     if (err != cudaSuccess) return err;
-    k_rr_solve<B><<<e.nblocks, 256, rr_smem<B>(), st>>>(
+    constexpr int threads = (B / 2) * 32 > 256 ? (B / 2) * 32 : 256;
+    k_rr_solve<B><<<e.nblocks, threads, rr_smem<B>(), st>>>(
         e.meta, e.state, e.SH, e.T, e.theta, e.max_sweeps);
     return cudaGetLastError();
   });
