@@ -132,25 +132,44 @@ k_gpanel(const BlockMeta *__restrict__ meta,
 #pragma unroll
     for (int c = 0; c < CN; ++c) acc[r][c] = 0.f;
 
-  for (int k0 = 0; k0 < sp; k0 += KC) {
+  // The next k-chunk is fetched into registers while the current one is
+  // multiplied from shared memory, so global (L2) latency overlaps compute.
+  constexpr int BV = (KC * B / 4 + 255) / 256;     // float4 of `in` per thread
+  float4 ga[2], gb[BV];
+  auto fetch = [&](int k0) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int idx = tid + 256 * h;
       const int rr = idx >> 4, cc = (idx & 15) * 4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (k0 + rr < sp && row0 + cc < sp)
-        v = __ldg(reinterpret_cast<const float4 *>(
-            Gb + (int64_t)(k0 + rr) * sp + row0 + cc));
-      *reinterpret_cast<float4 *>(&As[rr][cc]) = v;
+      ga[h] = (row0 + cc < sp)
+                  ? __ldg(reinterpret_cast<const float4 *>(
+                        Gb + (int64_t)(k0 + rr) * sp + row0 + cc))
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int idx = tid; idx < KC * B / 4; idx += 256) {
+#pragma unroll
+    for (int h = 0; h < BV; ++h) {
+      const int idx = tid + 256 * h;
       const int rr = idx / (B / 4), cc = (idx % (B / 4)) * 4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (k0 + rr < sp)
-        v = *reinterpret_cast<const float4 *>(inb + (int64_t)(k0 + rr) * B + cc);
-      *reinterpret_cast<float4 *>(&Bs[rr][cc]) = v;
+      gb[h] = (idx < KC * B / 4)
+                  ? *reinterpret_cast<const float4 *>(inb + (int64_t)(k0 + rr) * B + cc)
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  fetch(0);
+  for (int k0 = 0; k0 < sp; k0 += KC) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int idx = tid + 256 * h;
+      *reinterpret_cast<float4 *>(&As[idx >> 4][(idx & 15) * 4]) = ga[h];
+    }
+#pragma unroll
+    for (int h = 0; h < BV; ++h) {
+      const int idx = tid + 256 * h;
+      if (idx < KC * B / 4)
+        *reinterpret_cast<float4 *>(&Bs[idx / (B / 4)][(idx % (B / 4)) * 4]) = gb[h];
     }
     __syncthreads();
+    if (k0 + KC < sp) fetch(k0 + KC);
 #pragma unroll 8
     for (int kk = 0; kk < KC; ++kk) {
       float a[4], b[CN];
