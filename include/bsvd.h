@@ -228,6 +228,43 @@ bsvd_status bsvd_phase_times(bsvd_ctx *ctx, double *ms);
  */
 int64_t bsvd_kernel_launches(const bsvd_ctx *ctx);
 
+/*
+ * Block counts and block means of a rating matrix, for callers that cannot
+ * allocate device memory during the call (the paper has no counterpart:
+ * this serves deployment, not the method). A serving process that has
+ * handed all of its device memory to its own pool, or a real-time loop
+ * whose memory is fixed before it starts, cannot call cudaMalloc; the
+ * context-based bsvd_partition does (it owns its buffers). This entry
+ * point allocates nothing: its scratch (per-block rating sums, block
+ * bounds, the largest |rating|, an error word; about 96 KiB) is one
+ * file-scope __device__ array that every GPU that loads the library holds
+ * until the process exits.
+ *
+ * Same grid and means as bsvd_partition with equal blocks (NULL bounds and
+ * permutations): counts[b] and mu[b] for b = bi * q + bj equal what
+ * bsvd_block_stats returns after bsvd_partition on the same input.
+ * m, n, nnz, p, q  as in bsvd_partition; p * q <= 4096, p, q <= 4096.
+ * u, i, x          device arrays of nnz entries (host memory is rejected,
+ *                  since staging it would need an allocation).
+ * counts, mu       device arrays of p * q entries, written by the call.
+ * stream           cudaStream_t (NULL: the legacy default stream); the call
+ *                  synchronises it before returning.
+ * The first call on each device looks up the scratch array's device
+ * address (once per device, with that device current); make that first
+ * call before any stream capture. Every call shares the array and clears
+ * the parts it accumulates into; calls that overlap on the GPU (other
+ * threads or streams, or work queued before this call finishes) race on
+ * it and must not be made.
+ * Errors (status only, there is no context): BSVD_EINVAL (bad sizes, a
+ * grid over the limit, a host pointer, an id out of range, a non-finite or
+ * too large rating), BSVD_ECUDA.
+ */
+bsvd_status bsvd_block_means_noalloc(int64_t m, int64_t n, int64_t nnz,
+                                     const int32_t *u, const int32_t *i,
+                                     const float *x, int32_t p, int32_t q,
+                                     int64_t *counts, float *mu,
+                                     void *stream);
+
 #ifdef __cplusplus
 }
 #endif

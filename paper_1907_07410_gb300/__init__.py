@@ -28,7 +28,7 @@ EXPORTS = ("bsvd_config_default", "bsvd_create", "bsvd_destroy",
            "bsvd_last_error", "bsvd_partition", "bsvd_factor", "bsvd_predict",
            "bsvd_rmse", "bsvd_block_stats", "bsvd_get_block",
            "bsvd_reconstruct", "bsvd_factor_report", "bsvd_phase_times",
-           "bsvd_kernel_launches")
+           "bsvd_kernel_launches", "bsvd_block_means_noalloc")
 
 
 class BsvdError(RuntimeError):
@@ -82,6 +82,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "bsvd_factor_report": (i32, [vp, vp, vp, vp, vp]),
         "bsvd_phase_times": (i32, [vp, vp]),
         "bsvd_kernel_launches": (i64, [vp]),
+        "bsvd_block_means_noalloc": (i32, [i64, i64, i64, vp, vp, vp, i32,
+                                           i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -273,6 +275,26 @@ def bsvd_kernel_launches(ctx) -> int:
 
 
 PHASES = ("partition", "gram", "eigen", "project", "predict")
+
+
+def bsvd_block_means_noalloc(m, n, u, i, x, p, q, counts, mu,
+                             stream=None) -> int:
+    """Block counts and means with no allocation (device arrays only).
+
+    For callers that cannot allocate device memory during the call; the
+    scratch lives in a fixed device array of the library (p * q <= 4096).
+    Returns the status code (0 on success) instead of raising, since there
+    is no context to hold an error message.
+    """
+    nnz = _len(u)
+    if _len(i) != nnz or _len(x) != nnz:
+        raise ValueError("u, i, x must have the same length")
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    return int(load().bsvd_block_means_noalloc(
+        m, n, nnz, _ptr(u, np.int32, "u"), _ptr(i, np.int32, "i"),
+        _ptr(x, np.float32, "x"), p, q, _ptr(counts, np.int64, "counts"),
+        _ptr(mu, np.float32, "mu"), stream))
 
 
 # ---- convenience wrapper ----------------------------------------------------
