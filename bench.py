@@ -247,7 +247,8 @@ def main():
         step_ms.append(e0.elapsed_time(e1))
         ph = ctx.phase_times()
         phases["partition"].append(part_ph)
-        for key in ("gram", "eigen", "project"):
+        for key in ("gram", "eigen", "project", "eigen_filter", "eigen_rr",
+                    "eigen_other"):
             phases[key].append(fac_ph[key])
         phases["predict"].append(ph["predict"])
     barrier()

@@ -212,12 +212,15 @@ bsvd_status bsvd_factor_report(bsvd_ctx *ctx, int32_t *iters,
                                int64_t *cycles);
 
 /*
- * Phase timings of the last call, in milliseconds of device time between
+ * Phase timings of the last calls, in milliseconds of device time between
  * CUDA events on the context's stream (needs profile = 1 in the config):
  *   ms[0] partition (count, means, scatter)   ms[1] Gram products
  *   ms[2] subspace iteration (eigen-solve)    ms[3] projection and norms
  *   ms[4] prediction / squared-error sum
- * Phases the last calls did not run read as 0. ms: host array of 5.
+ *   ms[5] inside ms[2]: Chebyshev filters and panel products
+ *   ms[6] inside ms[2]: Rayleigh-Ritz kernels (Grams, solve, rotate, check)
+ *   ms[7] the rest of ms[2] (start basis, host round trips between steps)
+ * Phases the last calls did not run read as 0. ms: host array of 8.
  */
 bsvd_status bsvd_phase_times(bsvd_ctx *ctx, double *ms);
 

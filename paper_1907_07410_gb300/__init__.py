@@ -265,7 +265,7 @@ def bsvd_factor_report(ctx, nblocks: int, full: bool = False):
 
 
 def bsvd_phase_times(ctx) -> np.ndarray:
-    ms = np.zeros(5, np.float64)
+    ms = np.zeros(8, np.float64)
     _check(ctx, load().bsvd_phase_times(ctx, ms.ctypes.data))
     return ms
 
@@ -274,7 +274,8 @@ def bsvd_kernel_launches(ctx) -> int:
     return int(load().bsvd_kernel_launches(ctx))
 
 
-PHASES = ("partition", "gram", "eigen", "project", "predict")
+PHASES = ("partition", "gram", "eigen", "project", "predict", "eigen_filter",
+          "eigen_rr", "eigen_other")
 
 
 def bsvd_block_means_noalloc(m, n, u, i, x, p, q, counts, mu,

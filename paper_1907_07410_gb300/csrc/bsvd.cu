@@ -72,8 +72,8 @@ struct bsvd_ctx {
 
   // tracing: kernel launch count and per-phase CUDA events
   int64_t launches = 0;
-  cudaEvent_t ev[6] = {};
-  double phase_ms[5] = {};
+  cudaEvent_t ev[10] = {};
+  double phase_ms[8] = {};
 
   GridDesc grid() const {
     GridDesc g;
@@ -382,7 +382,7 @@ bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
   CK(cudaMemsetAsync(c->d_W.p, 0, sizeof(float) * std::max<int64_t>(off, 1),
                      c->st), "partition");
   const GridDesc g = c->grid();
-  std::fill(c->phase_ms, c->phase_ms + 5, 0.0);
+  std::fill(c->phase_ms, c->phase_ms + 8, 0.0);
   mark(c, 0);
   CK(launch_count(g, nnz, (const int32_t *)du, (const int32_t *)di,
                   (const float *)dx, nb, c->d_counts.as<unsigned long long>(),
@@ -506,6 +506,7 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
     const int nrt = c->n_rowtiles;
 
     std::fill(c->phase_ms + 1, c->phase_ms + 4, 0.0);
+    std::fill(c->phase_ms + 5, c->phase_ms + 8, 0.0);
     mark(c, 0);
     CK(launch_gram_f32(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
                        c->n_gtiles, c->d_W.as<float>(), e.G, c->st), "factor: gram");
@@ -514,20 +515,31 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
     CK(launch_gpanel(e, rtd, nrt, 0, 0, 0, e.X, nullptr, e.Z, c->st), "factor: G X");
     c->launches += (c->n_gtiles > 0) + 2 * (nrt > 0);
     for (int it = 0; it <= c->cfg.max_iters + 1; ++it) {
+      mark(c, 6);
       CK(launch_small_gram(e, rtd, nrt, c->st), "factor: rr gram");
       CK(launch_rr_solve(e, c->st), "factor: rr solve");
       CK(launch_rotate(e, rtd, nrt, c->st), "factor: rotate");
       CK(cudaMemsetAsync(e.running, 0, 2 * sizeof(int32_t), c->st), "factor");
       CK(launch_check(e, c->st), "factor: check");
+      mark(c, 7);
       c->launches += 2 + 2 * (nrt > 0);
       int32_t run_deg[2] = {0, 0};
       CK(cudaMemcpyAsync(run_deg, e.running, sizeof run_deg,
                          cudaMemcpyDeviceToHost, c->st), "factor");
       CK(cudaStreamSynchronize(c->st), "factor");
+      if (c->cfg.profile) {
+        float ms = 0.f;
+        if (it > 0 && cudaEventElapsedTime(&ms, c->ev[8], c->ev[9]) == cudaSuccess)
+          c->phase_ms[5] += ms;
+        if (cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]) == cudaSuccess)
+          c->phase_ms[6] += ms;
+        cudaGetLastError();
+      }
       if (run_deg[0] == 0) break;
       const int deg = std::min(c->cfg.cheb_degree, std::max(2, run_deg[1]));
       // Chebyshev filter of even degree: Y_1 -> Z, Y_2 -> X, ..., Y_d -> X
       // step j reads Y_{j-1}, Y_{j-2} and overwrites Y_{j-2} with Y_j
+      mark(c, 8);
       for (int j = 1; j <= deg; ++j) {
         const bool even = j % 2 == 0;
         const float *in = even ? e.Z : e.X;
@@ -538,6 +550,7 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
       }
       CK(launch_gpanel(e, rtd, nrt, 0, 0, 0, e.X, nullptr, e.Z, c->st),
          "factor: G X");
+      mark(c, 9);
       c->launches += (deg + 1) * (nrt > 0);
     }
     mark(c, 2);
@@ -557,6 +570,8 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
     take(c, 1, 0, 1);
     take(c, 2, 1, 2);
     take(c, 3, 2, 3);
+    // host time inside the eigen phase: what neither products nor RR cover
+    c->phase_ms[7] = std::max(0.0, c->phase_ms[2] - c->phase_ms[5] - c->phase_ms[6]);
   }
   CK(cudaStreamSynchronize(c->st), "factor");
   c->factored = true;
@@ -779,7 +794,7 @@ bsvd_status bsvd_phase_times(bsvd_ctx *c, double *ms) {
   if (!c || !ms) return BSVD_EINVAL;
   if (!c->cfg.profile)
     return fail(c, BSVD_ESTATE, "phase_times: profiling is off");
-  for (int j = 0; j < 5; ++j) ms[j] = c->phase_ms[j];
+  for (int j = 0; j < 8; ++j) ms[j] = c->phase_ms[j];
   return BSVD_OK;
 }
 

@@ -66,7 +66,7 @@ cudaError_t launch_check(const EigBuffers &e, cudaStream_t st);
 
 // F_L = W^T F_s, then float64 norms (sigma) and sign canonicalisation.
 // ltiles: (block, first column l) pairs, kProjCols columns each.
-constexpr int kProjCols = 32;
+constexpr int kProjCols = 64;
 cudaError_t launch_project(const BlockMeta *meta, const int2 *ltiles,
                            int32_t ntiles, const float *W, const float *Fs,
                            float *FL, int32_t kp, cudaStream_t st);

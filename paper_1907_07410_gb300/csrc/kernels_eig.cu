@@ -650,27 +650,29 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   }
 }
 
-// F_L[l, :] = sum_a W[a, l] F_s[a, :] for kProjCols = 32 consecutive l
-// (one per lane). Warp w takes the
-// rows a = w, w + 8, ...; lane = l; the 8 partial sums are added in order.
+// F_L[l, :] = sum_a W[a, l] F_s[a, :] for kProjCols = 64 consecutive l: lane
+// t owns l = l0 + 2t, l0 + 2t + 1 (one float2 of each W row), warp w takes
+// the rows a = w, w + 8, ... and a row of F_s is read from shared memory as
+// float4s, so each shared load feeds 8 FMAs. The 8 warps' partial sums are
+// added in warp order. KM: kp rounded up to 8.
 template <int KM>
 __global__ void __launch_bounds__(256)
 k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
           const float *__restrict__ W, const float *__restrict__ Fs,
           float *__restrict__ FL, int kp) {
   constexpr int CH = 64;
-  __shared__ float Fsh[CH][KM];
-  __shared__ float red[8][32][17];
+  __shared__ __align__(16) float Fsh[CH][KM];
+  __shared__ float red[8][64][9];
   const int2 t = ltiles[blockIdx.x];
   const BlockMeta bm = meta[t.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int l = t.y + lane;
-  const bool lv = l < bm.L;
+  const int l = t.y + 2 * lane;
+  const bool lv = l < bm.L_pad;          // padded columns of W are zero
   const float *Wb = W + bm.w_off;
   const float *Fb = Fs + bm.fs_off;
-  float acc[KM];
+  float acc[2][KM];
 #pragma unroll
-  for (int j = 0; j < KM; ++j) acc[j] = 0.f;
+  for (int j = 0; j < KM; ++j) { acc[0][j] = 0.f; acc[1][j] = 0.f; }
   for (int a0 = 0; a0 < bm.s; a0 += CH) {
     for (int e = threadIdx.x; e < CH * KM; e += blockDim.x) {
       const int rr = e / KM, j = e % KM;
@@ -680,24 +682,36 @@ k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
     const int lim = min(CH, bm.s - a0);
     if (lv) {
       for (int rr = warp; rr < lim; rr += 8) {
-        const float w = Wb[(int64_t)(a0 + rr) * bm.L_pad + l];
+        const float2 w = *reinterpret_cast<const float2 *>(
+            Wb + (int64_t)(a0 + rr) * bm.L_pad + l);
 #pragma unroll
-        for (int j = 0; j < KM; ++j) acc[j] = fmaf(w, Fsh[rr][j], acc[j]);
+        for (int j = 0; j < KM; j += 4) {
+          const float4 f = *reinterpret_cast<const float4 *>(&Fsh[rr][j]);
+          acc[0][j] = fmaf(w.x, f.x, acc[0][j]);
+          acc[0][j + 1] = fmaf(w.x, f.y, acc[0][j + 1]);
+          acc[0][j + 2] = fmaf(w.x, f.z, acc[0][j + 2]);
+          acc[0][j + 3] = fmaf(w.x, f.w, acc[0][j + 3]);
+          acc[1][j] = fmaf(w.y, f.x, acc[1][j]);
+          acc[1][j + 1] = fmaf(w.y, f.y, acc[1][j + 1]);
+          acc[1][j + 2] = fmaf(w.y, f.z, acc[1][j + 2]);
+          acc[1][j + 3] = fmaf(w.y, f.w, acc[1][j + 3]);
+        }
       }
     }
     __syncthreads();
   }
-  // add the 8 warps' partial sums in warp order, 16 columns at a time
 #pragma unroll
-  for (int jc = 0; jc < KM; jc += 16) {
+  for (int jc = 0; jc < KM; jc += 8) {
 #pragma unroll
-    for (int jj = 0; jj < 16; ++jj)
-      if (jc + jj < KM) red[warp][lane][jj] = acc[jc + jj];
+    for (int jj = 0; jj < 8; ++jj) {
+      red[warp][2 * lane][jj] = acc[0][jc + jj];
+      red[warp][2 * lane + 1][jj] = acc[1][jc + jj];
+    }
     __syncthreads();
-    for (int e = threadIdx.x; e < 32 * 16; e += blockDim.x) {
-      const int ln = e >> 4, jj = e & 15, j = jc + jj;
+    for (int e = threadIdx.x; e < 64 * 8; e += blockDim.x) {
+      const int ln = e >> 3, jj = e & 7, j = jc + jj;
       const int ll = t.y + ln;
-      if (ll < bm.L && j < kp && j < KM) {
+      if (ll < bm.L && j < kp) {
         float s = 0.f;
 #pragma unroll
         for (int w = 0; w < 8; ++w) s += red[w][ln][jj];
@@ -708,69 +722,75 @@ k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
   }
 }
 
-// sigma_j = |F_L[:, j]| (float64 sums); then flip (F_s_j, F_L_j) so the
-// item-side vector's largest-|.| entry (lowest index on ties) is positive.
+// sigma_j = |F_L[:, j]| (float64 across threads); then flip (F_s_j, F_L_j) so
+// the item-side vector's largest-|.| entry (lowest index on ties) is
+// positive. Thread t reads whole rows t, t + 256, ... (kp floats each).
+template <int KM>
 __global__ void __launch_bounds__(256)
 k_finalize(const BlockMeta *__restrict__ meta, float *Fs, float *FL,
            double *sigma, int kp) {
-  __shared__ double sq[8][64];
-  __shared__ float bv[8][64];
-  __shared__ int bi[8][64];
-  __shared__ int flip[64];
+  __shared__ double sq[8][KM];
+  __shared__ float bv[8][KM];
+  __shared__ int bi[8][KM];
+  __shared__ int flip[KM];
   const int blk = blockIdx.x;
   const BlockMeta bm = meta[blk];
   const int keff = bm.keff;
-  if (keff == 0) {
-    for (int j = threadIdx.x; j < kp; j += blockDim.x) sigma[(int64_t)blk * kp + j] = 0.0;
-    return;
-  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float *Fsb = Fs + bm.fs_off;
   float *FLb = FL + bm.fl_off;
   const float *vec = bm.trans ? Fsb : FLb;     // item-side vectors
   const int len = bm.trans ? bm.s : bm.L;
-  // lane -> column j (two passes of 32 when kp > 32); warp -> rows
-  for (int jb = 0; jb < kp; jb += 32) {
-    const int j = jb + lane;
-    double acc = 0.0;
-    float best = -1.f;
-    int bidx = 0x7fffffff;
-    if (j < keff) {
-      for (int l = warp; l < bm.L; l += 8) {
-        const double v = FLb[(int64_t)l * kp + j];
-        acc = fma(v, v, acc);
-      }
-      for (int a = warp; a < len; a += 8) {
-        const float v = fabsf(vec[(int64_t)a * kp + j]);
-        if (v > best) { best = v; bidx = a; }
-      }
+  float part[KM], best[KM];
+  int bidx[KM];
+#pragma unroll
+  for (int j = 0; j < KM; ++j) { part[j] = 0.f; best[j] = -1.f; bidx[j] = 0x7fffffff; }
+  for (int l = threadIdx.x; l < bm.L; l += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < KM; ++j) {
+      const float v = j < kp ? FLb[(int64_t)l * kp + j] : 0.f;
+      part[j] = fmaf(v, v, part[j]);
     }
-    sq[warp][lane] = acc;
-    bv[warp][lane] = best;
-    bi[warp][lane] = bidx;
-    __syncthreads();
-    if (warp == 0 && j < keff) {
-      double s = 0.0;
-      float b = -1.f;
-      int ix = 0x7fffffff;
-      for (int w = 0; w < 8; ++w) {
-        s += sq[w][lane];
-        const float ob = bv[w][lane];
-        const int oi = bi[w][lane];
-        if (ob > b || (ob == b && oi < ix)) { b = ob; ix = oi; }
-      }
-      sigma[(int64_t)blk * kp + j] = sqrt(s);
-      flip[j] = (ix < len && vec[(int64_t)ix * kp + j] < 0.f) ? 1 : 0;
-    } else if (warp == 0 && j < kp) {
-      sigma[(int64_t)blk * kp + j] = 0.0;
-      flip[j] = 0;
-    }
-    __syncthreads();
   }
+  for (int a = threadIdx.x; a < len; a += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < KM; ++j) {
+      const float v = j < kp ? fabsf(vec[(int64_t)a * kp + j]) : 0.f;
+      if (v > best[j]) { best[j] = v; bidx[j] = a; }   // first index wins ties
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < KM; ++j) {
+    double d = part[j];
+    float b = best[j];
+    int ix = bidx[j];
+    for (int o = 16; o > 0; o >>= 1) {
+      d += __shfl_xor_sync(0xffffffffu, d, o);
+      const float ob = __shfl_xor_sync(0xffffffffu, b, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
+      if (ob > b || (ob == b && oi < ix)) { b = ob; ix = oi; }
+    }
+    if (lane == 0) { sq[warp][j] = d; bv[warp][j] = b; bi[warp][j] = ix; }
+  }
+  __syncthreads();
+  if (threadIdx.x < KM) {
+    const int j = threadIdx.x;
+    double s2 = 0.0;
+    float b = -1.f;
+    int ix = 0x7fffffff;
+    for (int w = 0; w < 8; ++w) {
+      s2 += sq[w][j];
+      if (bv[w][j] > b || (bv[w][j] == b && bi[w][j] < ix)) { b = bv[w][j]; ix = bi[w][j]; }
+    }
+    const bool live = j < keff;
+    flip[j] = (live && ix < len && vec[(int64_t)ix * kp + j] < 0.f) ? 1 : 0;
+    if (j < kp) sigma[(int64_t)blk * kp + j] = live ? sqrt(s2) : 0.0;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < bm.s * kp; e += blockDim.x)
-    if (flip[e % kp] && e % kp < keff) Fsb[e] = -Fsb[e];
+    if (flip[e % kp]) Fsb[e] = -Fsb[e];
   for (int e = threadIdx.x; e < bm.L * kp; e += blockDim.x)
-    if (flip[e % kp] && e % kp < keff) FLb[e] = -FLb[e];
+    if (flip[e % kp]) FLb[e] = -FLb[e];
 }
 
 template <int B>
@@ -873,14 +893,29 @@ cudaError_t launch_check(const EigBuffers &e, cudaStream_t st) {
   });
 }
 
+template <typename F>
+cudaError_t by_kmax(int kp, F &&f) {
+  switch ((kp + 7) / 8) {
+    case 1: return f(std::integral_constant<int, 8>());
+    case 2: return f(std::integral_constant<int, 16>());
+    case 3: return f(std::integral_constant<int, 24>());
+    case 4: return f(std::integral_constant<int, 32>());
+    case 5: return f(std::integral_constant<int, 40>());
+    case 6: return f(std::integral_constant<int, 48>());
+    case 7: return f(std::integral_constant<int, 56>());
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_project(const BlockMeta *meta, const int2 *ltiles,
                            int32_t ntiles, const float *W, const float *Fs,
                            float *FL, int32_t kp, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
-  if (kp <= 16) k_project<16><<<ntiles, 256, 0, st>>>(meta, ltiles, W, Fs, FL, kp);
-  else if (kp <= 32) k_project<32><<<ntiles, 256, 0, st>>>(meta, ltiles, W, Fs, FL, kp);
-  else k_project<56><<<ntiles, 256, 0, st>>>(meta, ltiles, W, Fs, FL, kp);
-  return cudaGetLastError();
+  return by_kmax(kp, [&](auto km) {
+    constexpr int KM = decltype(km)::value;
+    k_project<KM><<<ntiles, 256, 0, st>>>(meta, ltiles, W, Fs, FL, kp);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_finalize(const BlockMeta *meta, int32_t nblocks,
@@ -888,8 +923,11 @@ cudaError_t launch_finalize(const BlockMeta *meta, int32_t nblocks,
                             int32_t k, cudaStream_t st) {
   (void)k;
   if (nblocks <= 0) return cudaSuccess;
-  k_finalize<<<nblocks, 256, 0, st>>>(meta, Fs, FL, sigma, kp);
-  return cudaGetLastError();
+  return by_kmax(kp, [&](auto km) {
+    constexpr int KM = decltype(km)::value;
+    k_finalize<KM><<<nblocks, 256, 0, st>>>(meta, Fs, FL, sigma, kp);
+    return cudaGetLastError();
+  });
 }
 
 }  // namespace bsvd
