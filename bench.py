@@ -31,6 +31,9 @@ import synth  # noqa: E402
 
 FP32_LANES_PER_SM = 128
 SMS = 152
+# DRAM bytes (read + write) of one k_gram_tc launch, from the ncu capture
+# summarised in profiles/k_gram_tc_medium-4x4-k20.md; None until captured.
+GRAM_TC_TRAFFIC = {}
 
 
 def load_peaks():
@@ -48,8 +51,8 @@ def fp32_alu_peak_tflops(peaks):
 
 
 def gram_flops(blocks):
-    """Symmetric Gram: s(s+1)/2 entries, 2L flops each, per block."""
-    return float(sum(L * s * (s + 1) for (s, L) in blocks))
+    """Algorithmic Gram work: 2 m_b n_b s_b flop per block (s = min side)."""
+    return float(sum(2.0 * L * s * s for (s, L) in blocks))
 
 
 def block_shapes(w):
@@ -290,8 +293,19 @@ def main():
     shapes = block_shapes(w)
     gflops = gram_flops(shapes)
     gram_ms = statistics.mean(phases["gram"])
-    alu_peak = fp32_alu_peak_tflops(peaks)
     achieved = gflops / (gram_ms * 1e-3) / 1e12
+    gram_path = ctx.gram_path()
+    if gram_path == 2:
+        roof = {"kernel": "k_gram_tc", "bound": "tensor",
+                "peak": peaks.get("bf16_tflops", 1900.0),
+                "peak_source": "bf16 dense, burst, of %s" % peak_kind,
+                "traffic": GRAM_TC_TRAFFIC.get(w.name)}
+    else:
+        roof = {"kernel": "k_gram_f32", "bound": "alu",
+                "peak": fp32_alu_peak_tflops(peaks),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz"
+                               % peaks.get("sm_max_mhz", 2070.0),
+                "traffic": None}
     value = world * nblocks * args.steps / (total_ms * 1e-3)
     proj_flops = 2.0 * sum(L * s * w.k for (s, L) in shapes)
     pred_flops = 2.0 * w.k * r.u_test.size
@@ -307,6 +321,8 @@ def main():
                    "nnz_train": int(r.u_train.size),
                    "nnz_test": int(r.u_test.size), "p": w.p, "q": w.q,
                    "k": w.k, "precision": "fp32",
+                   "gram": "tensor cores, exact" if gram_path == 2
+                           else "fp32 simt",
                    "l2": "flushed (256 MB write) before each step, untimed"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
@@ -314,12 +330,12 @@ def main():
         "phases_ms": {k: statistics.mean(v) for k, v in phases.items()},
         "rmse": rm, "rmse_oracle": gold,
         "rmse_parity": (gold is not None and abs(rm - gold) <= 1e-4),
-        "roofline": {"kernel": "k_gram_f32", "bound": "alu",
-                     "achieved": achieved, "peak": alu_peak,
-                     "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                     "traffic": None,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz"
-                                    % peaks.get("sm_max_mhz", 2070.0)},
+        "roofline": {"kernel": roof["kernel"], "bound": roof["bound"],
+                     "achieved": achieved, "peak": roof["peak"],
+                     "unit": "TFLOP/s", "frac": achieved / roof["peak"],
+                     "traffic": roof["traffic"],
+                     "algorithmic_flops_per_launch": gflops,
+                     "peak_source": roof["peak_source"]},
         "gpu_launches": int(launches),
         "e2e": {"value": world * nblocks * args.steps / (e2e_total * 1e-3),
                 "unit": "block-SVDs/s",

@@ -74,7 +74,9 @@ typedef struct {
     int32_t max_iters;    /* subspace iterations cap; <= 0: default (30) */
     int32_t max_sweeps;   /* Jacobi sweeps cap per small solve; <= 0: 30 */
     int32_t profile;      /* 1: time each phase with CUDA events */
-    int32_t reserved;     /* must be 0 */
+    int32_t gram_path;    /* 0: tensor cores when exact, else FP32 SIMT;
+                             1: FP32 SIMT always; 2: tensor cores or
+                             BSVD_EINVAL from bsvd_factor */
     double tol;           /* residual |G v - theta v| <= tol * theta_1;
                              <= 0: default (1e-5) */
     uint64_t seed;        /* seed of the start basis */
@@ -138,6 +140,9 @@ bsvd_status bsvd_partition(bsvd_ctx *ctx, int64_t m, int64_t n, int64_t nnz,
  * The library forms the Gram matrix of the block's shorter side and finds
  * its top eigenpairs by Chebyshev-filtered subspace iteration with
  * Rayleigh-Ritz steps solved by Jacobi. Factors stay on the device.
+ * The Gram runs on the tensor cores, exactly, when every rating minus its
+ * block's rounded mean is a small integer (integer rating scales), else on
+ * the FP32 SIMT pipes; gram_path in the config can force either.
  * k >= 0; k = 0 keeps no factor (predictions are then the block means).
  * The limit is k <= 56.
  * Errors: BSVD_ESTATE (no partition), BSVD_EINVAL (k out of range),
@@ -230,6 +235,12 @@ bsvd_status bsvd_phase_times(bsvd_ctx *ctx, double *ms);
  * Returns -1 for a NULL context.
  */
 int64_t bsvd_kernel_launches(const bsvd_ctx *ctx);
+
+/*
+ * Which Gram kernel the last bsvd_factor ran: 1 FP32 SIMT, 2 tensor cores
+ * (exact), 0 none yet (or k = 0), -1 for a NULL context.
+ */
+int32_t bsvd_gram_path(const bsvd_ctx *ctx);
 
 /*
  * Block counts and block means of a rating matrix, for callers that cannot

@@ -28,7 +28,8 @@ EXPORTS = ("bsvd_config_default", "bsvd_create", "bsvd_destroy",
            "bsvd_last_error", "bsvd_partition", "bsvd_factor", "bsvd_predict",
            "bsvd_rmse", "bsvd_block_stats", "bsvd_get_block",
            "bsvd_reconstruct", "bsvd_factor_report", "bsvd_phase_times",
-           "bsvd_kernel_launches", "bsvd_block_means_noalloc")
+           "bsvd_kernel_launches", "bsvd_block_means_noalloc",
+           "bsvd_gram_path")
 
 
 class BsvdError(RuntimeError):
@@ -43,7 +44,7 @@ class Config(ctypes.Structure):
                 ("oversample", ctypes.c_int32),
                 ("cheb_degree", ctypes.c_int32),
                 ("max_iters", ctypes.c_int32), ("max_sweeps", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("gram_path", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p)]
 
@@ -82,6 +83,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "bsvd_factor_report": (i32, [vp, vp, vp, vp, vp]),
         "bsvd_phase_times": (i32, [vp, vp]),
         "bsvd_kernel_launches": (i64, [vp]),
+        "bsvd_gram_path": (i32, [vp]),
         "bsvd_block_means_noalloc": (i32, [i64, i64, i64, vp, vp, vp, i32,
                                            i32, vp, vp, vp]),
     }
@@ -274,6 +276,10 @@ def bsvd_kernel_launches(ctx) -> int:
     return int(load().bsvd_kernel_launches(ctx))
 
 
+def bsvd_gram_path(ctx) -> int:
+    return int(load().bsvd_gram_path(ctx))
+
+
 PHASES = ("partition", "gram", "eigen", "project", "predict", "eigen_filter",
           "eigen_rr", "eigen_other")
 
@@ -388,3 +394,6 @@ class Context:
 
     def kernel_launches(self) -> int:
         return bsvd_kernel_launches(self.handle)
+
+    def gram_path(self) -> int:
+        return bsvd_gram_path(self.handle)

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "bsvd.h"
 #include "kernels.h"
 
@@ -39,6 +41,29 @@ struct DevBuf {
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType,
+                                  cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, looked up through the runtime.
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
 }  // namespace
 
 struct bsvd_ctx {
@@ -58,6 +83,10 @@ struct bsvd_ctx {
   int64_t arena = 0;
   DevBuf d_rb, d_cb, d_rperm, d_cperm, d_seen, d_meta, d_counts, d_sums,
       d_maxabs, d_mu, d_W, d_err;
+  // bf16 [Y; M] planes, per-block shift and delta, TMA maps (tensor Gram)
+  bool tc_planes = false, tc_exact = false;
+  int32_t gram_used = 0;    // 1: FP32 SIMT, 2: tensor cores (last factor)
+  DevBuf d_VX, d_shift, d_delta, d_maps, d_flag;
 
   // factor
   bool factored = false;
@@ -150,8 +179,10 @@ bsvd_status read_errors(bsvd_ctx *c, const char *what) {
     if (h & kErrValue) msg += " non-finite rating or |x| >= 2^31;";
     if (h & kErrSumRange) msg += " ratings too large for exact block sums;";
     if (h & kErrBadPerm) msg += " invalid permutation;";
+    if (h & kErrTimeout) msg += " a device-side wait timed out;";
     CK(cudaMemsetAsync(c->d_err.p, 0, sizeof(int32_t), c->st), what);
-    return fail(c, BSVD_EINVAL, "%s", msg.c_str());
+    return fail(c, (h & kErrTimeout) ? BSVD_ETIMEOUT : BSVD_EINVAL, "%s",
+                msg.c_str());
   }
   return BSVD_OK;
 }
@@ -219,7 +250,8 @@ bsvd_status bsvd_create(const bsvd_config *cfg, bsvd_ctx **out) {
     if (c->cfg.max_sweeps <= 0) c->cfg.max_sweeps = 30;
     if (!(c->cfg.tol > 0)) c->cfg.tol = 1e-5;
   }
-  if (c->cfg.precision != BSVD_FP32 || c->cfg.reserved != 0 ||
+  if (c->cfg.precision != BSVD_FP32 || c->cfg.gram_path < 0 ||
+      c->cfg.gram_path > 2 ||
       c->cfg.cheb_degree % 2 != 0 ||
       c->cfg.cheb_degree > 64 || (c->cfg.clamp && !(c->cfg.clamp_lo <= c->cfg.clamp_hi))) {
     delete c;
@@ -253,7 +285,8 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->d_SH, &c->d_RP, &c->d_T, &c->d_theta, &c->d_state, &c->d_Fs,
                     &c->d_FL, &c->d_sigma, &c->d_running, &c->d_gtiles,
                     &c->d_rowtiles, &c->d_ltiles, &c->s_a, &c->s_b, &c->s_c,
-                    &c->s_out, &c->d_partials, &c->d_rmse};
+                    &c->s_out, &c->d_partials, &c->d_rmse, &c->d_VX,
+                    &c->d_shift, &c->d_delta, &c->d_maps, &c->d_flag};
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   for (DevBuf *b : bufs) b->release();
@@ -305,7 +338,7 @@ bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
 
   // block shapes and the dense arena layout
   c->meta.assign(c->nblocks, BlockMeta());
-  int64_t off = 0;
+  int64_t off = 0, vxoff = 0;
   for (int32_t bi = 0; bi < p; ++bi) {
     for (int32_t bj = 0; bj < q; ++bj) {
       BlockMeta &bm = c->meta[bi * q + bj];
@@ -321,6 +354,9 @@ bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
       bm.col0 = c->cb[bj];
       bm.w_off = off;
       off += (int64_t)bm.s_pad * bm.L_pad;
+      bm.s128 = (int32_t)round_up(bm.s, 128);
+      bm.vx_off = vxoff;
+      vxoff += 2 * (int64_t)bm.s128 * bm.L_pad;
     }
   }
   c->arena = off;
@@ -397,10 +433,64 @@ bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
                     c->d_mu.as<float>(), c->d_W.as<float>(), c->st),
      "partition: scatter");
   c->launches += nnz > 0 ? 3 : 1;
+  // bf16 planes for the exact tensor-core Gram
+  c->tc_planes = c->cfg.gram_path != 1;
+  c->tc_exact = false;
+  if (c->tc_planes) {
+    CK(c->d_VX.ensure(2 * std::max<int64_t>(vxoff, 1)), "partition");
+    CK(c->d_shift.ensure(sizeof(float) * nb), "partition");
+    CK(c->d_delta.ensure(sizeof(float) * nb), "partition");
+    CK(c->d_flag.ensure(sizeof(int32_t)), "partition");
+    CK(cudaMemsetAsync(c->d_VX.p, 0, 2 * std::max<int64_t>(vxoff, 1), c->st),
+       "partition");
+    CK(cudaMemsetAsync(c->d_flag.p, 0, sizeof(int32_t), c->st), "partition");
+    CK(launch_plane_shift(nb, c->d_counts.as<unsigned long long>(),
+                          c->d_sums.as<long long>(), c->d_shift.as<float>(),
+                          c->d_delta.as<float>(), c->st), "partition: shift");
+    CK(launch_scatter_planes(g, c->d_meta.as<BlockMeta>(), nnz,
+                             (const int32_t *)du, (const int32_t *)di,
+                             (const float *)dx, c->d_shift.as<float>(),
+                             c->d_VX.as<__nv_bfloat16>(), c->d_flag.as<int32_t>(),
+                             c->st), "partition: planes");
+    c->launches += nnz > 0 ? 2 : 1;
+  }
   mark(c, 1);
   bsvd_status s = read_errors(c, "partition");
   if (s != BSVD_OK) return s;
   take(c, 0, 0, 1);
+  if (c->tc_planes) {
+    int32_t flag = 0;
+    CK(cudaMemcpy(&flag, c->d_flag.p, sizeof flag, cudaMemcpyDeviceToHost),
+       "partition");
+    c->tc_exact = (flag & kErrNotExact) == 0;
+    if (c->tc_exact) {
+      // one TMA map per block over its [Y; M] planes
+      EncodeTiledFn enc = tensor_map_encoder();
+      if (!enc) return fail(c, BSVD_ECUDA, "partition: no cuTensorMapEncodeTiled");
+      std::vector<CUtensorMap> maps(nb);
+      std::memset(maps.data(), 0, sizeof(CUtensorMap) * nb);
+      for (int32_t b = 0; b < nb; ++b) {
+        const BlockMeta &bm = c->meta[b];
+        if (bm.s == 0) continue;
+        cuuint64_t dims[2] = {(cuuint64_t)bm.L_pad, (cuuint64_t)(2 * bm.s128)};
+        cuuint64_t strides[1] = {(cuuint64_t)bm.L_pad * 2};
+        cuuint32_t box[2] = {64, 128};
+        cuuint32_t es[2] = {1, 1};
+        CUresult r = enc(&maps[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                         c->d_VX.as<__nv_bfloat16>() + bm.vx_off, dims,
+                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+          return fail(c, BSVD_ECUDA, "partition: tensor map %d failed (%d)", b,
+                      (int)r);
+      }
+      CK(c->d_maps.ensure(sizeof(CUtensorMap) * nb), "partition");
+      CK(cudaMemcpy(c->d_maps.p, maps.data(), sizeof(CUtensorMap) * nb,
+                    cudaMemcpyHostToDevice), "partition");
+    }
+  }
   c->parted = true;
   return BSVD_OK;
 }
@@ -410,6 +500,10 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
   c->err.clear();
   if (!c->parted) return fail(c, BSVD_ESTATE, "factor: no partition");
   if (k < 0 || k > 56) return fail(c, BSVD_EINVAL, "factor: k=%d outside [0, 56]", k);
+  if (c->cfg.gram_path == 2 && !(c->tc_planes && c->tc_exact))
+    return fail(c, BSVD_EINVAL,
+                "factor: tensor-core Gram needs ratings that are small integer "
+                "offsets from their block's rounded mean");
   c->factored = false;
   c->any_capped = false;
   c->k = k;
@@ -508,8 +602,17 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
     std::fill(c->phase_ms + 1, c->phase_ms + 4, 0.0);
     std::fill(c->phase_ms + 5, c->phase_ms + 8, 0.0);
     mark(c, 0);
-    CK(launch_gram_f32(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
-                       c->n_gtiles, c->d_W.as<float>(), e.G, c->st), "factor: gram");
+    c->gram_used = (c->tc_planes && c->tc_exact) ? 2 : 1;
+    if (c->gram_used == 2) {
+      CK(launch_gram_tc(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
+                        c->n_gtiles, c->d_maps.as<CUtensorMap>(),
+                        c->d_delta.as<float>(), e.G, c->d_err.as<int32_t>(),
+                        c->st), "factor: gram (tensor cores)");
+    } else {
+      CK(launch_gram_f32(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
+                         c->n_gtiles, c->d_W.as<float>(), e.G, c->st),
+         "factor: gram");
+    }
     mark(c, 1);
     CK(launch_init_panels(e, rtd, nrt, c->st), "factor: init");
     CK(launch_gpanel(e, rtd, nrt, 0, 0, 0, e.X, nullptr, e.Z, c->st), "factor: G X");
@@ -574,6 +677,10 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
     c->phase_ms[7] = std::max(0.0, c->phase_ms[2] - c->phase_ms[5] - c->phase_ms[6]);
   }
   CK(cudaStreamSynchronize(c->st), "factor");
+  {
+    bsvd_status es = read_errors(c, "factor");
+    if (es != BSVD_OK) return es;
+  }
   c->factored = true;
   if (c->any_capped)
     return fail(c, BSVD_ENOTCONV, "factor: some blocks hit the iteration cap");
@@ -801,5 +908,7 @@ bsvd_status bsvd_phase_times(bsvd_ctx *c, double *ms) {
 int64_t bsvd_kernel_launches(const bsvd_ctx *c) {
   return c ? c->launches : -1;
 }
+
+int32_t bsvd_gram_path(const bsvd_ctx *c) { return c ? c->gram_used : -1; }
 
 }  // extern "C"

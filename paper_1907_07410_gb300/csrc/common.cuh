@@ -28,6 +28,9 @@ struct BlockMeta {
   int32_t trans;        // 1: W = B^T (s indexes items); 0: W = B
   int32_t keff;         // retained rank min(k, s) (set by factor)
   int32_t t0, nt;       // the block's 64-row tiles in the row-tile table
+  int32_t s128;         // s rounded up to 128 (rows of each bf16 plane)
+  int32_t pad0;
+  int64_t vx_off;       // bf16 planes offset: [Y; M], 2 s128 x L_pad
   int64_t row0, col0;   // first row / column position of the block
   int64_t w_off;        // W arena offset (floats)
   int64_t g_off;        // Gram offset, s_pad x s_pad
@@ -60,7 +63,9 @@ enum : int32_t {
   kErrIndex = 1,        // an id outside [0, m) or [0, n)
   kErrValue = 2,        // a non-finite rating or |x| >= 2^31
   kErrSumRange = 4,     // count * max|x| >= 2^31 in some block
-  kErrBadPerm = 8       // a permutation entry out of range or repeated
+  kErrBadPerm = 8,      // a permutation entry out of range or repeated
+  kErrTimeout = 16,     // a bounded device-side wait gave up
+  kErrNotExact = 32     // a rating is not an exact small integer offset
 };
 
 // Grid description used by every kernel that maps (user, item) to a block.

@@ -1,6 +1,9 @@
 // Launchers of the libbsvd kernels (host side). Every launcher queues work
 // on the given stream and returns the launch status.
 #pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace bsvd {
@@ -27,6 +30,28 @@ cudaError_t launch_scatter(const GridDesc &g, const BlockMeta *meta,
 cudaError_t launch_gram_f32(const BlockMeta *meta, const int4 *tiles,
                             int32_t ntiles, const float *W, float *G,
                             cudaStream_t st);
+
+// ---- exact tensor-core Gram (kernels_gram_tc.cu) ------------------------
+// maps: one TMA map per block over its [Y; M] bf16 planes (2 s128 x L_pad,
+// 128 x 64 boxes, 128-byte swizzle); delta: mu - round(mu) per block.
+cudaError_t launch_gram_tc(const BlockMeta *meta, const int4 *tiles,
+                           int32_t ntiles, const CUtensorMap *maps,
+                           const float *delta, float *G, int32_t *err,
+                           cudaStream_t st);
+
+// ---- bf16 planes for the tensor-core Gram (kernels_partition.cu) ----------
+// shift[b] = round(mu_b) (exact mean from the sums), delta[b] = mu_b - shift.
+cudaError_t launch_plane_shift(int32_t nblocks, const unsigned long long *counts,
+                               const long long *sums, float *shift,
+                               float *delta, cudaStream_t st);
+// Y = x - shift, M = 1 at every rating, into the zeroed planes; sets
+// kErrNotExact in *flag when some x - shift is not an integer small enough
+// (|y|^2 L_pad < 2^24, |y| <= 256) for the tensor-core Gram to be exact.
+cudaError_t launch_scatter_planes(const GridDesc &g, const BlockMeta *meta,
+                                  int64_t nnz, const int32_t *u,
+                                  const int32_t *i, const float *x,
+                                  const float *shift, __nv_bfloat16 *VX,
+                                  int32_t *flag, cudaStream_t st);
 
 // ---- subspace iteration (kernels_eig.cu) --------------------------------
 struct EigBuffers {

@@ -151,6 +151,45 @@ k_scatter(GridDesc g, const BlockMeta *__restrict__ meta, int64_t nnz,
   }
 }
 
+__global__ void __launch_bounds__(256)
+k_plane_shift(int32_t nblocks, const unsigned long long *counts,
+              const long long *sums, float *shift, float *delta) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblocks;
+       b += gridDim.x * blockDim.x) {
+    const unsigned long long cb = counts[b];
+    double mu = 0.0;
+    if (cb) mu = __ddiv_rn(__dmul_rn((double)sums[b], 0x1p-32), (double)cb);
+    const double c = rint(mu);
+    shift[b] = (float)c;
+    delta[b] = __double2float_rn(mu - c);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_scatter_planes(GridDesc g, const BlockMeta *__restrict__ meta, int64_t nnz,
+                 const int32_t *__restrict__ u, const int32_t *__restrict__ it,
+                 const float *__restrict__ x, const float *__restrict__ shift,
+                 __nv_bfloat16 *__restrict__ VX, int32_t *flag) {
+  int32_t bad = 0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int32_t blk, r, c, a, l;
+    if (!locate(g, u[t], it[t], &blk, &r, &c)) continue;   // flagged in pass 1
+    const BlockMeta &bm = meta[blk];
+    to_w(bm, r, c, &a, &l);
+    const float y = __fsub_rn(x[t], shift[blk]);
+    // exact in bf16, and every Gram partial sum below 2^24 in f32:
+    // |y|^2 L_pad < 2^24
+    const float lim = sqrtf(16777216.f / (float)bm.L_pad);
+    if (!(y == rintf(y) && fabsf(y) <= fminf(lim, 256.f))) bad = 1;
+    __nv_bfloat16 *pl = VX + bm.vx_off;
+    pl[(int64_t)a * bm.L_pad + l] = __float2bfloat16_rn(y);
+    pl[(int64_t)(bm.s128 + a) * bm.L_pad + l] = __float2bfloat16_rn(1.f);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+    atomicOr(flag, kErrNotExact);
+}
+
 int grid_for(int64_t n, int per_thread) {
   int64_t want = (n + 256LL * per_thread - 1) / (256LL * per_thread);
   if (want < 1) want = 1;
@@ -159,6 +198,26 @@ int grid_for(int64_t n, int per_thread) {
 }
 
 }  // namespace
+
+cudaError_t launch_plane_shift(int32_t nblocks, const unsigned long long *counts,
+                               const long long *sums, float *shift,
+                               float *delta, cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  k_plane_shift<<<(nblocks + 255) / 256, 256, 0, st>>>(nblocks, counts, sums,
+                                                       shift, delta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_planes(const GridDesc &g, const BlockMeta *meta,
+                                  int64_t nnz, const int32_t *u,
+                                  const int32_t *i, const float *x,
+                                  const float *shift, __nv_bfloat16 *VX,
+                                  int32_t *flag, cudaStream_t st) {
+  if (nnz <= 0) return cudaSuccess;
+  k_scatter_planes<<<grid_for(nnz, 4), 256, 0, st>>>(g, meta, nnz, u, i, x,
+                                                     shift, VX, flag);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_perm_check(const int32_t *perm, int64_t n, int32_t *seen,
                               int32_t *err, cudaStream_t st) {

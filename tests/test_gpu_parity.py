@@ -263,3 +263,41 @@ def test_bad_inputs_are_rejected():
         ctx.partition(5, 5, u[:1], i[:1], x[:1], 1, 1,
                       row_perm=np.array([0, 1, 2, 3, 3], np.int32))
     assert e.value.status == bs.EINVAL
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_gram_paths_match_oracle(path):
+    """FP32 SIMT Gram (path 1) and exact tensor-core Gram (path 2)."""
+    w = synth.SMALL
+    r = synth.generate(w)
+    part = oracle.partition(w.m, w.n, r.u_train, r.i_train, r.x_train, w.p,
+                            w.q)
+    model = oracle.factor(part, w.k)
+    ctx = gpu_run(r, w.p, w.q, w.k, ctx_kw=dict(gram_path=path))
+    assert ctx.gram_path() == path
+    check_factors(ctx, model)
+    check_rmse(ctx, model, r)
+
+
+def test_default_gram_path_uses_tensor_cores_on_integer_ratings():
+    w = synth.SMALL
+    r = synth.generate(w)
+    ctx = gpu_run(r, w.p, w.q, w.k)
+    assert ctx.gram_path() == 2
+
+
+def test_non_integer_ratings_fall_back_to_simt_gram():
+    r = synth.random_ratings(21, 300, 200, 6000, 600)
+    r.x_train = (r.x_train + np.float32(0.37)).astype(np.float32)
+    r.x_test = (r.x_test + np.float32(0.37)).astype(np.float32)
+    part = oracle.partition(300, 200, r.u_train, r.i_train, r.x_train, 2, 2)
+    model = oracle.factor(part, 6)
+    ctx = gpu_run(r, 2, 2, 6)
+    assert ctx.gram_path() == 1
+    check_factors(ctx, model)
+    check_rmse(ctx, model, r)
+    forced = bs.Context(gram_path=2)
+    forced.partition(300, 200, r.u_train, r.i_train, r.x_train, 2, 2)
+    with pytest.raises(bs.BsvdError) as e:
+        forced.factor(6)
+    assert e.value.status == bs.EINVAL
