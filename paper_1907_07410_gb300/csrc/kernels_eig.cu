@@ -83,15 +83,34 @@ k_init_panels(const BlockMeta *__restrict__ meta,
 
 // out = alpha * G in + beta * in + gamma * in2, on rows [row0, row0 + 64).
 // G is symmetric, so the tile G[k0:k0+32, row0:row0+64] is read row-wise.
+//
+// 512 threads: four groups of 128 split the k range (group g takes chunks
+// g, g + 4, ...), each with its own shared buffers, named barrier and a
+// register prefetch of its next chunk, so four independent load streams
+// are in flight per CTA. Thread (ty, tx) of a group owns rows 4ty..4ty+3 and
+// columns tx*CN .. tx*CN+CN-1 (CN = B/8): 2 + CN/4 shared loads feed 4 CN
+// FMAs. The four partial tiles are then added in group order (a fixed
+// order, so results do not depend on scheduling) and the Chebyshev step is
+// applied.
 template <int B>
-__global__ void __launch_bounds__(256)
+struct PanelSmem {
+  float As[4][KC][TR + 4];
+  float Bs[4][KC][B + 4];
+};
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(128) : "memory");
+}
+
+template <int B>
+__global__ void __launch_bounds__(512, (B >= 64 ? 1 : 2))
 k_gpanel(const BlockMeta *__restrict__ meta,
          const SolverState *__restrict__ state,
          const int2 *__restrict__ rowtiles, const float *__restrict__ G,
          const float *in, const float *in2, float *out, int mode, int step) {
-  constexpr int CN = B / 16;               // output columns per thread
-  __shared__ __align__(16) float As[KC][TR + 4];
-  __shared__ __align__(16) float Bs[KC][B + 4];
+  constexpr int CN = B / 8;                // output columns per thread
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PanelSmem<B> &sm = *reinterpret_cast<PanelSmem<B> *>(smem_raw);
   const int2 t = rowtiles[blockIdx.x];
   const SolverState st = state[t.x];
   if (st.status != kRunning) return;
@@ -124,22 +143,21 @@ k_gpanel(const BlockMeta *__restrict__ meta,
     }
   }
 
-  const int tid = threadIdx.x;
-  const int ty = tid >> 4, tx = tid & 15;
+  const int g = threadIdx.x >> 7, tid = threadIdx.x & 127;
+  const int ty = tid >> 3, tx = tid & 7;
   float acc[4][CN];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < CN; ++c) acc[r][c] = 0.f;
 
-  // The next k-chunk is fetched into registers while the current one is
-  // multiplied from shared memory, so global (L2) latency overlaps compute.
-  constexpr int BV = (KC * B / 4 + 255) / 256;     // float4 of `in` per thread
-  float4 ga[2], gb[BV];
+  constexpr int AV = KC * TR / 4 / 128;            // float4 of G per thread
+  constexpr int BV = (KC * B / 4 + 127) / 128;     // float4 of `in` per thread
+  float4 ga[AV], gb[BV];
   auto fetch = [&](int k0) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int idx = tid + 256 * h;
+    for (int h = 0; h < AV; ++h) {
+      const int idx = tid + 128 * h;
       const int rr = idx >> 4, cc = (idx & 15) * 4;
       ga[h] = (row0 + cc < sp)
                   ? __ldg(reinterpret_cast<const float4 *>(
@@ -148,57 +166,87 @@ k_gpanel(const BlockMeta *__restrict__ meta,
     }
 #pragma unroll
     for (int h = 0; h < BV; ++h) {
-      const int idx = tid + 256 * h;
+      const int idx = tid + 128 * h;
       const int rr = idx / (B / 4), cc = (idx % (B / 4)) * 4;
       gb[h] = (idx < KC * B / 4)
                   ? *reinterpret_cast<const float4 *>(inb + (int64_t)(k0 + rr) * B + cc)
                   : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
-  fetch(0);
-  for (int k0 = 0; k0 < sp; k0 += KC) {
+  const int nchunks = sp / KC;
+  if (g < nchunks) fetch(g * KC);
+  for (int ch = g; ch < nchunks; ch += 4) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int idx = tid + 256 * h;
-      *reinterpret_cast<float4 *>(&As[idx >> 4][(idx & 15) * 4]) = ga[h];
+    for (int h = 0; h < AV; ++h) {
+      const int idx = tid + 128 * h;
+      *reinterpret_cast<float4 *>(&sm.As[g][idx >> 4][(idx & 15) * 4]) = ga[h];
     }
 #pragma unroll
     for (int h = 0; h < BV; ++h) {
-      const int idx = tid + 256 * h;
+      const int idx = tid + 128 * h;
       if (idx < KC * B / 4)
-        *reinterpret_cast<float4 *>(&Bs[idx / (B / 4)][(idx % (B / 4)) * 4]) = gb[h];
+        *reinterpret_cast<float4 *>(&sm.Bs[g][idx / (B / 4)][(idx % (B / 4)) * 4]) = gb[h];
     }
-    __syncthreads();
-    if (k0 + KC < sp) fetch(k0 + KC);
+    group_sync(g);
+    if (ch + 4 < nchunks) fetch((ch + 4) * KC);
 #pragma unroll 8
     for (int kk = 0; kk < KC; ++kk) {
       float a[4], b[CN];
       *reinterpret_cast<float4 *>(a) =
-          *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+          *reinterpret_cast<const float4 *>(&sm.As[g][kk][ty * 4]);
 #pragma unroll
-      for (int c = 0; c < CN; ++c) b[c] = Bs[kk][tx * CN + c];
+      for (int c = 0; c < CN; c += 4) {
+        if (CN >= 4) {
+          *reinterpret_cast<float4 *>(&b[c]) =
+              *reinterpret_cast<const float4 *>(&sm.Bs[g][kk][tx * CN + c]);
+        }
+      }
+      if (CN < 4) {
+#pragma unroll
+        for (int c = 0; c < CN; ++c) b[c] = sm.Bs[g][kk][tx * CN + c];
+      }
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < CN; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
     }
-    __syncthreads();
+    group_sync(g);
   }
+  // add the four partial tiles in group order, then apply the step
+  __syncthreads();
+  float (*red)[TR][B + 1] = reinterpret_cast<float (*)[TR][B + 1]>(smem_raw);
+  if (g > 0) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < CN; ++c) red[g - 1][ty * 4 + r][tx * CN + c] = acc[r][c];
+  }
+  __syncthreads();
+  if (g != 0) return;
   const float *in2b = in2 ? in2 + bm.x_off : nullptr;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const int row = row0 + ty * 4 + r;
+    const int lr = ty * 4 + r;
+    const int row = row0 + lr;
     if (row >= sp) continue;
 #pragma unroll
     for (int c = 0; c < CN; ++c) {
       const int col = tx * CN + c;
       const int64_t o = (int64_t)row * B + col;
-      float v = alpha * acc[r][c];
+      const float sum = ((acc[r][c] + red[0][lr][col]) + red[1][lr][col]) + red[2][lr][col];
+      float v = alpha * sum;
       if (beta != 0.f) v = fmaf(beta, inb[o], v);
       if (gamma != 0.f) v = fmaf(gamma, in2b[o], v);
       outb[o] = v;
     }
   }
+}
+
+template <int B>
+size_t panel_smem() {
+  const size_t a = sizeof(PanelSmem<B>);
+  const size_t r = sizeof(float) * 3 * TR * (B + 1);
+  return a > r ? a : r;
 }
 
 // Partial S = X^T X and H = X^T Z over the 64 rows of one row tile, for
@@ -841,8 +889,13 @@ cudaError_t launch_gpanel(const EigBuffers &e, const int2 *rowtiles,
   if (ntiles <= 0) return cudaSuccess;
   return by_width(e.bsub, [&](auto w) {
     constexpr int B = decltype(w)::value;
-    k_gpanel<B><<<ntiles, 256, 0, st>>>(e.meta, e.state, rowtiles, e.G, in,
-                                        in2, out, mode, step);
+    cudaError_t err = cudaFuncSetAttribute(
+        k_gpanel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)panel_smem<B>());
+    if (err != cudaSuccess) return err;
+    k_gpanel<B><<<ntiles, 512, panel_smem<B>(), st>>>(e.meta, e.state, rowtiles,
+                                                      e.G, in, in2, out, mode,
+                                                      step);
     return cudaGetLastError();
   });
 }
