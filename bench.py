@@ -183,6 +183,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default=synth.MEDIUM.name,
                     choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=("fp32", "tf32"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -215,7 +216,8 @@ def main():
     u_tr, i_tr, x_tr = dev(r.u_train), dev(r.i_train), dev(r.x_train)
     u_te, i_te, x_te = dev(r.u_test), dev(r.i_test), dev(r.x_test)
     stream = torch.cuda.current_stream()
-    ctx = bs.Context(stream=stream, profile=1)
+    ctx = bs.Context(stream=stream, profile=1,
+                     precision=0 if args.precision == "fp32" else 1)
     nblocks = w.p * w.q
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -295,7 +297,13 @@ def main():
     gram_ms = statistics.mean(phases["gram"])
     achieved = gflops / (gram_ms * 1e-3) / 1e12
     gram_path = ctx.gram_path()
-    if gram_path == 2:
+    if gram_path == 3:
+        # tf32 peak: the bf16 measurement scaled by the nominal ratio 1/2
+        roof = {"kernel": "k_gram_tf32", "bound": "tensor",
+                "peak": 0.5 * peaks.get("bf16_tflops", 1900.0),
+                "peak_source": "0.5 x bf16 dense burst, of %s" % peak_kind,
+                "traffic": None}
+    elif gram_path == 2:
         roof = {"kernel": "k_gram_tc", "bound": "tensor",
                 "peak": peaks.get("bf16_tflops", 1900.0),
                 "peak_source": "bf16 dense, burst, of %s" % peak_kind,
@@ -320,9 +328,9 @@ def main():
         "config": {"workload": w.name, "m": w.m, "n": w.n,
                    "nnz_train": int(r.u_train.size),
                    "nnz_test": int(r.u_test.size), "p": w.p, "q": w.q,
-                   "k": w.k, "precision": "fp32",
-                   "gram": "tensor cores, exact" if gram_path == 2
-                           else "fp32 simt",
+                   "k": w.k, "precision": args.precision,
+                   "gram": {1: "fp32 simt", 2: "tensor cores, exact",
+                            3: "tensor cores, tf32"}.get(gram_path, "none"),
                    "l2": "flushed (256 MB write) before each step, untimed"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},

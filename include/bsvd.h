@@ -60,7 +60,11 @@ typedef enum {
 } bsvd_status;
 
 typedef enum {
-    BSVD_FP32 = 0       /* float32 blocks, Gram products and solver */
+    BSVD_FP32 = 0,      /* float32 result: exact tensor-core Gram when the
+                           ratings allow it, else FP32 SIMT Gram */
+    BSVD_TF32 = 1       /* single-pass TF32 tensor-core Gram (inputs
+                           truncated to 10-bit mantissas); float32 solver,
+                           float64 norms for sigma */
 } bsvd_precision;
 
 typedef struct {
@@ -238,7 +242,8 @@ int64_t bsvd_kernel_launches(const bsvd_ctx *ctx);
 
 /*
  * Which Gram kernel the last bsvd_factor ran: 1 FP32 SIMT, 2 tensor cores
- * (exact), 0 none yet (or k = 0), -1 for a NULL context.
+ * (exact), 3 tensor cores (single-pass tf32), 0 none yet (or k = 0), -1
+ * for a NULL context.
  */
 int32_t bsvd_gram_path(const bsvd_ctx *ctx);
 

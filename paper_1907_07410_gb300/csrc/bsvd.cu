@@ -85,8 +85,9 @@ struct bsvd_ctx {
       d_maxabs, d_mu, d_W, d_err;
   // bf16 [Y; M] planes, per-block shift and delta, TMA maps (tensor Gram)
   bool tc_planes = false, tc_exact = false;
-  int32_t gram_used = 0;    // 1: FP32 SIMT, 2: tensor cores (last factor)
+  int32_t gram_used = 0;    // 1: FP32 SIMT, 2: exact tensor, 3: tf32 tensor
   DevBuf d_VX, d_shift, d_delta, d_maps, d_flag;
+  DevBuf d_wmaps;           // TMA maps over the float32 blocks (tf32 Gram)
 
   // factor
   bool factored = false;
@@ -250,7 +251,8 @@ bsvd_status bsvd_create(const bsvd_config *cfg, bsvd_ctx **out) {
     if (c->cfg.max_sweeps <= 0) c->cfg.max_sweeps = 30;
     if (!(c->cfg.tol > 0)) c->cfg.tol = 1e-5;
   }
-  if (c->cfg.precision != BSVD_FP32 || c->cfg.gram_path < 0 ||
+  if ((c->cfg.precision != BSVD_FP32 && c->cfg.precision != BSVD_TF32) ||
+      c->cfg.gram_path < 0 ||
       c->cfg.gram_path > 2 ||
       c->cfg.cheb_degree % 2 != 0 ||
       c->cfg.cheb_degree > 64 || (c->cfg.clamp && !(c->cfg.clamp_lo <= c->cfg.clamp_hi))) {
@@ -286,7 +288,8 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->d_FL, &c->d_sigma, &c->d_running, &c->d_gtiles,
                     &c->d_rowtiles, &c->d_ltiles, &c->s_a, &c->s_b, &c->s_c,
                     &c->s_out, &c->d_partials, &c->d_rmse, &c->d_VX,
-                    &c->d_shift, &c->d_delta, &c->d_maps, &c->d_flag};
+                    &c->d_shift, &c->d_delta, &c->d_maps, &c->d_flag,
+                    &c->d_wmaps};
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   for (DevBuf *b : bufs) b->release();
@@ -434,7 +437,7 @@ bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
      "partition: scatter");
   c->launches += nnz > 0 ? 3 : 1;
   // bf16 planes for the exact tensor-core Gram
-  c->tc_planes = c->cfg.gram_path != 1;
+  c->tc_planes = c->cfg.gram_path != 1 && c->cfg.precision == BSVD_FP32;
   c->tc_exact = false;
   if (c->tc_planes) {
     CK(c->d_VX.ensure(2 * std::max<int64_t>(vxoff, 1)), "partition");
@@ -491,6 +494,32 @@ bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
                     cudaMemcpyHostToDevice), "partition");
     }
   }
+  if (c->cfg.precision == BSVD_TF32) {
+    // one TMA map per block over its float32 W (s_pad x L_pad)
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return fail(c, BSVD_ECUDA, "partition: no cuTensorMapEncodeTiled");
+    std::vector<CUtensorMap> maps(nb);
+    std::memset(maps.data(), 0, sizeof(CUtensorMap) * nb);
+    for (int32_t b = 0; b < nb; ++b) {
+      const BlockMeta &bm = c->meta[b];
+      if (bm.s == 0) continue;
+      cuuint64_t dims[2] = {(cuuint64_t)bm.L_pad, (cuuint64_t)bm.s_pad};
+      cuuint64_t strides[1] = {(cuuint64_t)bm.L_pad * 4};
+      cuuint32_t box[2] = {32, 128};
+      cuuint32_t es[2] = {1, 1};
+      CUresult r = enc(&maps[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                       c->d_W.as<float>() + bm.w_off, dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(c, BSVD_ECUDA, "partition: tensor map %d failed (%d)", b,
+                    (int)r);
+    }
+    CK(c->d_wmaps.ensure(sizeof(CUtensorMap) * nb), "partition");
+    CK(cudaMemcpy(c->d_wmaps.p, maps.data(), sizeof(CUtensorMap) * nb,
+                  cudaMemcpyHostToDevice), "partition");
+  }
   c->parted = true;
   return BSVD_OK;
 }
@@ -500,7 +529,8 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
   c->err.clear();
   if (!c->parted) return fail(c, BSVD_ESTATE, "factor: no partition");
   if (k < 0 || k > 56) return fail(c, BSVD_EINVAL, "factor: k=%d outside [0, 56]", k);
-  if (c->cfg.gram_path == 2 && !(c->tc_planes && c->tc_exact))
+  if (c->cfg.precision == BSVD_FP32 && c->cfg.gram_path == 2 &&
+      !(c->tc_planes && c->tc_exact))
     return fail(c, BSVD_EINVAL,
                 "factor: tensor-core Gram needs ratings that are small integer "
                 "offsets from their block's rounded mean");
@@ -602,8 +632,15 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
     std::fill(c->phase_ms + 1, c->phase_ms + 4, 0.0);
     std::fill(c->phase_ms + 5, c->phase_ms + 8, 0.0);
     mark(c, 0);
-    c->gram_used = (c->tc_planes && c->tc_exact) ? 2 : 1;
-    if (c->gram_used == 2) {
+    c->gram_used = c->cfg.precision == BSVD_TF32
+                       ? 3
+                       : ((c->tc_planes && c->tc_exact) ? 2 : 1);
+    if (c->gram_used == 3) {
+      CK(launch_gram_tf32(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
+                          c->n_gtiles, c->d_wmaps.as<CUtensorMap>(), e.G,
+                          c->d_err.as<int32_t>(), c->st),
+         "factor: gram (tf32 tensor cores)");
+    } else if (c->gram_used == 2) {
       CK(launch_gram_tc(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
                         c->n_gtiles, c->d_maps.as<CUtensorMap>(),
                         c->d_delta.as<float>(), e.G, c->d_err.as<int32_t>(),

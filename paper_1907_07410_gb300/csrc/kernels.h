@@ -39,6 +39,12 @@ cudaError_t launch_gram_tc(const BlockMeta *meta, const int4 *tiles,
                            const float *delta, float *G, int32_t *err,
                            cudaStream_t st);
 
+// Single-pass tf32 Gram of the float32 blocks; maps: one TMA map per block
+// over W (s_pad x L_pad f32, 128 x 32 boxes, 128-byte swizzle).
+cudaError_t launch_gram_tf32(const BlockMeta *meta, const int4 *tiles,
+                             int32_t ntiles, const CUtensorMap *maps, float *G,
+                             int32_t *err, cudaStream_t st);
+
 // ---- bf16 planes for the tensor-core Gram (kernels_partition.cu) ----------
 // shift[b] = round(mu_b) (exact mean from the sums), delta[b] = mu_b - shift.
 cudaError_t launch_plane_shift(int32_t nblocks, const unsigned long long *counts,

@@ -190,7 +190,155 @@ k_gram_tc(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
   if (warp == 0) tc::tmem_dealloc(taddr, 512);
 }
 
+// Single-pass tf32 Gram G = W W^T on the float32 blocks (any rating scale;
+// inputs are truncated to tf32, ~1e-3 relative error in G). Same tiling and
+// roles as k_gram_tc, one accumulator, 6 stages of {W_i, W_j} 128 x 32-float
+// boxes.
+constexpr int KF = 32;                          // floats per k-chunk (128 B)
+constexpr int FSTAGES = 6;
+constexpr int FTILE_BYTES = TT * KF * 4;        // 16 KiB
+constexpr int FSTAGE_BYTES = 2 * FTILE_BYTES;
+
+struct CtrlF {
+  uint64_t full[FSTAGES];
+  uint64_t empty[FSTAGES];
+  uint64_t done;
+  uint32_t tmem;
+  int abort;
+  int issued;
+  int consumed;
+};
+
+constexpr size_t kSmemBytesF = FSTAGES * FSTAGE_BYTES + sizeof(CtrlF) + 1024;
+
+__global__ void __launch_bounds__(128, 1)
+k_gram_tf32(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
+            const CUtensorMap *__restrict__ maps, float *__restrict__ G,
+            int32_t *err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  CtrlF &ct = *reinterpret_cast<CtrlF *>(base + FSTAGES * FSTAGE_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int4 tl = tiles[blockIdx.x];
+  const BlockMeta bm = meta[tl.x];
+  const CUtensorMap *map = maps + tl.x;
+  const bool diag = tl.y == tl.z;
+  const int yi = tl.y * TT, yj = tl.z * TT;
+  const int nk = (bm.L_pad + KF - 1) / KF;
+
+  if (warp == 0) tc::tmem_alloc(&ct.tmem, 128);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < FSTAGES; ++s) {
+      tc::mbar_init(&ct.full[s], 1);
+      tc::mbar_init(&ct.empty[s], 1);
+    }
+    tc::mbar_init(&ct.done, 1);
+    ct.abort = 0;
+    ct.issued = 0;
+    ct.consumed = 0;
+    tc::mbar_init_fence();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = ct.tmem;
+
+  if (warp == 0 && lane == 0) {
+    const uint32_t bytes = (diag ? 1 : 2) * FTILE_BYTES;
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % FSTAGES;
+      const uint32_t ph = (kc / FSTAGES) & 1;
+      if (!tc::mbar_wait(&ct.empty[s], ph ^ 1, kSpin) ||
+          *reinterpret_cast<volatile int *>(&ct.abort)) {
+        atomicOr(err, kErrTimeout);
+        ct.abort = 1;
+        break;
+      }
+      unsigned char *buf = base + s * FSTAGE_BYTES;
+      const int x = kc * KF;
+      tc::mbar_expect_tx(&ct.full[s], bytes);
+      tc::tma_load_2d(buf, map, x, yi, &ct.full[s]);
+      if (!diag) tc::tma_load_2d(buf + FTILE_BYTES, map, x, yj, &ct.full[s]);
+      ct.issued = kc + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = tc::idesc_tf32_f32(TT, TT);
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % FSTAGES;
+      const uint32_t ph = (kc / FSTAGES) & 1;
+      if (!tc::mbar_wait(&ct.full[s], ph, kSpin) ||
+          *reinterpret_cast<volatile int *>(&ct.abort)) {
+        atomicOr(err, kErrTimeout);
+        ct.abort = 1;
+        break;
+      }
+      ct.consumed = kc + 1;
+      tc::fence_after_sync();
+      unsigned char *buf = base + s * FSTAGE_BYTES;
+      const uint64_t dwi = tc::sdesc_kmajor_sw128(tc::smem_u32(buf));
+      const uint64_t dwj = diag ? dwi : tc::sdesc_kmajor_sw128(tc::smem_u32(buf + FTILE_BYTES));
+#pragma unroll
+      for (int kk = 0; kk < KF / 8; ++kk) {
+        const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+        tc::mma_tf32(taddr, dwi + 2 * kk, dwj + 2 * kk, idesc, acc);
+      }
+      tc::mma_commit(&ct.empty[s]);
+    }
+    tc::mma_commit(&ct.done);
+  }
+  __syncwarp();
+
+  const bool ready = tc::mbar_wait(&ct.done, 0, kSpin);
+  if (!ready && lane == 0) atomicOr(err, kErrTimeout);
+  __syncwarp();
+  if (ready && !*reinterpret_cast<volatile int *>(&ct.abort)) {
+    tc::fence_after_sync();
+    const int sp = bm.s_pad;
+    const int gi = yi + warp * 32 + lane;
+    float *Gb = G + bm.g_off;
+    const uint32_t lrow = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TT; c0 += 32) {
+      float a[32];
+      tc::tmem_ld32(taddr + lrow + c0, a);
+      const int gj0 = yj + c0;
+      if (gj0 >= sp) continue;
+      if (gi < sp) {
+        float4 *dst = reinterpret_cast<float4 *>(Gb + (int64_t)gi * sp + gj0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          dst[j] = make_float4(a[4 * j], a[4 * j + 1], a[4 * j + 2], a[4 * j + 3]);
+        if (!diag) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) Gb[(int64_t)(gj0 + j) * sp + gi] = a[j];
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x == 0 && ct.abort) {
+    for (int kc = ct.consumed; kc < ct.issued; ++kc)
+      tc::mbar_wait(&ct.full[kc % FSTAGES], (kc / FSTAGES) & 1, kSpin);
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, 128);
+}
+
 }  // namespace
+
+cudaError_t launch_gram_tf32(const BlockMeta *meta, const int4 *tiles,
+                             int32_t ntiles, const CUtensorMap *maps, float *G,
+                             int32_t *err, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(
+      k_gram_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)kSmemBytesF);
+  if (e != cudaSuccess) return e;
+  k_gram_tf32<<<ntiles, 128, kSmemBytesF, st>>>(meta, tiles, maps, G, err);
+  return cudaGetLastError();
+}
 
 size_t gram_tc_smem_bytes() { return kSmemBytes; }
 

@@ -1,0 +1,80 @@
+"""The precision form: the medium matrix on 8 x 8 and 16 x 16 grids, with
+the exact tensor-core Gram (float32 result) and the single-pass TF32 Gram.
+
+Bars against the FP64 oracle: singular values relative 1e-5 (float32 path)
+or 2e-3 (tf32 path) on the retained top-k; rank-k reconstruction relative
+Frobenius 1e-4 / 5e-3 where the block's gap is at least 1e-3; held-out RMSE
+within 1e-4 on both paths.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1907_07410_gb300 as bs  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SIGMA = {0: 1e-5, 1: 2e-3}
+RECON = {0: 1e-4, 1: 5e-3}
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run(w, r, precision):
+    ctx = bs.Context(precision=precision)
+    ctx.partition(w.m, w.n, dev(r.u_train), dev(r.i_train), dev(r.x_train),
+                  w.p, w.q)
+    ctx.factor(w.k)
+    return ctx
+
+
+@pytest.mark.parametrize("name", ["medium-6040x3952-8x8-k20",
+                                  "medium-6040x3952-16x16-k20"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_grids_against_golden(name, precision):
+    w = synth.WORKLOADS[name]
+    g = json.load(open(os.path.join(HERE, "golden", name + ".json")))
+    r = synth.generate(w)
+    assert r.digest() == g["digest"]
+    ctx = run(w, r, precision)
+    assert ctx.gram_path() == (2 if precision == 0 else 3)
+    counts, mu = ctx.block_stats()
+    assert counts.tolist() == g["counts"]
+    worst = 0.0
+    for b in range(w.p * w.q):
+        s = ctx.get_block(b)["sigma"]
+        ref = np.array(g["sigma"][b][:len(s)])
+        worst = max(worst, float(np.max(np.abs(s - ref) / ref)))
+    rm = ctx.rmse(dev(r.u_test), dev(r.i_test), dev(r.x_test))
+    print("%s precision=%d worst sigma rel %.2e  rmse %.9f oracle %.9f"
+          % (name, precision, worst, rm, g["rmse"]))
+    assert worst <= SIGMA[precision]
+    assert abs(rm - g["rmse"]) <= 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_reconstruction_bars(precision):
+    """Two sampled blocks of the 8 x 8 grid, recomputed by the oracle."""
+    w = synth.MEDIUM_8x8
+    r = synth.generate(w)
+    part = oracle.partition(w.m, w.n, r.u_train, r.i_train, r.x_train, w.p,
+                            w.q)
+    model = oracle.factor(part, w.k, blocks=[0, 37])
+    ctx = run(w, r, precision)
+    for b, f in model.blocks.items():
+        if f.gap < 1e-3:
+            continue
+        R_ref = f.P @ f.V.T
+        R_got = ctx.reconstruct(b, add_mean=False).astype(np.float64)
+        rel = np.linalg.norm(R_got - R_ref) / np.linalg.norm(R_ref)
+        print("block %d precision=%d recon rel %.2e" % (b, precision, rel))
+        assert rel <= RECON[precision]
