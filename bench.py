@@ -261,9 +261,8 @@ def main():
     launches = ctx.kernel_launches() - launches0
     total_ms = sum(step_ms)
     if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        from paper_1907_07410_gb300 import dist as bdist
+        total_ms = bdist.max_over_ranks(total_ms)
 
     # ---- end to end through the public API with host buffers -------------
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
@@ -282,9 +281,7 @@ def main():
     barrier()
     e2e_total = sum(e2e_ms)
     if dist is not None:
-        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+        e2e_total = bdist.max_over_ranks(e2e_total)
 
     if rank != 0:
         if dist is not None:
