@@ -137,6 +137,24 @@ bsvd_status bsvd_partition(bsvd_ctx *ctx, int64_t m, int64_t n, int64_t nnz,
                            const int32_t *row_perm, const int32_t *col_perm);
 
 /*
+ * Partition a batch of independent rating matrices (Section 3's blocks
+ * used one by one; each is factorised as its own block). The nb matrices
+ * are stacked block-diagonally: matrix b owns rows [row_bounds[b],
+ * row_bounds[b+1]) and columns [col_bounds[b], col_bounds[b+1]) of one
+ * row_bounds[nb] x col_bounds[nb] matrix, and only these nb diagonal blocks
+ * exist (block b is matrix b). u, i, x as in bsvd_partition, in the
+ * stacked coordinates; a rating outside the diagonal blocks is an error.
+ * row_bounds, col_bounds: host arrays of nb + 1 non-decreasing positions
+ * starting at 0. Predictions take ids in the same stacked coordinates.
+ * Errors as bsvd_partition.
+ */
+bsvd_status bsvd_partition_diag(bsvd_ctx *ctx, int32_t nb,
+                                const int64_t *row_bounds,
+                                const int64_t *col_bounds, int64_t nnz,
+                                const int32_t *u, const int32_t *i,
+                                const float *x);
+
+/*
  * Truncated SVD of every block (Section 2, Eq. 1 and the rank-k truncation
  * after it): keep the k_eff = min(k, min(m_b, n_b)) largest singular values
  * of each centred block B_b and their singular vectors.
@@ -154,6 +172,12 @@ bsvd_status bsvd_partition(bsvd_ctx *ctx, int64_t m, int64_t n, int64_t nnz,
  * stored and usable), BSVD_ENOMEM, BSVD_ECUDA.
  */
 bsvd_status bsvd_factor(bsvd_ctx *ctx, int32_t k);
+
+/*
+ * bsvd_factor with a rank per block: ks is a host array of one k per block
+ * (p*q entries, or nb after bsvd_partition_diag), each in [0, 56].
+ */
+bsvd_status bsvd_factor_ks(bsvd_ctx *ctx, const int32_t *ks);
 
 /*
  * Predict nq ratings (Section 2.1, Eq. 2): yhat = mu_b + P_b[r,:] . V_b[c,:]

@@ -29,7 +29,7 @@ EXPORTS = ("bsvd_config_default", "bsvd_create", "bsvd_destroy",
            "bsvd_rmse", "bsvd_block_stats", "bsvd_get_block",
            "bsvd_reconstruct", "bsvd_factor_report", "bsvd_phase_times",
            "bsvd_kernel_launches", "bsvd_block_means_noalloc",
-           "bsvd_gram_path")
+           "bsvd_gram_path", "bsvd_partition_diag", "bsvd_factor_ks")
 
 
 class BsvdError(RuntimeError):
@@ -73,6 +73,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "bsvd_partition": (i32, [vp, i64, i64, i64, vp, vp, vp, i32, i32, vp,
                                  vp, vp, vp]),
         "bsvd_factor": (i32, [vp, i32]),
+        "bsvd_partition_diag": (i32, [vp, i32, vp, vp, i64, vp, vp, vp]),
+        "bsvd_factor_ks": (i32, [vp, vp]),
         "bsvd_predict": (i32, [vp, i64, vp, vp, vp]),
         "bsvd_rmse": (i32, [vp, i64, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]),
         "bsvd_block_stats": (i32, [vp, ctypes.POINTER(i32), vp, vp]),
@@ -179,6 +181,27 @@ def bsvd_partition(ctx, m, n, u, i, x, p, q, row_bounds=None, col_bounds=None,
         _ptr(cb, np.int64, "col_bounds"), _ptr(row_perm, np.int32, "row_perm"),
         _ptr(col_perm, np.int32, "col_perm"))
     return _check(ctx, st)
+
+
+def bsvd_partition_diag(ctx, row_bounds, col_bounds, u, i, x) -> int:
+    rb = np.ascontiguousarray(row_bounds, np.int64)
+    cb = np.ascontiguousarray(col_bounds, np.int64)
+    if rb.size != cb.size or rb.size < 2:
+        raise ValueError("row_bounds and col_bounds need nb + 1 entries")
+    nnz = _len(u)
+    if _len(i) != nnz or _len(x) != nnz:
+        raise ValueError("u, i, x must have the same length")
+    st = load().bsvd_partition_diag(
+        ctx, rb.size - 1, rb.ctypes.data, cb.ctypes.data, nnz,
+        _ptr(u, np.int32, "u"), _ptr(i, np.int32, "i"),
+        _ptr(x, np.float32, "x"))
+    return _check(ctx, st)
+
+
+def bsvd_factor_ks(ctx, ks) -> int:
+    ks = np.ascontiguousarray(ks, np.int32)
+    st = load().bsvd_factor_ks(ctx, ks.ctypes.data)
+    return _check(ctx, st, allow=(ENOTCONV,))
 
 
 def bsvd_factor(ctx, k) -> int:
@@ -358,8 +381,16 @@ class Context:
                        col_bounds, row_perm, col_perm)
         self.nblocks = p * q
 
+    def partition_diag(self, row_bounds, col_bounds, u, i, x):
+        bsvd_partition_diag(self.handle, row_bounds, col_bounds, u, i, x)
+        self.nblocks = len(row_bounds) - 1
+
     def factor(self, k, warn=True):
-        st = bsvd_factor(self.handle, k)
+        """k: one rank for every block, or a sequence of one per block."""
+        if np.ndim(k) == 0:
+            st = bsvd_factor(self.handle, int(k))
+        else:
+            st = bsvd_factor_ks(self.handle, k)
         self.last_status = st
         if st == ENOTCONV and warn:
             warnings.warn("bsvd_factor: " + bsvd_last_error(self.handle))

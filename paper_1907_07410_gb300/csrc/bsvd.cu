@@ -78,6 +78,7 @@ struct bsvd_ctx {
   int32_t p = 0, q = 0, nblocks = 0;
   std::vector<int64_t> rb, cb;
   bool eq_r = true, eq_c = true, has_rperm = false, has_cperm = false;
+  bool diag = false;        // block-diagonal batch of independent blocks
   int64_t br = 0, bc = 0;
   std::vector<BlockMeta> meta;
   int64_t arena = 0;
@@ -110,6 +111,8 @@ struct bsvd_ctx {
     g.m = m; g.n = n; g.p = p; g.q = q;
     g.equal_rows = eq_r ? 1 : 0;
     g.equal_cols = eq_c ? 1 : 0;
+    g.diag = diag ? 1 : 0;
+    g.pad = 0;
     g.br = br; g.bc = bc;
     g.row_bounds = d_rb.as<int64_t>();
     g.col_bounds = d_cb.as<int64_t>();
@@ -176,7 +179,7 @@ bsvd_status read_errors(bsvd_ctx *c, const char *what) {
   CK(cudaStreamSynchronize(c->st), what);
   if (h) {
     std::string msg = std::string(what) + ":";
-    if (h & kErrIndex) msg += " id out of range;";
+    if (h & kErrIndex) msg += " id out of range or off the block diagonal;";
     if (h & kErrValue) msg += " non-finite rating or |x| >= 2^31;";
     if (h & kErrSumRange) msg += " ratings too large for exact block sums;";
     if (h & kErrBadPerm) msg += " invalid permutation;";
@@ -262,7 +265,8 @@ bsvd_status bsvd_create(const bsvd_config *cfg, bsvd_ctx **out) {
   c->st = static_cast<cudaStream_t>(c->cfg.stream);
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       c->d_err.ensure(sizeof(int32_t)) != cudaSuccess ||
-      cudaMemset(c->d_err.p, 0, sizeof(int32_t)) != cudaSuccess) {
+      cudaMemsetAsync(c->d_err.p, 0, sizeof(int32_t), c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return BSVD_ECUDA;
@@ -302,12 +306,13 @@ const char *bsvd_last_error(const bsvd_ctx *c) {
   return c ? c->err.c_str() : "null context";
 }
 
-bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
-                           const int32_t *u, const int32_t *i,
-                           const float *x, int32_t p, int32_t q,
-                           const int64_t *row_bounds,
-                           const int64_t *col_bounds,
-                           const int32_t *row_perm, const int32_t *col_perm) {
+static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
+                                  int64_t nnz, const int32_t *u,
+                                  const int32_t *i, const float *x, int32_t p,
+                                  int32_t q, const int64_t *row_bounds,
+                                  const int64_t *col_bounds,
+                                  const int32_t *row_perm,
+                                  const int32_t *col_perm, bool diag) {
   if (!c) return BSVD_EINVAL;
   c->err.clear();
   if (m < 1 || n < 1 || m > INT32_MAX || n > INT32_MAX || nnz < 0)
@@ -327,7 +332,8 @@ bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
   c->parted = false;
   c->factored = false;
   c->m = m; c->n = n; c->nnz = nnz; c->p = p; c->q = q;
-  c->nblocks = p * q;
+  c->diag = diag;
+  c->nblocks = diag ? p : p * q;
   c->eq_r = row_bounds == nullptr;
   c->eq_c = col_bounds == nullptr;
   c->br = (m + p - 1) / p;
@@ -344,7 +350,8 @@ bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
   int64_t off = 0, vxoff = 0;
   for (int32_t bi = 0; bi < p; ++bi) {
     for (int32_t bj = 0; bj < q; ++bj) {
-      BlockMeta &bm = c->meta[bi * q + bj];
+      if (diag && bi != bj) continue;
+      BlockMeta &bm = c->meta[diag ? bi : bi * q + bj];
       std::memset(&bm, 0, sizeof bm);
       bm.mb = (int32_t)(c->rb[bi + 1] - c->rb[bi]);
       bm.nb = (int32_t)(c->cb[bj + 1] - c->cb[bj]);
@@ -463,8 +470,9 @@ bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
   take(c, 0, 0, 1);
   if (c->tc_planes) {
     int32_t flag = 0;
-    CK(cudaMemcpy(&flag, c->d_flag.p, sizeof flag, cudaMemcpyDeviceToHost),
-       "partition");
+    CK(cudaMemcpyAsync(&flag, c->d_flag.p, sizeof flag, cudaMemcpyDeviceToHost,
+                       c->st), "partition");
+    CK(cudaStreamSynchronize(c->st), "partition");
     c->tc_exact = (flag & kErrNotExact) == 0;
     if (c->tc_exact) {
       // one TMA map per block over its [Y; M] planes
@@ -490,8 +498,10 @@ bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
                       (int)r);
       }
       CK(c->d_maps.ensure(sizeof(CUtensorMap) * nb), "partition");
-      CK(cudaMemcpy(c->d_maps.p, maps.data(), sizeof(CUtensorMap) * nb,
-                    cudaMemcpyHostToDevice), "partition");
+      // stream-ordered: the context's stream may be a non-blocking one
+      CK(cudaMemcpyAsync(c->d_maps.p, maps.data(), sizeof(CUtensorMap) * nb,
+                         cudaMemcpyHostToDevice, c->st), "partition");
+      CK(cudaStreamSynchronize(c->st), "partition");
     }
   }
   if (c->cfg.precision == BSVD_TF32) {
@@ -517,17 +527,60 @@ bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
                     (int)r);
     }
     CK(c->d_wmaps.ensure(sizeof(CUtensorMap) * nb), "partition");
-    CK(cudaMemcpy(c->d_wmaps.p, maps.data(), sizeof(CUtensorMap) * nb,
-                  cudaMemcpyHostToDevice), "partition");
+    CK(cudaMemcpyAsync(c->d_wmaps.p, maps.data(), sizeof(CUtensorMap) * nb,
+                       cudaMemcpyHostToDevice, c->st), "partition");
+    CK(cudaStreamSynchronize(c->st), "partition");
   }
   c->parted = true;
   return BSVD_OK;
 }
 
+bsvd_status bsvd_partition(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
+                           const int32_t *u, const int32_t *i,
+                           const float *x, int32_t p, int32_t q,
+                           const int64_t *row_bounds,
+                           const int64_t *col_bounds,
+                           const int32_t *row_perm, const int32_t *col_perm) {
+  return partition_impl(c, m, n, nnz, u, i, x, p, q, row_bounds, col_bounds,
+                        row_perm, col_perm, false);
+}
+
+bsvd_status bsvd_partition_diag(bsvd_ctx *c, int32_t nb,
+                                const int64_t *row_bounds,
+                                const int64_t *col_bounds, int64_t nnz,
+                                const int32_t *u, const int32_t *i,
+                                const float *x) {
+  if (!c) return BSVD_EINVAL;
+  if (nb < 1 || !row_bounds || !col_bounds)
+    return fail(c, BSVD_EINVAL, "partition_diag: need nb >= 1 and bounds");
+  return partition_impl(c, row_bounds[nb], col_bounds[nb], nnz, u, i, x, nb,
+                        nb, row_bounds, col_bounds, nullptr, nullptr, true);
+}
+
+static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks);
+
 bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
+  return factor_impl(c, k, nullptr);
+}
+
+bsvd_status bsvd_factor_ks(bsvd_ctx *c, const int32_t *ks) {
+  if (!c) return BSVD_EINVAL;
+  if (!ks) return fail(c, BSVD_EINVAL, "factor_ks: null k array");
+  return factor_impl(c, 0, ks);
+}
+
+static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
   if (!c) return BSVD_EINVAL;
   c->err.clear();
   if (!c->parted) return fail(c, BSVD_ESTATE, "factor: no partition");
+  if (ks) {
+    k = 0;
+    for (int32_t b = 0; b < c->nblocks; ++b) {
+      if (ks[b] < 0 || ks[b] > 56)
+        return fail(c, BSVD_EINVAL, "factor: k[%d]=%d outside [0, 56]", b, ks[b]);
+      k = std::max(k, ks[b]);
+    }
+  }
   if (k < 0 || k > 56) return fail(c, BSVD_EINVAL, "factor: k=%d outside [0, 56]", k);
   if (c->cfg.precision == BSVD_FP32 && c->cfg.gram_path == 2 &&
       !(c->tc_planes && c->tc_exact))
@@ -547,7 +600,7 @@ bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
   std::vector<SolverState> st0(nb);
   for (int32_t b = 0; b < nb; ++b) {
     BlockMeta &bm = c->meta[b];
-    bm.keff = std::min(k, bm.s);
+    bm.keff = std::min(ks ? ks[b] : k, bm.s);
     bm.g_off = goff;
     bm.x_off = xoff;
     bm.fs_off = fsoff;

@@ -69,15 +69,19 @@ enum : int32_t {
 };
 
 // Grid description used by every kernel that maps (user, item) to a block.
+// Every field has a default, so a descriptor filled field by field never
+// carries an indeterminate value.
 struct GridDesc {
-  int64_t m, n;
-  int32_t p, q;
-  int32_t equal_rows, equal_cols;   // 1: equal ceil-sized blocks
-  int64_t br, bc;                   // equal block sizes
-  const int64_t *row_bounds;        // device, p + 1
-  const int64_t *col_bounds;        // device, q + 1
-  const int32_t *row_perm;          // device or null
-  const int32_t *col_perm;          // device or null
+  int64_t m = 0, n = 0;
+  int32_t p = 0, q = 0;
+  int32_t equal_rows = 0, equal_cols = 0;   // 1: equal ceil-sized blocks
+  int32_t diag = 0;                 // 1: only the p diagonal blocks exist
+  int32_t pad = 0;
+  int64_t br = 0, bc = 0;           // equal block sizes
+  const int64_t *row_bounds = nullptr;   // device, p + 1
+  const int64_t *col_bounds = nullptr;   // device, q + 1
+  const int32_t *row_perm = nullptr;     // device or null
+  const int32_t *col_perm = nullptr;     // device or null
 };
 
 // Largest j with bounds[j] <= v, for bounds[0] = 0 <= v < bounds[count].
@@ -103,7 +107,12 @@ __device__ __forceinline__ bool locate(const GridDesc &g, int32_t u,
   else bi = upper_index(g.row_bounds, g.p, ru);
   if (g.equal_cols) bj = (int32_t)(ci / g.bc);
   else bj = upper_index(g.col_bounds, g.q, ci);
-  *blk = bi * g.q + bj;
+  if (g.diag) {
+    if (bi != bj) return false;     // off the block diagonal
+    *blk = bi;
+  } else {
+    *blk = bi * g.q + bj;
+  }
   *r = (int32_t)(ru - g.row_bounds[bi]);
   *c = (int32_t)(ci - g.col_bounds[bj]);
   return true;

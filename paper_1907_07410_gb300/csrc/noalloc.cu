@@ -115,7 +115,7 @@ extern "C" bsvd_status bsvd_block_means_noalloc(
     k_equal_bounds<<<(q + 256) / 256, 256, 0, st>>>(sc->col_bounds, q, n, bc);
     e = cudaGetLastError();
   }
-  GridDesc g;
+  GridDesc g{};
   g.m = m; g.n = n; g.p = p; g.q = q;
   g.equal_rows = 1; g.equal_cols = 1;
   g.br = br; g.bc = bc;
