@@ -168,6 +168,32 @@ def make_grid(m, n, p, q, row_bounds=None, col_bounds=None, row_perm=None,
                 None if col_perm is None else np.asarray(col_perm, np.int64))
 
 
+def activity_quantile_cut(ids, size: int, parts: int):
+    """Uneven grid side for the batched form (reading of "split at activity
+    quantiles"): order ids by training-rating count, busiest first, ties by
+    lower id; cut where the ratings before the cut first reach g/parts of
+    all ratings (exact integer comparison parts * before >= g * total).
+    Returns (perm: id -> position, bounds: parts + 1 positions)."""
+    counts = [0] * size
+    for v in ids:
+        counts[int(v)] += 1
+    order = sorted(range(size), key=lambda x: (-counts[x], x))
+    perm = np.empty(size, np.int64)
+    for pos, x in enumerate(order):
+        perm[x] = pos
+    total = sum(counts)
+    bounds = [0]
+    before = 0
+    pos = 0
+    for g in range(1, parts):
+        while pos < size and parts * before < g * total:
+            before += counts[order[pos]]
+            pos += 1
+        bounds.append(pos)
+    bounds.append(size)
+    return perm, np.array(bounds, np.int64)
+
+
 @dataclasses.dataclass
 class Partition:
     grid: Grid
