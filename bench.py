@@ -6,6 +6,10 @@ eigen-solve, projection, held-out prediction and RMSE. The default workload
 is the MovieLens-1M-shaped matrix (6040 users x 3952 items, 1,000,209
 ratings, 90/10 split) on a 4 x 4 grid with k = 20.
 
+At N=1 the line also carries the served form ("served"): Poisson streams of
+factorise-then-predict requests through the continuous-batching server, at
+each --serve-rates rate, beside the same requests run one at a time.
+
 Prints one JSON line (rank 0). Usage:
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank solves its own copy of the workload (weak scaling;
@@ -55,13 +59,23 @@ def gram_flops(blocks):
     return float(sum(2.0 * L * s * s for (s, L) in blocks))
 
 
-def block_shapes(w):
+def grid_bounds(w, gridkw):
+    """Row and column bounds of the workload's grid."""
+    if gridkw:
+        return gridkw["row_bounds"], gridkw["col_bounds"]
     br, bc = -(-w.m // w.p), -(-w.n // w.q)
+    rb = np.minimum(np.arange(w.p + 1) * br, w.m)
+    cb = np.minimum(np.arange(w.q + 1) * bc, w.n)
+    return rb, cb
+
+
+def block_shapes(w, gridkw=None):
+    rb, cb = grid_bounds(w, gridkw)
     shapes = []
     for bi in range(w.p):
-        mb = min(w.m, (bi + 1) * br) - bi * br
+        mb = int(rb[bi + 1] - rb[bi])
         for bj in range(w.q):
-            nb = min(w.n, (bj + 1) * bc) - bj * bc
+            nb = int(cb[bj + 1] - cb[bj])
             shapes.append((min(mb, nb), max(mb, nb)))
     return shapes
 
@@ -127,15 +141,18 @@ def golden_rmse(w):
     return None
 
 
-def oracle_sample(w, r, nblocks, threads):
+def oracle_sample(w, r, nblocks, threads, gridkw=None):
     """The oracle (as it stands) on a bounded sample: partition of all the
-    ratings, factorisation of `nblocks` blocks, RMSE over their held-out
-    ratings. Returns (seconds, blocks)."""
+    ratings, factorisation of the `nblocks` blocks with the fewest cells
+    (lowest ids on ties), RMSE over their held-out ratings.
+    Returns (seconds, blocks)."""
     import oracle
     t0 = time.perf_counter()
     part = oracle.partition(w.m, w.n, r.u_train, r.i_train, r.x_train, w.p,
-                            w.q)
-    ids = list(range(min(nblocks, w.p * w.q)))
+                            w.q, **(gridkw or {}))
+    cells = [np.prod(part.grid.block_shape(b)) for b in range(w.p * w.q)]
+    ids = sorted(int(b) for b in
+                 np.argsort(cells, kind="stable")[:min(nblocks, w.p * w.q)])
     model = oracle.factor(part, w.k, blocks=ids, threads=threads)
     b, _, _ = part.grid.locate(r.u_test, r.i_test)
     sel = np.isin(b, ids)
@@ -149,16 +166,18 @@ def run_reference(args, w, r, rank):
     if rank != 0:
         return
     cores = min(os.cpu_count() or 1, w.p * w.q)
+    gridkw = host_grid(w, r)
     times = []
     for step in range(args.warmup + args.steps):
-        dt, nb = oracle_sample(w, r, cores, cores)
+        dt, nb = oracle_sample(w, r, cores, cores, gridkw)
         if step >= args.warmup:
             times.append(dt)
     total = sum(times)
     value = nb * len(times) / total
     sample = ("per step: oracle partition of all %d training ratings, FP64 "
-              "Jacobi SVD of %d of the %d blocks (one thread each), RMSE over "
-              "their held-out ratings" % (r.u_train.size, nb, w.p * w.q))
+              "Jacobi SVD of the %d smallest of the %d blocks (one thread "
+              "each), RMSE over their held-out ratings"
+              % (r.u_train.size, nb, w.p * w.q))
     line = {
         "impl": "reference", "metric": "block SVDs/s", "value": value,
         "unit": "block-SVDs/s", "n_gpus": args.gpus, "steps": args.steps,
@@ -175,16 +194,134 @@ def run_reference(args, w, r, rank):
     print(json.dumps(line), flush=True)
 
 
+def served_pool():
+    """The served form's request pool and the held-out ratings per request."""
+    from paper_1907_07410_gb300 import serve
+    pool, qy = [], []
+    for d in synth.served_requests(synth.SERVED_POOL_SEED,
+                                   synth.SERVED_POOL_SIZE, dense=False):
+        pool.append(serve.Request(d["m"], d["n"], d["k"], d["r"], d["c"],
+                                  d["x"], d["qr"], d["qc"]))
+        qy.append(d["qy"])
+    return pool, qy
+
+
+def poisson_run(srv, pool, rate, count, seed):
+    """Submit `count` copies of pool requests (cycling) at Poisson arrivals
+    of `rate` per second; return (results in submission order, seconds from
+    the first arrival to the last completion)."""
+    import dataclasses
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=count)
+    due = np.cumsum(gaps)
+    futs, reqs = [], []
+    t0 = time.perf_counter()
+    for j in range(count):
+        wait = t0 + due[j] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        q = dataclasses.replace(pool[j % len(pool)])
+        reqs.append(q)
+        futs.append(srv.submit(q))
+    res = [f.result(timeout=600) for f in futs]
+    span = max(q.arrival + r.latency for q, r in zip(reqs, res)) - min(
+        q.arrival for q in reqs)
+    return res, span
+
+
+def serve_leg(rates, workers=4, max_batch=64, budget=120e9):
+    """The served form: Poisson streams of factorise-then-predict requests
+    through the continuous-batching server at each rate, beside the same
+    requests run one at a time through one context."""
+    import paper_1907_07410_gb300 as bs
+    from paper_1907_07410_gb300 import serve
+    pool, qy = served_pool()
+    P = len(pool)
+    out = {"pool": P, "requests": "rows ~U[128,8192] x cols ~U[64,2048], "
+           "3-10% observed, k in {10,20,40}, 64 held-out queries each",
+           "workers": workers, "max_batch": max_batch,
+           "hbm_budget_gb": budget / 1e9, "sweep": []}
+    served_y = [None] * P
+    with serve.Server(workers=workers, max_batch=max_batch,
+                      hbm_budget=budget) as srv:
+        for f in [srv.submit(__import__("dataclasses").replace(q))
+                  for q in pool * 2]:
+            f.result(timeout=600)                  # warm-up: buffers, code
+        for n, rate in enumerate(rates):
+            count = int(min(max(rate * 2.0, 64), 1500))
+            nb0 = len(srv.batches)
+            res, span = poisson_run(srv, pool, rate, count, 1000 + n)
+            for j, r in enumerate(res[:P]):
+                served_y[j] = r.yhat
+            sizes = [len(ids) for ids, _ in srv.batches[nb0:]]
+            lat = serve.latency_percentiles(res)
+            out["sweep"].append({
+                "rate": rate, "requests": count,
+                "throughput_rps": count / span, "p50_ms": lat["p50_ms"],
+                "p99_ms": lat["p99_ms"],
+                "mean_batch": float(np.mean(sizes)),
+                "batches": len(sizes)})
+        out["max_in_flight"] = srv.max_in_flight
+        out["max_held_gb"] = srv.max_held / 1e9
+    # one at a time: one context, one request per call, no overlap
+    ctx = bs.Context()
+    for q in pool:
+        serve.run_batch(ctx, [q])
+    one_y, lat1 = [None] * P, []
+    t0 = time.perf_counter()
+    count1 = 2 * P
+    for j in range(count1):
+        t = time.perf_counter()
+        y = serve.run_batch(ctx, [pool[j % P]])[0]
+        lat1.append(time.perf_counter() - t)
+        one_y[j % P] = y
+    span1 = time.perf_counter() - t0
+    out["one_at_a_time"] = {
+        "requests": count1, "throughput_rps": count1 / span1,
+        "p50_ms": float(np.percentile(lat1, 50) * 1e3),
+        "p99_ms": float(np.percentile(lat1, 99) * 1e3)}
+    ctx.close()
+    err_s = np.concatenate([served_y[j] - qy[j] for j in range(P)])
+    err_1 = np.concatenate([one_y[j] - qy[j] for j in range(P)])
+    out["rmse"] = float(np.sqrt(np.mean(err_s.astype(np.float64) ** 2)))
+    out["rmse_one_at_a_time"] = float(np.sqrt(np.mean(
+        err_1.astype(np.float64) ** 2)))
+    out["max_abs_diff_served_vs_one"] = float(max(
+        np.max(np.abs(served_y[j] - one_y[j])) for j in range(P)))
+    gpath = os.path.join(ROOT, "tests", "golden",
+                         "served-pool-%d.json" % P)
+    if os.path.exists(gpath):
+        with open(gpath) as f:
+            g = json.load(f)
+        ids = [q["index"] for q in g["requests"]]
+        e = np.concatenate([served_y[j] - qy[j] for j in ids])
+        got = float(np.sqrt(np.mean(e.astype(np.float64) ** 2)))
+        out["rmse_oracle_subset"] = {
+            "requests": len(ids), "served": got, "oracle": g["rmse"],
+            "parity": abs(got - g["rmse"]) <= 1e-4}
+    return out
+
+
+def host_grid(w, r):
+    """Bounds and permutations of an activity-quantile grid (host side)."""
+    if w.grid != "quantile":
+        return None
+    from paper_1907_07410_gb300 import grid
+    return grid.quantile_grid(r.u_train, r.i_train, w.m, w.n, w.p, w.q)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default=synth.MEDIUM.name,
                     choices=sorted(synth.WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=("fp32", "tf32"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-rates", default="50,500,5000",
+                    help="Poisson rates (req/s) of the served-form leg; "
+                         "empty to skip it")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -213,6 +350,13 @@ def main():
         torch.cuda.synchronize()
 
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    gridkw = host_grid(w, r)
+    pkw = {}
+    if gridkw:
+        pkw = dict(row_bounds=gridkw["row_bounds"],
+                   col_bounds=gridkw["col_bounds"],
+                   row_perm=dev(gridkw["row_perm"]),
+                   col_perm=dev(gridkw["col_perm"]))
     u_tr, i_tr, x_tr = dev(r.u_train), dev(r.i_train), dev(r.x_train)
     u_te, i_te, x_te = dev(r.u_test), dev(r.i_test), dev(r.x_test)
     stream = torch.cuda.current_stream()
@@ -222,7 +366,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step():
-        ctx.partition(w.m, w.n, u_tr, i_tr, x_tr, w.p, w.q)
+        ctx.partition(w.m, w.n, u_tr, i_tr, x_tr, w.p, w.q, **pkw)
         ctx.factor(w.k)
         return ctx.rmse(u_te, i_te, x_te)
 
@@ -241,8 +385,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        part_ph = None
-        ctx.partition(w.m, w.n, u_tr, i_tr, x_tr, w.p, w.q)
+        ctx.partition(w.m, w.n, u_tr, i_tr, x_tr, w.p, w.q, **pkw)
         part_ph = ctx.phase_times()["partition"]
         ctx.factor(w.k)
         fac_ph = ctx.phase_times()
@@ -268,13 +411,19 @@ def main():
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
     h_u, h_i, h_x = pin(r.u_train), pin(r.i_train), pin(r.x_train)
     h_ut, h_it, h_xt = pin(r.u_test), pin(r.i_test), pin(r.x_test)
+    pkw_host = {}
+    if gridkw:
+        pkw_host = dict(row_bounds=gridkw["row_bounds"],
+                        col_bounds=gridkw["col_bounds"],
+                        row_perm=pin(gridkw["row_perm"]),
+                        col_perm=pin(gridkw["col_perm"]))
     e2e_ms = []
     barrier()
     for _ in range(args.steps):
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.partition(w.m, w.n, h_u, h_i, h_x, w.p, w.q)
+        ctx.partition(w.m, w.n, h_u, h_i, h_x, w.p, w.q, **pkw_host)
         ctx.factor(w.k)
         rm_e2e = ctx.rmse(h_ut, h_it, h_xt)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
@@ -289,7 +438,7 @@ def main():
         return
 
     peaks, peak_kind = load_peaks()
-    shapes = block_shapes(w)
+    shapes = block_shapes(w, gridkw)
     gflops = gram_flops(shapes)
     gram_ms = statistics.mean(phases["gram"])
     achieved = gflops / (gram_ms * 1e-3) / 1e12
@@ -344,19 +493,23 @@ def main():
         "gpu_launches": int(launches),
         "e2e": {"value": world * nblocks * args.steps / (e2e_total * 1e-3),
                 "unit": "block-SVDs/s",
-                "h2d_bytes_per_step": int(12 * (r.u_train.size + r.u_test.size)),
+                "h2d_bytes_per_step": int(12 * (r.u_train.size + r.u_test.size)
+                                          + (4 * (w.m + w.n) if gridkw else 0)),
                 "d2h_bytes_per_step": 8, "rmse": rm_e2e},
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:
         cores = min(os.cpu_count() or 1, nblocks)
-        dt, nb = oracle_sample(w, r, cores, cores)
+        dt, nb = oracle_sample(w, r, cores, cores, gridkw)
         line["cpu_baseline"] = {
             "value": nb / dt, "unit": "block-SVDs/s", "cores": cores,
             "kind": "oracle",
             "sample": "oracle partition of all ratings + FP64 Jacobi SVD of "
-                      "%d of %d blocks (one thread each) + their held-out "
-                      "RMSE, %.1f s" % (nb, nblocks, dt)}
+                      "the %d smallest of %d blocks (one thread each) + their "
+                      "held-out RMSE, %.1f s" % (nb, nblocks, dt)}
+    rates = [float(v) for v in args.serve_rates.split(",") if v.strip()]
+    if world == 1 and rates:
+        line["served"] = serve_leg(rates)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -49,6 +49,7 @@ class Workload:
     seed_index: int
     min_per_user: int = 20
     held_out_frac: float = 0.1
+    grid: str = "equal"    # "equal" blocks or "quantile" (activity) cuts
 
     @property
     def seed(self) -> int:
@@ -67,10 +68,15 @@ MEDIUM_8x8 = dataclasses.replace(MEDIUM, name="medium-6040x3952-8x8-k20",
 MEDIUM_16x16 = dataclasses.replace(MEDIUM, name="medium-6040x3952-16x16-k20",
                                    p=16, q=16)
 LARGE = Workload("large-480189x17770-32x8-k40", 480_189, 17_770, 100_480_507,
-                 40, 1.2, 0.9, 32, 8, 40, 3)
+                 40, 1.2, 0.9, 32, 8, 40, 3, grid="quantile")
+
+# A mid-size long-tailed matrix for the uneven (activity-quantile) grid,
+# small enough for the oracle to factorise every block.
+UNEVEN = Workload("uneven-20000x3000-8x4-k40", 20_000, 3_000, 1_500_000, 40,
+                  1.2, 0.9, 8, 4, 40, 4, grid="quantile")
 
 WORKLOADS = {w.name: w for w in (SMALL, MEDIUM, MEDIUM_8x8, MEDIUM_16x16,
-                                 LARGE)}
+                                 LARGE, UNEVEN)}
 
 
 @dataclasses.dataclass
@@ -247,17 +253,26 @@ def random_ratings(seed: int, m: int, n: int, nnz_train: int,
                    uu[nnz_train:], ii[nnz_train:], x[nnz_train:])
 
 
+# The request pool of the served form: 32 requests drawn by served_requests
+# with this seed (shapes rows ~U[128, 8192], cols ~U[64, 2048]).
+SERVED_POOL_SEED = 20190717
+SERVED_POOL_SIZE = 32
+
+
 def served_requests(seed: int, count: int,
                     ks: tuple[int, ...] = (10, 20, 40),
                     rows: tuple[int, int] = (128, 8192),
                     cols: tuple[int, int] = (64, 2048),
                     density: tuple[float, float] = (0.03, 0.10),
-                    d: int = 10, queries: int = 64) -> list[dict]:
+                    d: int = 10, queries: int = 64,
+                    dense: bool = True) -> list[dict]:
     """Dense single-block requests for the served form.
 
-    Each request is an m_b x n_b float32 matrix whose zeros mean "missing",
-    a rank k and ``queries`` held-out (row, col, rating) triples taken out of
-    the observed cells. Ratings follow the same latent model as ``generate``.
+    Each request is an m_b x n_b float32 matrix whose zeros mean "missing"
+    (``dense``; the same cells as COO in ``r``, ``c``, ``x``), a rank k and
+    ``queries`` held-out (row, col, rating) triples taken out of the
+    observed cells. Ratings follow the same latent model as ``generate``.
+    ``dense=False`` leaves the dense matrix out (None).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
@@ -276,11 +291,15 @@ def served_requests(seed: int, count: int,
             3.5 + np.einsum("ij,ij->i", U[r], V[c])
             + rng.normal(0.0, 0.8, size=nobs)), 1, 5).astype(np.float32)
         q = rng.permutation(nobs)[:queries]
-        dense = np.zeros((mb, nb), np.float32)
         keep = np.ones(nobs, bool)
         keep[q] = False
-        dense[r[keep], c[keep]] = val[keep]
-        out.append(dict(m=mb, n=nb, k=k, dense=dense,
+        full = None
+        if dense:
+            full = np.zeros((mb, nb), np.float32)
+            full[r[keep], c[keep]] = val[keep]
+        out.append(dict(m=mb, n=nb, k=k, dense=full,
+                        r=r[keep].astype(np.int32), c=c[keep].astype(np.int32),
+                        x=val[keep],
                         qr=r[q].astype(np.int32), qc=c[q].astype(np.int32),
                         qy=val[q]))
     return out

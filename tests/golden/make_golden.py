@@ -1,9 +1,10 @@
-"""Write the oracle's results for the medium workloads to JSON fixtures.
+"""Write the oracle's results for the synthetic workloads to JSON fixtures
+(``served`` selects the served form's request pool).
 
 Calls only ``oracle`` and the seeded generator ``synth``: no stored value
 here comes from the CUDA library. Run from the repository root:
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py [workload names | served]
 """
 from __future__ import annotations
 
@@ -24,8 +25,13 @@ import synth  # noqa: E402
 def golden(w: synth.Workload) -> dict:
     r = synth.generate(w)
     t0 = time.time()
+    grid = {}
+    if w.grid == "quantile":
+        rp, rb = oracle.activity_quantile_cut(r.u_train, w.m, w.p)
+        cp, cb = oracle.activity_quantile_cut(r.i_train, w.n, w.q)
+        grid = dict(row_bounds=rb, col_bounds=cb, row_perm=rp, col_perm=cp)
     part = oracle.partition(w.m, w.n, r.u_train, r.i_train, r.x_train, w.p,
-                            w.q)
+                            w.q, **grid)
     model = oracle.factor(part, w.k)
     rmse = oracle.rmse(model, r.u_test, r.i_test, r.x_test)
     yhat = oracle.predict(model, r.u_test, r.i_test)
@@ -37,15 +43,57 @@ def golden(w: synth.Workload) -> dict:
                for b in range(w.p * w.q)],
         gap=[model.blocks[b].gap for b in range(w.p * w.q)],
         rmse=rmse,
+        row_bounds=part.grid.row_bounds.tolist(),
+        col_bounds=part.grid.col_bounds.tolist(),
         yhat_first_1000=yhat[:1000].tolist(),
         oracle_seconds=time.time() - t0,
     )
     return out
 
 
+SERVED_MAX_COST = 2e9   # m_b * n_b * min(m_b, n_b): the oracle's Jacobi work
+
+
+def served_golden() -> dict:
+    """The oracle on the cheaper requests of the served pool (each a 1 x 1
+    grid): predictions for its held-out queries, top singular values and
+    the RMSE over those queries."""
+    import concurrent.futures as cf
+    pool = synth.served_requests(synth.SERVED_POOL_SEED,
+                                 synth.SERVED_POOL_SIZE, dense=False)
+    ids = [j for j, d in enumerate(pool)
+           if d["m"] * d["n"] * min(d["m"], d["n"]) <= SERVED_MAX_COST]
+    t0 = time.time()
+
+    def one(j):
+        d = pool[j]
+        part = oracle.partition(d["m"], d["n"], d["r"], d["c"], d["x"], 1, 1)
+        model = oracle.factor(part, d["k"], threads=1)
+        f = model.blocks[0]
+        return dict(index=j, m=d["m"], n=d["n"], k=d["k"], nnz=len(d["r"]),
+                    mu64=float(part.mu64[0]),
+                    sigma=f.sigma[:d["k"] + 1].tolist(), gap=f.gap,
+                    yhat=oracle.predict(model, d["qr"], d["qc"]).tolist())
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        reqs = list(ex.map(one, ids))
+    err = np.concatenate([np.array(q["yhat"]) - pool[q["index"]]["qy"]
+                          for q in reqs])
+    return dict(workload="served-pool-%d" % synth.SERVED_POOL_SIZE,
+                seed=synth.SERVED_POOL_SEED, max_cost=SERVED_MAX_COST,
+                requests=reqs, rmse=float(np.sqrt(np.mean(err ** 2))),
+                oracle_seconds=time.time() - t0)
+
+
 def main():
     names = sys.argv[1:] or [synth.MEDIUM.name]
     for name in names:
+        if name == "served":
+            g = served_golden()
+            path = os.path.join(HERE, g["workload"] + ".json")
+            with open(path, "w") as f:
+                json.dump(g, f, indent=1)
+            print(path, "rmse", g["rmse"], "%.1fs" % g["oracle_seconds"])
+            continue
         w = synth.WORKLOADS[name]
         g = golden(w)
         path = os.path.join(HERE, w.name + ".json")
