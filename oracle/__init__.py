@@ -54,13 +54,16 @@ MAX_SWEEPS = 60
 
 
 def build(force: bool = False) -> str:
-    """Compile the C Jacobi routine (plain gcc, no architecture flags)."""
+    """Compile the C Jacobi routine (plain gcc, no architecture flags), and
+    the blocked-SGD pass of ``oracle.sgd``."""
     if force or not os.path.exists(_LIB) or (
             os.path.getmtime(_LIB) < os.path.getmtime(_SRC)):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+    from . import sgd
+    sgd.build(force)
     return _LIB
 
 
