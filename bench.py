@@ -38,6 +38,7 @@ SMS = 152
 # DRAM bytes (read + write) of one k_gram_tc launch, from the ncu capture
 # summarised in profiles/k_gram_tc_medium-4x4-k20.md; None until captured.
 GRAM_TC_TRAFFIC = {"medium-6040x3952-4x4-k20": 133.9e6}
+GRAM_BF16_TRAFFIC = {}
 
 
 def load_peaks():
@@ -317,7 +318,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default=synth.MEDIUM.name,
                     choices=sorted(synth.WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=("fp32", "tf32"))
+    ap.add_argument("--precision", default="fp32",
+                    choices=("fp32", "tf32", "bf16"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-rates", default="50,500,5000",
                     help="Poisson rates (req/s) of the served-form leg; "
@@ -361,7 +363,8 @@ def main():
     u_te, i_te, x_te = dev(r.u_test), dev(r.i_test), dev(r.x_test)
     stream = torch.cuda.current_stream()
     ctx = bs.Context(stream=stream, profile=1,
-                     precision=0 if args.precision == "fp32" else 1)
+                     precision={"fp32": bs.FP32, "tf32": bs.TF32,
+                                "bf16": bs.BF16}[args.precision])
     nblocks = w.p * w.q
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -443,7 +446,12 @@ def main():
     gram_ms = statistics.mean(phases["gram"])
     achieved = gflops / (gram_ms * 1e-3) / 1e12
     gram_path = ctx.gram_path()
-    if gram_path == 3:
+    if gram_path == 4:
+        roof = {"kernel": "k_gram_bf16", "bound": "tensor",
+                "peak": peaks.get("bf16_tflops", 1900.0),
+                "peak_source": "bf16 dense, burst, of %s" % peak_kind,
+                "traffic": GRAM_BF16_TRAFFIC.get(w.name)}
+    elif gram_path == 3:
         # tf32 peak: the bf16 measurement scaled by the nominal ratio 1/2
         roof = {"kernel": "k_gram_tf32", "bound": "tensor",
                 "peak": 0.5 * peaks.get("bf16_tflops", 1900.0),
@@ -469,14 +477,17 @@ def main():
         "metric": "block SVDs/s", "value": value, "unit": "block-SVDs/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "tf32": "tf32 gram, f32",
+                  "bf16": "bf16 gram, f32"}[args.precision],
         "data": "synthetic (seeded MovieLens-1M-shaped ratings, in HBM)",
         "config": {"workload": w.name, "m": w.m, "n": w.n,
                    "nnz_train": int(r.u_train.size),
                    "nnz_test": int(r.u_test.size), "p": w.p, "q": w.q,
                    "k": w.k, "precision": args.precision,
                    "gram": {1: "fp32 simt", 2: "tensor cores, exact",
-                            3: "tensor cores, tf32"}.get(gram_path, "none"),
+                            3: "tensor cores, tf32",
+                            4: "tensor cores, bf16"}.get(gram_path, "none"),
                    "l2": "flushed (256 MB write) before each step, untimed"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},

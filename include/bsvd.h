@@ -62,8 +62,12 @@ typedef enum {
 typedef enum {
     BSVD_FP32 = 0,      /* float32 result: exact tensor-core Gram when the
                            ratings allow it, else FP32 SIMT Gram */
-    BSVD_TF32 = 1       /* single-pass TF32 tensor-core Gram (inputs
+    BSVD_TF32 = 1,      /* single-pass TF32 tensor-core Gram (inputs
                            truncated to 10-bit mantissas); float32 solver,
+                           float64 norms for sigma */
+    BSVD_BF16 = 2       /* single-pass BF16 tensor-core Gram over a bf16
+                           copy of the centred blocks (8-bit mantissas),
+                           f32 accumulation; float32 solver and projection,
                            float64 norms for sigma */
 } bsvd_precision;
 
@@ -78,13 +82,18 @@ typedef struct {
     int32_t max_iters;    /* subspace iterations cap; <= 0: default (30) */
     int32_t max_sweeps;   /* Jacobi sweeps cap per small solve; <= 0: 30 */
     int32_t profile;      /* 1: time each phase with CUDA events */
-    int32_t gram_path;    /* 0: tensor cores when exact, else FP32 SIMT;
-                             1: FP32 SIMT always; 2: tensor cores or
-                             BSVD_EINVAL from bsvd_factor */
+    int32_t gram_path;    /* BSVD_FP32 only (the others always use their
+                             tensor-core Gram). 0: tensor cores when exact,
+                             else FP32 SIMT; 1: FP32 SIMT always; 2: tensor
+                             cores or BSVD_EINVAL from bsvd_factor */
     double tol;           /* residual |G v - theta v| <= tol * theta_1;
                              <= 0: default (1e-5) */
     uint64_t seed;        /* seed of the start basis */
     void *stream;         /* cudaStream_t, or NULL for the default stream */
+    int32_t panel_path;   /* panel products G X of the eigen-solver:
+                             0: tensor cores (three tf32 passes, float32
+                             accuracy); 1: FP32 SIMT */
+    int32_t reserved;     /* must be 0 */
 } bsvd_config;
 
 /* Fill *cfg with the defaults listed above. */
@@ -162,9 +171,11 @@ bsvd_status bsvd_partition_diag(bsvd_ctx *ctx, int32_t nb,
  * The library forms the Gram matrix of the block's shorter side and finds
  * its top eigenpairs by Chebyshev-filtered subspace iteration with
  * Rayleigh-Ritz steps solved by Jacobi. Factors stay on the device.
- * The Gram runs on the tensor cores, exactly, when every rating minus its
- * block's rounded mean is a small integer (integer rating scales), else on
- * the FP32 SIMT pipes; gram_path in the config can force either.
+ * With BSVD_FP32 the Gram runs on the tensor cores, exactly, when every
+ * rating minus its block's rounded mean is a small integer (integer rating
+ * scales), else on the FP32 SIMT pipes; gram_path in the config can force
+ * either. BSVD_TF32 and BSVD_BF16 run a single reduced-precision product
+ * on the tensor cores.
  * k >= 0; k = 0 keeps no factor (predictions are then the block means).
  * The limit is k <= 56.
  * Errors: BSVD_ESTATE (no partition), BSVD_EINVAL (k out of range),
@@ -236,13 +247,15 @@ bsvd_status bsvd_reconstruct(bsvd_ctx *ctx, int32_t b, int32_t add_mean,
 /*
  * Per-block solver report after bsvd_factor (host arrays of p*q entries,
  * any may be NULL): Rayleigh-Ritz steps used, 1 where the block converged,
- * Jacobi sweeps summed over the steps, and SM clock cycles spent in the
+ * Jacobi sweeps summed over the steps, SM clock cycles spent in the
  * Rayleigh-Ritz kernel (3 per block: partial sums + Cholesky QR + H',
- * Jacobi, ordering + output), summed over the steps.
+ * Jacobi, ordering + output) summed over the steps, and the last
+ * relative residual max_i |G v_i - theta_i v_i| / theta_1 over the k_eff
+ * wanted pairs (converged means <= tol).
  */
 bsvd_status bsvd_factor_report(bsvd_ctx *ctx, int32_t *iters,
                                int32_t *converged, int32_t *sweeps,
-                               int64_t *cycles);
+                               int64_t *cycles, float *resid);
 
 /*
  * Phase timings of the last calls, in milliseconds of device time between
@@ -266,8 +279,8 @@ int64_t bsvd_kernel_launches(const bsvd_ctx *ctx);
 
 /*
  * Which Gram kernel the last bsvd_factor ran: 1 FP32 SIMT, 2 tensor cores
- * (exact), 3 tensor cores (single-pass tf32), 0 none yet (or k = 0), -1
- * for a NULL context.
+ * (exact), 3 tensor cores (single-pass tf32), 4 tensor cores (single-pass
+ * bf16), 0 none yet (or k = 0), -1 for a NULL context.
  */
 int32_t bsvd_gram_path(const bsvd_ctx *ctx);
 

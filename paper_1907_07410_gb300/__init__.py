@@ -20,6 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbsvd.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT, ESTATE = range(7)
+FP32, TF32, BF16 = range(3)           # bsvd_precision
 STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
                 ENOTCONV: "ENOTCONV", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
 
@@ -46,7 +47,8 @@ class Config(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("max_sweeps", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("gram_path", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("panel_path", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -281,11 +283,14 @@ def bsvd_factor_report(ctx, nblocks: int, full: bool = False):
     conv = np.zeros(nblocks, np.int32)
     sweeps = np.zeros(nblocks, np.int32)
     cycles = np.zeros((nblocks, 3), np.int64)
+    resid = np.zeros(nblocks, np.float32)
     st = load().bsvd_factor_report(ctx, iters.ctypes.data, conv.ctypes.data,
-                                   sweeps.ctypes.data, cycles.ctypes.data)
+                                   sweeps.ctypes.data, cycles.ctypes.data,
+                                   resid.ctypes.data)
     _check(ctx, st)
     if full:
-        return dict(iters=iters, converged=conv, sweeps=sweeps, cycles=cycles)
+        return dict(iters=iters, converged=conv, sweeps=sweeps, cycles=cycles,
+                    resid=resid)
     return iters, conv
 
 

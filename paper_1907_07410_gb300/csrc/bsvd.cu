@@ -86,7 +86,7 @@ struct bsvd_ctx {
       d_maxabs, d_mu, d_W, d_err;
   // bf16 [Y; M] planes, per-block shift and delta, TMA maps (tensor Gram)
   bool tc_planes = false, tc_exact = false;
-  int32_t gram_used = 0;    // 1: FP32 SIMT, 2: exact tensor, 3: tf32 tensor
+  int32_t gram_used = 0;    // 1: FP32 SIMT, 2: exact tensor, 3: tf32, 4: bf16
   DevBuf d_VX, d_shift, d_delta, d_maps, d_flag;
   DevBuf d_wmaps;           // TMA maps over the float32 blocks (tf32 Gram)
 
@@ -96,6 +96,10 @@ struct bsvd_ctx {
   DevBuf d_G, d_X, d_Z, d_SH, d_RP, d_T, d_theta, d_state, d_Fs, d_FL, d_sigma,
       d_running, d_gtiles, d_rowtiles, d_ltiles;
   int32_t n_gtiles = 0, n_rowtiles = 0, n_ltiles = 0;
+  // tensor-core panel products: 128-row tiles and one TMA map per block of G
+  DevBuf d_ptiles, d_gmaps, d_xmaps;
+  int32_t n_ptiles = 0;
+  std::vector<CUtensorMap> h_gmaps, h_xmaps;
   bool any_capped = false;
 
   // staging of host arguments and results
@@ -239,6 +243,8 @@ void bsvd_config_default(bsvd_config *cfg) {
   cfg->tol = 1e-5;
   cfg->seed = 0x5eed5eedull;
   cfg->stream = nullptr;
+  cfg->panel_path = 0;
+  cfg->reserved = 0;
 }
 
 bsvd_status bsvd_create(const bsvd_config *cfg, bsvd_ctx **out) {
@@ -254,9 +260,11 @@ bsvd_status bsvd_create(const bsvd_config *cfg, bsvd_ctx **out) {
     if (c->cfg.max_sweeps <= 0) c->cfg.max_sweeps = 30;
     if (!(c->cfg.tol > 0)) c->cfg.tol = 1e-5;
   }
-  if ((c->cfg.precision != BSVD_FP32 && c->cfg.precision != BSVD_TF32) ||
+  if ((c->cfg.precision != BSVD_FP32 && c->cfg.precision != BSVD_TF32 &&
+       c->cfg.precision != BSVD_BF16) ||
       c->cfg.gram_path < 0 ||
-      c->cfg.gram_path > 2 ||
+      c->cfg.gram_path > 2 || c->cfg.panel_path < 0 ||
+      c->cfg.panel_path > 1 || c->cfg.reserved != 0 ||
       c->cfg.cheb_degree % 2 != 0 ||
       c->cfg.cheb_degree > 64 || (c->cfg.clamp && !(c->cfg.clamp_lo <= c->cfg.clamp_hi))) {
     delete c;
@@ -293,7 +301,7 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->d_rowtiles, &c->d_ltiles, &c->s_a, &c->s_b, &c->s_c,
                     &c->s_out, &c->d_partials, &c->d_rmse, &c->d_VX,
                     &c->d_shift, &c->d_delta, &c->d_maps, &c->d_flag,
-                    &c->d_wmaps};
+                    &c->d_wmaps, &c->d_ptiles, &c->d_gmaps, &c->d_xmaps};
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   for (DevBuf *b : bufs) b->release();
@@ -366,7 +374,9 @@ static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
       off += (int64_t)bm.s_pad * bm.L_pad;
       bm.s128 = (int32_t)round_up(bm.s, 128);
       bm.vx_off = vxoff;
-      vxoff += 2 * (int64_t)bm.s128 * bm.L_pad;
+      // exact Gram: planes [Y; M]; bf16 Gram: one bf16 copy of W
+      vxoff += (c->cfg.precision == BSVD_BF16 ? 1 : 2) * (int64_t)bm.s128 *
+               bm.L_pad;
     }
   }
   c->arena = off;
@@ -438,9 +448,16 @@ static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
                   c->d_sums.as<long long>(), c->d_maxabs.as<unsigned int>(),
                   c->d_mu.as<float>(), c->d_err.as<int32_t>(), c->st),
      "partition: means");
+  __nv_bfloat16 *wh = nullptr;
+  if (c->cfg.precision == BSVD_BF16) {
+    CK(c->d_VX.ensure(2 * std::max<int64_t>(vxoff, 1)), "partition");
+    CK(cudaMemsetAsync(c->d_VX.p, 0, 2 * std::max<int64_t>(vxoff, 1), c->st),
+       "partition");
+    wh = c->d_VX.as<__nv_bfloat16>();
+  }
   CK(launch_scatter(g, c->d_meta.as<BlockMeta>(), nnz, (const int32_t *)du,
                     (const int32_t *)di, (const float *)dx,
-                    c->d_mu.as<float>(), c->d_W.as<float>(), c->st),
+                    c->d_mu.as<float>(), c->d_W.as<float>(), wh, c->st),
      "partition: scatter");
   c->launches += nnz > 0 ? 3 : 1;
   // bf16 planes for the exact tensor-core Gram
@@ -474,8 +491,11 @@ static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
                        c->st), "partition");
     CK(cudaStreamSynchronize(c->st), "partition");
     c->tc_exact = (flag & kErrNotExact) == 0;
-    if (c->tc_exact) {
-      // one TMA map per block over its [Y; M] planes
+  }
+  if ((c->tc_planes && c->tc_exact) || c->cfg.precision == BSVD_BF16) {
+    const int64_t plane_rows = c->cfg.precision == BSVD_BF16 ? 1 : 2;
+    {
+      // one TMA map per block over its bf16 rows: [Y; M] or the bf16 W
       EncodeTiledFn enc = tensor_map_encoder();
       if (!enc) return fail(c, BSVD_ECUDA, "partition: no cuTensorMapEncodeTiled");
       std::vector<CUtensorMap> maps(nb);
@@ -483,7 +503,8 @@ static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
       for (int32_t b = 0; b < nb; ++b) {
         const BlockMeta &bm = c->meta[b];
         if (bm.s == 0) continue;
-        cuuint64_t dims[2] = {(cuuint64_t)bm.L_pad, (cuuint64_t)(2 * bm.s128)};
+        cuuint64_t dims[2] = {(cuuint64_t)bm.L_pad,
+                              (cuuint64_t)(plane_rows * bm.s128)};
         cuuint64_t strides[1] = {(cuuint64_t)bm.L_pad * 2};
         cuuint32_t box[2] = {64, 128};
         cuuint32_t es[2] = {1, 1};
@@ -596,7 +617,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
 
   int64_t goff = 0, xoff = 0, fsoff = 0, floff = 0;
   std::vector<int4> gt;
-  std::vector<int2> rt, lt;
+  std::vector<int2> rt, lt, pt;
   std::vector<SolverState> st0(nb);
   for (int32_t b = 0; b < nb; ++b) {
     BlockMeta &bm = c->meta[b];
@@ -620,12 +641,15 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     for (int32_t ti = 0; ti < T; ++ti)
       for (int32_t tj = ti; tj < T; ++tj) gt.push_back(make_int4(b, ti, tj, 0));
     for (int32_t r = 0; r < bm.s_pad; r += 64) rt.push_back(make_int2(b, r));
+    for (int32_t r = 0; r < bm.s_pad; r += 128) pt.push_back(make_int2(b, r));
     bm.nt = (int32_t)rt.size() - bm.t0;
     for (int32_t l = 0; l < bm.L; l += kProjCols) lt.push_back(make_int2(b, l));
   }
   c->n_gtiles = (int32_t)gt.size();
   c->n_rowtiles = (int32_t)rt.size();
   c->n_ltiles = (int32_t)lt.size();
+  c->n_ptiles = (int32_t)pt.size();
+  const bool panel_tc = c->cfg.panel_path == 0;
 
   CK(c->d_G.ensure(sizeof(float) * std::max<int64_t>(goff, 1)), "factor");
   CK(c->d_X.ensure(sizeof(float) * std::max<int64_t>(xoff, 1)), "factor");
@@ -656,6 +680,65 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
   if (!lt.empty())
     CK(cudaMemcpyAsync(c->d_ltiles.p, lt.data(), sizeof(int2) * lt.size(),
                        cudaMemcpyHostToDevice, c->st), "factor");
+  if (panel_tc && !pt.empty()) {
+    // one TMA map per block over its Gram matrix (s_pad x s_pad float32,
+    // 128-row x 32-float boxes) for the tensor-core panel products
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return fail(c, BSVD_ECUDA, "factor: no cuTensorMapEncodeTiled");
+    c->h_gmaps.assign(nb, CUtensorMap());
+    std::memset(c->h_gmaps.data(), 0, sizeof(CUtensorMap) * nb);
+    for (int32_t b = 0; b < nb; ++b) {
+      const BlockMeta &bm = c->meta[b];
+      if (bm.s == 0) continue;
+      cuuint64_t dims[2] = {(cuuint64_t)bm.s_pad, (cuuint64_t)bm.s_pad};
+      cuuint64_t strides[1] = {(cuuint64_t)bm.s_pad * 4};
+      cuuint32_t box[2] = {32, 128};
+      cuuint32_t es[2] = {1, 1};
+      CUresult r = enc(&c->h_gmaps[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                       c->d_G.as<float>() + bm.g_off, dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(c, BSVD_ECUDA, "factor: Gram tensor map %d failed (%d)", b,
+                    (int)r);
+    }
+    CK(c->d_gmaps.ensure(sizeof(CUtensorMap) * nb), "factor");
+    CK(cudaMemcpyAsync(c->d_gmaps.p, c->h_gmaps.data(),
+                       sizeof(CUtensorMap) * nb, cudaMemcpyHostToDevice, c->st),
+       "factor");
+    // and over the two panel buffers X, Z (s_pad x B float32, 32-row boxes):
+    // maps [0, nb) read X, maps [nb, 2 nb) read Z
+    c->h_xmaps.assign(2 * (size_t)nb, CUtensorMap());
+    std::memset(c->h_xmaps.data(), 0, sizeof(CUtensorMap) * 2 * nb);
+    for (int h = 0; h < 2; ++h) {
+      float *panel = h == 0 ? c->d_X.as<float>() : c->d_Z.as<float>();
+      for (int32_t b = 0; b < nb; ++b) {
+        const BlockMeta &bm = c->meta[b];
+        if (bm.s == 0) continue;
+        cuuint64_t dims[2] = {(cuuint64_t)B, (cuuint64_t)bm.s_pad};
+        cuuint64_t strides[1] = {(cuuint64_t)B * 4};
+        cuuint32_t box[2] = {(cuuint32_t)B, 32};
+        cuuint32_t es[2] = {1, 1};
+        CUresult r = enc(&c->h_xmaps[(size_t)h * nb + b],
+                         CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, panel + bm.x_off,
+                         dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+          return fail(c, BSVD_ECUDA, "factor: panel tensor map %d failed (%d)",
+                      b, (int)r);
+      }
+    }
+    CK(c->d_xmaps.ensure(sizeof(CUtensorMap) * 2 * nb), "factor");
+    CK(cudaMemcpyAsync(c->d_xmaps.p, c->h_xmaps.data(),
+                       sizeof(CUtensorMap) * 2 * nb, cudaMemcpyHostToDevice,
+                       c->st), "factor");
+    CK(c->d_ptiles.ensure(sizeof(int2) * pt.size()), "factor");
+    CK(cudaMemcpyAsync(c->d_ptiles.p, pt.data(), sizeof(int2) * pt.size(),
+                       cudaMemcpyHostToDevice, c->st), "factor");
+  }
   CK(cudaMemsetAsync(c->d_Fs.p, 0, sizeof(float) * std::max<int64_t>(fsoff, 1), c->st), "factor");
   CK(cudaMemsetAsync(c->d_FL.p, 0, sizeof(float) * std::max<int64_t>(floff, 1), c->st), "factor");
   CK(cudaMemsetAsync(c->d_sigma.p, 0, sizeof(double) * kp * (int64_t)nb, c->st), "factor");
@@ -681,14 +764,33 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     e.seed = c->cfg.seed;
     const int2 *rtd = c->d_rowtiles.as<int2>();
     const int nrt = c->n_rowtiles;
+    // out = alpha G in + beta in + gamma in2 (see launch_gpanel)
+    auto panel = [&](int mode, int step, int deg, const float *in,
+                     const float *in2, float *out) -> cudaError_t {
+      if (panel_tc) {
+        const CUtensorMap *xm = c->d_xmaps.as<CUtensorMap>() +
+                                (in == e.X ? 0 : (size_t)nb);
+        return launch_gpanel_tc(B, e.meta, e.state, c->d_ptiles.as<int2>(),
+                                c->n_ptiles, c->d_gmaps.as<CUtensorMap>(), xm,
+                                in, in2, out, mode, step,
+                                c->d_err.as<int32_t>(), c->st);
+      }
+      return launch_gpanel(e, rtd, nrt, mode, step, deg, in, in2, out, c->st);
+    };
 
     std::fill(c->phase_ms + 1, c->phase_ms + 4, 0.0);
     std::fill(c->phase_ms + 5, c->phase_ms + 8, 0.0);
     mark(c, 0);
-    c->gram_used = c->cfg.precision == BSVD_TF32
-                       ? 3
-                       : ((c->tc_planes && c->tc_exact) ? 2 : 1);
-    if (c->gram_used == 3) {
+    c->gram_used = c->cfg.precision == BSVD_TF32   ? 3
+                   : c->cfg.precision == BSVD_BF16 ? 4
+                   : (c->tc_planes && c->tc_exact) ? 2
+                                                   : 1;
+    if (c->gram_used == 4) {
+      CK(launch_gram_bf16(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
+                          c->n_gtiles, c->d_maps.as<CUtensorMap>(), e.G,
+                          c->d_err.as<int32_t>(), c->st),
+         "factor: gram (bf16 tensor cores)");
+    } else if (c->gram_used == 3) {
       CK(launch_gram_tf32(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
                           c->n_gtiles, c->d_wmaps.as<CUtensorMap>(), e.G,
                           c->d_err.as<int32_t>(), c->st),
@@ -705,7 +807,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     }
     mark(c, 1);
     CK(launch_init_panels(e, rtd, nrt, c->st), "factor: init");
-    CK(launch_gpanel(e, rtd, nrt, 0, 0, 0, e.X, nullptr, e.Z, c->st), "factor: G X");
+    CK(panel(0, 0, 0, e.X, nullptr, e.Z), "factor: G X");
     c->launches += (c->n_gtiles > 0) + 2 * (nrt > 0);
     for (int it = 0; it <= c->cfg.max_iters + 1; ++it) {
       mark(c, 6);
@@ -738,11 +840,9 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
         const float *in = even ? e.Z : e.X;
         const float *in2 = j == 1 ? nullptr : (even ? e.X : e.Z);
         float *out = even ? e.X : e.Z;
-        CK(launch_gpanel(e, rtd, nrt, j == 1 ? 1 : 2, j, deg, in, in2, out,
-                         c->st), "factor: filter");
+        CK(panel(j == 1 ? 1 : 2, j, deg, in, in2, out), "factor: filter");
       }
-      CK(launch_gpanel(e, rtd, nrt, 0, 0, 0, e.X, nullptr, e.Z, c->st),
-         "factor: G X");
+      CK(panel(0, 0, 0, e.X, nullptr, e.Z), "factor: G X");
       mark(c, 9);
       c->launches += (deg + 1) * (nrt > 0);
     }
@@ -969,7 +1069,7 @@ bsvd_status bsvd_reconstruct(bsvd_ctx *c, int32_t b, int32_t add_mean,
 
 bsvd_status bsvd_factor_report(bsvd_ctx *c, int32_t *iters,
                                int32_t *converged, int32_t *sweeps,
-                               int64_t *cycles) {
+                               int64_t *cycles, float *resid) {
   if (!c) return BSVD_EINVAL;
   c->err.clear();
   if (!c->factored) return fail(c, BSVD_ESTATE, "factor_report: no factors");
@@ -983,6 +1083,7 @@ bsvd_status bsvd_factor_report(bsvd_ctx *c, int32_t *iters,
     if (sweeps) sweeps[b] = s[b].sweeps;
     if (cycles)
       for (int j = 0; j < 3; ++j) cycles[3 * b + j] = s[b].cycles[j];
+    if (resid) resid[b] = s[b].resid;
   }
   return BSVD_OK;
 }

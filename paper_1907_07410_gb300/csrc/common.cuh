@@ -51,12 +51,43 @@ struct SolverState {
   int32_t degree;       // Chebyshev degree of the next filter (even)
   uint64_t refill;      // Ritz columns refilled with random vectors
   int32_t sweeps;       // Jacobi sweeps used so far
-  int32_t pad;
+  float amp;            // this block's filter amplification cap (0: default)
   int64_t cycles[3];    // SM clock cycles in the Rayleigh-Ritz kernel:
                         // [0] sums + Cholesky QR + H', [1] Jacobi, [2] rest
 };
 
 enum : int32_t { kRunning = 0, kConverged = 1, kCapped = 2 };
+
+// Coefficients of one panel product out = alpha G in + beta in + gamma in2.
+// mode 0: the plain product G in. mode 1 and 2: step `step` (1, then 2 ..
+// degree) of the scaled three-term Chebyshev recurrence that damps the
+// interval [0, cut] and keeps the value at the scaling point a0 at 1
+// (Zhou and Saad's filtered subspace iteration).
+__device__ __forceinline__ void cheb_coeffs(const SolverState &st, int mode,
+                                            int step, float *alpha,
+                                            float *beta, float *gamma) {
+  *alpha = 1.f;
+  *beta = 0.f;
+  *gamma = 0.f;
+  if (mode < 1) return;
+  // damped interval [0, cut]: centre c, half-width e; p(a0) = 1
+  const float e = 0.5f * st.cut, c = 0.5f * st.cut;
+  const float sig1 = e / (st.a0 - c);
+  if (mode == 1) {
+    *alpha = sig1 / e;
+    *beta = -c * *alpha;
+    return;
+  }
+  const float tau = 2.f / sig1;
+  float sig = sig1, sig_prev = sig1;
+  for (int j = 2; j <= step; ++j) {
+    sig_prev = sig;
+    sig = 1.f / (tau - sig);
+  }
+  *alpha = 2.f * sig / e;
+  *beta = -c * *alpha;
+  *gamma = -sig_prev * sig;
+}
 
 // Error bits raised by kernels (read back by the calling entry point).
 enum : int32_t {

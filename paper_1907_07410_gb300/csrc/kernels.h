@@ -23,7 +23,7 @@ cudaError_t launch_means(int32_t nblocks, const unsigned long long *counts,
 cudaError_t launch_scatter(const GridDesc &g, const BlockMeta *meta,
                            int64_t nnz, const int32_t *u, const int32_t *i,
                            const float *x, const float *mu, float *W,
-                           cudaStream_t st);
+                           __nv_bfloat16 *Wh, cudaStream_t st);
 
 // ---- Gram (kernels_gram.cu) ---------------------------------------------
 // tiles: (block, tile_i, tile_j, 0) with tile_i <= tile_j, 128 x 128 tiles.
@@ -42,6 +42,11 @@ cudaError_t launch_gram_tc(const BlockMeta *meta, const int4 *tiles,
 // Single-pass tf32 Gram of the float32 blocks; maps: one TMA map per block
 // over W (s_pad x L_pad f32, 128 x 32 boxes, 128-byte swizzle).
 cudaError_t launch_gram_tf32(const BlockMeta *meta, const int4 *tiles,
+                             int32_t ntiles, const CUtensorMap *maps, float *G,
+                             int32_t *err, cudaStream_t st);
+
+// single-product bf16 Gram over the bf16 copy of the centred blocks
+cudaError_t launch_gram_bf16(const BlockMeta *meta, const int4 *tiles,
                              int32_t ntiles, const CUtensorMap *maps, float *G,
                              int32_t *err, cudaStream_t st);
 
@@ -79,6 +84,16 @@ struct EigBuffers {
   float tol;
   uint64_t seed;
 };
+
+// Panel product on the tensor cores (three tf32 passes): tiles are
+// (block, first row) pairs of 128 rows, gmaps one TMA map per block over G,
+// xmaps one per block over `in` (s_pad x bsub float32, 32-row boxes).
+cudaError_t launch_gpanel_tc(int32_t bsub, const BlockMeta *meta,
+                             const SolverState *state, const int2 *tiles,
+                             int32_t ntiles, const CUtensorMap *gmaps,
+                             const CUtensorMap *xmaps, const float *in,
+                             const float *in2, float *out, int mode, int step,
+                             int32_t *err, cudaStream_t st);
 
 // row tiles: (block, first row) pairs, 64 rows each.
 cudaError_t launch_init_panels(const EigBuffers &e, const int2 *rowtiles,

@@ -30,6 +30,16 @@
 // degree d <= max_degree with C_d(t_1) <= kMaxAmplification (at least 2).
 // Steep spectra get short filters and more Rayleigh-Ritz steps.
 //
+// The same ratio is the spread between the filtered columns. Where the
+// lower Ritz vectors are still poor (a wanted value near a dense bulk of
+// unwanted ones), their errors along the top directions grow by up to
+// C_d(t_1), the columns collapse onto those directions, and the Cholesky
+// QR drops them. Refilled columns would collapse again in the next filter,
+// and a cut taken at the smallest surviving Ritz value lands on a wanted
+// one, so the solve stalls. A block that dropped columns therefore divides
+// its own cap by kAmpBackoff (down to kMinAmplification) for the rest of
+// its solve, and keeps its previous cut for that step.
+//
 // A block with s <= bsub starts from the identity basis, so the first
 // Rayleigh-Ritz step is an exact eigen-decomposition of G.
 #include <float.h>
@@ -44,6 +54,8 @@ namespace {
 
 constexpr int TR = 64;       // panel rows per CTA
 constexpr float kMaxAmplification = 3e6f;
+constexpr float kMinAmplification = 1e3f;
+constexpr float kAmpBackoff = 1e2f;
 constexpr float kCutFloor = 1e-3f;   // cut >= kCutFloor * theta_1
 constexpr float kPivotDrop = 1e-4f;  // squared sine of the angle to the span
 constexpr int KC = 32;       // k-chunk of the panel GEMM
@@ -122,26 +134,8 @@ k_gpanel(const BlockMeta *__restrict__ meta,
   const float *inb = in + bm.x_off;
   float *outb = out + bm.x_off;
 
-  float alpha = 1.f, beta = 0.f, gamma = 0.f;
-  if (mode >= 1) {
-    // damped interval [0, cut]: centre c, half-width e; p(a0) = 1
-    const float e = 0.5f * st.cut, c = 0.5f * st.cut;
-    const float sig1 = e / (st.a0 - c);
-    if (mode == 1) {
-      alpha = sig1 / e;
-      beta = -c * alpha;
-    } else {
-      const float tau = 2.f / sig1;
-      float sig = sig1, sig_prev = sig1;
-      for (int j = 2; j <= step; ++j) {
-        sig_prev = sig;
-        sig = 1.f / (tau - sig);
-      }
-      alpha = 2.f * sig / e;
-      beta = -c * alpha;
-      gamma = -sig_prev * sig;
-    }
-  }
+  float alpha, beta, gamma;
+  cheb_coeffs(st, mode, step, &alpha, &beta, &gamma);
 
   const int g = threadIdx.x >> 7, tid = threadIdx.x & 127;
   const int ty = tid >> 3, tx = tid & 7;
@@ -667,7 +661,13 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
       s_done = 1;
     } else {
       const int ndrop = __popcll(st.refill);
+      float amp = st.amp > 0.f ? st.amp : kMaxAmplification;
       float cut = th[max(0, n - 1 - ndrop)];
+      if (ndrop > 0) {
+        amp = fmaxf(amp / kAmpBackoff, kMinAmplification);
+        if (st.cut > 0.f) cut = fminf(cut, st.cut);
+      }
+      st.amp = amp;
       cut = fmaxf(cut, kCutFloor * t1);
       if (cut >= 0.5f * t1) cut = 0.5f * t1;
       st.cut = cut;
@@ -675,7 +675,7 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
       const float tt = 2.f * t1 / cut - 1.f;   // >= 3
       const float at = acoshf(tt);
       int d = 2;
-      while (d + 2 <= max_degree && coshf((float)(d + 2) * at) <= kMaxAmplification)
+      while (d + 2 <= max_degree && coshf((float)(d + 2) * at) <= amp)
         d += 2;
       st.degree = d;
       atomicAdd(running, 1);

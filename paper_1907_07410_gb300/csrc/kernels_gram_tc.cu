@@ -190,10 +190,14 @@ k_gram_tc(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
   if (warp == 0) tc::tmem_dealloc(taddr, 512);
 }
 
-// Single-pass tf32 Gram G = W W^T on the float32 blocks (any rating scale;
-// inputs are truncated to tf32, ~1e-3 relative error in G). Same tiling and
-// roles as k_gram_tc, one accumulator, 6 stages of {W_i, W_j} 128 x 32-float
-// boxes.
+// Single-product Gram G = W W^T in reduced precision (any rating scale):
+//   * k_gram_tf32 reads the float32 blocks, truncated to tf32 by the MMA
+//     (10-bit mantissa);
+//   * k_gram_bf16 reads a bf16 copy of the centred blocks (8-bit mantissa).
+// Both accumulate in f32. Same tiling and roles as k_gram_tc, with one
+// accumulator and 6 stages of {W_i, W_j} boxes of 128 rows x 128 bytes
+// (32 floats or 64 bf16). Either way a k-chunk is four MMAs of 32 bytes of
+// K each (K = 8 tf32 or K = 16 bf16), so the descriptor steps match.
 constexpr int KF = 32;                          // floats per k-chunk (128 B)
 constexpr int FSTAGES = 6;
 constexpr int FTILE_BYTES = TT * KF * 4;        // 16 KiB
@@ -211,8 +215,9 @@ struct CtrlF {
 
 constexpr size_t kSmemBytesF = FSTAGES * FSTAGE_BYTES + sizeof(CtrlF) + 1024;
 
-__global__ void __launch_bounds__(128, 1)
-k_gram_tf32(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
+template <bool kBf16>
+__device__ __forceinline__ void
+gram_single(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
             const CUtensorMap *__restrict__ maps, float *__restrict__ G,
             int32_t *err) {
   extern __shared__ unsigned char smem_raw[];
@@ -225,7 +230,8 @@ k_gram_tf32(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
   const CUtensorMap *map = maps + tl.x;
   const bool diag = tl.y == tl.z;
   const int yi = tl.y * TT, yj = tl.z * TT;
-  const int nk = (bm.L_pad + KF - 1) / KF;
+  constexpr int kElems = kBf16 ? 64 : KF;        // elements per k-chunk
+  const int nk = (bm.L_pad + kElems - 1) / kElems;
 
   if (warp == 0) tc::tmem_alloc(&ct.tmem, 128);
   if (threadIdx.x == 0) {
@@ -256,14 +262,15 @@ k_gram_tf32(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
         break;
       }
       unsigned char *buf = base + s * FSTAGE_BYTES;
-      const int x = kc * KF;
+      const int x = kc * kElems;
       tc::mbar_expect_tx(&ct.full[s], bytes);
       tc::tma_load_2d(buf, map, x, yi, &ct.full[s]);
       if (!diag) tc::tma_load_2d(buf + FTILE_BYTES, map, x, yj, &ct.full[s]);
       ct.issued = kc + 1;
     }
   } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc = tc::idesc_tf32_f32(TT, TT);
+    constexpr uint32_t idesc =
+        kBf16 ? tc::idesc_bf16_f32(TT, TT) : tc::idesc_tf32_f32(TT, TT);
     for (int kc = 0; kc < nk; ++kc) {
       const int s = kc % FSTAGES;
       const uint32_t ph = (kc / FSTAGES) & 1;
@@ -279,9 +286,12 @@ k_gram_tf32(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
       const uint64_t dwi = tc::sdesc_kmajor_sw128(tc::smem_u32(buf));
       const uint64_t dwj = diag ? dwi : tc::sdesc_kmajor_sw128(tc::smem_u32(buf + FTILE_BYTES));
 #pragma unroll
-      for (int kk = 0; kk < KF / 8; ++kk) {
+      for (int kk = 0; kk < 4; ++kk) {          // 32 bytes of K per MMA
         const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
-        tc::mma_tf32(taddr, dwi + 2 * kk, dwj + 2 * kk, idesc, acc);
+        if constexpr (kBf16)
+          tc::mma_bf16(taddr, dwi + 2 * kk, dwj + 2 * kk, idesc, acc);
+        else
+          tc::mma_tf32(taddr, dwi + 2 * kk, dwj + 2 * kk, idesc, acc);
       }
       tc::mma_commit(&ct.empty[s]);
     }
@@ -326,7 +336,33 @@ k_gram_tf32(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
   if (warp == 0) tc::tmem_dealloc(taddr, 128);
 }
 
+__global__ void __launch_bounds__(128, 1)
+k_gram_tf32(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
+            const CUtensorMap *__restrict__ maps, float *__restrict__ G,
+            int32_t *err) {
+  gram_single<false>(meta, tiles, maps, G, err);
+}
+
+__global__ void __launch_bounds__(128, 1)
+k_gram_bf16(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
+            const CUtensorMap *__restrict__ maps, float *__restrict__ G,
+            int32_t *err) {
+  gram_single<true>(meta, tiles, maps, G, err);
+}
+
 }  // namespace
+
+cudaError_t launch_gram_bf16(const BlockMeta *meta, const int4 *tiles,
+                             int32_t ntiles, const CUtensorMap *maps, float *G,
+                             int32_t *err, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(
+      k_gram_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)kSmemBytesF);
+  if (e != cudaSuccess) return e;
+  k_gram_bf16<<<ntiles, 128, kSmemBytesF, st>>>(meta, tiles, maps, G, err);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gram_tf32(const BlockMeta *meta, const int4 *tiles,
                              int32_t ntiles, const CUtensorMap *maps, float *G,

@@ -140,14 +140,17 @@ __global__ void __launch_bounds__(256)
 k_scatter(GridDesc g, const BlockMeta *__restrict__ meta, int64_t nnz,
           const int32_t *__restrict__ u, const int32_t *__restrict__ it,
           const float *__restrict__ x, const float *__restrict__ mu,
-          float *__restrict__ W) {
+          float *__restrict__ W, __nv_bfloat16 *__restrict__ Wh) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
        t += (int64_t)gridDim.x * blockDim.x) {
     int32_t blk, r, c, a, l;
     if (!locate(g, u[t], it[t], &blk, &r, &c)) continue;   // flagged in pass 1
     const BlockMeta &bm = meta[blk];
     to_w(bm, r, c, &a, &l);
-    W[bm.w_off + (int64_t)a * bm.L_pad + l] = __fsub_rn(x[t], mu[blk]);
+    const float w = __fsub_rn(x[t], mu[blk]);
+    W[bm.w_off + (int64_t)a * bm.L_pad + l] = w;
+    // bf16 copy for the bf16 Gram: s128 x L_pad per block at vx_off
+    if (Wh) Wh[bm.vx_off + (int64_t)a * bm.L_pad + l] = __float2bfloat16_rn(w);
   }
 }
 
@@ -252,9 +255,10 @@ cudaError_t launch_means(int32_t nblocks, const unsigned long long *counts,
 cudaError_t launch_scatter(const GridDesc &g, const BlockMeta *meta,
                            int64_t nnz, const int32_t *u, const int32_t *i,
                            const float *x, const float *mu, float *W,
-                           cudaStream_t st) {
+                           __nv_bfloat16 *Wh, cudaStream_t st) {
   if (nnz <= 0) return cudaSuccess;
-  k_scatter<<<grid_for(nnz, 4), 256, 0, st>>>(g, meta, nnz, u, i, x, mu, W);
+  k_scatter<<<grid_for(nnz, 4), 256, 0, st>>>(g, meta, nnz, u, i, x, mu, W,
+                                              Wh);
   return cudaGetLastError();
 }
 

@@ -35,6 +35,7 @@ def test_config_layout_matches_header():
     assert cfg.cheb_degree == 8 and cfg.max_iters == 30
     assert abs(cfg.tol - 1e-5) < 1e-20
     assert cfg.clamp_lo == 1.0 and cfg.clamp_hi == 5.0
-    # int32 x2, float x2, int32 x6, double, uint64, pointer
-    assert ctypes.sizeof(bs.Config) == 64
+    # int32 x2, float x2, int32 x6, double, uint64, pointer, int32 x2
+    assert ctypes.sizeof(bs.Config) == 72
     assert bs.Config.tol.offset == 40 and bs.Config.stream.offset == 56
+    assert bs.Config.panel_path.offset == 64 and cfg.panel_path == 0

@@ -1,10 +1,11 @@
-"""The precision form: the medium matrix on 8 x 8 and 16 x 16 grids, with
-the exact tensor-core Gram (float32 result) and the single-pass TF32 Gram.
+"""The precision form: the medium matrix on 4 x 4, 8 x 8 and 16 x 16 grids,
+with the exact tensor-core Gram (float32 result), the single-pass TF32 Gram
+and the single-pass BF16 Gram.
 
 Bars against the FP64 oracle: singular values relative 1e-5 (float32 path)
-or 2e-3 (tf32 path) on the retained top-k; rank-k reconstruction relative
-Frobenius 1e-4 / 5e-3 where the block's gap is at least 1e-3; held-out RMSE
-within 1e-4 on both paths.
+or 2e-3 (tf32 and bf16 paths) on the retained top-k; rank-k reconstruction
+relative Frobenius 1e-4 / 5e-3 where the block's gap is at least 1e-3;
+held-out RMSE within 1e-4 on every path.
 """
 import json
 import os
@@ -21,8 +22,9 @@ pytestmark = pytest.mark.gpu
 import paper_1907_07410_gb300 as bs  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SIGMA = {0: 1e-5, 1: 2e-3}
-RECON = {0: 1e-4, 1: 5e-3}
+SIGMA = {0: 1e-5, 1: 2e-3, 2: 2e-3}
+RECON = {0: 1e-4, 1: 5e-3, 2: 5e-3}
+GRAM_PATH = {0: 2, 1: 3, 2: 4}
 
 
 def dev(a):
@@ -37,16 +39,17 @@ def run(w, r, precision):
     return ctx
 
 
-@pytest.mark.parametrize("name", ["medium-6040x3952-8x8-k20",
+@pytest.mark.parametrize("name", ["medium-6040x3952-4x4-k20",
+                                  "medium-6040x3952-8x8-k20",
                                   "medium-6040x3952-16x16-k20"])
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_grids_against_golden(name, precision):
     w = synth.WORKLOADS[name]
     g = json.load(open(os.path.join(HERE, "golden", name + ".json")))
     r = synth.generate(w)
     assert r.digest() == g["digest"]
     ctx = run(w, r, precision)
-    assert ctx.gram_path() == (2 if precision == 0 else 3)
+    assert ctx.gram_path() == GRAM_PATH[precision]
     counts, mu = ctx.block_stats()
     assert counts.tolist() == g["counts"]
     worst = 0.0
@@ -61,7 +64,7 @@ def test_grids_against_golden(name, precision):
     assert abs(rm - g["rmse"]) <= 1e-4
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_reconstruction_bars(precision):
     """Two sampled blocks of the 8 x 8 grid, recomputed by the oracle."""
     w = synth.MEDIUM_8x8
