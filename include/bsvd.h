@@ -285,6 +285,92 @@ int64_t bsvd_kernel_launches(const bsvd_ctx *ctx);
 int32_t bsvd_gram_path(const bsvd_ctx *ctx);
 
 /*
+ * ---- The paper's own method: blocked SGD (Algorithms 1-2) ----------------
+ *
+ * The biased latent-factor model of Section 2.2 (Eq. 3):
+ *   x_ui ~ p_u . q_i + bu_u + bi_i,
+ * fitted by stochastic gradient descent (Eq. 10-13) block by block.
+ *   * Schedule (Section 3, Figure 2): the blocks of the last bsvd_partition
+ *     grid are visited in steps of blocks that share no block row and no
+ *     block column: step s holds blocks ((j + s) mod p, j), j < q, when
+ *     p >= q, else (i, (i + s) mod q), i < p. The blocks of a step run at
+ *     once, one warp each.
+ *   * Within a block (Algorithm 2): its ratings row by row, then column by
+ *     column. For each rating, with err = x - bu - bi - p . q:
+ *       bu += a_ubias (err - b_ubias bu),  bi += a_ibias (err - b_ibias bi),
+ *       p_f += a_user (err q_f - b_user p_f),
+ *       q_f += a_item (err p_f - b_item q_f)   (p_f before this rating).
+ *     Where the listing and Eq. 10-13 differ, this follows the equations:
+ *     each bias is regularised by itself.
+ *   * Epochs (Algorithm 1): up to max_steps passes over all blocks; after
+ *     each, the training RMSE is measured and training stops once it
+ *     improved by less than delta.
+ * Arithmetic is float64 with one rounding per operation (no fused
+ * multiply-add) and the dot product summed over f = 0 .. k-1 in order, so
+ * results equal a sequential float64 implementation bit for bit.
+ */
+typedef struct {
+    double a_user, b_user;     /* user factors p_u (Eq. 10) */
+    double a_item, b_item;     /* item factors q_i (Eq. 11) */
+    double a_ubias, b_ubias;   /* user biases (Eq. 12) */
+    double a_ibias, b_ibias;   /* item biases (Eq. 13) */
+    double delta;              /* minimum RMSE improvement per epoch */
+    int32_t k;                 /* latent factors, 1 .. 32 */
+    int32_t max_steps;         /* STEPS of Algorithm 1, >= 0 */
+} bsvd_sgd_params;
+
+/*
+ * The experiments' values (Section 5, "Hyper-parameters", SVD model):
+ * user factors a = 0.019, b = 0.019; item factors a = 0.004, b = 0.019;
+ * user biases a = 0.004, b = 0.019; item biases a = 0.013, b = 0.007;
+ * delta = 1e-4; k = 13; max_steps = 100.
+ */
+void bsvd_sgd_params_default(bsvd_sgd_params *prm);
+
+/*
+ * Lay out the training ratings in epoch order on the device, for the grid
+ * of the last bsvd_partition or bsvd_partition_diag call (same ids; the
+ * ratings themselves need not be the ones partitioned).
+ * u, i, x: host or device arrays of nnz entries; nnz < 2^40, and no block
+ * wider than 2^23 columns. Repeated (u, i) cells are kept, in input order.
+ * Errors: BSVD_ESTATE (no partition), BSVD_EINVAL (sizes, an id out of
+ * range or off the block diagonal), BSVD_ENOMEM, BSVD_ECUDA.
+ */
+bsvd_status bsvd_sgd_prepare(bsvd_ctx *ctx, int64_t nnz, const int32_t *u,
+                             const int32_t *i, const float *x);
+
+/*
+ * Algorithm 1 from factors P0 (m x k) and Q0 (n x k), row-major float64,
+ * host or device (the starting values are the caller's: the paper draws
+ * them at random), and zero biases. The model stays on the device.
+ * rmse: host array of max_steps + 1 doubles, or NULL: the training RMSE
+ * before the first epoch, then after each epoch run. *steps_run (may be
+ * NULL): epochs run.
+ * Errors: BSVD_ESTATE (no bsvd_sgd_prepare), BSVD_EINVAL (parameters),
+ * BSVD_ENOMEM, BSVD_ECUDA.
+ */
+bsvd_status bsvd_sgd_train(bsvd_ctx *ctx, const bsvd_sgd_params *prm,
+                           const double *P0, const double *Q0, double *rmse,
+                           int32_t *steps_run);
+
+/*
+ * Eq. 3 for nq (user, item) pairs of the trained model:
+ * yhat = (sum_f p_uf q_if, in f order) + bu_u + bi_i. u, i: host or device
+ * arrays; yhat: host or device array of nq doubles.
+ * Errors: BSVD_ESTATE (not trained), BSVD_EINVAL (an id out of range).
+ */
+bsvd_status bsvd_sgd_predict(bsvd_ctx *ctx, int64_t nq, const int32_t *u,
+                             const int32_t *i, double *yhat);
+
+/*
+ * Copy the trained model to host arrays (any may be NULL): P (m x k), Q
+ * (n x k), row-major, bu (m), bi (n).
+ * Errors: BSVD_ESTATE (not trained), BSVD_ECUDA.
+ */
+bsvd_status bsvd_sgd_get(bsvd_ctx *ctx, double *P, double *Q, double *bu,
+                         double *bi);
+
+/*
  * Block counts and block means of a rating matrix, for callers that cannot
  * allocate device memory during the call (the paper has no counterpart:
  * this serves deployment, not the method). A serving process that has

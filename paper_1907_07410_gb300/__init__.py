@@ -30,7 +30,9 @@ EXPORTS = ("bsvd_config_default", "bsvd_create", "bsvd_destroy",
            "bsvd_rmse", "bsvd_block_stats", "bsvd_get_block",
            "bsvd_reconstruct", "bsvd_factor_report", "bsvd_phase_times",
            "bsvd_kernel_launches", "bsvd_block_means_noalloc",
-           "bsvd_gram_path", "bsvd_partition_diag", "bsvd_factor_ks")
+           "bsvd_gram_path", "bsvd_partition_diag", "bsvd_factor_ks",
+           "bsvd_sgd_params_default", "bsvd_sgd_prepare", "bsvd_sgd_train",
+           "bsvd_sgd_predict", "bsvd_sgd_get")
 
 
 class BsvdError(RuntimeError):
@@ -49,6 +51,16 @@ class Config(ctypes.Structure):
                 ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("panel_path", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class SgdParams(ctypes.Structure):
+    """bsvd_sgd_params: rates named by the parameter they update."""
+    _fields_ = [("a_user", ctypes.c_double), ("b_user", ctypes.c_double),
+                ("a_item", ctypes.c_double), ("b_item", ctypes.c_double),
+                ("a_ubias", ctypes.c_double), ("b_ubias", ctypes.c_double),
+                ("a_ibias", ctypes.c_double), ("b_ibias", ctypes.c_double),
+                ("delta", ctypes.c_double), ("k", ctypes.c_int32),
+                ("max_steps", ctypes.c_int32)]
 
 
 _lib = None
@@ -84,12 +96,18 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                  ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
                                  vp, vp, vp, vp]),
         "bsvd_reconstruct": (i32, [vp, i32, i32, vp]),
-        "bsvd_factor_report": (i32, [vp, vp, vp, vp, vp]),
+        "bsvd_factor_report": (i32, [vp, vp, vp, vp, vp, vp]),
         "bsvd_phase_times": (i32, [vp, vp]),
         "bsvd_kernel_launches": (i64, [vp]),
         "bsvd_gram_path": (i32, [vp]),
         "bsvd_block_means_noalloc": (i32, [i64, i64, i64, vp, vp, vp, i32,
                                            i32, vp, vp, vp]),
+        "bsvd_sgd_params_default": (None, [ctypes.POINTER(SgdParams)]),
+        "bsvd_sgd_prepare": (i32, [vp, i64, vp, vp, vp]),
+        "bsvd_sgd_train": (i32, [vp, ctypes.POINTER(SgdParams), vp, vp, vp,
+                                 ctypes.POINTER(i32)]),
+        "bsvd_sgd_predict": (i32, [vp, i64, vp, vp, vp]),
+        "bsvd_sgd_get": (i32, [vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -312,6 +330,55 @@ PHASES = ("partition", "gram", "eigen", "project", "predict", "eigen_filter",
           "eigen_rr", "eigen_other")
 
 
+def bsvd_sgd_params_default() -> SgdParams:
+    prm = SgdParams()
+    load().bsvd_sgd_params_default(ctypes.byref(prm))
+    return prm
+
+
+def bsvd_sgd_prepare(ctx, u, i, x) -> int:
+    nnz = _len(u)
+    if _len(i) != nnz or _len(x) != nnz:
+        raise ValueError("u, i, x must have the same length")
+    st = load().bsvd_sgd_prepare(ctx, nnz, _ptr(u, np.int32, "u"),
+                                 _ptr(i, np.int32, "i"),
+                                 _ptr(x, np.float32, "x"))
+    return _check(ctx, st)
+
+
+def bsvd_sgd_train(ctx, prm: SgdParams, P0, Q0):
+    """Returns (training RMSE history, epochs run)."""
+    hist = np.zeros(prm.max_steps + 1, np.float64)
+    ran = ctypes.c_int32(0)
+    st = load().bsvd_sgd_train(ctx, ctypes.byref(prm),
+                               _ptr(P0, np.float64, "P0"),
+                               _ptr(Q0, np.float64, "Q0"), hist.ctypes.data,
+                               ctypes.byref(ran))
+    _check(ctx, st)
+    return hist[:ran.value + 1].copy(), ran.value
+
+
+def bsvd_sgd_predict(ctx, u, i, yhat) -> int:
+    nq = _len(u)
+    if _len(i) != nq or _len(yhat) != nq:
+        raise ValueError("u, i, yhat must have the same length")
+    st = load().bsvd_sgd_predict(ctx, nq, _ptr(u, np.int32, "u"),
+                                 _ptr(i, np.int32, "i"),
+                                 _ptr(yhat, np.float64, "yhat"))
+    return _check(ctx, st)
+
+
+def bsvd_sgd_get(ctx, m, n, k):
+    P = np.zeros((m, k), np.float64)
+    Q = np.zeros((n, k), np.float64)
+    bu = np.zeros(m, np.float64)
+    bi = np.zeros(n, np.float64)
+    st = load().bsvd_sgd_get(ctx, P.ctypes.data, Q.ctypes.data,
+                             bu.ctypes.data, bi.ctypes.data)
+    _check(ctx, st)
+    return P, Q, bu, bi
+
+
 def bsvd_block_means_noalloc(m, n, u, i, x, p, q, counts, mu,
                              stream=None) -> int:
     """Block counts and means with no allocation (device arrays only).
@@ -433,3 +500,34 @@ class Context:
 
     def gram_path(self) -> int:
         return bsvd_gram_path(self.handle)
+
+    # ---- the paper's blocked SGD (Algorithms 1-2) ------------------------
+    def sgd_prepare(self, u, i, x):
+        """Epoch order of the training ratings on the last partition's grid
+        (call partition first)."""
+        bsvd_sgd_prepare(self.handle, u, i, x)
+        self._sgd_shape = None
+
+    def sgd_train(self, P0, Q0, **params):
+        """Algorithm 1 from P0 (m x k), Q0 (n x k) float64; params override
+        the Section 5 defaults (a_user, ..., delta, max_steps). Returns
+        (training RMSE history, epochs run)."""
+        prm = bsvd_sgd_params_default()
+        prm.k = int(np.shape(P0)[1])
+        for key, v in params.items():
+            if not hasattr(prm, key):
+                raise TypeError("unknown SGD parameter %r" % key)
+            setattr(prm, key, v)
+        self._sgd_shape = (int(np.shape(P0)[0]), int(np.shape(Q0)[0]), prm.k)
+        return bsvd_sgd_train(self.handle, prm, P0, Q0)
+
+    def sgd_predict(self, u, i, out=None):
+        if out is None:
+            out = np.zeros(_len(u), np.float64)
+        bsvd_sgd_predict(self.handle, u, i, out)
+        return out
+
+    def sgd_get(self):
+        """(P, Q, bu, bi) of the trained model, as host arrays."""
+        m, n, k = self._sgd_shape
+        return bsvd_sgd_get(self.handle, m, n, k)

@@ -100,6 +100,16 @@ struct bsvd_ctx {
   DevBuf d_ptiles, d_gmaps, d_xmaps;
   int32_t n_ptiles = 0;
   std::vector<CUtensorMap> h_gmaps, h_xmaps;
+
+  // blocked SGD (Algorithms 1-2): ratings in epoch order, block ranges,
+  // schedule, model
+  bool sgd_ready = false, sgd_trained = false;
+  int64_t sgd_nnz = 0;
+  int32_t sgd_k = 0;
+  DevBuf d_sgd_cnt, d_sgd_off, d_sgd_key, d_sgd_src, d_sgd_u, d_sgd_i,
+      d_sgd_x, d_sgd_range, d_sgd_blocks, d_sgd_P, d_sgd_Q, d_sgd_bu,
+      d_sgd_bi, d_sgd_sum;
+  std::vector<int32_t> sgd_step_off;   // steps: blocks [off[s], off[s+1])
   bool any_capped = false;
 
   // staging of host arguments and results
@@ -301,7 +311,11 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->d_rowtiles, &c->d_ltiles, &c->s_a, &c->s_b, &c->s_c,
                     &c->s_out, &c->d_partials, &c->d_rmse, &c->d_VX,
                     &c->d_shift, &c->d_delta, &c->d_maps, &c->d_flag,
-                    &c->d_wmaps, &c->d_ptiles, &c->d_gmaps, &c->d_xmaps};
+                    &c->d_wmaps, &c->d_ptiles, &c->d_gmaps, &c->d_xmaps,
+                    &c->d_sgd_cnt, &c->d_sgd_off, &c->d_sgd_key,
+                    &c->d_sgd_src, &c->d_sgd_u, &c->d_sgd_i, &c->d_sgd_x,
+                    &c->d_sgd_range, &c->d_sgd_blocks, &c->d_sgd_P,
+                    &c->d_sgd_Q, &c->d_sgd_bu, &c->d_sgd_bi, &c->d_sgd_sum};
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   for (DevBuf *b : bufs) b->release();
@@ -323,6 +337,8 @@ static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
                                   const int32_t *col_perm, bool diag) {
   if (!c) return BSVD_EINVAL;
   c->err.clear();
+  c->sgd_ready = false;      // a new grid invalidates the SGD order
+  c->sgd_trained = false;
   if (m < 1 || n < 1 || m > INT32_MAX || n > INT32_MAX || nnz < 0)
     return fail(c, BSVD_EINVAL, "partition: bad sizes m=%lld n=%lld nnz=%lld",
                 (long long)m, (long long)n, (long long)nnz);
@@ -1101,5 +1117,217 @@ int64_t bsvd_kernel_launches(const bsvd_ctx *c) {
 }
 
 int32_t bsvd_gram_path(const bsvd_ctx *c) { return c ? c->gram_used : -1; }
+
+// ---- blocked SGD (Algorithms 1-2) ----------------------------------------
+
+void bsvd_sgd_params_default(bsvd_sgd_params *prm) {
+  if (!prm) return;
+  prm->a_user = 0.019;
+  prm->b_user = 0.019;
+  prm->a_item = 0.004;
+  prm->b_item = 0.019;
+  prm->a_ubias = 0.004;
+  prm->b_ubias = 0.019;
+  prm->a_ibias = 0.013;
+  prm->b_ibias = 0.007;
+  prm->delta = 1e-4;
+  prm->k = 13;
+  prm->max_steps = 100;
+}
+
+bsvd_status bsvd_sgd_prepare(bsvd_ctx *c, int64_t nnz, const int32_t *u,
+                             const int32_t *i, const float *x) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (!c->parted) return fail(c, BSVD_ESTATE, "sgd_prepare: no partition");
+  if (nnz < 0 || nnz >= ((int64_t)1 << 40) || (nnz > 0 && (!u || !i || !x)))
+    return fail(c, BSVD_EINVAL, "sgd_prepare: bad arguments");
+  for (int32_t j = 0; j < c->q; ++j)
+    if (c->cb[j + 1] - c->cb[j] >= ((int64_t)1 << 23))
+      return fail(c, BSVD_EINVAL, "sgd_prepare: a block is too wide");
+  c->sgd_ready = false;
+  c->sgd_trained = false;
+  const GridDesc g = c->grid();
+  const int32_t nb = c->nblocks;
+  const int64_t nbuckets = (int64_t)(c->diag ? c->p : c->q) * c->m;
+  const void *du = u, *di = i, *dx = x;
+  CK(device_view(c, u, sizeof(int32_t) * nnz, c->s_a, &du), "sgd_prepare");
+  CK(device_view(c, i, sizeof(int32_t) * nnz, c->s_b, &di), "sgd_prepare");
+  CK(device_view(c, x, sizeof(float) * nnz, c->s_c, &dx), "sgd_prepare");
+  const size_t n1 = (size_t)std::max<int64_t>(nnz, 1);
+  CK(c->d_sgd_cnt.ensure(sizeof(unsigned long long) * nbuckets), "sgd_prepare");
+  CK(c->d_sgd_off.ensure(sizeof(int64_t) * (nbuckets + 1)), "sgd_prepare");
+  CK(c->d_sgd_key.ensure(sizeof(int64_t) * n1), "sgd_prepare");
+  CK(c->d_sgd_src.ensure(sizeof(int64_t) * n1), "sgd_prepare");
+  CK(c->d_sgd_u.ensure(sizeof(int32_t) * n1), "sgd_prepare");
+  CK(c->d_sgd_i.ensure(sizeof(int32_t) * n1), "sgd_prepare");
+  CK(c->d_sgd_x.ensure(sizeof(float) * n1), "sgd_prepare");
+  CK(c->d_sgd_range.ensure(sizeof(int64_t) * 2 * nb), "sgd_prepare");
+  CK(launch_sgd_order(g, nb, nnz, (const int32_t *)du, (const int32_t *)di,
+                      (const float *)dx, c->d_sgd_cnt.as<unsigned long long>(),
+                      c->d_sgd_off.as<int64_t>(), c->d_sgd_key.as<int64_t>(),
+                      c->d_sgd_src.as<int64_t>(), c->d_sgd_u.as<int32_t>(),
+                      c->d_sgd_i.as<int32_t>(), c->d_sgd_x.as<float>(),
+                      c->d_sgd_range.as<int64_t>(), c->d_err.as<int32_t>(),
+                      c->st), "sgd_prepare");
+  c->launches += nnz > 0 ? 6 : 2;
+  bsvd_status s = read_errors(c, "sgd_prepare");
+  if (s != BSVD_OK) return s;
+  // the diagonal schedule (Figure 2): blocks sharing no block row or column
+  std::vector<int32_t> blocks;
+  c->sgd_step_off.assign(1, 0);
+  if (c->diag) {
+    for (int32_t b = 0; b < nb; ++b) blocks.push_back(b);
+    c->sgd_step_off.push_back(nb);
+  } else if (c->p >= c->q) {
+    for (int32_t st = 0; st < c->p; ++st) {
+      for (int32_t j = 0; j < c->q; ++j)
+        blocks.push_back(((j + st) % c->p) * c->q + j);
+      c->sgd_step_off.push_back((int32_t)blocks.size());
+    }
+  } else {
+    for (int32_t st = 0; st < c->q; ++st) {
+      for (int32_t r = 0; r < c->p; ++r)
+        blocks.push_back(r * c->q + (r + st) % c->q);
+      c->sgd_step_off.push_back((int32_t)blocks.size());
+    }
+  }
+  CK(c->d_sgd_blocks.ensure(sizeof(int32_t) * blocks.size()), "sgd_prepare");
+  CK(cudaMemcpyAsync(c->d_sgd_blocks.p, blocks.data(),
+                     sizeof(int32_t) * blocks.size(), cudaMemcpyHostToDevice,
+                     c->st), "sgd_prepare");
+  CK(cudaStreamSynchronize(c->st), "sgd_prepare");
+  c->sgd_nnz = nnz;
+  c->sgd_ready = true;
+  return BSVD_OK;
+}
+
+static bsvd_status sgd_rmse(bsvd_ctx *c, double *out) {
+  double sum = 0.0;
+  CK(c->d_partials.ensure(sizeof(double) * kSqerrBlocks), "sgd_train");
+  CK(launch_sgd_sqerr(c->sgd_nnz, c->d_sgd_u.as<int32_t>(),
+                      c->d_sgd_i.as<int32_t>(), c->d_sgd_x.as<float>(),
+                      c->sgd_k, c->d_sgd_P.as<double>(), c->d_sgd_Q.as<double>(),
+                      c->d_sgd_bu.as<double>(), c->d_sgd_bi.as<double>(),
+                      c->d_partials.as<double>(), c->d_sgd_sum.as<double>(),
+                      c->st), "sgd_train");
+  c->launches += 2;
+  CK(cudaMemcpyAsync(&sum, c->d_sgd_sum.p, sizeof sum, cudaMemcpyDeviceToHost,
+                     c->st), "sgd_train");
+  CK(cudaStreamSynchronize(c->st), "sgd_train");
+  *out = c->sgd_nnz > 0 ? std::sqrt(sum / (double)c->sgd_nnz) : 0.0;
+  return BSVD_OK;
+}
+
+bsvd_status bsvd_sgd_train(bsvd_ctx *c, const bsvd_sgd_params *prm,
+                           const double *P0, const double *Q0, double *rmse,
+                           int32_t *steps_run) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (!c->sgd_ready) return fail(c, BSVD_ESTATE, "sgd_train: no sgd_prepare");
+  if (!prm || prm->k < 1 || prm->k > 32 || prm->max_steps < 0 ||
+      !(std::isfinite(prm->a_user) && std::isfinite(prm->b_user) &&
+        std::isfinite(prm->a_item) && std::isfinite(prm->b_item) &&
+        std::isfinite(prm->a_ubias) && std::isfinite(prm->b_ubias) &&
+        std::isfinite(prm->a_ibias) && std::isfinite(prm->b_ibias)) ||
+      std::isnan(prm->delta) || !P0 || !Q0)
+    return fail(c, BSVD_EINVAL, "sgd_train: bad parameters");
+  const int32_t k = prm->k;
+  c->sgd_trained = false;
+  c->sgd_k = k;
+  const size_t pb = sizeof(double) * (size_t)std::max<int64_t>(c->m * k, 1);
+  const size_t qb = sizeof(double) * (size_t)std::max<int64_t>(c->n * k, 1);
+  CK(c->d_sgd_P.ensure(pb), "sgd_train");
+  CK(c->d_sgd_Q.ensure(qb), "sgd_train");
+  CK(c->d_sgd_bu.ensure(sizeof(double) * std::max<int64_t>(c->m, 1)), "sgd_train");
+  CK(c->d_sgd_bi.ensure(sizeof(double) * std::max<int64_t>(c->n, 1)), "sgd_train");
+  CK(c->d_sgd_sum.ensure(sizeof(double)), "sgd_train");
+  CK(cudaMemcpyAsync(c->d_sgd_P.p, P0, sizeof(double) * c->m * k,
+                     cudaMemcpyDefault, c->st), "sgd_train");
+  CK(cudaMemcpyAsync(c->d_sgd_Q.p, Q0, sizeof(double) * c->n * k,
+                     cudaMemcpyDefault, c->st), "sgd_train");
+  CK(cudaMemsetAsync(c->d_sgd_bu.p, 0, sizeof(double) * c->m, c->st), "sgd_train");
+  CK(cudaMemsetAsync(c->d_sgd_bi.p, 0, sizeof(double) * c->n, c->st), "sgd_train");
+  const SgdRates r{prm->a_user, prm->b_user, prm->a_item, prm->b_item,
+                   prm->a_ubias, prm->b_ubias, prm->a_ibias, prm->b_ibias};
+  double prev = 0.0;
+  bsvd_status s = sgd_rmse(c, &prev);
+  if (s != BSVD_OK) return s;
+  if (rmse) rmse[0] = prev;
+  int32_t ran = 0;
+  for (int32_t step = 0; step < prm->max_steps; ++step) {
+    for (size_t t = 0; t + 1 < c->sgd_step_off.size(); ++t) {
+      const int32_t a = c->sgd_step_off[t], b = c->sgd_step_off[t + 1];
+      CK(launch_sgd_step(b - a, c->d_sgd_blocks.as<int32_t>() + a,
+                         c->d_sgd_range.as<int64_t>(), c->d_sgd_u.as<int32_t>(),
+                         c->d_sgd_i.as<int32_t>(), c->d_sgd_x.as<float>(), k,
+                         c->d_sgd_P.as<double>(), c->d_sgd_Q.as<double>(),
+                         c->d_sgd_bu.as<double>(), c->d_sgd_bi.as<double>(), r,
+                         c->st), "sgd_train");
+      c->launches += 1;
+    }
+    ++ran;
+    double cur = 0.0;
+    s = sgd_rmse(c, &cur);
+    if (s != BSVD_OK) return s;
+    if (rmse) rmse[ran] = cur;
+    const bool stop = prev - cur < prm->delta;
+    prev = cur;
+    if (stop) break;
+  }
+  if (steps_run) *steps_run = ran;
+  c->sgd_trained = true;
+  return BSVD_OK;
+}
+
+bsvd_status bsvd_sgd_predict(bsvd_ctx *c, int64_t nq, const int32_t *u,
+                             const int32_t *i, double *yhat) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (!c->sgd_trained) return fail(c, BSVD_ESTATE, "sgd_predict: not trained");
+  if (nq < 0 || (nq > 0 && (!u || !i || !yhat)))
+    return fail(c, BSVD_EINVAL, "sgd_predict: bad arguments");
+  if (nq == 0) return BSVD_OK;
+  const void *du, *di;
+  CK(device_view(c, u, sizeof(int32_t) * nq, c->s_a, &du), "sgd_predict");
+  CK(device_view(c, i, sizeof(int32_t) * nq, c->s_b, &di), "sgd_predict");
+  const bool dev_out = is_device_ptr(yhat);
+  double *out = yhat;
+  if (!dev_out) {
+    CK(c->s_out.ensure(sizeof(double) * nq), "sgd_predict");
+    out = c->s_out.as<double>();
+  }
+  CK(launch_sgd_predict(nq, (const int32_t *)du, (const int32_t *)di,
+                        c->sgd_k, c->m, c->n, c->d_sgd_P.as<double>(),
+                        c->d_sgd_Q.as<double>(), c->d_sgd_bu.as<double>(),
+                        c->d_sgd_bi.as<double>(), out, c->d_err.as<int32_t>(),
+                        c->st), "sgd_predict");
+  c->launches += 1;
+  if (!dev_out)
+    CK(cudaMemcpyAsync(yhat, out, sizeof(double) * nq, cudaMemcpyDeviceToHost,
+                       c->st), "sgd_predict");
+  return read_errors(c, "sgd_predict");
+}
+
+bsvd_status bsvd_sgd_get(bsvd_ctx *c, double *P, double *Q, double *bu,
+                         double *bi) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (!c->sgd_trained) return fail(c, BSVD_ESTATE, "sgd_get: not trained");
+  if (P)
+    CK(cudaMemcpyAsync(P, c->d_sgd_P.p, sizeof(double) * c->m * c->sgd_k,
+                       cudaMemcpyDefault, c->st), "sgd_get");
+  if (Q)
+    CK(cudaMemcpyAsync(Q, c->d_sgd_Q.p, sizeof(double) * c->n * c->sgd_k,
+                       cudaMemcpyDefault, c->st), "sgd_get");
+  if (bu)
+    CK(cudaMemcpyAsync(bu, c->d_sgd_bu.p, sizeof(double) * c->m,
+                       cudaMemcpyDefault, c->st), "sgd_get");
+  if (bi)
+    CK(cudaMemcpyAsync(bi, c->d_sgd_bi.p, sizeof(double) * c->n,
+                       cudaMemcpyDefault, c->st), "sgd_get");
+  CK(cudaStreamSynchronize(c->st), "sgd_get");
+  return BSVD_OK;
+}
 
 }  // extern "C"

@@ -120,6 +120,38 @@ cudaError_t launch_finalize(const BlockMeta *meta, int32_t nblocks,
                             float *Fs, float *FL, double *sigma, int32_t kp,
                             int32_t k, cudaStream_t st);
 
+// ---- blocked SGD, the paper's Algorithms 1-2 (kernels_sgd.cu) -------------
+struct SgdRates {
+  double a_user, b_user, a_item, b_item, a_ubias, b_ubias, a_ibias, b_ibias;
+};
+
+// Epoch order of the ratings: cnt and off hold (diag ? p : q) * m (+1)
+// buckets; key, src, su, si, sx hold nnz entries; range 2 per block.
+cudaError_t launch_sgd_order(const GridDesc &g, int32_t nblocks, int64_t nnz,
+                             const int32_t *u, const int32_t *i, const float *x,
+                             unsigned long long *cnt, int64_t *off,
+                             int64_t *key, int64_t *src, int32_t *su,
+                             int32_t *si, float *sx, int64_t *range,
+                             int32_t *err, cudaStream_t st);
+// One schedule step: nb blocks (ids in `blocks`), one warp each.
+cudaError_t launch_sgd_step(int32_t nb, const int32_t *blocks,
+                            const int64_t *range, const int32_t *su,
+                            const int32_t *si, const float *sx, int32_t k,
+                            double *P, double *Q, double *bu, double *bi,
+                            const SgdRates &r, cudaStream_t st);
+// Sum of squared training errors into *out (fixed order); partials holds
+// kSqerrBlocks doubles.
+cudaError_t launch_sgd_sqerr(int64_t nnz, const int32_t *u, const int32_t *i,
+                             const float *x, int32_t k, const double *P,
+                             const double *Q, const double *bu,
+                             const double *bi, double *partials, double *out,
+                             cudaStream_t st);
+cudaError_t launch_sgd_predict(int64_t nq, const int32_t *u, const int32_t *i,
+                               int32_t k, int64_t m, int64_t n,
+                               const double *P, const double *Q,
+                               const double *bu, const double *bi,
+                               double *yhat, int32_t *err, cudaStream_t st);
+
 // ---- prediction (kernels_predict.cu) ------------------------------------
 struct PredictArgs {
   GridDesc g;

@@ -1,0 +1,317 @@
+// The paper's own method: blocked stochastic gradient descent on the biased
+// latent-factor model (Section 2.2, Eq. 3 and 10-13; Algorithms 1-2), with
+// the blocks of one schedule step (Figure 2) processed at once.
+//
+// Epoch order. Algorithm 2 walks a block row by row, then column by column,
+// so each block's ratings are laid out row-major once, on the device:
+//   * bucket = (block column bj, the user's row position in the grid), so a
+//     block (bi, bj) is the consecutive buckets bj * m + [rb[bi], rb[bi+1]);
+//   * count, exclusive scan (one CTA, fixed order), scatter, then sort each
+//     bucket by (local column, input index): the order is deterministic
+//     even though the scatter is not.
+//
+// Step kernel. One warp per block of the step (the blocks of a step share
+// no user and no item, so they are independent). The warp walks its block's
+// ratings in order; lane f holds factor f of the current user and item.
+// The dot product is summed over f = 0 .. k-1 in order (every lane runs the
+// same chain of shuffles and adds, so all hold the same value) and every
+// operation is an explicitly rounded float64 add/sub/mul, so the result is
+// bit-identical to a sequential float64 loop without contraction.
+#include "kernels.h"
+
+namespace bsvd {
+
+namespace {
+
+__device__ __forceinline__ int64_t sgd_bucket(const GridDesc &g, int32_t blk,
+                                              int32_t r, int64_t m) {
+  const int32_t bi = g.diag ? blk : blk / g.q;
+  const int32_t bj = g.diag ? blk : blk % g.q;
+  const int64_t row0 = g.equal_rows ? (int64_t)bi * g.br : g.row_bounds[bi];
+  return (int64_t)bj * m + row0 + r;
+}
+
+__global__ void __launch_bounds__(256)
+k_sgd_count(GridDesc g, int64_t nnz, const int32_t *__restrict__ u,
+            const int32_t *__restrict__ it, unsigned long long *__restrict__ cnt,
+            int32_t *err) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int32_t blk, r, c;
+    if (!locate(g, u[t], it[t], &blk, &r, &c)) {
+      atomicOr(err, kErrIndex);
+      continue;
+    }
+    atomicAdd(&cnt[sgd_bucket(g, blk, r, g.m)], 1ull);
+  }
+}
+
+// Exclusive prefix sum of n counts into off[0 .. n] (off[n] = total), by one
+// CTA of 1024 threads: each thread sums a contiguous segment, the segment
+// sums are scanned in shared memory, then each thread writes its segment.
+__global__ void __launch_bounds__(1024)
+k_scan_exclusive(int64_t n, const unsigned long long *__restrict__ cnt,
+                 int64_t *__restrict__ off) {
+  __shared__ long long part[1024];
+  const int64_t seg = (n + 1023) / 1024;
+  const int64_t a = (int64_t)threadIdx.x * seg;
+  const int64_t b = a + seg < n ? a + seg : n;
+  long long s = 0;
+  for (int64_t e = a; e < b; ++e) s += (long long)cnt[e];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 1; w < 1024; w <<= 1) {
+    const long long v = threadIdx.x >= w ? part[threadIdx.x - w] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  long long run = part[threadIdx.x] - s;    // exclusive prefix of the segment
+  for (int64_t e = a; e < b; ++e) {
+    off[e] = run;
+    run += (long long)cnt[e];
+  }
+  if (threadIdx.x == 1023) off[n] = part[1023];
+}
+
+__global__ void __launch_bounds__(256)
+k_sgd_fill(GridDesc g, int64_t nnz, const int32_t *__restrict__ u,
+           const int32_t *__restrict__ it, const int64_t *__restrict__ off,
+           unsigned long long *__restrict__ cursor,
+           int64_t *__restrict__ key, int64_t *__restrict__ src) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int32_t blk, r, c;
+    if (!locate(g, u[t], it[t], &blk, &r, &c)) continue;   // flagged before
+    const int64_t bkt = sgd_bucket(g, blk, r, g.m);
+    const int64_t slot = off[bkt] + (int64_t)atomicAdd(&cursor[bkt], 1ull);
+    key[slot] = ((int64_t)c << 40) | t;     // nnz < 2^40 is checked by the host
+    src[slot] = t;
+  }
+}
+
+// One thread per bucket: insertion sort by key (local column, input index).
+__global__ void __launch_bounds__(256)
+k_sgd_sort(int64_t nbuckets, const int64_t *__restrict__ off,
+           int64_t *__restrict__ key, int64_t *__restrict__ src) {
+  for (int64_t bk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       bk < nbuckets; bk += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = off[bk], b = off[bk + 1];
+    for (int64_t e = a + 1; e < b; ++e) {
+      const int64_t kv = key[e], sv = src[e];
+      int64_t d = e - 1;
+      while (d >= a && key[d] > kv) {
+        key[d + 1] = key[d];
+        src[d + 1] = src[d];
+        --d;
+      }
+      key[d + 1] = kv;
+      src[d + 1] = sv;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_sgd_gather(int64_t nnz, const int64_t *__restrict__ src,
+             const int32_t *__restrict__ u, const int32_t *__restrict__ it,
+             const float *__restrict__ x, int32_t *__restrict__ su,
+             int32_t *__restrict__ si, float *__restrict__ sx) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = src[t];
+    su[t] = u[s];
+    si[t] = it[s];
+    sx[t] = x[s];
+  }
+}
+
+// [start, end) of every block's ratings in the epoch order
+__global__ void __launch_bounds__(256)
+k_sgd_ranges(GridDesc g, int32_t nblocks, const int64_t *__restrict__ off,
+             int64_t *__restrict__ range) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblocks;
+       b += gridDim.x * blockDim.x) {
+    const int32_t bi = g.diag ? b : b / g.q;
+    const int32_t bj = g.diag ? b : b % g.q;
+    const int64_t r0 = g.equal_rows ? (int64_t)bi * g.br : g.row_bounds[bi];
+    int64_t r1 = g.equal_rows ? (int64_t)(bi + 1) * g.br : g.row_bounds[bi + 1];
+    if (r1 > g.m) r1 = g.m;
+    range[2 * b] = off[(int64_t)bj * g.m + r0];
+    range[2 * b + 1] = off[(int64_t)bj * g.m + r1];
+  }
+}
+
+// One schedule step: warp w takes block blocks[w] and runs Algorithm 2 on it.
+__global__ void __launch_bounds__(32)
+k_sgd_step(const int32_t *__restrict__ blocks, const int64_t *__restrict__ range,
+           const int32_t *__restrict__ su, const int32_t *__restrict__ si,
+           const float *__restrict__ sx, int32_t k, double *P, double *Q,
+           double *bu, double *bi, SgdRates r) {
+  const int lane = threadIdx.x;
+  const int32_t b = blocks[blockIdx.x];
+  const int64_t t0 = range[2 * b], t1 = range[2 * b + 1];
+  const bool mine = lane < k;
+  for (int64_t t = t0; t < t1; ++t) {
+    const int32_t uu = su[t], ii = si[t];
+    const double x = (double)sx[t];
+    double *p = P + (int64_t)uu * k;
+    double *q = Q + (int64_t)ii * k;
+    const double pf = mine ? p[lane] : 0.0;
+    const double qf = mine ? q[lane] : 0.0;
+    const double prod = __dmul_rn(pf, qf);
+    double dot = 0.0;
+    for (int f = 0; f < k; ++f)
+      dot = __dadd_rn(dot, __shfl_sync(0xffffffffu, prod, f));
+    const double bu0 = bu[uu], bi0 = bi[ii];
+    const double e = __dsub_rn(__dsub_rn(__dsub_rn(x, bu0), bi0), dot);
+    if (lane == 0) {
+      bu[uu] = __dadd_rn(bu0, __dmul_rn(r.a_ubias,
+                                        __dsub_rn(e, __dmul_rn(r.b_ubias, bu0))));
+      bi[ii] = __dadd_rn(bi0, __dmul_rn(r.a_ibias,
+                                        __dsub_rn(e, __dmul_rn(r.b_ibias, bi0))));
+    }
+    if (mine) {
+      p[lane] = __dadd_rn(pf, __dmul_rn(r.a_user, __dsub_rn(
+                                  __dmul_rn(e, qf), __dmul_rn(r.b_user, pf))));
+      q[lane] = __dadd_rn(qf, __dmul_rn(r.a_item, __dsub_rn(
+                                  __dmul_rn(e, pf), __dmul_rn(r.b_item, qf))));
+    }
+    // the next rating may read what this one wrote, in another lane
+    __syncwarp();
+  }
+}
+
+// Eq. 3 in the oracle's order: (sum_f p_f q_f, in f order) + bu + bi
+__device__ __forceinline__ double sgd_eval(int32_t k, const double *P,
+                                           const double *Q, const double *bu,
+                                           const double *bi, int32_t uu,
+                                           int32_t ii) {
+  const double *p = P + (int64_t)uu * k;
+  const double *q = Q + (int64_t)ii * k;
+  double dot = 0.0;
+  for (int f = 0; f < k; ++f) dot = __dadd_rn(dot, __dmul_rn(p[f], q[f]));
+  return __dadd_rn(__dadd_rn(dot, bu[uu]), bi[ii]);
+}
+
+__global__ void __launch_bounds__(256)
+k_sgd_predict(int64_t nq, const int32_t *__restrict__ u,
+              const int32_t *__restrict__ it, int32_t k, int64_t m, int64_t n,
+              const double *__restrict__ P, const double *__restrict__ Q,
+              const double *__restrict__ bu, const double *__restrict__ bi,
+              double *__restrict__ yhat, int32_t *err) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nq;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t uu = u[t], ii = it[t];
+    if (uu < 0 || uu >= m || ii < 0 || ii >= n) {
+      atomicOr(err, kErrIndex);
+      yhat[t] = 0.0;
+      continue;
+    }
+    yhat[t] = sgd_eval(k, P, Q, bu, bi, uu, ii);
+  }
+}
+
+// Squared training errors: per-CTA partial sums in a fixed tree, then one
+// CTA adds the partials in index order.
+__global__ void __launch_bounds__(256)
+k_sgd_sqerr(int64_t nnz, const int32_t *__restrict__ u,
+            const int32_t *__restrict__ it, const float *__restrict__ x,
+            int32_t k, const double *__restrict__ P,
+            const double *__restrict__ Q, const double *__restrict__ bu,
+            const double *__restrict__ bi, double *__restrict__ partials) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double d = __dsub_rn((double)x[t], sgd_eval(k, P, Q, bu, bi, u[t],
+                                                      it[t]));
+    acc = __dadd_rn(acc, __dmul_rn(d, d));
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(512)
+k_sgd_sum(const double *__restrict__ partials, int n, double *out) {
+  __shared__ double red[512];
+  red[threadIdx.x] = threadIdx.x < n ? partials[threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int w = 256; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+int sgd_grid(int64_t n) {
+  int64_t want = (n + 255) / 256;
+  if (want < 1) want = 1;
+  if (want > 152 * 8) want = 152 * 8;
+  return (int)want;
+}
+
+}  // namespace
+
+cudaError_t launch_sgd_order(const GridDesc &g, int32_t nblocks, int64_t nnz,
+                             const int32_t *u, const int32_t *i, const float *x,
+                             unsigned long long *cnt, int64_t *off,
+                             int64_t *key, int64_t *src, int32_t *su,
+                             int32_t *si, float *sx, int64_t *range,
+                             int32_t *err, cudaStream_t st) {
+  const int64_t nbuckets = (int64_t)(g.diag ? g.p : g.q) * g.m;
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * nbuckets,
+                                  st);
+  if (e != cudaSuccess) return e;
+  if (nnz > 0)
+    k_sgd_count<<<sgd_grid(nnz), 256, 0, st>>>(g, nnz, u, i, cnt, err);
+  k_scan_exclusive<<<1, 1024, 0, st>>>(nbuckets, cnt, off);
+  e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * nbuckets, st);
+  if (e != cudaSuccess) return e;
+  if (nnz > 0) {
+    k_sgd_fill<<<sgd_grid(nnz), 256, 0, st>>>(g, nnz, u, i, off, cnt, key, src);
+    k_sgd_sort<<<sgd_grid(nbuckets), 256, 0, st>>>(nbuckets, off, key, src);
+    k_sgd_gather<<<sgd_grid(nnz), 256, 0, st>>>(nnz, src, u, i, x, su, si, sx);
+  }
+  k_sgd_ranges<<<(nblocks + 255) / 256, 256, 0, st>>>(g, nblocks, off, range);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sgd_step(int32_t nb, const int32_t *blocks,
+                            const int64_t *range, const int32_t *su,
+                            const int32_t *si, const float *sx, int32_t k,
+                            double *P, double *Q, double *bu, double *bi,
+                            const SgdRates &r, cudaStream_t st) {
+  if (nb <= 0) return cudaSuccess;
+  k_sgd_step<<<nb, 32, 0, st>>>(blocks, range, su, si, sx, k, P, Q, bu, bi, r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sgd_sqerr(int64_t nnz, const int32_t *u, const int32_t *i,
+                             const float *x, int32_t k, const double *P,
+                             const double *Q, const double *bu,
+                             const double *bi, double *partials, double *out,
+                             cudaStream_t st) {
+  static_assert(kSqerrBlocks <= 512, "final sum is one CTA of 512");
+  k_sgd_sqerr<<<kSqerrBlocks, 256, 0, st>>>(nnz, u, i, x, k, P, Q, bu, bi,
+                                            partials);
+  k_sgd_sum<<<1, 512, 0, st>>>(partials, kSqerrBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sgd_predict(int64_t nq, const int32_t *u, const int32_t *i,
+                               int32_t k, int64_t m, int64_t n,
+                               const double *P, const double *Q,
+                               const double *bu, const double *bi,
+                               double *yhat, int32_t *err, cudaStream_t st) {
+  if (nq <= 0) return cudaSuccess;
+  k_sgd_predict<<<sgd_grid(nq), 256, 0, st>>>(nq, u, i, k, m, n, P, Q, bu, bi,
+                                              yhat, err);
+  return cudaGetLastError();
+}
+
+}  // namespace bsvd

@@ -303,3 +303,13 @@ def served_requests(seed: int, count: int,
                         qr=r[q].astype(np.int32), qc=c[q].astype(np.int32),
                         qy=val[q]))
     return out
+
+
+def sgd_start(m: int, n: int, k: int, seed: int = 13):
+    """Starting factors of the blocked SGD: P0 (m x k) and Q0 (n x k), float64,
+    entries N(0, 0.1^2). The paper only says the latent feature matrices
+    start from random values; the distribution and scale are this module's
+    choice."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return (rng.normal(0.0, 0.1, size=(m, k)),
+            rng.normal(0.0, 0.1, size=(n, k)))

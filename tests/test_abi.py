@@ -39,3 +39,23 @@ def test_config_layout_matches_header():
     assert ctypes.sizeof(bs.Config) == 72
     assert bs.Config.tol.offset == 40 and bs.Config.stream.offset == 56
     assert bs.Config.panel_path.offset == 64 and cfg.panel_path == 0
+
+
+def test_binding_signatures_match_header_arity():
+    """Every declared function has ctypes argument types, as many as the
+    header's parameter list (a missing one would silently convert a pointer
+    to a C int)."""
+    lib = bs.load()
+    text = ""
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text += open(os.path.join(ROOT, "include", fn)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    decls = re.findall(r"\b(bsvd_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", text)
+    assert len(decls) >= 20
+    for name, params in decls:
+        params = params.strip()
+        arity = 0 if params in ("", "void") else params.count(",") + 1
+        f = getattr(lib, name)
+        assert f.argtypes is not None, name
+        assert len(f.argtypes) == arity, (name, len(f.argtypes), arity)
