@@ -8,7 +8,9 @@ ratings, 90/10 split) on a 4 x 4 grid with k = 20.
 
 At N=1 the line also carries the served form ("served"): Poisson streams of
 factorise-then-predict requests through the continuous-batching server, at
-each --serve-rates rate, beside the same requests run one at a time.
+each --serve-rates rate, beside the same requests run one at a time; and the
+paper's own blocked SGD ("sgd", Algorithms 1-2): seconds per epoch on the
+same matrix, beside one epoch of the FP64 oracle.
 
 Prints one JSON line (rank 0). Usage:
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -302,6 +304,60 @@ def serve_leg(rates, workers=4, max_batch=64, budget=120e9):
     return out
 
 
+def sgd_leg(r, w, epochs=10, grids=(8, 64)):
+    """The paper's own method (blocked SGD, Algorithms 1-2) on the same
+    matrix: `epochs` epochs from seeded starting factors with the Section 5
+    hyper-parameters (k = 13), on the 8 x 8 grid the paper's CPU run used
+    and on a finer grid (more blocks per step). The time of an epoch covers
+    its schedule steps and the training-RMSE of Algorithm 1's stopping rule.
+    Beside it, one epoch of the sequential FP64 oracle on the host."""
+    import torch
+    import paper_1907_07410_gb300 as bs
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    k = 13
+    P0, Q0 = synth.sgd_start(w.m, w.n, k)
+    dP, dQ = dev(P0), dev(Q0)
+    u, i, x = dev(r.u_train), dev(r.i_train), dev(r.x_train)
+    out = {"k": k, "epochs": epochs, "rates": "Section 5 (SVD model)",
+           "start": "P0, Q0 ~ N(0, 0.1^2) (seeded), biases 0", "grids": []}
+    for g in grids:
+        ctx = bs.Context()
+        ctx.partition(w.m, w.n, u, i, x, g, g)
+        ctx.sgd_prepare(u, i, x)
+        ctx.sgd_train(dP, dQ, max_steps=1, delta=-1e300)       # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist, ran = ctx.sgd_train(dP, dQ, max_steps=epochs, delta=-1e300)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        yh = ctx.sgd_predict(r.u_test, r.i_test)
+        test = float(np.sqrt(np.mean((yh - r.x_test) ** 2)))
+        out["grids"].append({
+            "grid": "%dx%d" % (g, g), "s_per_epoch": dt / ran,
+            "ratings_per_s": r.u_train.size * ran / dt,
+            "train_rmse_start": float(hist[0]),
+            "train_rmse_end": float(hist[-1]), "test_rmse_end": test})
+    # the oracle: one epoch, sequential, on the host
+    import oracle
+    from oracle import sgd as osgd
+    grid = oracle.make_grid(w.m, w.n, grids[0], grids[0])
+    order = osgd.processing_order(grid, r.u_train, r.i_train)
+    uo, io, xo = r.u_train[order], r.i_train[order], r.x_train[order]
+    P, Q = P0.copy(), Q0.copy()
+    bu, bi = np.zeros(w.m), np.zeros(w.n)
+    t0 = time.perf_counter()
+    osgd.sgd_pass(uo, io, xo, P, Q, bu, bi, osgd.Rates())
+    out["cpu_baseline"] = {"kind": "oracle", "cores": 1,
+                           "s_per_epoch": time.perf_counter() - t0,
+                           "sample": "one epoch of the sequential FP64 oracle "
+                                     "(C), %dx%d grid order" % (grids[0],
+                                                                grids[0])}
+    out["paper_context"] = ("BGSVD 13.45 s/iteration and BCSVD 34.53 "
+                            "s/iteration on MovieLens 1M (Tesla M40, Xeon "
+                            "E5-2640 v3); real data, not comparable")
+    return out
+
+
 def host_grid(w, r):
     """Bounds and permutations of an activity-quantile grid (host side)."""
     if w.grid != "quantile":
@@ -321,6 +377,8 @@ def main():
     ap.add_argument("--precision", default="fp32",
                     choices=("fp32", "tf32", "bf16"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sgd", action="store_true",
+                    help="skip the blocked-SGD leg (the paper's Algorithms 1-2)")
     ap.add_argument("--serve-rates", default="50,500,5000",
                     help="Poisson rates (req/s) of the served-form leg; "
                          "empty to skip it")
@@ -521,6 +579,8 @@ def main():
     rates = [float(v) for v in args.serve_rates.split(",") if v.strip()]
     if world == 1 and rates:
         line["served"] = serve_leg(rates)
+    if world == 1 and not args.no_sgd and w.name == synth.MEDIUM.name:
+        line["sgd"] = sgd_leg(r, w)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
