@@ -304,7 +304,7 @@ def serve_leg(rates, workers=4, max_batch=64, budget=120e9):
     return out
 
 
-def sgd_leg(r, w, epochs=10, grids=(8, 64)):
+def sgd_leg(r, w, epochs=10, grids=(8, 64, 256)):
     """The paper's own method (blocked SGD, Algorithms 1-2) on the same
     matrix: `epochs` epochs from seeded starting factors with the Section 5
     hyper-parameters (k = 13), on the 8 x 8 grid the paper's CPU run used

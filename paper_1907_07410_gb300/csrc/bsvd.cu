@@ -1260,15 +1260,18 @@ bsvd_status bsvd_sgd_train(bsvd_ctx *c, const bsvd_sgd_params *prm,
       const int32_t a = c->sgd_step_off[t], b = c->sgd_step_off[t + 1];
       CK(launch_sgd_step(b - a, c->d_sgd_blocks.as<int32_t>() + a,
                          c->d_sgd_range.as<int64_t>(), c->d_sgd_u.as<int32_t>(),
-                         c->d_sgd_i.as<int32_t>(), c->d_sgd_x.as<float>(), k,
-                         c->d_sgd_P.as<double>(), c->d_sgd_Q.as<double>(),
-                         c->d_sgd_bu.as<double>(), c->d_sgd_bi.as<double>(), r,
+                         c->d_sgd_i.as<int32_t>(), c->d_sgd_x.as<float>(),
+                         c->sgd_nnz, k, c->d_sgd_P.as<double>(),
+                         c->d_sgd_Q.as<double>(), c->d_sgd_bu.as<double>(),
+                         c->d_sgd_bi.as<double>(), r, c->d_err.as<int32_t>(),
                          c->st), "sgd_train");
       c->launches += 1;
     }
     ++ran;
     double cur = 0.0;
     s = sgd_rmse(c, &cur);
+    if (s != BSVD_OK) return s;
+    s = read_errors(c, "sgd_train");
     if (s != BSVD_OK) return s;
     if (rmse) rmse[ran] = cur;
     const bool stop = prev - cur < prm->delta;

@@ -136,9 +136,10 @@ cudaError_t launch_sgd_order(const GridDesc &g, int32_t nblocks, int64_t nnz,
 // One schedule step: nb blocks (ids in `blocks`), one warp each.
 cudaError_t launch_sgd_step(int32_t nb, const int32_t *blocks,
                             const int64_t *range, const int32_t *su,
-                            const int32_t *si, const float *sx, int32_t k,
-                            double *P, double *Q, double *bu, double *bi,
-                            const SgdRates &r, cudaStream_t st);
+                            const int32_t *si, const float *sx, int64_t nnz,
+                            int32_t k, double *P, double *Q, double *bu,
+                            double *bi, const SgdRates &r, int32_t *err,
+                            cudaStream_t st);
 // Sum of squared training errors into *out (fixed order); partials holds
 // kSqerrBlocks doubles.
 cudaError_t launch_sgd_sqerr(int64_t nnz, const int32_t *u, const int32_t *i,

@@ -27,7 +27,8 @@ __device__ __forceinline__ int64_t sgd_bucket(const GridDesc &g, int32_t blk,
                                               int32_t r, int64_t m) {
   const int32_t bi = g.diag ? blk : blk / g.q;
   const int32_t bj = g.diag ? blk : blk % g.q;
-  const int64_t row0 = g.equal_rows ? (int64_t)bi * g.br : g.row_bounds[bi];
+  int64_t row0 = g.equal_rows ? (int64_t)bi * g.br : g.row_bounds[bi];
+  if (row0 > m) row0 = m;
   return (int64_t)bj * m + row0 + r;
 }
 
@@ -133,8 +134,12 @@ k_sgd_ranges(GridDesc g, int32_t nblocks, const int64_t *__restrict__ off,
        b += gridDim.x * blockDim.x) {
     const int32_t bi = g.diag ? b : b / g.q;
     const int32_t bj = g.diag ? b : b % g.q;
-    const int64_t r0 = g.equal_rows ? (int64_t)bi * g.br : g.row_bounds[bi];
+    // with equal blocks, trailing block rows can lie wholly past m (e.g.
+    // 256 rows of ceil(6040 / 256) = 24): clamp both ends, so such a block
+    // has an empty range and every index stays inside off[0 .. buckets]
+    int64_t r0 = g.equal_rows ? (int64_t)bi * g.br : g.row_bounds[bi];
     int64_t r1 = g.equal_rows ? (int64_t)(bi + 1) * g.br : g.row_bounds[bi + 1];
+    if (r0 > g.m) r0 = g.m;
     if (r1 > g.m) r1 = g.m;
     range[2 * b] = off[(int64_t)bj * g.m + r0];
     range[2 * b + 1] = off[(int64_t)bj * g.m + r1];
@@ -142,42 +147,77 @@ k_sgd_ranges(GridDesc g, int32_t nblocks, const int64_t *__restrict__ off,
 }
 
 // One schedule step: warp w takes block blocks[w] and runs Algorithm 2 on it.
+//
+// Software pipelined: while rating t is updated, the ids, rating, factor
+// rows and biases of rating t+1 are loaded. A user (item) shared by t and
+// t+1 is not reloaded: the values just computed for t are carried in
+// registers instead (every lane computes the new biases the same way, lane
+// 0 stores them). Anything else t+1 reads was last written by an earlier
+// rating, in program order in the same lane (factors) or before the
+// __syncwarp that ends that rating (biases). The arithmetic is unchanged,
+// so the results stay bit-identical to the sequential order.
 __global__ void __launch_bounds__(32)
 k_sgd_step(const int32_t *__restrict__ blocks, const int64_t *__restrict__ range,
            const int32_t *__restrict__ su, const int32_t *__restrict__ si,
-           const float *__restrict__ sx, int32_t k, double *P, double *Q,
-           double *bu, double *bi, SgdRates r) {
+           const float *__restrict__ sx, int64_t nnz, int32_t k, double *P,
+           double *Q, double *bu, double *bi, SgdRates r, int32_t *err) {
   const int lane = threadIdx.x;
   const int32_t b = blocks[blockIdx.x];
   const int64_t t0 = range[2 * b], t1 = range[2 * b + 1];
+  if (t0 < 0 || t1 > nnz || t0 > t1) {     // never expected: refuse to run
+    if (lane == 0) atomicOr(err, kErrIndex);
+    return;
+  }
+  if (t0 == t1) return;
   const bool mine = lane < k;
+  int32_t uu = su[t0], ii = si[t0];
+  float xx = sx[t0];
+  double pf = mine ? P[(int64_t)uu * k + lane] : 0.0;
+  double qf = mine ? Q[(int64_t)ii * k + lane] : 0.0;
+  double bu0 = bu[uu], bi0 = bi[ii];
   for (int64_t t = t0; t < t1; ++t) {
-    const int32_t uu = su[t], ii = si[t];
-    const double x = (double)sx[t];
-    double *p = P + (int64_t)uu * k;
-    double *q = Q + (int64_t)ii * k;
-    const double pf = mine ? p[lane] : 0.0;
-    const double qf = mine ? q[lane] : 0.0;
+    // loads for rating t+1, except rows and biases it shares with t
+    const bool more = t + 1 < t1;
+    const int32_t un = more ? su[t + 1] : uu;
+    const int32_t in = more ? si[t + 1] : ii;
+    const float xn = more ? sx[t + 1] : 0.f;
+    const bool new_u = un != uu, new_i = in != ii;
+    const double pn = (mine && new_u) ? P[(int64_t)un * k + lane] : 0.0;
+    const double qn = (mine && new_i) ? Q[(int64_t)in * k + lane] : 0.0;
+    const double bun = new_u ? bu[un] : 0.0;
+    const double bin = new_i ? bi[in] : 0.0;
+    // rating t
     const double prod = __dmul_rn(pf, qf);
     double dot = 0.0;
     for (int f = 0; f < k; ++f)
       dot = __dadd_rn(dot, __shfl_sync(0xffffffffu, prod, f));
-    const double bu0 = bu[uu], bi0 = bi[ii];
-    const double e = __dsub_rn(__dsub_rn(__dsub_rn(x, bu0), bi0), dot);
+    const double e = __dsub_rn(__dsub_rn(__dsub_rn((double)xx, bu0), bi0), dot);
+    const double bu1 = __dadd_rn(bu0, __dmul_rn(r.a_ubias, __dsub_rn(
+                                          e, __dmul_rn(r.b_ubias, bu0))));
+    const double bi1 = __dadd_rn(bi0, __dmul_rn(r.a_ibias, __dsub_rn(
+                                          e, __dmul_rn(r.b_ibias, bi0))));
+    const double p1 = __dadd_rn(pf, __dmul_rn(r.a_user, __dsub_rn(
+                                        __dmul_rn(e, qf), __dmul_rn(r.b_user, pf))));
+    const double q1 = __dadd_rn(qf, __dmul_rn(r.a_item, __dsub_rn(
+                                        __dmul_rn(e, pf), __dmul_rn(r.b_item, qf))));
     if (lane == 0) {
-      bu[uu] = __dadd_rn(bu0, __dmul_rn(r.a_ubias,
-                                        __dsub_rn(e, __dmul_rn(r.b_ubias, bu0))));
-      bi[ii] = __dadd_rn(bi0, __dmul_rn(r.a_ibias,
-                                        __dsub_rn(e, __dmul_rn(r.b_ibias, bi0))));
+      bu[uu] = bu1;
+      bi[ii] = bi1;
     }
     if (mine) {
-      p[lane] = __dadd_rn(pf, __dmul_rn(r.a_user, __dsub_rn(
-                                  __dmul_rn(e, qf), __dmul_rn(r.b_user, pf))));
-      q[lane] = __dadd_rn(qf, __dmul_rn(r.a_item, __dsub_rn(
-                                  __dmul_rn(e, pf), __dmul_rn(r.b_item, qf))));
+      P[(int64_t)uu * k + lane] = p1;
+      Q[(int64_t)ii * k + lane] = q1;
     }
-    // the next rating may read what this one wrote, in another lane
+    // the next rating's loads (issued above or in the next iteration) may
+    // read what this one wrote, in another lane
     __syncwarp();
+    pf = new_u ? pn : p1;
+    qf = new_i ? qn : q1;
+    bu0 = new_u ? bun : bu1;
+    bi0 = new_i ? bin : bi1;
+    uu = un;
+    ii = in;
+    xx = xn;
   }
 }
 
@@ -283,11 +323,13 @@ cudaError_t launch_sgd_order(const GridDesc &g, int32_t nblocks, int64_t nnz,
 
 cudaError_t launch_sgd_step(int32_t nb, const int32_t *blocks,
                             const int64_t *range, const int32_t *su,
-                            const int32_t *si, const float *sx, int32_t k,
-                            double *P, double *Q, double *bu, double *bi,
-                            const SgdRates &r, cudaStream_t st) {
+                            const int32_t *si, const float *sx, int64_t nnz,
+                            int32_t k, double *P, double *Q, double *bu,
+                            double *bi, const SgdRates &r, int32_t *err,
+                            cudaStream_t st) {
   if (nb <= 0) return cudaSuccess;
-  k_sgd_step<<<nb, 32, 0, st>>>(blocks, range, su, si, sx, k, P, Q, bu, bi, r);
+  k_sgd_step<<<nb, 32, 0, st>>>(blocks, range, su, si, sx, nnz, k, P, Q, bu,
+                                bi, r, err);
   return cudaGetLastError();
 }
 

@@ -161,3 +161,13 @@ def test_call_order_and_bad_arguments():
     assert e.value.status == bs.ESTATE
     hist, ran = ctx.sgd_train(P0, Q0, max_steps=0)
     assert ran == 0 and len(hist) == 1
+
+
+def test_equal_grid_with_empty_trailing_block_rows():
+    """300 users on 32 block rows of ceil(300 / 32) = 10: block row 31 lies
+    wholly past the last user, and so do its blocks in every step."""
+    r = synth.random_ratings(33, 300, 200, 5000, 0)
+    ctx, hist, ran, ref = run_both(r, 32, 32, 5, 2)
+    assert_same(ctx, hist, ran, ref)
+    ctx, hist, ran, ref = run_both(r, 32, 7, 5, 2)
+    assert_same(ctx, hist, ran, ref)
