@@ -721,31 +721,50 @@ k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
   float acc[2][KM];
 #pragma unroll
   for (int j = 0; j < KM; ++j) { acc[0][j] = 0.f; acc[1][j] = 0.f; }
+  // W rows of the chunk at a0 that this warp handles: warp + 8 h
+  auto load_w = [&](int a0, float2 (&w)[CH / 8]) {
+    const int lim = min(CH, bm.s - a0);
+#pragma unroll
+    for (int h = 0; h < CH / 8; ++h) {
+      const int rr = warp + 8 * h;
+      w[h] = (lv && rr < lim) ? *reinterpret_cast<const float2 *>(
+                                    Wb + (int64_t)(a0 + rr) * bm.L_pad + l)
+                              : make_float2(0.f, 0.f);
+    }
+  };
+  // the warp's 8 rows of a chunk are all in flight at once, and the next
+  // chunk's rows are loaded while this chunk's products run
+  float2 w[CH / 8], wn[CH / 8];
+  load_w(0, w);
   for (int a0 = 0; a0 < bm.s; a0 += CH) {
     for (int e = threadIdx.x; e < CH * KM; e += blockDim.x) {
       const int rr = e / KM, j = e % KM;
       Fsh[rr][j] = (a0 + rr < bm.s && j < kp) ? Fb[(int64_t)(a0 + rr) * kp + j] : 0.f;
     }
     __syncthreads();
+    if (a0 + CH < bm.s) load_w(a0 + CH, wn);
     const int lim = min(CH, bm.s - a0);
     if (lv) {
-      for (int rr = warp; rr < lim; rr += 8) {
-        const float2 w = *reinterpret_cast<const float2 *>(
-            Wb + (int64_t)(a0 + rr) * bm.L_pad + l);
+#pragma unroll
+      for (int h = 0; h < CH / 8; ++h) {
+        const int rr = warp + 8 * h;
+        if (rr >= lim) break;
 #pragma unroll
         for (int j = 0; j < KM; j += 4) {
           const float4 f = *reinterpret_cast<const float4 *>(&Fsh[rr][j]);
-          acc[0][j] = fmaf(w.x, f.x, acc[0][j]);
-          acc[0][j + 1] = fmaf(w.x, f.y, acc[0][j + 1]);
-          acc[0][j + 2] = fmaf(w.x, f.z, acc[0][j + 2]);
-          acc[0][j + 3] = fmaf(w.x, f.w, acc[0][j + 3]);
-          acc[1][j] = fmaf(w.y, f.x, acc[1][j]);
-          acc[1][j + 1] = fmaf(w.y, f.y, acc[1][j + 1]);
-          acc[1][j + 2] = fmaf(w.y, f.z, acc[1][j + 2]);
-          acc[1][j + 3] = fmaf(w.y, f.w, acc[1][j + 3]);
+          acc[0][j] = fmaf(w[h].x, f.x, acc[0][j]);
+          acc[0][j + 1] = fmaf(w[h].x, f.y, acc[0][j + 1]);
+          acc[0][j + 2] = fmaf(w[h].x, f.z, acc[0][j + 2]);
+          acc[0][j + 3] = fmaf(w[h].x, f.w, acc[0][j + 3]);
+          acc[1][j] = fmaf(w[h].y, f.x, acc[1][j]);
+          acc[1][j + 1] = fmaf(w[h].y, f.y, acc[1][j + 1]);
+          acc[1][j + 2] = fmaf(w[h].y, f.z, acc[1][j + 2]);
+          acc[1][j + 3] = fmaf(w[h].y, f.w, acc[1][j + 3]);
         }
       }
     }
+#pragma unroll
+    for (int h = 0; h < CH / 8; ++h) w[h] = wn[h];
     __syncthreads();
   }
 #pragma unroll
