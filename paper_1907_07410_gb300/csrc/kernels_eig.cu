@@ -58,6 +58,23 @@ constexpr float kMinAmplification = 1e3f;
 constexpr float kAmpBackoff = 1e2f;
 constexpr float kCutFloor = 1e-3f;   // cut >= kCutFloor * theta_1
 constexpr float kPivotDrop = 1e-4f;  // squared sine of the angle to the span
+
+// hardware approximations (PTX .approx instructions, flush-to-zero)
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 constexpr int KC = 32;       // k-chunk of the panel GEMM
 
 __device__ __forceinline__ float hash_uniform(uint64_t seed, uint64_t a,
@@ -351,11 +368,18 @@ __device__ int onesided_jacobi(float (*Ac)[B + 1], float (*Vc)[B + 1], int n,
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
         if (!(ga * ga > (tol * tol) * (al * be))) continue;
-        const float zeta = (be - al) * __frcp_rn(2.f * ga);
-        const float t = copysignf(__frcp_rn(fabsf(zeta) +
-                                            __fsqrt_rn(fmaf(zeta, zeta, 1.f))),
-                                  zeta);
-        const float c = __frsqrt_rn(fmaf(t, t, 1.f));
+        // The angle only has to be close to the optimal one (any rotation
+        // near it still converges), so t uses the hardware's approximate
+        // reciprocal and square root; what must be accurate is c^2 + s^2 = 1,
+        // so c = 1/sqrt(1 + t^2) gets one Newton step after the approximate
+        // reciprocal square root. |zeta| large enough to overflow zeta^2
+        // gives t = 0 and no rotation, as before.
+        const float zeta = (be - al) * rcp_approx(2.f * ga);
+        const float t = copysignf(
+            rcp_approx(fabsf(zeta) + sqrt_approx(fmaf(zeta, zeta, 1.f))), zeta);
+        const float x = fmaf(t, t, 1.f);
+        float c = rsqrt_approx(x);
+        c = c * fmaf(-0.5f * x, c * c, 1.5f);
         const float s = t * c;
         if (s == 0.f) continue;
         if (lane == 0) *flag = 1;
@@ -416,6 +440,8 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
     float s = 0.f, h = 0.f;
+    // unrolled so the loads run ahead; the adds stay in tile order
+#pragma unroll 8
     for (int t = 0; t < bm.nt; ++t) {
       s += part[(int64_t)t * 2 * B * B + i * B + j];
       h += part[(int64_t)t * 2 * B * B + B * B + i * B + j];
@@ -635,6 +661,7 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   const float *th = theta + (int64_t)blk * B;
   if (threadIdx.x < B) {
     float a = 0.f, b = 0.f;
+#pragma unroll 8
     for (int t = 0; t < bm.nt; ++t) {
       const float *rp = RP + (int64_t)(bm.t0 + t) * 2 * B;
       a += rp[threadIdx.x];
