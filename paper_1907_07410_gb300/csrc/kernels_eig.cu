@@ -462,24 +462,36 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
     sm.S[i][j] = (di > 0.f && dj > 0.f) ? sm.S[i][j] / (di * dj) : (i == j ? 0.f : 0.f);
   }
   __syncthreads();
-  // 3. Cholesky S_n = L L^T, left-looking: column j from columns < j, one
-  // barrier per column. Every thread recomputes the pivot (same operands,
-  // same order), row i's thread writes L[i][j]. Weak pivots are dropped:
-  // the column is treated as zero below its unit diagonal.
+  // 3. Cholesky S_n = L L^T, right-looking: for each column j, the pivot
+  // S[j][j] already holds S_jj - sum_{l<j} L_jl^2 (subtracted one l at a
+  // time, in order), the column below it is scaled, then every thread
+  // updates its entries of the trailing triangle, S[i][l] -= L_ij L_lj.
+  // This is the same sequence of fused multiply-adds per entry as a
+  // left-looking loop over l, but with O(1) work per thread per column.
+  // Weak pivots are dropped: the column is treated as zero below its unit
+  // diagonal, so it also changes nothing in the trailing update.
   for (int j = 0; j < n; ++j) {
-    float piv = sm.S[j][j];
-    for (int l = 0; l < j; ++l) piv = fmaf(-sm.S[j][l], sm.S[j][l], piv);
+    const float piv = sm.S[j][j];
     const bool drop = !(piv > kPivotDrop);
     const float ljj = drop ? 1.f : __fsqrt_rn(piv);
     const float inv = __frcp_rn(ljj);
-    for (int i = j + 1 + tid; i < n; i += blockDim.x) {
-      float v = sm.S[i][j];
-      for (int l = 0; l < j; ++l) v = fmaf(-sm.S[i][l], sm.S[j][l], v);
-      sm.S[i][j] = drop ? 0.f : v * inv;
-    }
+    for (int i = j + 1 + tid; i < n; i += blockDim.x)
+      sm.S[i][j] = drop ? 0.f : sm.S[i][j] * inv;
     if (tid == 0) {
       sm.drop[j] = drop;
       sm.key[j] = ljj;          // L's diagonal; S[j][j] stays readable
+    }
+    __syncthreads();
+    // trailing triangle j < l <= i < n, one entry per thread
+    const int m = n - 1 - j;
+    for (int e = tid; e < m * (m + 1) / 2; e += blockDim.x) {
+      // e -> (ii, ll) with 0 <= ll <= ii < m, row-major over the triangle
+      int ii = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+      while (ii * (ii + 1) / 2 > e) --ii;
+      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+      const int ll = e - ii * (ii + 1) / 2;
+      const int i = j + 1 + ii, l = j + 1 + ll;
+      sm.S[i][l] = fmaf(-sm.S[i][j], sm.S[l][j], sm.S[i][l]);
     }
     __syncthreads();
   }
