@@ -249,13 +249,15 @@ bsvd_status bsvd_reconstruct(bsvd_ctx *ctx, int32_t b, int32_t add_mean,
  * any may be NULL): Rayleigh-Ritz steps used, 1 where the block converged,
  * Jacobi sweeps summed over the steps, SM clock cycles spent in the
  * Rayleigh-Ritz kernel (3 per block: partial sums + Cholesky QR + H',
- * Jacobi, ordering + output) summed over the steps, and the last
+ * Jacobi, ordering + output) summed over the steps, the last
  * relative residual max_i |G v_i - theta_i v_i| / theta_1 over the k_eff
- * wanted pairs (converged means <= tol).
+ * wanted pairs (converged means <= tol), and the number of panel products
+ * G X run for the block (each 2 s_pad^2 b multiply-adds' worth of work).
  */
 bsvd_status bsvd_factor_report(bsvd_ctx *ctx, int32_t *iters,
                                int32_t *converged, int32_t *sweeps,
-                               int64_t *cycles, float *resid);
+                               int64_t *cycles, float *resid,
+                               int32_t *products);
 
 /*
  * Phase timings of the last calls, in milliseconds of device time between

@@ -96,7 +96,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                  ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
                                  vp, vp, vp, vp]),
         "bsvd_reconstruct": (i32, [vp, i32, i32, vp]),
-        "bsvd_factor_report": (i32, [vp, vp, vp, vp, vp, vp]),
+        "bsvd_factor_report": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "bsvd_phase_times": (i32, [vp, vp]),
         "bsvd_kernel_launches": (i64, [vp]),
         "bsvd_gram_path": (i32, [vp]),
@@ -302,13 +302,14 @@ def bsvd_factor_report(ctx, nblocks: int, full: bool = False):
     sweeps = np.zeros(nblocks, np.int32)
     cycles = np.zeros((nblocks, 3), np.int64)
     resid = np.zeros(nblocks, np.float32)
+    products = np.zeros(nblocks, np.int32)
     st = load().bsvd_factor_report(ctx, iters.ctypes.data, conv.ctypes.data,
                                    sweeps.ctypes.data, cycles.ctypes.data,
-                                   resid.ctypes.data)
+                                   resid.ctypes.data, products.ctypes.data)
     _check(ctx, st)
     if full:
         return dict(iters=iters, converged=conv, sweeps=sweeps, cycles=cycles,
-                    resid=resid)
+                    resid=resid, products=products)
     return iters, conv
 
 

@@ -1085,7 +1085,8 @@ bsvd_status bsvd_reconstruct(bsvd_ctx *c, int32_t b, int32_t add_mean,
 
 bsvd_status bsvd_factor_report(bsvd_ctx *c, int32_t *iters,
                                int32_t *converged, int32_t *sweeps,
-                               int64_t *cycles, float *resid) {
+                               int64_t *cycles, float *resid,
+                               int32_t *products) {
   if (!c) return BSVD_EINVAL;
   c->err.clear();
   if (!c->factored) return fail(c, BSVD_ESTATE, "factor_report: no factors");
@@ -1100,6 +1101,7 @@ bsvd_status bsvd_factor_report(bsvd_ctx *c, int32_t *iters,
     if (cycles)
       for (int j = 0; j < 3; ++j) cycles[3 * b + j] = s[b].cycles[j];
     if (resid) resid[b] = s[b].resid;
+    if (products) products[b] = s[b].products;
   }
   return BSVD_OK;
 }

@@ -52,6 +52,8 @@ struct SolverState {
   uint64_t refill;      // Ritz columns refilled with random vectors
   int32_t sweeps;       // Jacobi sweeps used so far
   float amp;            // this block's filter amplification cap (0: default)
+  int32_t products;     // panel products G X run for this block
+  int32_t pad;
   int64_t cycles[3];    // SM clock cycles in the Rayleigh-Ritz kernel:
                         // [0] sums + Cholesky QR + H', [1] Jacobi, [2] rest
 };

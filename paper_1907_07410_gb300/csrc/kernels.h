@@ -89,7 +89,7 @@ struct EigBuffers {
 // (block, first row) pairs of 128 rows, gmaps one TMA map per block over G,
 // xmaps one per block over `in` (s_pad x bsub float32, 32-row boxes).
 cudaError_t launch_gpanel_tc(int32_t bsub, const BlockMeta *meta,
-                             const SolverState *state, const int2 *tiles,
+                             SolverState *state, const int2 *tiles,
                              int32_t ntiles, const CUtensorMap *gmaps,
                              const CUtensorMap *xmaps, const float *in,
                              const float *in2, float *out, int mode, int step,

@@ -133,8 +133,7 @@ __device__ __forceinline__ void group_sync(int g) {
 
 template <int B>
 __global__ void __launch_bounds__(512, (B >= 64 ? 1 : 2))
-k_gpanel(const BlockMeta *__restrict__ meta,
-         const SolverState *__restrict__ state,
+k_gpanel(const BlockMeta *__restrict__ meta, SolverState *state,
          const int2 *__restrict__ rowtiles, const float *__restrict__ G,
          const float *in, const float *in2, float *out, int mode, int step) {
   constexpr int CN = B / 8;                // output columns per thread
@@ -144,6 +143,7 @@ k_gpanel(const BlockMeta *__restrict__ meta,
   const SolverState st = state[t.x];
   if (st.status != kRunning) return;
   if (mode >= 1 && step > st.degree) return;   // this block's filter is done
+  if (t.y == 0 && threadIdx.x == 0) atomicAdd(&state[t.x].products, 1);
   const BlockMeta bm = meta[t.x];
   const int sp = bm.s_pad;
   const int row0 = t.y;

@@ -109,8 +109,7 @@ __device__ __forceinline__ uint32_t sw128(int r, int c) {
 
 template <int B>
 __global__ void __launch_bounds__(192, 1)
-k_gpanel_tc(const BlockMeta *__restrict__ meta,
-            const SolverState *__restrict__ state,
+k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
             const int2 *__restrict__ tiles, const CUtensorMap *__restrict__ gmaps,
             const CUtensorMap *__restrict__ xmaps, const float *in,
             const float *in2, float *out, int mode, int step, int32_t *err) {
@@ -128,6 +127,7 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta,
   if (mode >= 1 && step > st.degree) return;
   const BlockMeta bm = meta[t.x];
   const int sp = bm.s_pad, row0 = t.y;
+  if (row0 == 0 && threadIdx.x == 0) atomicAdd(&state[t.x].products, 1);
   const int nk = sp / PK;                 // s_pad is a multiple of 32
   const float *inb = in + bm.x_off;
   float alpha, beta, gamma;
@@ -316,7 +316,7 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta,
 }
 
 template <int B>
-cudaError_t launch_b(const BlockMeta *meta, const SolverState *state,
+cudaError_t launch_b(const BlockMeta *meta, SolverState *state,
                      const int2 *tiles, int32_t ntiles,
                      const CUtensorMap *gmaps, const CUtensorMap *xmaps,
                      const float *in, const float *in2, float *out, int mode,
@@ -335,7 +335,7 @@ cudaError_t launch_b(const BlockMeta *meta, const SolverState *state,
 }  // namespace
 
 cudaError_t launch_gpanel_tc(int32_t bsub, const BlockMeta *meta,
-                             const SolverState *state, const int2 *tiles,
+                             SolverState *state, const int2 *tiles,
                              int32_t ntiles, const CUtensorMap *gmaps,
                              const CUtensorMap *xmaps, const float *in,
                              const float *in2, float *out, int mode, int step,
