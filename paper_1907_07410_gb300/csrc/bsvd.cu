@@ -98,6 +98,7 @@ struct bsvd_ctx {
   int32_t n_gtiles = 0, n_rowtiles = 0, n_ltiles = 0;
   // tensor-core panel products: 128-row tiles and one TMA map per block of G
   DevBuf d_ptiles, d_gmaps, d_xmaps;
+  DevBuf d_XB, d_ZB;         // B forms of the panels X, Z (2 s_pad x B floats)
   int32_t n_ptiles = 0;
   std::vector<CUtensorMap> h_gmaps, h_xmaps;
 
@@ -311,7 +312,7 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->d_rowtiles, &c->d_ltiles, &c->s_a, &c->s_b, &c->s_c,
                     &c->s_out, &c->d_partials, &c->d_rmse, &c->d_VX,
                     &c->d_shift, &c->d_delta, &c->d_maps, &c->d_flag,
-                    &c->d_wmaps, &c->d_ptiles, &c->d_gmaps, &c->d_xmaps,
+                    &c->d_wmaps, &c->d_ptiles, &c->d_gmaps, &c->d_xmaps, &c->d_XB, &c->d_ZB,
                     &c->d_sgd_cnt, &c->d_sgd_off, &c->d_sgd_key,
                     &c->d_sgd_src, &c->d_sgd_u, &c->d_sgd_i, &c->d_sgd_x,
                     &c->d_sgd_range, &c->d_sgd_blocks, &c->d_sgd_P,
@@ -723,23 +724,26 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     CK(cudaMemcpyAsync(c->d_gmaps.p, c->h_gmaps.data(),
                        sizeof(CUtensorMap) * nb, cudaMemcpyHostToDevice, c->st),
        "factor");
-    // and over the two panel buffers X, Z (s_pad x B float32, 32-row boxes):
+    // and over the B forms of the two panel buffers (per block: s_pad / 32
+    // chunks of 2 B rows x 32 floats, one chunk per box, 128-byte swizzle):
     // maps [0, nb) read X, maps [nb, 2 nb) read Z
+    CK(c->d_XB.ensure(sizeof(float) * 2 * std::max<int64_t>(xoff, 1)), "factor");
+    CK(c->d_ZB.ensure(sizeof(float) * 2 * std::max<int64_t>(xoff, 1)), "factor");
     c->h_xmaps.assign(2 * (size_t)nb, CUtensorMap());
     std::memset(c->h_xmaps.data(), 0, sizeof(CUtensorMap) * 2 * nb);
     for (int h = 0; h < 2; ++h) {
-      float *panel = h == 0 ? c->d_X.as<float>() : c->d_Z.as<float>();
+      float *bform = h == 0 ? c->d_XB.as<float>() : c->d_ZB.as<float>();
       for (int32_t b = 0; b < nb; ++b) {
         const BlockMeta &bm = c->meta[b];
         if (bm.s == 0) continue;
-        cuuint64_t dims[2] = {(cuuint64_t)B, (cuuint64_t)bm.s_pad};
-        cuuint64_t strides[1] = {(cuuint64_t)B * 4};
-        cuuint32_t box[2] = {(cuuint32_t)B, 32};
+        cuuint64_t dims[2] = {32, (cuuint64_t)(bm.s_pad / 32) * 2 * B};
+        cuuint64_t strides[1] = {128};
+        cuuint32_t box[2] = {32, (cuuint32_t)(2 * B)};
         cuuint32_t es[2] = {1, 1};
         CUresult r = enc(&c->h_xmaps[(size_t)h * nb + b],
-                         CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, panel + bm.x_off,
+                         CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, bform + 2 * bm.x_off,
                          dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS)
@@ -780,18 +784,27 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     e.seed = c->cfg.seed;
     const int2 *rtd = c->d_rowtiles.as<int2>();
     const int nrt = c->n_rowtiles;
-    // out = alpha G in + beta in + gamma in2 (see launch_gpanel)
+    // out = alpha G in + beta in + gamma in2 (see launch_gpanel). The
+    // tensor-core path reads the B form of `in` and writes that of `out`.
     auto panel = [&](int mode, int step, int deg, const float *in,
                      const float *in2, float *out) -> cudaError_t {
       if (panel_tc) {
         const CUtensorMap *xm = c->d_xmaps.as<CUtensorMap>() +
                                 (in == e.X ? 0 : (size_t)nb);
+        float *out_bf = out == e.X ? c->d_XB.as<float>() : c->d_ZB.as<float>();
         return launch_gpanel_tc(B, e.meta, e.state, c->d_ptiles.as<int2>(),
                                 c->n_ptiles, c->d_gmaps.as<CUtensorMap>(), xm,
-                                in, in2, out, mode, step,
+                                in, in2, out, out_bf, mode, step,
                                 c->d_err.as<int32_t>(), c->st);
       }
       return launch_gpanel(e, rtd, nrt, mode, step, deg, in, in2, out, c->st);
+    };
+    // B form of X after a kernel other than a panel product wrote it
+    auto bform_x = [&]() -> cudaError_t {
+      if (!panel_tc) return cudaSuccess;
+      ++c->launches;
+      return launch_bform(B, e.meta, e.state, c->d_ptiles.as<int2>(),
+                          c->n_ptiles, e.X, c->d_XB.as<float>(), c->st);
     };
 
     std::fill(c->phase_ms + 1, c->phase_ms + 4, 0.0);
@@ -823,6 +836,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     }
     mark(c, 1);
     CK(launch_init_panels(e, rtd, nrt, c->st), "factor: init");
+    CK(bform_x(), "factor: B form");
     CK(panel(0, 0, 0, e.X, nullptr, e.Z), "factor: G X");
     c->launches += (c->n_gtiles > 0) + 2 * (nrt > 0);
     for (int it = 0; it <= c->cfg.max_iters + 1; ++it) {
@@ -851,6 +865,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
       // Chebyshev filter of even degree: Y_1 -> Z, Y_2 -> X, ..., Y_d -> X
       // step j reads Y_{j-1}, Y_{j-2} and overwrites Y_{j-2} with Y_j
       mark(c, 8);
+      CK(bform_x(), "factor: B form");
       for (int j = 1; j <= deg; ++j) {
         const bool even = j % 2 == 0;
         const float *in = even ? e.Z : e.X;

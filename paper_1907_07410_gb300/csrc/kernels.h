@@ -87,13 +87,23 @@ struct EigBuffers {
 
 // Panel product on the tensor cores (three tf32 passes): tiles are
 // (block, first row) pairs of 128 rows, gmaps one TMA map per block over G,
-// xmaps one per block over `in` (s_pad x bsub float32, 32-row boxes).
+// xmaps one per block over the B form of `in` (32-float rows, 2 bsub-row
+// boxes, 128-byte swizzle). The B form of a panel P (s_pad x bsub) sits at
+// 2 x_off: for each 32-row chunk, bsub rows of hi(P) then bsub rows of
+// lo(P), 32 floats each (hi = P rounded to 10 mantissa bits, lo = P - hi).
+// out_bf (optional) receives the B form of `out`.
 cudaError_t launch_gpanel_tc(int32_t bsub, const BlockMeta *meta,
                              SolverState *state, const int2 *tiles,
                              int32_t ntiles, const CUtensorMap *gmaps,
                              const CUtensorMap *xmaps, const float *in,
-                             const float *in2, float *out, int mode, int step,
-                             int32_t *err, cudaStream_t st);
+                             const float *in2, float *out, float *out_bf,
+                             int mode, int step, int32_t *err,
+                             cudaStream_t st);
+// B form of `in` for the blocks still running (tiles as above).
+cudaError_t launch_bform(int32_t bsub, const BlockMeta *meta,
+                         const SolverState *state, const int2 *tiles,
+                         int32_t ntiles, const float *in, float *in_bf,
+                         cudaStream_t st);
 
 // row tiles: (block, first row) pairs, 64 rows each.
 cudaError_t launch_init_panels(const EigBuffers &e, const int2 *rowtiles,

@@ -3,7 +3,7 @@
 // for one 128-row tile of one block's Gram matrix G (s_pad x s_pad, float32,
 // symmetric) and its b-column panel `in` (s_pad x b, row-major).
 //
-// Precision: three tf32 passes. Every float32 operand x is split into
+// Precision: three tf32 products. Every float32 operand x is split into
 // hi = x rounded to 10 mantissa bits (exact in tf32) and lo = x - hi
 // (exact in float32, |lo| <= 2^-11 |x|), and
 //   G in ~= G_hi in_hi + G_hi in_lo + G_lo in_hi.
@@ -12,35 +12,46 @@
 // bits to the MMA) makes the result independent of how the hardware narrows
 // f32 to tf32.
 //
+// The panel operand is read in "B form": for each 32-row chunk of `in`,
+// b rows of hi (one per panel column, its 32 values of that chunk), then b
+// rows of lo, 32 floats each (s_pad x 2b floats per block). It is K-major,
+// as the MMA's B operand must be, and the split is done once per panel
+// rather than once per 128-row tile of G. The epilogue writes the B form of
+// `out` next to it (when asked), so each product feeds the next; launch_bform
+// converts a panel written by another kernel.
+//
+// Data path, per stage of 64 floats of K:
+//   * warp 0: TMA loads into a ring of stages: the G tile (128 rows x 64
+//     floats, as two 32-float boxes) and the two matching B-form chunks
+//     (2b rows x 32 floats each), all with 128-byte swizzling;
+//   * warps 2-5 (converters): each thread reads one row of the G tile,
+//     splits it in registers and stores hi and lo into a tensor-memory slot
+//     (tcgen05.st; lane = row, one column per K element), the A operand
+//     layout of kind::tf32. The tensor core reads shared memory at 128 bytes
+//     per cycle, so an A operand read from shared memory (4 KiB per K = 8)
+//     would cost 32 cycles per MMA;
+//   * warp 1: per K = 8 slice, two MMAs with A in tensor memory:
+//     G_hi x [in_hi | in_lo] (N = 2b) and G_lo x in_hi (N = b). The first
+//     gives the main product and one cross term side by side; the second adds
+//     the other cross term onto the first's cross half.
+// Warps 0 and 1 run their loops as whole warps, so addresses and
+// descriptors stay warp-uniform, and one elected lane issues. Measured on
+// GB300 (clock stamps per stage), a single lane running the same loop took
+// about 90 cycles per MMA and 300 more per satisfied barrier wait; now a
+// stage's 16 MMAs issue in about 400 cycles and the converters, at about
+// 500 cycles per 32 floats of K, set the pace. One 988-row block (8 CTAs)
+// takes about 17 us per product, a 4000-row block about 44 us.
+//
 // Accumulation: the tensor core's f32 accumulator does not round to
 // nearest at each step (a measured one-signed error growing with the number
 // of accumulating MMAs), so long chains drift: one accumulator over the
-// whole K range of a 1000-row block gave errors near 1e-5 relative. The
-// hi*hi products therefore go round-robin into four accumulators and the
-// two small cross terms into a fifth; the epilogue adds the five in a fixed
-// order. This brings the product to within about 1e-6 of float64 on such
-// blocks, comparable to the FP32 SIMT product, as the 1e-5 residual test of
-// the solver needs.
+// whole K range of a 1000-row block gave errors near 1e-5 relative. The K
+// slices therefore go round-robin into R accumulators (4, or 2 for b = 64,
+// as tensor memory allows) and the epilogue adds them in a fixed order,
+// main halves and cross halves separately, then the two sums.
 //
-// CTA roles (192 threads):
-//   * warp 0, one lane: TMA loads into a ring of stages: the G tile, 128 rows
-//     x 32 floats with 128-byte swizzling, and the matching 32 rows of `in`
-//     (32 x b floats, plain layout);
-//   * warps 2-5: split each G tile in place (hi) and into a second buffer
-//     (lo) (the swizzle is a permutation of 16-byte chunks, so elementwise
-//     work ignores it); split the rows of `in` and store them transposed
-//     (one 128-byte row per panel column, the same swizzle), so both MMA
-//     operands are K-major;
-//   * warp 1, one lane: tcgen05.mma kind::tf32, M = 128, N = b, K = 8,
-//     three per K slice, into 5 b TMEM columns; its commit frees the stage.
-// Then the epilogue: warp w of warps 2-5 reads TMEM lanes 32 (w mod 4) ..
-// +31, i.e. one output row per thread.
-//
-// Measured on GB300 (clock64 stamps per stage): issuing a stage's 12 MMAs
-// takes about 850 cycles, and its conversion about 1000, so the kernel is
-// bound by MMA issue and conversion latency, not by memory: per launch it
-// is 2.6x faster than the FP32 SIMT product on 4000-row blocks and 1.2-1.5x
-// on 1000-row blocks.
+// Tensor memory (512 columns): R accumulators of 2b columns, then SA slots
+// of 128 columns (64 hi, 64 lo) for the A operand.
 //
 // Every wait is bounded; a timeout sets kErrTimeout and the CTA drains its
 // copies in flight and frees its tensor memory before returning.
@@ -52,34 +63,42 @@ namespace bsvd {
 namespace {
 
 constexpr int PT = 128;                  // G rows per CTA (MMA M)
-constexpr int PK = 32;                   // floats of K per stage (128 bytes)
+constexpr int PK = 64;                   // floats of K per stage
+constexpr int PH = 32;                   // floats per 128-byte swizzle row
+constexpr int kThreads = 192;            // 6 warps
 constexpr int kMaxStages = 4;
+constexpr int kSlots = 2;                // A slots in tensor memory
 constexpr uint32_t kSpinP = 1u << 22;    // mbarrier polls before giving up
 constexpr uint32_t kHiMask = 0xFFFFE000u;
 constexpr uint32_t kHiHalf = 0x00001000u;
-constexpr int A_BYTES = PT * PK * 4;     // 16 KiB
-constexpr int kAcc = 5;                  // 4 hi*hi accumulators + cross terms
+constexpr int G_HALF = PT * PH * 4;      // 16 KiB: one 32-float box of G
+constexpr int G_BYTES = 2 * G_HALF;
+constexpr int kTmemCols = 512;
 
 template <int B>
 struct PanelTc {
-  static constexpr int B_BYTES = B * PK * 4;    // B rows of 128 bytes
-  static constexpr int X_BYTES = PK * B * 4;    // 32 rows of `in`
-  // A hi (TMA destination, split in place), A lo, B hi, B lo, rows of `in`
-  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES + X_BYTES;
+  static constexpr int BOP_HALF = 2 * B * 128;      // one B-form chunk
+  static constexpr int BOP_BYTES = 2 * BOP_HALF;
+  static constexpr int STAGE = G_BYTES + BOP_BYTES;
   static constexpr int STAGES = B >= 64 ? 3 : 4;
-  static constexpr int TMEM_COLS = kAcc * B <= 128 ? 128
-                                   : (kAcc * B <= 256 ? 256 : 512);
+  static constexpr int R = B >= 64 ? 2 : 4;          // accumulators
+  static constexpr int ACC_COLS = R * 2 * B;
+  static constexpr bool kWaitSlot = kSlots < STAGES; // else implied by `empty`
+  static_assert(STAGE % 1024 == 0, "stage regions stay 1024-byte aligned");
+  static_assert(ACC_COLS + kSlots * 2 * PK <= kTmemCols, "tensor memory");
+  static_assert(STAGES <= kMaxStages && STAGES >= kSlots, "ring sizes");
 };
 
 struct PanelCtrl {
   uint64_t full[kMaxStages];    // G tile and rows of `in` landed (TMA bytes)
-  uint64_t ready[kMaxStages];   // operands split and stored (4 converter warps)
   uint64_t empty[kMaxStages];   // the stage's MMAs completed
+  uint64_t ready[kSlots];       // A slot written (4 converter warps)
+  uint64_t afree[kSlots];       // the MMAs reading the A slot completed
   uint64_t done;                // every MMA completed
   uint32_t tmem;
   int abort;
   int issued;                   // stages whose loads were issued
-  int consumed;                 // stages the converters saw land
+  int consumed;                 // stages the A converters saw land
 };
 
 template <int B>
@@ -107,18 +126,39 @@ __device__ __forceinline__ uint32_t sw128(int r, int c) {
   return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
 }
 
+// Sum of the R accumulators' 32 columns at `col`, in a fixed order:
+// (a0 + a1) + (a2 + a3), or a0 + a1.
 template <int B>
-__global__ void __launch_bounds__(192, 1)
+__device__ __forceinline__ void acc_sum(uint32_t taddr, uint32_t col,
+                                        float (&v)[32]) {
+  using L = PanelTc<B>;
+  float t[32];
+  tc::tmem_ld32(taddr + col, v);
+  tc::tmem_ld32(taddr + col + 2 * B, t);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] += t[j];
+  if constexpr (L::R == 4) {
+    float u[32];
+    tc::tmem_ld32(taddr + col + 4 * B, u);
+    tc::tmem_ld32(taddr + col + 6 * B, t);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] += u[j] + t[j];
+  }
+}
+
+template <int B>
+__global__ void __launch_bounds__(kThreads, 1)
 k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
             const int2 *__restrict__ tiles, const CUtensorMap *__restrict__ gmaps,
             const CUtensorMap *__restrict__ xmaps, const float *in,
-            const float *in2, float *out, int mode, int step, int32_t *err) {
+            const float *in2, float *out, float *out_bf, int mode, int step,
+            int32_t *err) {
   using L = PanelTc<B>;
-  constexpr int PSTAGES = L::STAGES;
+  constexpr int S = L::STAGES;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  PanelCtrl &ct = *reinterpret_cast<PanelCtrl *>(base + PSTAGES * L::STAGE);
+  PanelCtrl &ct = *reinterpret_cast<PanelCtrl *>(base + S * L::STAGE);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int2 t = tiles[blockIdx.x];
   const SolverState st = state[t.x];
@@ -128,27 +168,24 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
   const BlockMeta bm = meta[t.x];
   const int sp = bm.s_pad, row0 = t.y;
   if (row0 == 0 && threadIdx.x == 0) atomicAdd(&state[t.x].products, 1);
-  const int nk = sp / PK;                 // s_pad is a multiple of 32
+  // s_pad is a multiple of 32: a last half stage reads zeros past s_pad
+  const int nk = (sp + PK - 1) / PK;
   const float *inb = in + bm.x_off;
   float alpha, beta, gamma;
   cheb_coeffs(st, mode, step, &alpha, &beta, &gamma);
 
-  auto a_hi = [&](int s) { return base + s * L::STAGE; };
-  auto a_lo = [&](int s) { return base + s * L::STAGE + A_BYTES; };
-  auto b_hi = [&](int s) { return base + s * L::STAGE + 2 * A_BYTES; };
-  auto b_lo = [&](int s) {
-    return base + s * L::STAGE + 2 * A_BYTES + L::B_BYTES;
-  };
-  auto x_raw = [&](int s) {
-    return base + s * L::STAGE + 2 * A_BYTES + 2 * L::B_BYTES;
-  };
+  auto g_tile = [&](int s) { return base + s * L::STAGE; };
+  auto b_op = [&](int s) { return base + s * L::STAGE + G_BYTES; };
 
-  if (warp == 0) tc::tmem_alloc(&ct.tmem, L::TMEM_COLS);
+  if (warp == 0) tc::tmem_alloc(&ct.tmem, kTmemCols);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < PSTAGES; ++s) {
+    for (int s = 0; s < S; ++s) {
       tc::mbar_init(&ct.full[s], 1);
-      tc::mbar_init(&ct.ready[s], 4);
       tc::mbar_init(&ct.empty[s], 1);
+    }
+    for (int a = 0; a < kSlots; ++a) {
+      tc::mbar_init(&ct.ready[a], 4);
+      tc::mbar_init(&ct.afree[a], 1);
     }
     tc::mbar_init(&ct.done, 1);
     ct.abort = 0;
@@ -160,102 +197,119 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = ct.tmem;
+  const uint32_t aslots = taddr + L::ACC_COLS;    // A slot a at +128 a
   volatile int *abort_flag = &ct.abort;
 
   if (warp == 0) {
-    if (lane == 0) {
-      const CUtensorMap *map = gmaps + t.x;
-      const CUtensorMap *xmap = xmaps + t.x;
-      for (int kc = 0; kc < nk; ++kc) {
-        const int s = kc % PSTAGES;
-        const uint32_t ph = (kc / PSTAGES) & 1;
-        if (!tc::mbar_wait(&ct.empty[s], ph ^ 1, kSpinP) || *abort_flag) {
-          atomicOr(err, kErrTimeout);
-          ct.abort = 1;
-          break;
-        }
-        tc::mbar_expect_tx(&ct.full[s], A_BYTES + L::X_BYTES);
-        tc::tma_load_2d(a_hi(s), map, kc * PK, row0, &ct.full[s]);
-        tc::tma_load_2d(x_raw(s), xmap, 0, kc * PK, &ct.full[s]);
+    // the whole warp runs the loop (warp-uniform addresses); one lane issues
+    const CUtensorMap *map = gmaps + t.x;
+    const CUtensorMap *xmap = xmaps + t.x;
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % S;
+      const uint32_t ph = (kc / S) & 1;
+      const bool ok = __all_sync(
+          0xffffffffu,
+          tc::mbar_wait(&ct.empty[s], ph ^ 1, kSpinP) && !*abort_flag);
+      if (!ok) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        ct.abort = 1;
+        break;
+      }
+      if (tc::elect_one()) {
+        const int k0 = kc * PK;
+        tc::mbar_expect_tx(&ct.full[s], G_BYTES + L::BOP_BYTES);
+        tc::tma_load_2d(g_tile(s), map, k0, row0, &ct.full[s]);
+        tc::tma_load_2d(g_tile(s) + G_HALF, map, k0 + PH, row0, &ct.full[s]);
+        // B-form chunks 2 kc and 2 kc + 1 (past the last: zero fill)
+        tc::tma_load_2d(b_op(s), xmap, 0, 2 * kc * 2 * B, &ct.full[s]);
+        tc::tma_load_2d(b_op(s) + L::BOP_HALF, xmap, 0, (2 * kc + 1) * 2 * B,
+                        &ct.full[s]);
         ct.issued = kc + 1;
       }
+      __syncwarp();
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_tf32_f32(PT, B);
-      for (int kc = 0; kc < nk; ++kc) {
-        const int c = kc % PSTAGES;
-        const uint32_t ph = (kc / PSTAGES) & 1;
-        if (!tc::mbar_wait(&ct.ready[c], ph, kSpinP) || *abort_flag) {
-          atomicOr(err, kErrTimeout);
-          ct.abort = 1;
-          break;
-        }
-        tc::fence_after_sync();
-        const uint64_t dah = tc::sdesc_kmajor_sw128(tc::smem_u32(a_hi(c)));
-        const uint64_t dal = tc::sdesc_kmajor_sw128(tc::smem_u32(a_lo(c)));
-        const uint64_t dbh = tc::sdesc_kmajor_sw128(tc::smem_u32(b_hi(c)));
-        const uint64_t dbl = tc::sdesc_kmajor_sw128(tc::smem_u32(b_lo(c)));
-#pragma unroll
-        for (int kk = 0; kk < PK / 8; ++kk) {    // 32 bytes of K per MMA
-          const uint64_t o = 2 * kk;
-          // hi*hi into accumulator kk (of 4), cross terms into the fifth
-          tc::mma_tf32(taddr + kk * B, dah + o, dbh + o, idesc,
-                       kc > 0 ? 1u : 0u);
-          tc::mma_tf32(taddr + 4 * B, dah + o, dbl + o, idesc,
-                       (kc > 0 || kk > 0) ? 1u : 0u);
-          tc::mma_tf32(taddr + 4 * B, dal + o, dbh + o, idesc, 1u);
-        }
-        tc::mma_commit(&ct.empty[c]);
-      }
-      tc::mma_commit(&ct.done);
-    }
-  } else {
-    // converters: 128 threads
-    const int cid = threadIdx.x - 64;
+    // the whole warp runs the loop (warp-uniform descriptors); one lane issues
+    constexpr uint32_t idesc2 = tc::idesc_tf32_f32(PT, 2 * B);
+    constexpr uint32_t idesc1 = tc::idesc_tf32_f32(PT, B);
     for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % PSTAGES;
-      const uint32_t ph = (kc / PSTAGES) & 1;
+      const int s = kc % S, a = kc % kSlots;
+      const bool ok = __all_sync(
+          0xffffffffu, tc::mbar_wait(&ct.ready[a], (kc / kSlots) & 1, kSpinP) &&
+                           !*abort_flag);
+      if (!ok) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        ct.abort = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint64_t db0 = tc::sdesc_kmajor_sw128(tc::smem_u32(b_op(s)));
+      const uint64_t db1 =
+          tc::sdesc_kmajor_sw128(tc::smem_u32(b_op(s) + L::BOP_HALF));
+      const uint32_t ahi = aslots + 2 * PK * a, alo = ahi + PK;
+      if (tc::elect_one()) {
+        // K slice 8 kc + kk goes to accumulator kk mod R; the first R
+        // slices start their accumulators
+#pragma unroll
+        for (int kk = 0; kk < PK / 8; ++kk) {
+          const uint32_t d = taddr + 2 * B * (kk % L::R);
+          const uint64_t db = (kk < 4 ? db0 : db1) + 2 * (kk & 3);
+          const uint32_t acc = (kc > 0 || kk >= L::R) ? 1u : 0u;
+          // [G_hi in_hi | G_hi in_lo], then G_lo in_hi onto the cross half
+          tc::mma_tf32_ta(d, ahi + 8 * kk, db, idesc2, acc);
+          tc::mma_tf32_ta(d + B, alo + 8 * kk, db, idesc1, 1u);
+        }
+        tc::mma_commit(&ct.empty[s]);
+        tc::mma_commit(&ct.afree[a]);
+      }
+      __syncwarp();
+    }
+    if (tc::elect_one()) tc::mma_commit(&ct.done);
+    __syncwarp();
+  } else {
+    // converters: 128 threads; warp w may touch TMEM lanes 32 (w mod 4) ..
+    const int cid = threadIdx.x - 64;
+    const int q = warp & 3;
+    const int r = q * 32 + lane;                  // G tile row of this thread
+    const uint32_t lrow = (uint32_t)(q * 32) << 16;
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % S, a = kc % kSlots;
+      const uint32_t ph = (kc / S) & 1;
       // warp-uniform: every lane breaks, or none does
-      const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&ct.full[s], ph,
-                                                            kSpinP) &&
-                                                  !*abort_flag);
+      bool ok = tc::mbar_wait(&ct.full[s], ph, kSpinP);
+      if constexpr (L::kWaitSlot)
+        ok = ok && tc::mbar_wait(&ct.afree[a], ((kc / kSlots) & 1) ^ 1, kSpinP);
+      ok = __all_sync(0xffffffffu, ok && !*abort_flag);
       if (!ok) {
         if (lane == 0) atomicOr(err, kErrTimeout);
         ct.abort = 1;
         break;
       }
       if (cid == 0) ct.consumed = kc + 1;
-      // A: split the 128 x 32 tile in place (hi) and into the lo buffer
-      float4 *ah = reinterpret_cast<float4 *>(a_hi(s));
-      float4 *al = reinterpret_cast<float4 *>(a_lo(s));
+      tc::fence_after_sync();
+      // this thread's row of the G tile, split into hi and lo columns
 #pragma unroll
-      for (int h = 0; h < A_BYTES / 16 / 128; ++h) {
-        const int i = cid + 128 * h;
-        const float4 g = ah[i];
-        const float4 gh = hi4(g);
-        ah[i] = gh;
-        al[i] = sub4(g, gh);
-      }
-      // B: rows k0 .. k0+31 of `in` (plain layout), stored transposed.
-      // Thread (n, part) takes column n and the 16-byte chunks q = part,
-      // part + P, ... of its 128-byte row (4 consecutive k each).
-      constexpr int P = 128 / B;              // threads per column (2, 4, 8)
-      const int n = cid % B, part = cid / B;
-      const float *src = reinterpret_cast<const float *>(x_raw(s)) + n;
+      for (int kh = 0; kh < 2; ++kh) {
+        const unsigned char *g = g_tile(s) + kh * G_HALF;
+        float h[32], l[32];
 #pragma unroll
-      for (int q = part; q < PK / 4; q += P) {
-        const float4 v = make_float4(src[(4 * q + 0) * B], src[(4 * q + 1) * B],
-                                     src[(4 * q + 2) * B], src[(4 * q + 3) * B]);
-        const float4 vh = hi4(v);
-        const uint32_t off = sw128(n, q);
-        *reinterpret_cast<float4 *>(b_hi(s) + off) = vh;
-        *reinterpret_cast<float4 *>(b_lo(s) + off) = sub4(v, vh);
+        for (int c = 0; c < 8; ++c) {
+          const float4 v = *reinterpret_cast<const float4 *>(g + sw128(r, c));
+          const float4 vh = hi4(v), vl = sub4(v, vh);
+          h[4 * c + 0] = vh.x; h[4 * c + 1] = vh.y;
+          h[4 * c + 2] = vh.z; h[4 * c + 3] = vh.w;
+          l[4 * c + 0] = vl.x; l[4 * c + 1] = vl.y;
+          l[4 * c + 2] = vl.z; l[4 * c + 3] = vl.w;
+        }
+        const uint32_t ta = aslots + lrow + 2 * PK * a + PH * kh;
+        tc::tmem_st32(ta, h);
+        tc::tmem_st32(ta + PK, l);
       }
-      // order these writes before the MMAs' (async proxy) reads
-      tc::fence_proxy_async_smem();
+      tc::tmem_wait_st();
+      // order the tensor-memory stores before the MMAs
+      tc::fence_before_sync();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&ct.ready[s]);
+      if (lane == 0) tc::mbar_arrive(&ct.ready[a]);
     }
   }
   __syncwarp();
@@ -273,32 +327,50 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
       const uint32_t lrow = (uint32_t)(q * 32) << 16;
       const float *in2b = in2 ? in2 + bm.x_off : nullptr;
       float *outb = out + bm.x_off;
-#pragma unroll 1
-      for (int c0 = 0; c0 < B; c0 += 32) {
-        // the five accumulators, added in a fixed order (warp-collective
-        // loads, before any per-lane branch)
-        float a[32], t2[32];
-        tc::tmem_ld32(taddr + lrow + c0, a);
-        tc::tmem_ld32(taddr + lrow + B + c0, t2);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) a[j] += t2[j];
-        float a23[32];
-        tc::tmem_ld32(taddr + lrow + 2 * B + c0, a23);
-        tc::tmem_ld32(taddr + lrow + 3 * B + c0, t2);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) a23[j] += t2[j];
-        tc::tmem_ld32(taddr + lrow + 4 * B + c0, t2);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) a[j] = (a[j] + a23[j]) + t2[j];
+      // B form of `out`: chunk r / 32, position r mod 32 (lanes of a warp
+      // hold 32 consecutive rows of one chunk: coalesced rows of 128 bytes)
+      float *bfb = out_bf ? out_bf + 2 * bm.x_off + (int64_t)(r >> 5) * 2 * B * 32 +
+                                (r & 31)
+                          : nullptr;
+      if constexpr (B == 16) {
+        // one load covers both halves: 16 main columns, then 16 cross
+        float v[32];
+        acc_sum<B>(taddr + lrow, 0, v);
         if (r < sp) {
-          constexpr int W = B < 32 ? B : 32;
 #pragma unroll
-          for (int j = 0; j < W; ++j) {
-            const int64_t o = (int64_t)r * B + c0 + j;
-            float v = alpha * a[j];
-            if (beta != 0.f) v = fmaf(beta, inb[o], v);
-            if (gamma != 0.f) v = fmaf(gamma, in2b[o], v);
-            outb[o] = v;
+          for (int c = 0; c < 16; ++c) {
+            const int64_t o = (int64_t)r * B + c;
+            float y = alpha * (v[c] + v[16 + c]);
+            if (beta != 0.f) y = fmaf(beta, inb[o], y);
+            if (gamma != 0.f) y = fmaf(gamma, in2b[o], y);
+            outb[o] = y;
+            if (bfb) {
+              const float yh = hi1(y);
+              bfb[c * 32] = yh;
+              bfb[(B + c) * 32] = __fsub_rn(y, yh);
+            }
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int c0 = 0; c0 < B; c0 += 32) {
+          float v[32], w[32];
+          acc_sum<B>(taddr + lrow, c0, v);        // main halves
+          acc_sum<B>(taddr + lrow, B + c0, w);    // cross halves
+          if (r < sp) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+              const int64_t o = (int64_t)r * B + c0 + c;
+              float y = alpha * (v[c] + w[c]);
+              if (beta != 0.f) y = fmaf(beta, inb[o], y);
+              if (gamma != 0.f) y = fmaf(gamma, in2b[o], y);
+              outb[o] = y;
+              if (bfb) {
+                const float yh = hi1(y);
+                bfb[(c0 + c) * 32] = yh;
+                bfb[(B + c0 + c) * 32] = __fsub_rn(y, yh);
+              }
+            }
           }
         }
       }
@@ -309,27 +381,58 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
   if (threadIdx.x == 0 && ct.abort) {
     // drain G tiles that were issued but never seen to land
     for (int kc = ct.consumed; kc < ct.issued; ++kc)
-      tc::mbar_wait(&ct.full[kc % PSTAGES], (kc / PSTAGES) & 1, kSpinP);
+      tc::mbar_wait(&ct.full[kc % S], (kc / S) & 1, kSpinP);
   }
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(taddr, L::TMEM_COLS);
+  if (warp == 0) tc::tmem_dealloc(taddr, kTmemCols);
 }
 
 template <int B>
 cudaError_t launch_b(const BlockMeta *meta, SolverState *state,
                      const int2 *tiles, int32_t ntiles,
                      const CUtensorMap *gmaps, const CUtensorMap *xmaps,
-                     const float *in, const float *in2, float *out, int mode,
-                     int step, int32_t *err, cudaStream_t st) {
+                     const float *in, const float *in2, float *out,
+                     float *out_bf, int mode, int step, int32_t *err,
+                     cudaStream_t st) {
   static_assert(panel_tc_smem<B>() <= 227 * 1024, "shared memory");
-  static_assert(kAcc * B <= PanelTc<B>::TMEM_COLS, "tensor memory");
   cudaError_t e = cudaFuncSetAttribute(
       k_gpanel_tc<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
       (int)panel_tc_smem<B>());
   if (e != cudaSuccess) return e;
-  k_gpanel_tc<B><<<ntiles, 192, panel_tc_smem<B>(), st>>>(
-      meta, state, tiles, gmaps, xmaps, in, in2, out, mode, step, err);
+  k_gpanel_tc<B><<<ntiles, kThreads, panel_tc_smem<B>(), st>>>(
+      meta, state, tiles, gmaps, xmaps, in, in2, out, out_bf, mode, step, err);
   return cudaGetLastError();
+}
+
+// B form of a panel written by another kernel: one CTA per 128-row tile,
+// one thread per row; the lanes of a warp write 32 consecutive positions of
+// one chunk row.
+template <int B>
+__global__ void __launch_bounds__(128)
+k_bform(const BlockMeta *__restrict__ meta, const SolverState *__restrict__ state,
+        const int2 *__restrict__ tiles, const float *__restrict__ in,
+        float *__restrict__ in_bf) {
+  const int2 t = tiles[blockIdx.x];
+  if (state[t.x].status != kRunning) return;
+  const BlockMeta bm = meta[t.x];
+  const int r = t.y + threadIdx.x;
+  if (r >= bm.s_pad) return;
+  const float4 *src =
+      reinterpret_cast<const float4 *>(in + bm.x_off + (int64_t)r * B);
+  float *dst = in_bf + 2 * bm.x_off + (int64_t)(r >> 5) * 2 * B * 32 + (r & 31);
+#pragma unroll
+  for (int c4 = 0; c4 < B / 4; ++c4) {
+    const float4 v = src[c4];
+    const float4 vh = hi4(v), vl = sub4(v, vh);
+    dst[(4 * c4 + 0) * 32] = vh.x;
+    dst[(4 * c4 + 1) * 32] = vh.y;
+    dst[(4 * c4 + 2) * 32] = vh.z;
+    dst[(4 * c4 + 3) * 32] = vh.w;
+    dst[(B + 4 * c4 + 0) * 32] = vl.x;
+    dst[(B + 4 * c4 + 1) * 32] = vl.y;
+    dst[(B + 4 * c4 + 2) * 32] = vl.z;
+    dst[(B + 4 * c4 + 3) * 32] = vl.w;
+  }
 }
 
 }  // namespace
@@ -338,18 +441,33 @@ cudaError_t launch_gpanel_tc(int32_t bsub, const BlockMeta *meta,
                              SolverState *state, const int2 *tiles,
                              int32_t ntiles, const CUtensorMap *gmaps,
                              const CUtensorMap *xmaps, const float *in,
-                             const float *in2, float *out, int mode, int step,
-                             int32_t *err, cudaStream_t st) {
+                             const float *in2, float *out, float *out_bf,
+                             int mode, int step, int32_t *err,
+                             cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   switch (bsub) {
     case 16: return launch_b<16>(meta, state, tiles, ntiles, gmaps, xmaps, in,
-                                 in2, out, mode, step, err, st);
+                                 in2, out, out_bf, mode, step, err, st);
     case 32: return launch_b<32>(meta, state, tiles, ntiles, gmaps, xmaps, in,
-                                 in2, out, mode, step, err, st);
+                                 in2, out, out_bf, mode, step, err, st);
     case 64: return launch_b<64>(meta, state, tiles, ntiles, gmaps, xmaps, in,
-                                 in2, out, mode, step, err, st);
+                                 in2, out, out_bf, mode, step, err, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_bform(int32_t bsub, const BlockMeta *meta,
+                         const SolverState *state, const int2 *tiles,
+                         int32_t ntiles, const float *in, float *in_bf,
+                         cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  switch (bsub) {
+    case 16: k_bform<16><<<ntiles, 128, 0, st>>>(meta, state, tiles, in, in_bf); break;
+    case 32: k_bform<32><<<ntiles, 128, 0, st>>>(meta, state, tiles, in, in_bf); break;
+    case 64: k_bform<64><<<ntiles, 128, 0, st>>>(meta, state, tiles, in, in_bf); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace bsvd
