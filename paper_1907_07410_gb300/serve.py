@@ -75,17 +75,18 @@ def _round_up(v, m):
 def footprint(m: int, n: int, nnz: int, nq: int = 0) -> int:
     """Upper bound on the device bytes one m x n request with nnz observed
     cells adds to a batch: the float32 block (32-padded), the two bf16
-    planes (128-padded rows), the Gram, two 64-wide subspace panels and
-    their per-row-tile partials, the Rayleigh-Ritz matrix, both factors at
-    the widest k, and the staged COO triples and queries. The batch's subspace width and
+    planes (128-padded rows), the Gram, two 64-wide subspace panels, their
+    split (hi, lo) copies for the tensor cores and their per-row-tile
+    partials, the Rayleigh-Ritz matrix, both factors at the widest k, and
+    the staged COO triples and queries. The batch's subspace width and
     factor width are its largest request's, so the widest ones are
     assumed."""
     s, L = min(m, n), max(m, n)
     sp, Lp, s128 = _round_up(s, 32), _round_up(L, 32), _round_up(s, 128)
     B, kp = 64, 56
     return (4 * sp * Lp + 4 * s128 * Lp + 4 * sp * sp + 8 * sp * B
-            + 8 * B * B * (sp // 64 + 1) + 4 * B * B + 4 * (sp + Lp) * kp
-            + 12 * (nnz + nq) + (1 << 12))
+            + 16 * sp * B + 8 * B * B * (sp // 64 + 1) + 4 * B * B
+            + 4 * (sp + Lp) * kp + 12 * (nnz + nq) + (1 << 12))
 
 
 class Server:
