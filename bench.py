@@ -41,6 +41,9 @@ SMS = 152
 # summarised in profiles/k_gram_tc_medium-4x4-k20.md; None until captured.
 GRAM_TC_TRAFFIC = {"medium-6040x3952-4x4-k20": 133.9e6}
 GRAM_BF16_TRAFFIC = {}
+# DRAM bytes of one k_gpanel_tc launch with every block running, from the
+# ncu capture summarised in profiles/k_gpanel_tc_medium-4x4-k20.md.
+PANEL_TRAFFIC = {"medium-6040x3952-4x4-k20": 67.97e6}
 
 
 def load_peaks():
@@ -552,7 +555,10 @@ def main():
     # the dominant kernel: panel products G X of the eigen-solver, counted
     # per block by the library (the last timed step's factorisation). The
     # first product of each block runs before the filter phase's events, so
-    # it is left out of both the work and the time.
+    # it is left out of both the work and the time. Its arithmetic intensity
+    # (2 s^2 b flops per 4 s^2 bytes of G, b/2 flop/B) is far below the
+    # tensor ridge, so its roofline is bandwidth: algorithmic bytes per
+    # product = G once (4 s^2) + the panel in and the panel out (4 s b each).
     rep = ctx.factor_report(full=True)
     bsub = 16 if w.k + max(8, w.k // 2) <= 16 else (
         32 if w.k + max(8, w.k // 2) <= 32 else 64)
@@ -562,26 +568,28 @@ def main():
         n_f = max(int(prods) - 1, 0)
         b_b = min(bsub, s_b)
         pflops += n_f * 2.0 * s_b * s_b * b_b
-        s_pad = -(-s_b // 32) * 32
-        pbytes += n_f * 4.0 * s_pad * s_pad
+        pbytes += n_f * (4.0 * s_b * s_b + 8.0 * s_b * b_b)
         nprod += int(prods)
     t_filter = statistics.mean(phases["eigen_filter"]) * 1e-3
     tf32_peak = 0.5 * peaks.get("bf16_tflops", 1900.0)
-    p_ach = pflops / t_filter / 1e12 if t_filter > 0 else 0.0
-    roof_eigen = {
-        "kernel": "k_gpanel_tc", "bound": "tensor",
-        "achieved": p_ach, "peak": tf32_peak, "unit": "TFLOP/s",
-        "frac": p_ach / tf32_peak,
-        "peak_source": "tf32 = 0.5 x bf16 dense burst, of %s" % peak_kind,
-        "frac_of_fp32_equivalent": p_ach / (tf32_peak / 3.0),
-        "g_read_gbs": pbytes / t_filter / 1e9 if t_filter > 0 else 0.0,
-        "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0),
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    p_gbs = pbytes / t_filter / 1e9 if t_filter > 0 else 0.0
+    p_tf = pflops / t_filter / 1e12 if t_filter > 0 else 0.0
+    roof_panel = {
+        "kernel": "k_gpanel_tc", "bound": "hbm",
+        "achieved": p_gbs, "peak": hbm_peak, "unit": "GB/s",
+        "frac": p_gbs / hbm_peak,
+        "traffic": PANEL_TRAFFIC.get(w.name),
+        "peak_source": "STREAM-style copy, of %s" % peak_kind,
         "products": nprod,
-        "algorithmic_flops": pflops,
-        "note": "algorithmic flops 2 s^2 b per block product over the "
-                "filter phase's time; the kernel issues three tf32 passes "
-                "per product (float32 accuracy), so one third of the tf32 "
-                "peak is its ceiling; G is re-read every product"}
+        "algorithmic_bytes": pbytes,
+        "tensor_tflops": p_tf,
+        "tensor_frac_of_fp32_equivalent": p_tf / (tf32_peak / 3.0),
+        "note": "algorithmic bytes (G once, panel in and out) of the filter "
+                "phase's block products over that phase's event time; "
+                "tensor_tflops counts 2 s^2 b flops per product against "
+                "one third of the tf32 peak (0.5 x measured bf16), as the "
+                "kernel issues three tf32 products for float32 accuracy"}
     value = world * nblocks * args.steps / (total_ms * 1e-3)
     proj_flops = 2.0 * sum(L * s * w.k for (s, L) in shapes)
     pred_flops = 2.0 * w.k * r.u_test.size
@@ -609,13 +617,13 @@ def main():
         "phases_ms": {k: statistics.mean(v) for k, v in phases.items()},
         "rmse": rm, "rmse_oracle": gold,
         "rmse_parity": (gold is not None and abs(rm - gold) <= 1e-4),
-        "roofline": {"kernel": roof["kernel"], "bound": roof["bound"],
-                     "achieved": achieved, "peak": roof["peak"],
-                     "unit": "TFLOP/s", "frac": achieved / roof["peak"],
-                     "traffic": roof["traffic"],
-                     "algorithmic_flops_per_launch": gflops,
-                     "peak_source": roof["peak_source"]},
-        "roofline_eigen": roof_eigen,
+        "roofline": roof_panel,
+        "roofline_gram": {"kernel": roof["kernel"], "bound": roof["bound"],
+                          "achieved": achieved, "peak": roof["peak"],
+                          "unit": "TFLOP/s", "frac": achieved / roof["peak"],
+                          "traffic": roof["traffic"],
+                          "algorithmic_flops_per_launch": gflops,
+                          "peak_source": roof["peak_source"]},
         "gpu_launches": int(launches),
         "e2e": {"value": world * nblocks * args.steps / (e2e_total * 1e-3),
                 "unit": "block-SVDs/s",
