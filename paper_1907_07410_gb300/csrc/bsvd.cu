@@ -844,7 +844,9 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
       CK(launch_small_gram(e, rtd, nrt, c->st), "factor: rr gram");
       CK(launch_rr_solve(e, c->st), "factor: rr solve");
       CK(launch_rotate(e, rtd, nrt, c->st), "factor: rotate");
-      CK(cudaMemsetAsync(e.running, 0, 2 * sizeof(int32_t), c->st), "factor");
+      // k_rotate clears the running counters that k_check fills
+      if (nrt == 0)
+        CK(cudaMemsetAsync(e.running, 0, 2 * sizeof(int32_t), c->st), "factor");
       CK(launch_check(e, c->st), "factor: check");
       mark(c, 7);
       c->launches += 2 + 2 * (nrt > 0);

@@ -19,6 +19,39 @@
 namespace bsvd {
 
 constexpr int kPad = 32;          // s and L are padded to multiples of this
+
+// Programmatic dependent launch. A kernel launched with launch_pdl may be
+// scheduled before the previous kernel in the stream has finished:
+// pdl_wait() blocks until that kernel has completed and its memory is
+// visible (a no-op for a kernel launched normally), so it comes before any
+// global access. pdl_trigger() lets the next kernel be scheduled once every
+// CTA of this one has called it or exited; single-wave kernels call it at
+// entry, so the next launch's scheduling overlaps their work.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+#ifdef __CUDACC__
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block,
+                       size_t smem, cudaStream_t st, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+#endif
+
 constexpr int kMaxSub = 64;       // widest subspace the small solver handles
 
 struct BlockMeta {

@@ -93,6 +93,8 @@ k_init_panels(const BlockMeta *__restrict__ meta,
               const SolverState *__restrict__ state,
               const int2 *__restrict__ rowtiles, float *__restrict__ X,
               uint64_t seed) {
+  pdl_wait();
+  pdl_trigger();
   const int2 t = rowtiles[blockIdx.x];
   const BlockMeta bm = meta[t.x];
   const int s = bm.s;
@@ -269,6 +271,8 @@ k_small_gram(const BlockMeta *__restrict__ meta,
              const SolverState *__restrict__ state,
              const int2 *__restrict__ rowtiles, const float *__restrict__ X,
              const float *__restrict__ Z, float *__restrict__ SHp) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int PER = (B * B + 255) / 256;
   __shared__ float Xs[TR][B + 1];
   __shared__ float Zs[TR][B + 1];
@@ -428,6 +432,8 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RRSmem<B> &sm = *reinterpret_cast<RRSmem<B> *>(smem_raw);
   const int blk = blockIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (state[blk].status != kRunning) return;
   const BlockMeta bm = meta[blk];
   const int n = state[blk].bsub;
@@ -597,9 +603,13 @@ k_rotate(const BlockMeta *__restrict__ meta,
          const SolverState *__restrict__ state,
          const int2 *__restrict__ rowtiles, const float *__restrict__ T,
          const float *__restrict__ theta, float *X, float *Z,
-         float *__restrict__ RP, uint64_t seed) {
+         float *__restrict__ RP, uint64_t seed, int32_t *running) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float (*Ts)[B + 1] = reinterpret_cast<float (*)[B + 1]>(smem_raw);
+  pdl_wait();
+  pdl_trigger();
+  // k_check, next in the stream, counts the blocks still running here
+  if (blockIdx.x == 0 && threadIdx.x < 2) running[threadIdx.x] = 0;
   float (*Xs)[B + 1] = Ts + B;
   float (*Zs)[B + 1] = Xs + TR;
   const int2 t = rowtiles[blockIdx.x];
@@ -666,6 +676,8 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   __shared__ float r2[B], x2[B];
   __shared__ int s_done;
   const int blk = blockIdx.x;
+  pdl_wait();
+  pdl_trigger();
   SolverState st = state[blk];
   if (st.status != kRunning) return;
   const BlockMeta bm = meta[blk];
@@ -750,6 +762,7 @@ k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
   constexpr int CH = 64;
   __shared__ __align__(16) float Fsh[CH][KM];
   __shared__ float red[8][64][9];
+  pdl_wait();
   const int2 t = ltiles[blockIdx.x];
   const BlockMeta bm = meta[t.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -840,6 +853,8 @@ k_finalize(const BlockMeta *__restrict__ meta, float *Fs, float *FL,
   __shared__ int bi[8][KM];
   __shared__ int flip[KM];
   const int blk = blockIdx.x;
+  pdl_wait();
+  pdl_trigger();
   const BlockMeta bm = meta[blk];
   const int keff = bm.keff;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -933,9 +948,8 @@ cudaError_t launch_init_panels(const EigBuffers &e, const int2 *rowtiles,
   if (ntiles <= 0) return cudaSuccess;
   return by_width(e.bsub, [&](auto w) {
     constexpr int B = decltype(w)::value;
-    k_init_panels<B><<<ntiles, 256, 0, st>>>(e.meta, e.state, rowtiles, e.X,
-                                             e.seed);
-    return cudaGetLastError();
+    return launch_pdl(k_init_panels<B>, dim3(ntiles), dim3(256), 0, st, e.meta,
+                      e.state, rowtiles, e.X, e.seed);
   });
 }
 
@@ -963,9 +977,9 @@ cudaError_t launch_small_gram(const EigBuffers &e, const int2 *rowtiles,
   if (ntiles <= 0) return cudaSuccess;
   return by_width(e.bsub, [&](auto w) {
     constexpr int B = decltype(w)::value;
-    k_small_gram<B><<<ntiles, 256, 0, st>>>(e.meta, e.state, rowtiles, e.X,
-                                            e.Z, e.SH);
-    return cudaGetLastError();
+    return launch_pdl(k_small_gram<B>, dim3(ntiles), dim3(256), 0, st, e.meta,
+                      e.state, rowtiles, (const float *)e.X,
+                      (const float *)e.Z, e.SH);
   });
 }
 
@@ -975,9 +989,9 @@ cudaError_t launch_rr_solve(const EigBuffers &e, cudaStream_t st) {
     cudaError_t err = set_attrs<B>();
     if (err != cudaSuccess) return err;
     constexpr int threads = (B / 2) * 32 > 256 ? (B / 2) * 32 : 256;
-    k_rr_solve<B><<<e.nblocks, threads, rr_smem<B>(), st>>>(
-        e.meta, e.state, e.SH, e.T, e.theta, e.max_sweeps);
-    return cudaGetLastError();
+    return launch_pdl(k_rr_solve<B>, dim3(e.nblocks), dim3(threads),
+                      rr_smem<B>(), st, e.meta, e.state, (const float *)e.SH,
+                      e.T, e.theta, e.max_sweeps);
   });
 }
 
@@ -988,19 +1002,20 @@ cudaError_t launch_rotate(const EigBuffers &e, const int2 *rowtiles,
     constexpr int B = decltype(w)::value;
     cudaError_t err = set_attrs<B>();
     if (err != cudaSuccess) return err;
-    k_rotate<B><<<ntiles, 256, rot_smem<B>(), st>>>(
-        e.meta, e.state, rowtiles, e.T, e.theta, e.X, e.Z, e.RP, e.seed);
-    return cudaGetLastError();
+    return launch_pdl(k_rotate<B>, dim3(ntiles), dim3(256), rot_smem<B>(), st,
+                      e.meta, (const SolverState *)e.state, rowtiles,
+                      (const float *)e.T, (const float *)e.theta, e.X, e.Z,
+                      e.RP, e.seed, e.running);
   });
 }
 
 cudaError_t launch_check(const EigBuffers &e, cudaStream_t st) {
   return by_width(e.bsub, [&](auto w) {
     constexpr int B = decltype(w)::value;
-    k_check<B><<<e.nblocks, 256, 0, st>>>(e.meta, e.state, e.X, e.RP,
-                                          e.theta, e.Fs, e.kp, e.max_iters,
-                                          e.max_degree, e.tol, e.running);
-    return cudaGetLastError();
+    return launch_pdl(k_check<B>, dim3(e.nblocks), dim3(256), 0, st, e.meta,
+                      e.state, (const float *)e.X, (const float *)e.RP,
+                      (const float *)e.theta, e.Fs, e.kp, e.max_iters,
+                      e.max_degree, e.tol, e.running);
   });
 }
 
@@ -1024,8 +1039,8 @@ cudaError_t launch_project(const BlockMeta *meta, const int2 *ltiles,
   if (ntiles <= 0) return cudaSuccess;
   return by_kmax(kp, [&](auto km) {
     constexpr int KM = decltype(km)::value;
-    k_project<KM><<<ntiles, 256, 0, st>>>(meta, ltiles, W, Fs, FL, kp);
-    return cudaGetLastError();
+    return launch_pdl(k_project<KM>, dim3(ntiles), dim3(256), 0, st, meta,
+                      ltiles, W, Fs, FL, kp);
   });
 }
 
@@ -1036,8 +1051,8 @@ cudaError_t launch_finalize(const BlockMeta *meta, int32_t nblocks,
   if (nblocks <= 0) return cudaSuccess;
   return by_kmax(kp, [&](auto km) {
     constexpr int KM = decltype(km)::value;
-    k_finalize<KM><<<nblocks, 256, 0, st>>>(meta, Fs, FL, sigma, kp);
-    return cudaGetLastError();
+    return launch_pdl(k_finalize<KM>, dim3(nblocks), dim3(256), 0, st, meta,
+                      Fs, FL, sigma, kp);
   });
 }
 

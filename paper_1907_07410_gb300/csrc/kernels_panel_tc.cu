@@ -204,7 +204,7 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
   tc::fence_after_sync();
   // everything above reads only what kernels before the previous one wrote
   // (tiles, meta, the solver state); the panels need the previous product
-  tc::grid_dep_wait();
+  pdl_wait();
   const uint32_t taddr = ct.tmem;
   const uint32_t aslots = taddr + L::ACC_COLS;    // A slot a at +128 a
   volatile int *abort_flag = &ct.abort;
@@ -325,7 +325,7 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
 
   // the next product may be scheduled now; it waits for this grid to
   // complete before it reads a panel
-  tc::grid_dep_launch();
+  pdl_trigger();
   if (warp >= 2) {
     const bool ready =
         __all_sync(0xffffffffu, tc::mbar_wait(&ct.done, 0, kSpinP));
@@ -418,19 +418,10 @@ cudaError_t launch_b(const BlockMeta *meta, SolverState *state,
       (int)panel_tc_smem<B>());
   if (e != cudaSuccess) return e;
   // programmatic dependent launch: this grid's prologue may overlap the end
-  // of the previous kernel in the stream (see grid_dep_wait)
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)ntiles);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = panel_tc_smem<B>();
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_gpanel_tc<B>, meta, state, tiles, gmaps,
-                            xmaps, in, in2, out, out_bf, mode, step, err);
+  // of the previous kernel in the stream (see pdl_wait)
+  return launch_pdl(k_gpanel_tc<B>, dim3((unsigned)ntiles), dim3(kThreads),
+                    panel_tc_smem<B>(), st, meta, state, tiles, gmaps, xmaps,
+                    in, in2, out, out_bf, mode, step, err);
 }
 
 // B form of a panel written by another kernel: one CTA per 128-row tile,
@@ -441,7 +432,8 @@ __global__ void __launch_bounds__(128)
 k_bform(const BlockMeta *__restrict__ meta, const SolverState *__restrict__ state,
         const int2 *__restrict__ tiles, const float *__restrict__ in,
         float *__restrict__ in_bf) {
-  tc::grid_dep_wait();
+  pdl_wait();
+  pdl_trigger();
   const int2 t = tiles[blockIdx.x];
   if (state[t.x].status != kRunning) return;
   const BlockMeta bm = meta[t.x];
@@ -492,12 +484,14 @@ cudaError_t launch_bform(int32_t bsub, const BlockMeta *meta,
                          cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   switch (bsub) {
-    case 16: k_bform<16><<<ntiles, 128, 0, st>>>(meta, state, tiles, in, in_bf); break;
-    case 32: k_bform<32><<<ntiles, 128, 0, st>>>(meta, state, tiles, in, in_bf); break;
-    case 64: k_bform<64><<<ntiles, 128, 0, st>>>(meta, state, tiles, in, in_bf); break;
+    case 16: return launch_pdl(k_bform<16>, dim3(ntiles), dim3(128), 0, st, meta,
+                               state, tiles, in, in_bf);
+    case 32: return launch_pdl(k_bform<32>, dim3(ntiles), dim3(128), 0, st, meta,
+                               state, tiles, in, in_bf);
+    case 64: return launch_pdl(k_bform<64>, dim3(ntiles), dim3(128), 0, st, meta,
+                               state, tiles, in, in_bf);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace bsvd

@@ -26,17 +26,6 @@ __device__ __forceinline__ bool elect_one() {
   return pred != 0;
 }
 
-// Programmatic dependent launch: wait until the preceding grid in the
-// stream has completed and its memory is visible (a no-op when this grid was
-// not launched as a programmatic dependent), and allow the next grid to be
-// scheduled once every CTA of this one has signalled or exited.
-__device__ __forceinline__ void grid_dep_wait() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-__device__ __forceinline__ void grid_dep_launch() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(count) : "memory");
