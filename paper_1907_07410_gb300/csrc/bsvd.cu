@@ -99,6 +99,7 @@ struct bsvd_ctx {
   // tensor-core panel products: 128-row tiles and one TMA map per block of G
   DevBuf d_ptiles, d_gmaps, d_xmaps;
   DevBuf d_XB, d_ZB;         // B forms of the panels X, Z (2 s_pad x B floats)
+  int32_t *h_run = nullptr;  // pinned: running count, largest degree
   int32_t n_ptiles = 0;
   std::vector<CUtensorMap> h_gmaps, h_xmaps;
 
@@ -322,6 +323,7 @@ void bsvd_destroy(bsvd_ctx *c) {
   for (DevBuf *b : bufs) b->release();
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
+  if (c->h_run) cudaFreeHost(c->h_run);
   delete c;
 }
 
@@ -850,8 +852,11 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
       CK(launch_check(e, c->st), "factor: check");
       mark(c, 7);
       c->launches += 2 + 2 * (nrt > 0);
-      int32_t run_deg[2] = {0, 0};
-      CK(cudaMemcpyAsync(run_deg, e.running, sizeof run_deg,
+      // pinned, so the copy is a direct DMA rather than a staged one
+      if (!c->h_run)
+        CK(cudaMallocHost(&c->h_run, 2 * sizeof(int32_t)), "factor");
+      int32_t *run_deg = c->h_run;
+      CK(cudaMemcpyAsync(run_deg, e.running, 2 * sizeof(int32_t),
                          cudaMemcpyDeviceToHost, c->st), "factor");
       CK(cudaStreamSynchronize(c->st), "factor");
       if (c->cfg.profile) {

@@ -466,6 +466,7 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
     const int i = e / n, j = e % n;
     const float di = sm.d[i], dj = sm.d[j];
     sm.S[i][j] = (di > 0.f && dj > 0.f) ? sm.S[i][j] / (di * dj) : (i == j ? 0.f : 0.f);
+    sm.Li[i][j] = i == j ? 1.f : 0.f;
   }
   __syncthreads();
   // 3. Cholesky S_n = L L^T, right-looking: for each column j, the pivot
@@ -476,6 +477,12 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   // left-looking loop over l, but with O(1) work per thread per column.
   // Weak pivots are dropped: the column is treated as zero below its unit
   // diagonal, so it also changes nothing in the trailing update.
+  // 4. L^-1 in the same sweep: Li starts as I; at step j row j is divided by
+  // L_jj (it has received all its updates) and then the rows below get
+  // Li[i][c] -= L_ij Li[j][c] for c <= j. Per entry these are the fused
+  // multiply-adds of forward substitution in the same order (l ascending,
+  // then the division), so the result is bitwise the same, but every step
+  // is parallel over the entries instead of one dependent chain per column.
   for (int j = 0; j < n; ++j) {
     const float piv = sm.S[j][j];
     const bool drop = !(piv > kPivotDrop);
@@ -483,6 +490,7 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
     const float inv = __frcp_rn(ljj);
     for (int i = j + 1 + tid; i < n; i += blockDim.x)
       sm.S[i][j] = drop ? 0.f : sm.S[i][j] * inv;
+    for (int c = tid; c <= j; c += blockDim.x) sm.Li[j][c] = sm.Li[j][c] / ljj;
     if (tid == 0) {
       sm.drop[j] = drop;
       sm.key[j] = ljj;          // L's diagonal; S[j][j] stays readable
@@ -499,19 +507,13 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
       const int i = j + 1 + ii, l = j + 1 + ll;
       sm.S[i][l] = fmaf(-sm.S[i][j], sm.S[l][j], sm.S[i][l]);
     }
+    // rows below j of L^-1, columns 0 .. j
+    for (int e = tid; e < m * (j + 1); e += blockDim.x) {
+      const int i = j + 1 + e / (j + 1), c = e % (j + 1);
+      sm.Li[i][c] = fmaf(-sm.S[i][j], sm.Li[j][c], sm.Li[i][c]);
+    }
     __syncthreads();
   }
-  // 4. L^-1 by forward substitution, one column per thread (the strict
-  // lower triangle of S holds L, key[] its diagonal)
-  for (int j = tid; j < n; j += blockDim.x) {
-    for (int i = 0; i < j; ++i) sm.Li[i][j] = 0.f;
-    for (int i = j; i < n; ++i) {
-      float acc = (i == j) ? 1.f : 0.f;
-      for (int l = j; l < i; ++l) acc = fmaf(-sm.S[i][l], sm.Li[l][j], acc);
-      sm.Li[i][j] = acc / sm.key[i];
-    }
-  }
-  __syncthreads();
   // 5. T1 = D^-1 L^-T, dropped basis columns are zero
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
@@ -749,18 +751,38 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   }
 }
 
+// Asynchronous 4-byte global -> shared copy (no register staging); with
+// `valid` false the destination is zero-filled and nothing is read.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src,
+                                          bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d),
+               "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // F_L[l, :] = sum_a W[a, l] F_s[a, :] for kProjCols = 64 consecutive l: lane
 // t owns l = l0 + 2t, l0 + 2t + 1 (one float2 of each W row), warp w takes
 // the rows a = w, w + 8, ... and a row of F_s is read from shared memory as
 // float4s, so each shared load feeds 8 FMAs. The 8 warps' partial sums are
-// added in warp order. KM: kp rounded up to 8.
+// added in warp order. The next 64-row chunk is in flight while the current
+// one's products run: the warp's W rows in registers, F_s as asynchronous
+// copies into the other half of a double-buffered shared array. KM: kp
+// rounded up to 8.
 template <int KM>
 __global__ void __launch_bounds__(256)
 k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
           const float *__restrict__ W, const float *__restrict__ Fs,
           float *__restrict__ FL, int kp) {
   constexpr int CH = 64;
-  __shared__ __align__(16) float Fsh[CH][KM];
+  __shared__ __align__(16) float Fsh[2][CH][KM];
   __shared__ float red[8][64][9];
   pdl_wait();
   const int2 t = ltiles[blockIdx.x];
@@ -784,17 +806,30 @@ k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
                               : make_float2(0.f, 0.f);
     }
   };
-  // the warp's 8 rows of a chunk are all in flight at once, and the next
-  // chunk's rows are loaded while this chunk's products run
-  float2 w[CH / 8], wn[CH / 8];
-  load_w(0, w);
-  for (int a0 = 0; a0 < bm.s; a0 += CH) {
+  // F_s rows a0 .. a0+63 into Fsh[buf] (zeros past s and past kp)
+  auto load_f = [&](int a0, int buf) {
     for (int e = threadIdx.x; e < CH * KM; e += blockDim.x) {
       const int rr = e / KM, j = e % KM;
-      Fsh[rr][j] = (a0 + rr < bm.s && j < kp) ? Fb[(int64_t)(a0 + rr) * kp + j] : 0.f;
+      const bool ok = a0 + rr < bm.s && j < kp;
+      cp_async4(&Fsh[buf][rr][j], ok ? Fb + (int64_t)(a0 + rr) * kp + j : Fb,
+                ok);
+    }
+    cp_async_commit();
+  };
+  float2 w[CH / 8], wn[CH / 8];
+  load_w(0, w);
+  load_f(0, 0);
+  int buf = 0;
+  for (int a0 = 0; a0 < bm.s; a0 += CH, buf ^= 1) {
+    const bool more = a0 + CH < bm.s;
+    if (more) {
+      load_f(a0 + CH, buf ^ 1);
+      cp_async_wait<1>();      // this chunk's copies have landed
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
-    if (a0 + CH < bm.s) load_w(a0 + CH, wn);
+    if (more) load_w(a0 + CH, wn);
     const int lim = min(CH, bm.s - a0);
     if (lv) {
 #pragma unroll
@@ -803,7 +838,7 @@ k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
         if (rr >= lim) break;
 #pragma unroll
         for (int j = 0; j < KM; j += 4) {
-          const float4 f = *reinterpret_cast<const float4 *>(&Fsh[rr][j]);
+          const float4 f = *reinterpret_cast<const float4 *>(&Fsh[buf][rr][j]);
           acc[0][j] = fmaf(w[h].x, f.x, acc[0][j]);
           acc[0][j + 1] = fmaf(w[h].x, f.y, acc[0][j + 1]);
           acc[0][j + 2] = fmaf(w[h].x, f.z, acc[0][j + 2]);
@@ -817,6 +852,7 @@ k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
     }
 #pragma unroll
     for (int h = 0; h < CH / 8; ++h) w[h] = wn[h];
+    // every warp is done with Fsh[buf] before the next chunk refills it
     __syncthreads();
   }
 #pragma unroll
