@@ -24,10 +24,11 @@
 //   * warp 0: TMA loads into a ring of stages: the G tile (128 rows x 64
 //     floats, as two 32-float boxes) and the two matching B-form chunks
 //     (2b rows x 32 floats each), all with 128-byte swizzling;
-//   * warps 2-5 (converters): each thread reads one row of the G tile,
-//     splits it in registers and stores hi and lo into a tensor-memory slot
-//     (tcgen05.st; lane = row, one column per K element), the A operand
-//     layout of kind::tf32. The tensor core reads shared memory at 128 bytes
+//   * warps 2-9 (converters, two per TMEM lane quarter, one per 32-float
+//     half of the stage): each thread reads one row of its half of the G
+//     tile, splits it in registers and stores hi and lo into a
+//     tensor-memory slot (tcgen05.st; lane = row, one column per K
+//     element), the A operand layout of kind::tf32. The tensor core reads shared memory at 128 bytes
 //     per cycle, so an A operand read from shared memory (4 KiB per K = 8)
 //     would cost 32 cycles per MMA;
 //   * warp 1: per K = 8 slice, two MMAs with A in tensor memory:
@@ -38,15 +39,17 @@
 // descriptors stay warp-uniform, and one elected lane issues. Measured on
 // GB300 (clock stamps per stage), a single lane running the same loop took
 // about 90 cycles per MMA and 300 more per satisfied barrier wait; now a
-// stage's 16 MMAs issue in about 400 cycles and the converters, at about
-// 500 cycles per 32 floats of K, set the pace.
+// stage's 16 MMAs issue in about 400 cycles. Eight converter warps (four
+// took about 1000 cycles per stage) bring the kernel to about 740 cycles
+// per 32 floats of K on a 988-row block.
 //
 // Launch: programmatic dependent launch. A product's prologue (tile, state,
 // barriers, tensor memory) overlaps the end of the previous kernel, and
 // griddepcontrol.wait precedes every read of a panel and every write of
 // `out`. The epilogue reads in, in2 and writes out with 16-byte accesses (a
-// thread owns a row). Back to back, 16 blocks of 988 rows take 13.5 us per
-// product (18.6 us with plain launches and scalar epilogue accesses).
+// thread owns a row). Back to back, 16 blocks of 988 rows take 12.4 us per
+// product (18.6 us with plain launches, scalar epilogue accesses and four
+// converter warps).
 //
 // Accumulation: the tensor core's f32 accumulator does not round to
 // nearest at each step (a measured one-signed error growing with the number
@@ -71,7 +74,8 @@ namespace {
 constexpr int PT = 128;                  // G rows per CTA (MMA M)
 constexpr int PK = 64;                   // floats of K per stage
 constexpr int PH = 32;                   // floats per 128-byte swizzle row
-constexpr int kThreads = 192;            // 6 warps
+constexpr int kThreads = 320;            // 10 warps
+constexpr int kConv = 8;                 // converter warps (2..9)
 constexpr int kMaxStages = 4;
 constexpr int kSlots = 2;                // A slots in tensor memory
 constexpr uint32_t kSpinP = 1u << 22;    // mbarrier polls before giving up
@@ -98,7 +102,7 @@ struct PanelTc {
 struct PanelCtrl {
   uint64_t full[kMaxStages];    // G tile and rows of `in` landed (TMA bytes)
   uint64_t empty[kMaxStages];   // the stage's MMAs completed
-  uint64_t ready[kSlots];       // A slot written (4 converter warps)
+  uint64_t ready[kSlots];       // A slot written (the 8 converter warps)
   uint64_t afree[kSlots];       // the MMAs reading the A slot completed
   uint64_t done;                // every MMA completed
   uint32_t tmem;
@@ -132,23 +136,23 @@ __device__ __forceinline__ uint32_t sw128(int r, int c) {
   return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
 }
 
-// Sum of the R accumulators' 32 columns at `col`, in a fixed order:
+// Sum of the R accumulators' 16 columns at `col`, in a fixed order:
 // (a0 + a1) + (a2 + a3), or a0 + a1.
 template <int B>
 __device__ __forceinline__ void acc_sum(uint32_t taddr, uint32_t col,
-                                        float (&v)[32]) {
+                                        float (&v)[16]) {
   using L = PanelTc<B>;
-  float t[32];
-  tc::tmem_ld32(taddr + col, v);
-  tc::tmem_ld32(taddr + col + 2 * B, t);
+  float t[16];
+  tc::tmem_ld16(taddr + col, v);
+  tc::tmem_ld16(taddr + col + 2 * B, t);
 #pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] += t[j];
+  for (int j = 0; j < 16; ++j) v[j] += t[j];
   if constexpr (L::R == 4) {
-    float u[32];
-    tc::tmem_ld32(taddr + col + 4 * B, u);
-    tc::tmem_ld32(taddr + col + 6 * B, t);
+    float u[16];
+    tc::tmem_ld16(taddr + col + 4 * B, u);
+    tc::tmem_ld16(taddr + col + 6 * B, t);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] += u[j] + t[j];
+    for (int j = 0; j < 16; ++j) v[j] += u[j] + t[j];
   }
 }
 
@@ -190,7 +194,7 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
       tc::mbar_init(&ct.empty[s], 1);
     }
     for (int a = 0; a < kSlots; ++a) {
-      tc::mbar_init(&ct.ready[a], 4);
+      tc::mbar_init(&ct.ready[a], kConv);
       tc::mbar_init(&ct.afree[a], 1);
     }
     tc::mbar_init(&ct.done, 1);
@@ -276,9 +280,12 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
     if (tc::elect_one()) tc::mma_commit(&ct.done);
     __syncwarp();
   } else {
-    // converters: 128 threads; warp w may touch TMEM lanes 32 (w mod 4) ..
+    // converters: warps 2-9. Warp w may touch TMEM lanes 32 (w mod 4) ..
+    // +31, so two warps share each lane quarter: warps 2-5 split the first
+    // 32-float half of a stage's K range, warps 6-9 the second.
     const int cid = threadIdx.x - 64;
     const int q = warp & 3;
+    const int kh = (warp - 2) >> 2;
     const int r = q * 32 + lane;                  // G tile row of this thread
     const uint32_t lrow = (uint32_t)(q * 32) << 16;
     for (int kc = 0; kc < nk; ++kc) {
@@ -296,9 +303,8 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
       }
       if (cid == 0) ct.consumed = kc + 1;
       tc::fence_after_sync();
-      // this thread's row of the G tile, split into hi and lo columns
-#pragma unroll
-      for (int kh = 0; kh < 2; ++kh) {
+      // this thread's row of its half of the G tile, split into hi and lo
+      {
         const unsigned char *g = g_tile(s) + kh * G_HALF;
         float h[32], l[32];
 #pragma unroll
@@ -326,7 +332,7 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
   // the next product may be scheduled now; it waits for this grid to
   // complete before it reads a panel
   pdl_trigger();
-  if (warp >= 2) {
+  if (warp >= 2 && warp < 6) {
     const bool ready =
         __all_sync(0xffffffffu, tc::mbar_wait(&ct.done, 0, kSpinP));
     if (!ready && lane == 0) atomicOr(err, kErrTimeout);
@@ -378,19 +384,12 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
           }
         }
       };
-      if constexpr (B == 16) {
-        // one load covers both halves: 16 main columns, then 16 cross
-        float v[32];
-        acc_sum<B>(taddr + lrow, 0, v);
-        if (r < sp) finish(v, v + 16, 0, 16);
-      } else {
 #pragma unroll 1
-        for (int c0 = 0; c0 < B; c0 += 32) {
-          float v[32], w[32];
-          acc_sum<B>(taddr + lrow, c0, v);        // main halves
-          acc_sum<B>(taddr + lrow, B + c0, w);    // cross halves
-          if (r < sp) finish(v, w, c0, 32);
-        }
+      for (int c0 = 0; c0 < B; c0 += 16) {
+        float v[16], w[16];
+        acc_sum<B>(taddr + lrow, c0, v);        // main halves
+        acc_sum<B>(taddr + lrow, B + c0, w);    // cross halves
+        if (r < sp) finish(v, w, c0, 16);
       }
     }
   }
