@@ -177,6 +177,7 @@ def run_reference(args, w, r, rank):
         return
     import concurrent.futures as cf
     import oracle
+    oracle.build()           # once, before the worker threads use it
     cores = os.cpu_count() or 1
     gridkw = host_grid(w, r)
     t0 = time.perf_counter()

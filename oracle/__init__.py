@@ -42,6 +42,7 @@ import dataclasses
 import math
 import os
 import subprocess
+import threading
 
 import numpy as np
 
@@ -49,6 +50,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "jacobi_svd.c")
 _LIB = os.path.join(_HERE, "liboracle_jacobi.so")
 _lib = None
+_lock = threading.Lock()   # builds and loads from worker threads
 
 MAX_SWEEPS = 60
 
@@ -56,12 +58,13 @@ MAX_SWEEPS = 60
 def build(force: bool = False) -> str:
     """Compile the C Jacobi routine (plain gcc, no architecture flags), and
     the blocked-SGD pass of ``oracle.sgd``."""
-    if force or not os.path.exists(_LIB) or (
-            os.path.getmtime(_LIB) < os.path.getmtime(_SRC)):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    with _lock:
+        if force or not os.path.exists(_LIB) or (
+                os.path.getmtime(_LIB) < os.path.getmtime(_SRC)):
+            tmp = _LIB + ".tmp%d.%d" % (os.getpid(), threading.get_ident())
+            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared",
+                                   "-std=c99", "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB)
     from . import sgd
     sgd.build(force)
     return _LIB
@@ -69,8 +72,13 @@ def build(force: bool = False) -> str:
 
 def _load():
     global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+    if _lib is not None:
+        return _lib
+    path = build()
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(path)
         f = lib.oracle_jacobi_svd
         f.restype = ctypes.c_int
         dp = ctypes.POINTER(ctypes.c_double)

@@ -36,6 +36,7 @@ import ctypes
 import dataclasses
 import os
 import subprocess
+import threading
 
 import numpy as np
 
@@ -43,17 +44,19 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sgd.c")
 _LIB = os.path.join(_HERE, "liboracle_sgd.so")
 _lib = None
+_lock = threading.Lock()   # builds and loads from worker threads
 
 
 def build(force: bool = False) -> str:
     """Compile ``sgd.c``: plain gcc, no architecture flags, and no
     floating-point contraction, so each operation rounds once."""
-    if force or not os.path.exists(_LIB) or (
-            os.path.getmtime(_LIB) < os.path.getmtime(_SRC)):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC",
-                               "-shared", "-std=c99", "-o", tmp, _SRC])
-        os.replace(tmp, _LIB)
+    with _lock:
+        if force or not os.path.exists(_LIB) or (
+                os.path.getmtime(_LIB) < os.path.getmtime(_SRC)):
+            tmp = _LIB + ".tmp%d.%d" % (os.getpid(), threading.get_ident())
+            subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC",
+                                   "-shared", "-std=c99", "-o", tmp, _SRC])
+            os.replace(tmp, _LIB)
     return _LIB
 
 
@@ -65,8 +68,13 @@ class _Rates(ctypes.Structure):
 
 def _load():
     global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+    if _lib is not None:
+        return _lib
+    path = build()
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(path)
         f = lib.oracle_sgd_pass
         f.restype = None
         f.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
