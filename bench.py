@@ -43,7 +43,7 @@ GRAM_TC_TRAFFIC = {"medium-6040x3952-4x4-k20": 133.9e6}
 GRAM_BF16_TRAFFIC = {}
 # DRAM bytes of one k_gpanel_tc launch with every block running, from the
 # ncu capture summarised in profiles/k_gpanel_tc_medium-4x4-k20.md.
-PANEL_TRAFFIC = {}
+PANEL_TRAFFIC = {"medium-6040x3952-4x4-k20": 67.94e6}
 
 
 def load_peaks():
