@@ -283,3 +283,19 @@ def test_generator_shapes():
                            minlength=w.m)
     assert per_user.min() >= 20 and per_user.max() <= w.n
     assert set(np.unique(r.x_train).tolist()) <= {1.0, 2.0, 3.0, 4.0, 5.0}
+
+
+def test_oracle_is_usable_from_threads():
+    """The reference arm runs the oracle on a thread pool: loading the C
+    library from several threads at once, and running SVDs concurrently
+    (the C routine releases the GIL), gives the serial results."""
+    import concurrent.futures as cf
+    rng = np.random.default_rng(11)
+    mats = [rng.normal(size=(40 + 3 * t, 25 + t)) for t in range(8)]
+    serial = [oracle.svd(a) for a in mats]
+    oracle._lib = None                 # make the workers race to load it
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+        threaded = list(ex.map(oracle.svd, mats))
+    for (u0, s0, v0), (u1, s1, v1) in zip(serial, threaded):
+        assert np.array_equal(s0, s1)
+        assert np.array_equal(u0, u1) and np.array_equal(v0, v1)
