@@ -1,6 +1,8 @@
 // C ABI of libbsvd: context, argument checks, buffers and the order of
 // kernel launches for each call. See include/bsvd.h for the contract.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -12,6 +14,10 @@
 
 #include "bsvd.h"
 #include "kernels.h"
+
+// Longest the host polls for a step's convergence counters before it falls
+// back to a stream synchronisation.
+static constexpr int kPollMs = 50;
 
 using namespace bsvd;
 
@@ -99,7 +105,10 @@ struct bsvd_ctx {
   // tensor-core panel products: 128-row tiles and one TMA map per block of G
   DevBuf d_ptiles, d_gmaps, d_xmaps;
   DevBuf d_XB, d_ZB;         // B forms of the panels X, Z (2 s_pad x B floats)
-  int32_t *h_run = nullptr;  // pinned: running count, largest degree
+  // pinned and mapped: running count, largest degree, sequence number
+  int32_t *h_run = nullptr;
+  int32_t *d_run_host = nullptr;  // the same memory seen from the device
+  int32_t run_seq = 0;
   int32_t n_ptiles = 0;
   std::vector<CUtensorMap> h_gmaps, h_xmaps;
 
@@ -852,13 +861,35 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
       CK(launch_check(e, c->st), "factor: check");
       mark(c, 7);
       c->launches += 2 + 2 * (nrt > 0);
-      // pinned, so the copy is a direct DMA rather than a staged one
-      if (!c->h_run)
-        CK(cudaMallocHost(&c->h_run, 2 * sizeof(int32_t)), "factor");
-      int32_t *run_deg = c->h_run;
-      CK(cudaMemcpyAsync(run_deg, e.running, 2 * sizeof(int32_t),
-                         cudaMemcpyDeviceToHost, c->st), "factor");
-      CK(cudaStreamSynchronize(c->st), "factor");
+      // The counters reach the host through mapped pinned memory, written
+      // by k_publish; this thread polls the sequence word. That avoids a
+      // copy and a stream synchronisation per step. If the word does not
+      // arrive within kPollMs (an error, or a very slow step), the stream
+      // synchronisation below waits and reports any error.
+      if (!c->h_run) {
+        CK(cudaHostAlloc(&c->h_run, 4 * sizeof(int32_t), cudaHostAllocMapped),
+           "factor");
+        c->h_run[2] = 0;
+        CK(cudaHostGetDevicePointer(&c->d_run_host, c->h_run, 0), "factor");
+      }
+      const int32_t seq = ++c->run_seq;
+      CK(launch_publish(e.running, c->d_run_host, seq, c->st), "factor: publish");
+      ++c->launches;
+      {
+        volatile int32_t *hr = c->h_run;
+        const auto t0 = std::chrono::steady_clock::now();
+        bool seen = false;
+        for (uint32_t spin = 0;; ++spin) {
+          if (hr[2] == seq) { seen = true; break; }
+          if ((spin & 1023u) == 0 &&
+              std::chrono::steady_clock::now() - t0 >
+                  std::chrono::milliseconds(kPollMs))
+            break;
+        }
+        if (!seen) CK(cudaStreamSynchronize(c->st), "factor");
+        std::atomic_thread_fence(std::memory_order_acquire);
+      }
+      const int32_t run_deg[2] = {c->h_run[0], c->h_run[1]};
       if (c->cfg.profile) {
         float ms = 0.f;
         if (it > 0 && cudaEventElapsedTime(&ms, c->ev[8], c->ev[9]) == cudaSuccess)

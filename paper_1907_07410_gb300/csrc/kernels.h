@@ -119,6 +119,11 @@ cudaError_t launch_rr_solve(const EigBuffers &e, cudaStream_t st);
 cudaError_t launch_rotate(const EigBuffers &e, const int2 *rowtiles,
                           int32_t ntiles, cudaStream_t st);
 cudaError_t launch_check(const EigBuffers &e, cudaStream_t st);
+// Copies running[0..1] to host-mapped memory `host` (device pointer), then
+// writes `seq` to host[2], so a host thread that sees seq in host[2] reads
+// the counters of this step.
+cudaError_t launch_publish(const int32_t *running, int32_t *host, int32_t seq,
+                           cudaStream_t st);
 
 // F_L = W^T F_s, then float64 norms (sigma) and sign canonicalisation.
 // ltiles: (block, first column l) pairs, kProjCols columns each.

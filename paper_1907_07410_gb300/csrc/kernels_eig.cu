@@ -1064,6 +1064,24 @@ cudaError_t launch_check(const EigBuffers &e, cudaStream_t st) {
   });
 }
 
+// One thread: the step's running counters to the host, then the sequence
+// number (after a system-scope fence, so the host never sees the new
+// sequence number with old counters).
+__global__ void k_publish(const int32_t *__restrict__ running,
+                          volatile int32_t *host, int32_t seq) {
+  pdl_wait();
+  host[0] = running[0];
+  host[1] = running[1];
+  __threadfence_system();
+  host[2] = seq;
+}
+
+cudaError_t launch_publish(const int32_t *running, int32_t *host, int32_t seq,
+                           cudaStream_t st) {
+  return launch_pdl(k_publish, dim3(1), dim3(1), 0, st, running,
+                    (volatile int32_t *)host, seq);
+}
+
 template <typename F>
 cudaError_t by_kmax(int kp, F &&f) {
   switch ((kp + 7) / 8) {
