@@ -110,7 +110,10 @@ struct bsvd_ctx {
   int32_t *d_run_host = nullptr;  // the same memory seen from the device
   int32_t run_seq = 0;
   int32_t n_ptiles = 0;
-  std::vector<CUtensorMap> h_gmaps, h_xmaps;
+  std::vector<CUtensorMap> h_gmaps, h_xmaps, h_pwmaps;
+  // tensor-core projection: 128-column tiles of W and one TMA map per block
+  DevBuf d_pjtiles, d_pwmaps;
+  int32_t n_pjtiles = 0;
 
   // blocked SGD (Algorithms 1-2): ratings in epoch order, block ranges,
   // schedule, model
@@ -323,6 +326,7 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->s_out, &c->d_partials, &c->d_rmse, &c->d_VX,
                     &c->d_shift, &c->d_delta, &c->d_maps, &c->d_flag,
                     &c->d_wmaps, &c->d_ptiles, &c->d_gmaps, &c->d_xmaps, &c->d_XB, &c->d_ZB,
+                    &c->d_pjtiles, &c->d_pwmaps,
                     &c->d_sgd_cnt, &c->d_sgd_off, &c->d_sgd_key,
                     &c->d_sgd_src, &c->d_sgd_u, &c->d_sgd_i, &c->d_sgd_x,
                     &c->d_sgd_range, &c->d_sgd_blocks, &c->d_sgd_P,
@@ -645,7 +649,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
 
   int64_t goff = 0, xoff = 0, fsoff = 0, floff = 0;
   std::vector<int4> gt;
-  std::vector<int2> rt, lt, pt;
+  std::vector<int2> rt, lt, pt, pj;
   std::vector<SolverState> st0(nb);
   for (int32_t b = 0; b < nb; ++b) {
     BlockMeta &bm = c->meta[b];
@@ -672,11 +676,13 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     for (int32_t r = 0; r < bm.s_pad; r += 128) pt.push_back(make_int2(b, r));
     bm.nt = (int32_t)rt.size() - bm.t0;
     for (int32_t l = 0; l < bm.L; l += kProjCols) lt.push_back(make_int2(b, l));
+    for (int32_t l = 0; l < bm.L; l += 128) pj.push_back(make_int2(b, l));
   }
   c->n_gtiles = (int32_t)gt.size();
   c->n_rowtiles = (int32_t)rt.size();
   c->n_ltiles = (int32_t)lt.size();
   c->n_ptiles = (int32_t)pt.size();
+  c->n_pjtiles = (int32_t)pj.size();
   const bool panel_tc = c->cfg.panel_path == 0;
 
   CK(c->d_G.ensure(sizeof(float) * std::max<int64_t>(goff, 1)), "factor");
@@ -769,6 +775,36 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     CK(c->d_ptiles.ensure(sizeof(int2) * pt.size()), "factor");
     CK(cudaMemcpyAsync(c->d_ptiles.p, pt.data(), sizeof(int2) * pt.size(),
                        cudaMemcpyHostToDevice, c->st), "factor");
+    // the tensor-core projection F_L = W^T F_s: one TMA map per block over
+    // W (s_pad rows x L_pad columns, float32, boxes of 32 rows x 128
+    // columns, plain layout) and 128-column tiles
+    c->h_pwmaps.assign(nb, CUtensorMap());
+    std::memset(c->h_pwmaps.data(), 0, sizeof(CUtensorMap) * nb);
+    for (int32_t b = 0; b < nb; ++b) {
+      const BlockMeta &bm = c->meta[b];
+      if (bm.s == 0 || bm.L == 0) continue;
+      cuuint64_t dims[2] = {(cuuint64_t)bm.L_pad, (cuuint64_t)bm.s_pad};
+      cuuint64_t strides[1] = {(cuuint64_t)bm.L_pad * 4};
+      cuuint32_t box[2] = {128, 32};
+      cuuint32_t es[2] = {1, 1};
+      CUresult r = enc(&c->h_pwmaps[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                       c->d_W.as<float>() + bm.w_off, dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(c, BSVD_ECUDA, "factor: W tensor map %d failed (%d)", b,
+                    (int)r);
+    }
+    CK(c->d_pwmaps.ensure(sizeof(CUtensorMap) * std::max(nb, 1)), "factor");
+    CK(cudaMemcpyAsync(c->d_pwmaps.p, c->h_pwmaps.data(),
+                       sizeof(CUtensorMap) * nb, cudaMemcpyHostToDevice,
+                       c->st), "factor");
+    CK(c->d_pjtiles.ensure(sizeof(int2) * std::max<size_t>(pj.size(), 1)),
+       "factor");
+    if (!pj.empty())
+      CK(cudaMemcpyAsync(c->d_pjtiles.p, pj.data(), sizeof(int2) * pj.size(),
+                         cudaMemcpyHostToDevice, c->st), "factor");
   }
   CK(cudaMemsetAsync(c->d_Fs.p, 0, sizeof(float) * std::max<int64_t>(fsoff, 1), c->st), "factor");
   CK(cudaMemsetAsync(c->d_FL.p, 0, sizeof(float) * std::max<int64_t>(floff, 1), c->st), "factor");
@@ -916,9 +952,22 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
       c->launches += (deg + 1) * (nrt > 0);
     }
     mark(c, 2);
-    CK(launch_project(c->d_meta.as<BlockMeta>(), c->d_ltiles.as<int2>(),
-                      c->n_ltiles, c->d_W.as<float>(), e.Fs, c->d_FL.as<float>(),
-                      kp, c->st), "factor: project");
+    if (panel_tc) {
+      // F_s's split form goes into X's B-form buffer, free after the loop,
+      // and is read through X's maps
+      CK(launch_bform_fs(B, e.meta, c->d_ptiles.as<int2>(), c->n_ptiles, e.Fs,
+                         kp, c->d_XB.as<float>(), c->st), "factor: B form of F_s");
+      CK(launch_project_tc(B, e.meta, c->d_pjtiles.as<int2>(), c->n_pjtiles,
+                           c->d_pwmaps.as<CUtensorMap>(),
+                           c->d_xmaps.as<CUtensorMap>(), c->d_FL.as<float>(),
+                           kp, c->d_err.as<int32_t>(), c->st),
+         "factor: project (tensor cores)");
+      c->launches += (c->n_ptiles > 0);
+    } else {
+      CK(launch_project(c->d_meta.as<BlockMeta>(), c->d_ltiles.as<int2>(),
+                        c->n_ltiles, c->d_W.as<float>(), e.Fs,
+                        c->d_FL.as<float>(), kp, c->st), "factor: project");
+    }
     CK(launch_finalize(c->d_meta.as<BlockMeta>(), nb, e.Fs, c->d_FL.as<float>(),
                        c->d_sigma.as<double>(), kp, k, c->st), "factor: finalize");
     c->launches += (c->n_ltiles > 0) + (nb > 0);

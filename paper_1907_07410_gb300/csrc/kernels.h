@@ -99,6 +99,21 @@ cudaError_t launch_gpanel_tc(int32_t bsub, const BlockMeta *meta,
                              const float *in2, float *out, float *out_bf,
                              int mode, int step, int32_t *err,
                              cudaStream_t st);
+// F_L = W^T F_s on the tensor cores (three tf32 passes): tiles are (block,
+// first column l) pairs of 128 columns of W; wmaps one TMA map per block
+// over W (32-row x 128-column boxes, plain layout), fmaps one per block over
+// the B form of F_s (as xmaps), written by launch_bform_fs.
+cudaError_t launch_project_tc(int32_t bsub, const BlockMeta *meta,
+                              const int2 *tiles, int32_t ntiles,
+                              const CUtensorMap *wmaps,
+                              const CUtensorMap *fmaps, float *FL, int32_t kp,
+                              int32_t *err, cudaStream_t st);
+// B form of F_s (s_pad x kp per block, at fs_off) at 2 x_off of out_bf, in
+// the panel layout with bsub columns (zero past kp); tiles as for the
+// panel products.
+cudaError_t launch_bform_fs(int32_t bsub, const BlockMeta *meta,
+                            const int2 *tiles, int32_t ntiles, const float *Fs,
+                            int32_t kp, float *out_bf, cudaStream_t st);
 // B form of `in` for the blocks still running (tiles as above).
 cudaError_t launch_bform(int32_t bsub, const BlockMeta *meta,
                          const SolverState *state, const int2 *tiles,

@@ -64,6 +64,8 @@
 //
 // Every wait is bounded; a timeout sets kErrTimeout and the CTA drains its
 // copies in flight and frees its tensor memory before returning.
+#include <type_traits>
+
 #include "kernels.h"
 #include "tc_ptx.cuh"
 
@@ -423,6 +425,232 @@ cudaError_t launch_b(const BlockMeta *meta, SolverState *state,
                     in, in2, out, out_bf, mode, step, err);
 }
 
+// F_L = W^T F_s on the tensor cores, with the panel product's data path and
+// precision (three tf32 products, R accumulators): a CTA computes 128
+// consecutive rows l of F_L (columns of W) over the whole K range a < s.
+//   * A = the W^T tile: TMA boxes of W of 32 rows a x 128 columns l (plain
+//     layout). Converter thread l reads its column (a warp reads 32
+//     consecutive l of one row, no bank conflicts), splits it and stores hi
+//     and lo to tensor memory, as the panel kernel does with rows of G;
+//   * B = F_s in B form (launch_bform_fs), zero past column kp;
+//   * epilogue: F_L rows l < L, the kp columns.
+template <int B>
+__global__ void __launch_bounds__(kThreads, 1)
+k_project_tc(const BlockMeta *__restrict__ meta, const int2 *__restrict__ tiles,
+             const CUtensorMap *__restrict__ wmaps,
+             const CUtensorMap *__restrict__ fmaps, float *FL, int kp,
+             int32_t *err) {
+  using L = PanelTc<B>;
+  constexpr int S = L::STAGES;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  PanelCtrl &ct = *reinterpret_cast<PanelCtrl *>(base + S * L::STAGE);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int2 t = tiles[blockIdx.x];
+  const BlockMeta bm = meta[t.x];
+  const int l0 = t.y;
+  const int nk = (bm.s_pad + PK - 1) / PK;
+
+  auto w_tile = [&](int s) { return base + s * L::STAGE; };
+  auto b_op = [&](int s) { return base + s * L::STAGE + G_BYTES; };
+
+  if (warp == 0) tc::tmem_alloc(&ct.tmem, kTmemCols);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&ct.full[s], 1);
+      tc::mbar_init(&ct.empty[s], 1);
+    }
+    for (int a = 0; a < kSlots; ++a) {
+      tc::mbar_init(&ct.ready[a], kConv);
+      tc::mbar_init(&ct.afree[a], 1);
+    }
+    tc::mbar_init(&ct.done, 1);
+    ct.abort = 0;
+    ct.issued = 0;
+    ct.consumed = 0;
+    tc::mbar_init_fence();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  // F_s's B form comes from the previous kernel
+  pdl_wait();
+  const uint32_t taddr = ct.tmem;
+  const uint32_t aslots = taddr + L::ACC_COLS;
+  volatile int *abort_flag = &ct.abort;
+
+  if (warp == 0) {
+    const CUtensorMap *wmap = wmaps + t.x;
+    const CUtensorMap *fmap = fmaps + t.x;
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % S;
+      const uint32_t ph = (kc / S) & 1;
+      const bool ok = __all_sync(
+          0xffffffffu,
+          tc::mbar_wait(&ct.empty[s], ph ^ 1, kSpinP) && !*abort_flag);
+      if (!ok) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        ct.abort = 1;
+        break;
+      }
+      if (tc::elect_one()) {
+        const int k0 = kc * PK;
+        tc::mbar_expect_tx(&ct.full[s], G_BYTES + L::BOP_BYTES);
+        // rows a = k0 .. k0+31 and k0+32 .. k0+63 of W (zero past s_pad)
+        tc::tma_load_2d(w_tile(s), wmap, l0, k0, &ct.full[s]);
+        tc::tma_load_2d(w_tile(s) + G_HALF, wmap, l0, k0 + PH, &ct.full[s]);
+        tc::tma_load_2d(b_op(s), fmap, 0, 2 * kc * 2 * B, &ct.full[s]);
+        tc::tma_load_2d(b_op(s) + L::BOP_HALF, fmap, 0, (2 * kc + 1) * 2 * B,
+                        &ct.full[s]);
+        ct.issued = kc + 1;
+      }
+      __syncwarp();
+    }
+  } else if (warp == 1) {
+    constexpr uint32_t idesc2 = tc::idesc_tf32_f32(PT, 2 * B);
+    constexpr uint32_t idesc1 = tc::idesc_tf32_f32(PT, B);
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % S, a = kc % kSlots;
+      const bool ok = __all_sync(
+          0xffffffffu, tc::mbar_wait(&ct.ready[a], (kc / kSlots) & 1, kSpinP) &&
+                           !*abort_flag);
+      if (!ok) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        ct.abort = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint64_t db0 = tc::sdesc_kmajor_sw128(tc::smem_u32(b_op(s)));
+      const uint64_t db1 =
+          tc::sdesc_kmajor_sw128(tc::smem_u32(b_op(s) + L::BOP_HALF));
+      const uint32_t ahi = aslots + 2 * PK * a, alo = ahi + PK;
+      if (tc::elect_one()) {
+#pragma unroll
+        for (int kk = 0; kk < PK / 8; ++kk) {
+          const uint32_t d = taddr + 2 * B * (kk % L::R);
+          const uint64_t db = (kk < 4 ? db0 : db1) + 2 * (kk & 3);
+          const uint32_t acc = (kc > 0 || kk >= L::R) ? 1u : 0u;
+          tc::mma_tf32_ta(d, ahi + 8 * kk, db, idesc2, acc);
+          tc::mma_tf32_ta(d + B, alo + 8 * kk, db, idesc1, 1u);
+        }
+        tc::mma_commit(&ct.empty[s]);
+        tc::mma_commit(&ct.afree[a]);
+      }
+      __syncwarp();
+    }
+    if (tc::elect_one()) tc::mma_commit(&ct.done);
+    __syncwarp();
+  } else {
+    // converters (warps 2-9): lane quarter q, K half kh, as in k_gpanel_tc
+    const int cid = threadIdx.x - 64;
+    const int q = warp & 3;
+    const int kh = (warp - 2) >> 2;
+    const int r = q * 32 + lane;                  // row l0 + r of F_L
+    const uint32_t lrow = (uint32_t)(q * 32) << 16;
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % S, a = kc % kSlots;
+      const uint32_t ph = (kc / S) & 1;
+      bool ok = tc::mbar_wait(&ct.full[s], ph, kSpinP);
+      if constexpr (L::kWaitSlot)
+        ok = ok && tc::mbar_wait(&ct.afree[a], ((kc / kSlots) & 1) ^ 1, kSpinP);
+      ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+      if (!ok) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        ct.abort = 1;
+        break;
+      }
+      if (cid == 0) ct.consumed = kc + 1;
+      tc::fence_after_sync();
+      {
+        // the box holds 32 rows a of 128 floats (l): this thread's column
+        const float *wt =
+            reinterpret_cast<const float *>(w_tile(s) + kh * G_HALF) + r;
+        float h[32], lo[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const float v = wt[c * PT];
+          h[c] = hi1(v);
+          lo[c] = __fsub_rn(v, h[c]);
+        }
+        const uint32_t ta = aslots + lrow + 2 * PK * a + PH * kh;
+        tc::tmem_st32(ta, h);
+        tc::tmem_st32(ta + PK, lo);
+      }
+      tc::tmem_wait_st();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&ct.ready[a]);
+    }
+  }
+  __syncwarp();
+
+  pdl_trigger();
+  if (warp >= 2 && warp < 6) {
+    const bool ready =
+        __all_sync(0xffffffffu, tc::mbar_wait(&ct.done, 0, kSpinP));
+    if (!ready && lane == 0) atomicOr(err, kErrTimeout);
+    const bool go = __all_sync(0xffffffffu, ready && !*abort_flag);
+    if (go) {
+      tc::fence_after_sync();
+      const int q = warp & 3;
+      const int l = l0 + q * 32 + lane;
+      const uint32_t lrow = (uint32_t)(q * 32) << 16;
+      float *out = FL + bm.fl_off + (int64_t)l * kp;
+#pragma unroll 1
+      for (int c0 = 0; c0 < B; c0 += 16) {
+        if (c0 >= kp) break;                    // warp-uniform
+        float v[16], w[16];
+        acc_sum<B>(taddr + lrow, c0, v);
+        acc_sum<B>(taddr + lrow, B + c0, w);
+        if (l < bm.L) {
+          // kp is a multiple of 4: whole float4s up to it
+#pragma unroll
+          for (int c4 = 0; c4 < 4; ++c4) {
+            const int j = c0 + 4 * c4;
+            if (j < kp)
+              *reinterpret_cast<float4 *>(out + j) =
+                  make_float4(v[4 * c4] + w[4 * c4], v[4 * c4 + 1] + w[4 * c4 + 1],
+                              v[4 * c4 + 2] + w[4 * c4 + 2],
+                              v[4 * c4 + 3] + w[4 * c4 + 3]);
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x == 0 && ct.abort) {
+    for (int kc = ct.consumed; kc < ct.issued; ++kc)
+      tc::mbar_wait(&ct.full[kc % S], (kc / S) & 1, kSpinP);
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, kTmemCols);
+}
+
+// B form of F_s (s_pad x kp, row-major at fs_off) into the panel B-form
+// layout at 2 x_off, columns kp .. B-1 zero: one CTA per 128-row tile.
+template <int B>
+__global__ void __launch_bounds__(128)
+k_bform_fs(const BlockMeta *__restrict__ meta, const int2 *__restrict__ tiles,
+           const float *__restrict__ Fs, int kp, float *__restrict__ out_bf) {
+  pdl_wait();
+  pdl_trigger();
+  const int2 t = tiles[blockIdx.x];
+  const BlockMeta bm = meta[t.x];
+  const int r = t.y + threadIdx.x;
+  if (r >= bm.s_pad) return;
+  const float *src = Fs + bm.fs_off + (int64_t)r * kp;
+  float *dst = out_bf + 2 * bm.x_off + (int64_t)(r >> 5) * 2 * B * 32 + (r & 31);
+#pragma unroll 4
+  for (int j = 0; j < B; ++j) {
+    const float v = j < kp ? src[j] : 0.f;
+    const float vh = hi1(v);
+    dst[j * 32] = vh;
+    dst[(B + j) * 32] = __fsub_rn(v, vh);
+  }
+}
+
 // B form of a panel written by another kernel: one CTA per 128-row tile,
 // one thread per row; the lanes of a warp write 32 consecutive positions of
 // one chunk row.
@@ -473,6 +701,46 @@ cudaError_t launch_gpanel_tc(int32_t bsub, const BlockMeta *meta,
                                  in2, out, out_bf, mode, step, err, st);
     case 64: return launch_b<64>(meta, state, tiles, ntiles, gmaps, xmaps, in,
                                  in2, out, out_bf, mode, step, err, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_project_tc(int32_t bsub, const BlockMeta *meta,
+                              const int2 *tiles, int32_t ntiles,
+                              const CUtensorMap *wmaps,
+                              const CUtensorMap *fmaps, float *FL, int32_t kp,
+                              int32_t *err, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  auto go = [&](auto bw) -> cudaError_t {
+    constexpr int B = decltype(bw)::value;
+    static_assert(panel_tc_smem<B>() <= 227 * 1024, "shared memory");
+    cudaError_t e = cudaFuncSetAttribute(
+        k_project_tc<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)panel_tc_smem<B>());
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_project_tc<B>, dim3((unsigned)ntiles), dim3(kThreads),
+                      panel_tc_smem<B>(), st, meta, tiles, wmaps, fmaps, FL,
+                      (int)kp, err);
+  };
+  switch (bsub) {
+    case 16: return go(std::integral_constant<int, 16>());
+    case 32: return go(std::integral_constant<int, 32>());
+    case 64: return go(std::integral_constant<int, 64>());
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_bform_fs(int32_t bsub, const BlockMeta *meta,
+                            const int2 *tiles, int32_t ntiles, const float *Fs,
+                            int32_t kp, float *out_bf, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  switch (bsub) {
+    case 16: return launch_pdl(k_bform_fs<16>, dim3(ntiles), dim3(128), 0, st,
+                               meta, tiles, Fs, (int)kp, out_bf);
+    case 32: return launch_pdl(k_bform_fs<32>, dim3(ntiles), dim3(128), 0, st,
+                               meta, tiles, Fs, (int)kp, out_bf);
+    case 64: return launch_pdl(k_bform_fs<64>, dim3(ntiles), dim3(128), 0, st,
+                               meta, tiles, Fs, (int)kp, out_bf);
     default: return cudaErrorInvalidValue;
   }
 }
