@@ -90,7 +90,8 @@ typedef struct {
                              <= 0: default (1e-5) */
     uint64_t seed;        /* seed of the start basis */
     void *stream;         /* cudaStream_t, or NULL for the default stream */
-    int32_t panel_path;   /* panel products G X of the eigen-solver:
+    int32_t panel_path;   /* panel products G X of the eigen-solver and
+                             the projection F_L = W^T F_s:
                              0: tensor cores (three tf32 passes, float32
                              accuracy); 1: FP32 SIMT */
     int32_t reserved;     /* must be 0 */
