@@ -114,6 +114,10 @@ struct bsvd_ctx {
   // tensor-core projection: 128-column tiles of W and one TMA map per block
   DevBuf d_pjtiles, d_pwmaps;
   int32_t n_pjtiles = 0;
+  // the layout the uploaded tables and tensor maps were built for (see
+  // factor_impl), and the solver's initial state kept on the device
+  std::vector<unsigned char> fsig;
+  DevBuf d_state0;
 
   // blocked SGD (Algorithms 1-2): ratings in epoch order, block ranges,
   // schedule, model
@@ -326,7 +330,7 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->s_out, &c->d_partials, &c->d_rmse, &c->d_VX,
                     &c->d_shift, &c->d_delta, &c->d_maps, &c->d_flag,
                     &c->d_wmaps, &c->d_ptiles, &c->d_gmaps, &c->d_xmaps, &c->d_XB, &c->d_ZB,
-                    &c->d_pjtiles, &c->d_pwmaps,
+                    &c->d_pjtiles, &c->d_pwmaps, &c->d_state0,
                     &c->d_sgd_cnt, &c->d_sgd_off, &c->d_sgd_key,
                     &c->d_sgd_src, &c->d_sgd_u, &c->d_sgd_i, &c->d_sgd_x,
                     &c->d_sgd_range, &c->d_sgd_blocks, &c->d_sgd_P,
@@ -700,21 +704,62 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
   CK(c->d_gtiles.ensure(sizeof(int4) * std::max<size_t>(gt.size(), 1)), "factor");
   CK(c->d_rowtiles.ensure(sizeof(int2) * std::max<size_t>(rt.size(), 1)), "factor");
   CK(c->d_ltiles.ensure(sizeof(int2) * std::max<size_t>(lt.size(), 1)), "factor");
+  CK(c->d_state0.ensure(sizeof(SolverState) * std::max(nb, 1)), "factor");
+  const bool tc_maps = panel_tc && !pt.empty();
+  if (tc_maps) {
+    CK(c->d_gmaps.ensure(sizeof(CUtensorMap) * nb), "factor");
+    CK(c->d_XB.ensure(sizeof(float) * 2 * std::max<int64_t>(xoff, 1)), "factor");
+    CK(c->d_ZB.ensure(sizeof(float) * 2 * std::max<int64_t>(xoff, 1)), "factor");
+    CK(c->d_xmaps.ensure(sizeof(CUtensorMap) * 2 * nb), "factor");
+    CK(c->d_ptiles.ensure(sizeof(int2) * pt.size()), "factor");
+    CK(c->d_pwmaps.ensure(sizeof(CUtensorMap) * std::max(nb, 1)), "factor");
+    CK(c->d_pjtiles.ensure(sizeof(int2) * std::max<size_t>(pj.size(), 1)),
+       "factor");
+  }
+  // The tile tables, the TMA maps and the initial solver state depend only
+  // on the block layout (the metadata computed above, which includes every
+  // offset and keff), on B, kp and the panel path, and on the device
+  // addresses the maps point into. Repeated factorisations of one layout
+  // (the usual case: a new partition of the same shape) skip rebuilding
+  // and uploading them; uploads from pageable memory would each wait for
+  // the stream, and encoding the maps is host work the GPU idles through.
+  std::vector<unsigned char> sig;
+  {
+    auto put = [&](const void *p, size_t n) {
+      const unsigned char *b = static_cast<const unsigned char *>(p);
+      sig.insert(sig.end(), b, b + n);
+    };
+    put(c->meta.data(), sizeof(BlockMeta) * nb);
+    const int64_t head[4] = {B, kp, panel_tc ? 1 : 0, nb};
+    put(head, sizeof head);
+    const void *ptrs[] = {c->d_G.p, c->d_W.p, c->d_XB.p, c->d_ZB.p,
+                          c->d_gtiles.p, c->d_rowtiles.p, c->d_ltiles.p,
+                          c->d_gmaps.p, c->d_xmaps.p, c->d_ptiles.p,
+                          c->d_pwmaps.p, c->d_pjtiles.p, c->d_state0.p};
+    put(ptrs, sizeof ptrs);
+  }
+  const bool same_layout = sig == c->fsig;
+  c->fsig.clear();       // set again once everything below is uploaded
 
   CK(cudaMemcpyAsync(c->d_meta.p, c->meta.data(), sizeof(BlockMeta) * nb,
                      cudaMemcpyHostToDevice, c->st), "factor");
-  CK(cudaMemcpyAsync(c->d_state.p, st0.data(), sizeof(SolverState) * nb,
-                     cudaMemcpyHostToDevice, c->st), "factor");
-  if (!gt.empty())
-    CK(cudaMemcpyAsync(c->d_gtiles.p, gt.data(), sizeof(int4) * gt.size(),
+  if (!same_layout) {
+    CK(cudaMemcpyAsync(c->d_state0.p, st0.data(), sizeof(SolverState) * nb,
                        cudaMemcpyHostToDevice, c->st), "factor");
-  if (!rt.empty())
-    CK(cudaMemcpyAsync(c->d_rowtiles.p, rt.data(), sizeof(int2) * rt.size(),
-                       cudaMemcpyHostToDevice, c->st), "factor");
-  if (!lt.empty())
-    CK(cudaMemcpyAsync(c->d_ltiles.p, lt.data(), sizeof(int2) * lt.size(),
-                       cudaMemcpyHostToDevice, c->st), "factor");
-  if (panel_tc && !pt.empty()) {
+    if (!gt.empty())
+      CK(cudaMemcpyAsync(c->d_gtiles.p, gt.data(), sizeof(int4) * gt.size(),
+                         cudaMemcpyHostToDevice, c->st), "factor");
+    if (!rt.empty())
+      CK(cudaMemcpyAsync(c->d_rowtiles.p, rt.data(), sizeof(int2) * rt.size(),
+                         cudaMemcpyHostToDevice, c->st), "factor");
+    if (!lt.empty())
+      CK(cudaMemcpyAsync(c->d_ltiles.p, lt.data(), sizeof(int2) * lt.size(),
+                         cudaMemcpyHostToDevice, c->st), "factor");
+  }
+  if (nb > 0)
+    CK(cudaMemcpyAsync(c->d_state.p, c->d_state0.p, sizeof(SolverState) * nb,
+                       cudaMemcpyDeviceToDevice, c->st), "factor");
+  if (tc_maps && !same_layout) {
     // one TMA map per block over its Gram matrix (s_pad x s_pad float32,
     // 128-row x 32-float boxes) for the tensor-core panel products
     EncodeTiledFn enc = tensor_map_encoder();
@@ -806,6 +851,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
       CK(cudaMemcpyAsync(c->d_pjtiles.p, pj.data(), sizeof(int2) * pj.size(),
                          cudaMemcpyHostToDevice, c->st), "factor");
   }
+  c->fsig = std::move(sig);
   CK(cudaMemsetAsync(c->d_Fs.p, 0, sizeof(float) * std::max<int64_t>(fsoff, 1), c->st), "factor");
   CK(cudaMemsetAsync(c->d_FL.p, 0, sizeof(float) * std::max<int64_t>(floff, 1), c->st), "factor");
   CK(cudaMemsetAsync(c->d_sigma.p, 0, sizeof(double) * kp * (int64_t)nb, c->st), "factor");
