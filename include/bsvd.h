@@ -303,7 +303,7 @@ int32_t bsvd_gram_path(const bsvd_ctx *ctx);
  *       bu += a_ubias (err - b_ubias bu),  bi += a_ibias (err - b_ibias bi),
  *       p_f += a_user (err q_f - b_user p_f),
  *       q_f += a_item (err p_f - b_item q_f)   (p_f before this rating).
- *     Where the listing and Eq. 10-13 differ, this follows the equations:
+ *     Where Algorithm 2 and Eq. 10-13 differ, this follows the equations:
  *     each bias is regularised by itself.
  *   * Epochs (Algorithm 1): up to max_steps passes over all blocks; after
  *     each, the training RMSE is measured and training stops once it

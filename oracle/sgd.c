@@ -17,7 +17,7 @@
  *     p_u[f] <- p_u[f] + a_user (err q_i[f] - b_user p_u[f])   (Eq. 10)
  *     q_i[f] <- q_i[f] + a_item (err p_u[f] - b_item q_i[f])   (Eq. 11)
  *
- * Readings (the paper's listing and its equations disagree): each bias is
+ * Readings (Algorithm 2 and Eq. 10-13 disagree): each bias is
  * regularised by itself, as Eq. 12-13 write; the item-factor update uses the
  * user factor from before this rating, as Eq. 10-11 imply; the learning and
  * regularisation rates are named by the parameter they update.
