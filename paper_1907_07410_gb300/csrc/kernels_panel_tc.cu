@@ -28,9 +28,9 @@
 //     half of the stage): each thread reads one row of its half of the G
 //     tile, splits it in registers and stores hi and lo into a
 //     tensor-memory slot (tcgen05.st; lane = row, one column per K
-//     element), the A operand layout of kind::tf32. The tensor core reads shared memory at 128 bytes
-//     per cycle, so an A operand read from shared memory (4 KiB per K = 8)
-//     would cost 32 cycles per MMA;
+//     element), the A operand layout of kind::tf32. The tensor core reads
+//     shared memory at 128 bytes per cycle, so an A operand read from
+//     shared memory (4 KiB per K = 8) would cost 32 cycles per MMA;
 //   * warp 1: per K = 8 slice, two MMAs with A in tensor memory:
 //     G_hi x [in_hi | in_lo] (N = 2b) and G_lo x in_hi (N = b). The first
 //     gives the main product and one cross term side by side; the second adds
@@ -59,11 +59,14 @@
 // as tensor memory allows) and the epilogue adds them in a fixed order,
 // main halves and cross halves separately, then the two sums.
 //
-// Tensor memory (512 columns): R accumulators of 2b columns, then SA slots
-// of 128 columns (64 hi, 64 lo) for the A operand.
+// Tensor memory (512 columns): R accumulators of 2b columns, then kSlots
+// (2) slots of 128 columns (64 hi, 64 lo) for the A operand.
 //
 // Every wait is bounded; a timeout sets kErrTimeout and the CTA drains its
 // copies in flight and frees its tensor memory before returning.
+//
+// The projection F_L = W^T F_s (k_project_tc, with k_bform_fs for F_s's B
+// form) reuses this data path; see its comment below.
 #include <type_traits>
 
 #include "kernels.h"
