@@ -869,6 +869,8 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     e.theta = c->d_theta.as<float>();
     e.Fs = c->d_Fs.as<float>();
     e.running = c->d_running.as<int32_t>();
+    // k_rotate keeps X's B form current for the tensor-core products
+    e.XB = panel_tc ? c->d_XB.as<float>() : nullptr;
     e.bsub = B; e.kp = kp; e.k = k; e.nblocks = nb;
     e.max_iters = c->cfg.max_iters;
     e.max_sweeps = c->cfg.max_sweeps;
@@ -892,7 +894,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
       }
       return launch_gpanel(e, rtd, nrt, mode, step, deg, in, in2, out, c->st);
     };
-    // B form of X after a kernel other than a panel product wrote it
+    // B form of X after the random start (k_rotate writes it afterwards)
     auto bform_x = [&]() -> cudaError_t {
       if (!panel_tc) return cudaSuccess;
       ++c->launches;
@@ -985,7 +987,6 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
       // Chebyshev filter of even degree: Y_1 -> Z, Y_2 -> X, ..., Y_d -> X
       // step j reads Y_{j-1}, Y_{j-2} and overwrites Y_{j-2} with Y_j
       mark(c, 8);
-      CK(bform_x(), "factor: B form");
       for (int j = 1; j <= deg; ++j) {
         const bool even = j % 2 == 0;
         const float *in = even ? e.Z : e.X;

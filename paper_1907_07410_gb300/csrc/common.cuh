@@ -34,6 +34,13 @@ __device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// x rounded to the nearest value with 10 mantissa bits, ties away from 0
+// (exact in tf32): the "hi" part of the split x = hi + lo that the tensor-
+// core kernels use, lo = x - hi exactly.
+__device__ __forceinline__ float tf32_hi(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x00001000u) & 0xFFFFE000u);
+}
+
 #ifdef __CUDACC__
 template <typename... K, typename... A>
 cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block,

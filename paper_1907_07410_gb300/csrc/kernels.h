@@ -77,6 +77,7 @@ struct EigBuffers {
   float *theta;      // per block: bsub Ritz values, descending
   float *Fs;         // s_pad x kp per block
   int32_t *running;  // [0] blocks still iterating, [1] their largest degree
+  float *XB = nullptr;  // the B form of X for the tensor-core products, or null
   int32_t bsub, kp, k;
   int32_t nblocks;
   int32_t max_iters, max_sweeps;

@@ -614,7 +614,8 @@ k_rotate(const BlockMeta *__restrict__ meta,
          const SolverState *__restrict__ state,
          const int2 *__restrict__ rowtiles, const float *__restrict__ T,
          const float *__restrict__ theta, float *X, float *Z,
-         float *__restrict__ RP, uint64_t seed, int32_t *running) {
+         float *__restrict__ RP, uint64_t seed, int32_t *running,
+         float *__restrict__ XB) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float (*Ts)[B + 1] = reinterpret_cast<float (*)[B + 1]>(smem_raw);
   pdl_wait();
@@ -661,6 +662,15 @@ k_rotate(const BlockMeta *__restrict__ meta,
     }
     Xb[(int64_t)r * B + j] = ax;
     Zb[(int64_t)r * B + j] = az;
+    if (XB) {
+      // the B form of X for the tensor-core products that follow (rows past
+      // s keep the zeros an earlier conversion wrote)
+      const int gr = t.y + r;
+      float *bf = XB + 2 * bm.x_off + (int64_t)(gr >> 5) * 2 * B * 32 + (gr & 31);
+      const float h = tf32_hi(ax);
+      bf[j * 32] = h;
+      bf[(B + j) * 32] = __fsub_rn(ax, h);
+    }
     const float d = az - tj * ax;
     r2 = fmaf(d, d, r2);
     x2 = fmaf(ax, ax, x2);
@@ -1063,7 +1073,7 @@ cudaError_t launch_rotate(const EigBuffers &e, const int2 *rowtiles,
     return launch_pdl(k_rotate<B>, dim3(ntiles), dim3(256), rot_smem<B>(), st,
                       e.meta, (const SolverState *)e.state, rowtiles,
                       (const float *)e.T, (const float *)e.theta, e.X, e.Z,
-                      e.RP, e.seed, e.running);
+                      e.RP, e.seed, e.running, e.XB);
   });
 }
 

@@ -84,8 +84,6 @@ constexpr int kConv = 8;                 // converter warps (2..9)
 constexpr int kMaxStages = 4;
 constexpr int kSlots = 2;                // A slots in tensor memory
 constexpr uint32_t kSpinP = 1u << 22;    // mbarrier polls before giving up
-constexpr uint32_t kHiMask = 0xFFFFE000u;
-constexpr uint32_t kHiHalf = 0x00001000u;
 constexpr int G_HALF = PT * PH * 4;      // 16 KiB: one 32-float box of G
 constexpr int G_BYTES = 2 * G_HALF;
 constexpr int kTmemCols = 512;
@@ -121,10 +119,7 @@ constexpr size_t panel_tc_smem() {
   return PanelTc<B>::STAGES * PanelTc<B>::STAGE + sizeof(PanelCtrl) + 1024;
 }
 
-// x rounded to the nearest value with 10 mantissa bits (ties away from 0)
-__device__ __forceinline__ float hi1(float x) {
-  return __uint_as_float((__float_as_uint(x) + kHiHalf) & kHiMask);
-}
+__device__ __forceinline__ float hi1(float x) { return tf32_hi(x); }
 
 __device__ __forceinline__ float4 hi4(float4 v) {
   return make_float4(hi1(v.x), hi1(v.y), hi1(v.z), hi1(v.w));
