@@ -624,6 +624,7 @@ k_rotate(const BlockMeta *__restrict__ meta,
   if (blockIdx.x == 0 && threadIdx.x < 2) running[threadIdx.x] = 0;
   float (*Xs)[B + 1] = Ts + B;
   float (*Zs)[B + 1] = Xs + TR;
+  float (*Os)[B + 1] = Zs + TR;    // the new X rows, for the B form
   const int2 t = rowtiles[blockIdx.x];
   const SolverState st = state[t.x];
   if (st.status != kRunning) return;
@@ -662,15 +663,7 @@ k_rotate(const BlockMeta *__restrict__ meta,
     }
     Xb[(int64_t)r * B + j] = ax;
     Zb[(int64_t)r * B + j] = az;
-    if (XB) {
-      // the B form of X for the tensor-core products that follow (rows past
-      // s keep the zeros an earlier conversion wrote)
-      const int gr = t.y + r;
-      float *bf = XB + 2 * bm.x_off + (int64_t)(gr >> 5) * 2 * B * 32 + (gr & 31);
-      const float h = tf32_hi(ax);
-      bf[j * 32] = h;
-      bf[(B + j) * 32] = __fsub_rn(ax, h);
-    }
+    Os[r][j] = ax;
     const float d = az - tj * ax;
     r2 = fmaf(d, d, r2);
     x2 = fmaf(ax, ax, x2);
@@ -678,6 +671,22 @@ k_rotate(const BlockMeta *__restrict__ meta,
   r2s[grp][j] = r2;
   x2s[grp][j] = x2;
   __syncthreads();
+  if (XB) {
+    // the B form of X for the tensor-core products that follow: for each
+    // column, consecutive threads take consecutive rows of a 32-row chunk,
+    // so a warp stores 128 contiguous bytes (rows past s keep the zeros an
+    // earlier conversion wrote)
+    for (int e = threadIdx.x; e < TR * B; e += blockDim.x) {
+      const int c = e / TR, rr = e % TR;
+      if (rr >= rows) continue;
+      const int gr = t.y + rr;
+      float *bf = XB + 2 * bm.x_off + (int64_t)(gr >> 5) * 2 * B * 32 + (gr & 31);
+      const float v = Os[rr][c];
+      const float h = tf32_hi(v);
+      bf[c * 32] = h;
+      bf[(B + c) * 32] = __fsub_rn(v, h);
+    }
+  }
   if (threadIdx.x < B) {
     float a = 0.f, b = 0.f;
     for (int g = 0; g < G; ++g) { a += r2s[g][threadIdx.x]; b += x2s[g][threadIdx.x]; }
@@ -986,7 +995,7 @@ template <int B>
 size_t rr_smem() { return sizeof(RRSmem<B>); }
 
 template <int B>
-size_t rot_smem() { return sizeof(float) * (B + 2 * TR) * (B + 1); }
+size_t rot_smem() { return sizeof(float) * (B + 3 * TR) * (B + 1); }
 
 template <int B>
 cudaError_t set_attrs() {
