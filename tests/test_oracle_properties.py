@@ -60,3 +60,51 @@ def test_partition_properties(g):
         assert part.counts[b] == len(vals)
         if vals:
             assert part.mu32[b] == np.float32(math.fsum(vals) / len(vals))
+
+
+@st.composite
+def matrices(draw):
+    m = draw(st.integers(1, 12))
+    n = draw(st.integers(1, 12))
+    seed = draw(st.integers(0, 2**31 - 1))
+    kind = draw(st.sampled_from(["gauss", "small_ints", "dup_cols", "zero"]))
+    rng = np.random.default_rng(seed)
+    if kind == "gauss":
+        a = rng.normal(size=(m, n))
+    elif kind == "small_ints":          # many zeros and repeats, often rank-deficient
+        a = rng.integers(-3, 4, size=(m, n)).astype(np.float64)
+    elif kind == "dup_cols":            # repeated columns: exact rank deficiency
+        base = rng.normal(size=(m, max(1, n // 2)))
+        a = base[:, rng.integers(0, base.shape[1], size=n)]
+    else:
+        a = np.zeros((m, n))
+    return a
+
+
+@settings(max_examples=200, deadline=None)
+@given(matrices())
+def test_jacobi_svd_properties(a):
+    """Eq. 1 for any shape: A = U S V^T, descending non-negative S equal to
+    numpy's singular values, sum S^2 = ||A||_F^2. The short side's factor
+    (the accumulated rotations: V when m >= n, U otherwise) is orthonormal;
+    the long side's columns are orthonormal wherever the singular value is
+    not negligible (zero columns elsewhere)."""
+    m, n = a.shape
+    U, s, V = oracle.svd(a)
+    r = min(m, n)
+    assert U.shape == (m, r) and s.shape == (r,) and V.shape == (n, r)
+    assert np.all(s >= 0) and np.all(np.diff(s) <= 0)
+    scale = max(1.0, float(np.abs(a).max()))
+    ref = np.linalg.svd(a, compute_uv=False)
+    assert np.allclose(s, ref, rtol=0, atol=1e-12 * scale * (m + n))
+    assert np.allclose(U @ np.diag(s) @ V.T, a, rtol=0,
+                       atol=1e-12 * scale * (m + n))
+    fro2 = float(np.sum(a * a))
+    assert abs(float(np.sum(s * s)) - fro2) <= 1e-12 * max(1.0, fro2) * (m + n)
+    short, long_ = (V, U) if m >= n else (U, V)
+    assert np.allclose(short.T @ short, np.eye(r), rtol=0,
+                       atol=1e-12 * (m + n))
+    live = s > 1e-10 * max(s[0] if r else 0.0, 1e-300)
+    Ll = long_[:, live]
+    assert np.allclose(Ll.T @ Ll, np.eye(int(live.sum())), rtol=0,
+                       atol=1e-10 * (m + n))
