@@ -25,6 +25,10 @@ What it computes, step by step, with the passage each step follows:
    The full SVD B_b = U S V^T comes from FP64 one-sided Jacobi
    (``jacobi_svd.c``). Only the k_eff = min(k, min(m_b, n_b)) largest values
    are kept. P = U_k S_k (users x k) and V_k (items x k).
+   Blocks too large for Jacobi (the large uneven workload's biggest are
+   92,840 x 4,619) take the same truncated SVD through the FP64 symmetric
+   eigenproblem of the shorter side's Gram matrix (``factor_block_gram``),
+   pinned against the Jacobi route on blocks small enough for both.
 5. Predict (Section 2.1, Eq. 2 with S merged into the user factor):
    y_hat(u, i) = mu_b + P[r, :] . V_k[c, :].
 6. Score (Section 5, Table 1 "Test RMSE"):
@@ -300,6 +304,81 @@ def factor_block(B: np.ndarray, k: int) -> BlockFactors:
     P = U[:, :keff] * s[:keff]
     P, Vk = canonical_signs(P, V[:, :keff])
     return BlockFactors(keff, s, P, Vk)
+
+
+def block_entries(part: Partition, b: int):
+    """Local rows, columns and FP64 centred values x - mu_b of block b's
+    training ratings (step 3 without forming the dense matrix)."""
+    sel = part.block == b
+    return part.r[sel], part.c[sel], part.x[sel] - part.mu64[b]
+
+
+def factor_block_gram(part: Partition, b: int, k: int) -> BlockFactors:
+    """Step 4 for blocks too large for the Jacobi routine (a 92,840 x 4,619
+    block would take hours): the same truncated SVD (Eq. 1) through the
+    symmetric eigenproblem of the block's shorter side. The squared singular
+    values of B are the eigenvalues of G = B^T B (items side, when
+    n_b <= m_b) or G = B B^T (users side), and the eigenvectors of G are the
+    singular vectors of that side.
+
+    Steps, all in float64: G from the block's observed entries (a sparse
+    product; unobserved cells are 0 after centring); the k_eff + 1 largest
+    eigenpairs of G by LAPACK's symmetric eigensolver; sigma_i =
+    sqrt(max(lambda_i, 0)), descending; the other side's factor by one
+    product with B (P = B V when V is the eigenvector side, else
+    P = U S and V = B^T U S^-1). A singular value sigma_i has absolute error
+    about eps * sigma_1^2 / sigma_i, far below the tolerances the GPU path
+    is held to for the retained values. ``sigma`` holds only the k_eff + 1
+    largest values (enough for the gap), not all min(m_b, n_b).
+    """
+    import scipy.linalg
+    import scipy.sparse
+    mb, nb = part.grid.block_shape(b)
+    s_b = min(mb, nb)
+    keff = max(0, min(k, s_b))
+    if s_b == 0:
+        return BlockFactors(0, np.zeros(0), np.zeros((mb, 0)),
+                            np.zeros((nb, 0)))
+    r, c, v = block_entries(part, b)
+    B = scipy.sparse.csr_matrix((v, (r, c)), shape=(mb, nb))
+    items_side = nb <= mb
+    G = (B.T @ B) if items_side else (B @ B.T)
+    G = np.asarray(G.toarray(), np.float64)
+    want = min(keff + 1, s_b)
+    lam, W = scipy.linalg.eigh(G, subset_by_index=[s_b - want, s_b - 1])
+    lam, W = lam[::-1], W[:, ::-1]          # descending
+    sigma = np.sqrt(np.maximum(lam, 0.0))
+    Ws = W[:, :keff]
+    if items_side:
+        V = Ws
+        P = np.asarray(B @ V)
+    else:
+        sk = sigma[:keff]
+        P = Ws * sk
+        V = np.asarray(B.T @ Ws)
+        nz = sk > 0
+        V[:, nz] /= sk[nz]
+        V[:, ~nz] = 0.0
+    P, V = canonical_signs(P, V)
+    return BlockFactors(keff, sigma, P, V)
+
+
+def factor_gram(part: Partition, k: int, blocks=None,
+                threads: int | None = None) -> Model:
+    """factor_block_gram for every block (or the listed ones)."""
+    ids = list(range(part.grid.p * part.grid.q)) if blocks is None else list(
+        blocks)
+    threads = threads or os.cpu_count() or 1
+    out = {}
+    if threads == 1 or len(ids) == 1:
+        for b in ids:
+            out[b] = factor_block_gram(part, b, k)
+    else:
+        with _cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            for b, f in zip(ids, ex.map(
+                    lambda b: factor_block_gram(part, b, k), ids)):
+                out[b] = f
+    return Model(part, k, out)
 
 
 @dataclasses.dataclass

@@ -27,6 +27,8 @@ from __future__ import annotations
 import dataclasses
 import hashlib
 import math
+import os
+import tempfile
 
 import numpy as np
 
@@ -183,19 +185,26 @@ def sample_items(rng: np.random.Generator, counts: np.ndarray, n: int,
 
     active = np.nonzero(counts <= n // 8)[0]
     need = counts[active].copy()
-    have = np.zeros(0, np.int64)
+    rounds = []            # sorted, disjoint key sets, one per round
     while active.size:
         draw_u = np.repeat(active, need)
         draw_i = np.searchsorted(cdf, rng.random(draw_u.size), side="right")
         key = draw_u * n + np.minimum(draw_i, n - 1)
         key = _sorted_unique(key)
         # each user drew `need` times, so it cannot overshoot its deficit
-        key = key[~np.isin(key, have, assume_unique=True, kind="sort")]
-        have = np.sort(np.concatenate([have, key]))
+        for h in rounds:
+            if key.size == 0 or h.size == 0:
+                continue
+            pos = np.searchsorted(h, key)
+            pos[pos == h.size] = 0
+            key = key[h[pos] != key]
+        rounds.append(key)
         got = np.bincount(key // n, minlength=m)
         need = need - got[active]
         keep = need > 0
         active, need = active[keep], need[keep]
+    have = (np.sort(np.concatenate(rounds)) if rounds
+            else np.zeros(0, np.int64))
     users_out.append(have // n)
     items_out.append(have % n)
     uu = np.concatenate(users_out)
@@ -215,16 +224,61 @@ def ratings_from_latent(rng: np.random.Generator, m: int, n: int, d: int,
     U = rng.normal(0.0, 0.3, size=(m, d))
     V = rng.normal(0.0, 0.3, size=(n, d))
     x = np.empty(uu.size, np.float32)
+    sub = 1 << 16          # gather rows in small pieces (less temporary memory)
     for s in range(0, uu.size, chunk):
         e = min(uu.size, s + chunk)
-        dots = np.einsum("ij,ij->i", U[uu[s:e]], V[ii[s:e]])
+        dots = np.empty(e - s)
+        for a in range(s, e, sub):
+            z = min(e, a + sub)
+            dots[a - s:z - s] = np.einsum("ij,ij->i", U[uu[a:z]], V[ii[a:z]])
         eps = rng.normal(0.0, 0.8, size=e - s)
         x[s:e] = np.clip(_round_half_away(3.5 + dots + eps), 1, 5)
     return x
 
 
-def generate(w: Workload) -> Ratings:
-    """The full seeded COO for a workload, split into train and held-out."""
+# Workloads at least this large are cached on disk between processes.
+CACHE_MIN_NNZ = 10_000_000
+
+
+def _cache_path(w: Workload) -> str:
+    root = os.environ.get("BSVD_SYNTH_CACHE") or os.path.join(
+        tempfile.gettempdir(), "bsvd_synth_cache")
+    with open(__file__, "rb") as f:
+        tag = hashlib.sha256(f.read()).hexdigest()[:16]
+    return os.path.join(root, "%s-%s.npz" % (w.name, tag))
+
+
+def generate(w: Workload, cache: bool = True) -> Ratings:
+    """The full seeded COO for a workload, split into train and held-out.
+
+    Workloads of CACHE_MIN_NNZ ratings or more are kept in a cache directory
+    (``BSVD_SYNTH_CACHE``, else a folder in the system's temporary
+    directory), keyed by the workload's name and this file's contents, so
+    processes after the first load them instead of drawing them again."""
+    path = _cache_path(w) if cache and w.nnz >= CACHE_MIN_NNZ else None
+    if path and os.path.exists(path):
+        try:
+            with np.load(path) as z:
+                return Ratings(w.m, w.n, z["u_train"], z["i_train"],
+                               z["x_train"], z["u_test"], z["i_test"],
+                               z["x_test"])
+        except (OSError, KeyError, ValueError):
+            pass
+    r = _generate(w)
+    if path:
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + ".tmp%d.npz" % os.getpid()
+            np.savez(tmp, u_train=r.u_train, i_train=r.i_train,
+                     x_train=r.x_train, u_test=r.u_test, i_test=r.i_test,
+                     x_test=r.x_test)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+    return r
+
+
+def _generate(w: Workload) -> Ratings:
     rng = np.random.Generator(np.random.PCG64(w.seed))
     counts = user_counts(rng, w.m, w.n, w.nnz, w.s_user, w.min_per_user)
     w_item = _item_weights(rng, w.n, w.s_item)

@@ -299,3 +299,78 @@ def test_oracle_is_usable_from_threads():
     for (u0, s0, v0), (u1, s1, v1) in zip(serial, threaded):
         assert np.array_equal(s0, s1)
         assert np.array_equal(u0, u1) and np.array_equal(v0, v1)
+
+
+# --- the Gram route for blocks too large for Jacobi (Eq. 1) -----------------
+
+def _gram_route_agrees(part, k, blocks):
+    jac = oracle.factor(part, k, blocks=blocks)
+    gram = oracle.factor_gram(part, k, blocks=blocks)
+    for b in blocks:
+        fj, fg = jac.blocks[b], gram.blocks[b]
+        assert fg.keff == fj.keff
+        n = min(fj.keff + 1, fj.sigma.size)
+        # absolute error of the Gram route is about eps * sigma_1^2 / sigma_i
+        assert np.max(np.abs(fg.sigma[:n] - fj.sigma[:n])) <= 1e-11 * fj.sigma[0]
+        if fj.keff and fj.gap >= 1e-3:
+            Rj, Rg = fj.P @ fj.V.T, fg.P @ fg.V.T
+            assert np.linalg.norm(Rg - Rj) <= 1e-8 * np.linalg.norm(Rj)
+    return jac, gram
+
+
+@pytest.mark.parametrize("workload,k", [(synth.SMALL, 10), (synth.SMALL, 40)])
+def test_gram_route_matches_jacobi_users_side(workload, k):
+    """2 x 2 small grid: 472 x 841 blocks, the users side is shorter."""
+    w = workload
+    r = synth.generate(w)
+    part = oracle.partition(w.m, w.n, r.u_train, r.i_train, r.x_train, w.p,
+                            w.q)
+    _gram_route_agrees(part, k, [0, 3])
+
+
+def test_gram_route_matches_jacobi_items_side_and_predictions():
+    """A 4 x 12 cut of the medium matrix: 1510 x 330 blocks, the items side
+    is shorter; predictions of their held-out ratings agree too."""
+    w = synth.MEDIUM
+    r = synth.generate(w)
+    part = oracle.partition(w.m, w.n, r.u_train, r.i_train, r.x_train, 4, 12)
+    blocks = [0, 17, 47]
+    jac, gram = _gram_route_agrees(part, 20, blocks)
+    b, _, _ = part.grid.locate(r.u_test, r.i_test)
+    sel = np.isin(b, blocks)
+    yj = oracle.predict(jac, r.u_test[sel], r.i_test[sel])
+    yg = oracle.predict(gram, r.u_test[sel], r.i_test[sel])
+    gaps = np.array([jac.blocks[int(x)].gap for x in b[sel]])
+    ok = gaps >= 1e-3
+    assert ok.any()
+    assert np.max(np.abs(yj[ok] - yg[ok])) < 1e-8
+
+
+def test_gram_route_closed_forms():
+    """A diagonal block (only diagonal cells observed) has sigma = sorted
+    |x - mu|; a fully observed block 3 + u v^T with sum(u) = 0 has the one
+    singular value |u| |v|."""
+    d = np.array([1.0, 5.0, 2.0, 4.0, 4.0, 3.0], np.float32)
+    idx = np.arange(d.size, dtype=np.int32)
+    part = oracle.partition(8, 6, idx, idx, d, 1, 1)
+    mu = float(d.astype(np.float64).mean())
+    f = oracle.factor_block_gram(part, 0, 3)
+    want = np.sort(np.abs(d.astype(np.float64) - mu))[::-1]
+    assert np.max(np.abs(f.sigma[:4] - want[:4])) < 1e-13
+    # 9 x 5 rank one around the mean 3 (users side longer: items side G)
+    u = np.array([1, -1, 2, -2, 0, 3, -3, 1, -1], float)
+    v = np.array([1, 2, 0, -1, 3], float)
+    X = 3.0 + np.outer(u, v)
+    uu, ii = np.nonzero(np.ones_like(X))
+    for shape, (a, c) in (((9, 5), (uu, ii)), ((5, 9), (ii, uu))):
+        vals = X[uu, ii].astype(np.float32)
+        part = oracle.partition(shape[0], shape[1], a.astype(np.int32),
+                                c.astype(np.int32), vals, 1, 1)
+        assert part.mu64[0] == 3.0
+        f = oracle.factor_block_gram(part, 0, 2)
+        s1 = np.linalg.norm(u) * np.linalg.norm(v)
+        assert abs(f.sigma[0] - s1) < 1e-12 * s1
+        assert f.sigma[1] < 1e-6 * s1
+        R = f.P @ f.V.T
+        want = np.outer(u, v) if shape == (9, 5) else np.outer(u, v).T
+        assert np.max(np.abs(R[:, :] - want)) < 1e-10 * s1
