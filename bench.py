@@ -1,16 +1,25 @@
 """Benchmark of the block-SVD recommender hot path on GB300.
 
 One step = the whole hot path on one synthetic rating matrix already in
-HBM: partition + block means + dense scatter, Gram products, truncated
-eigen-solve, projection, held-out prediction and RMSE. The default workload
-is the MovieLens-1M-shaped matrix (6040 users x 3952 items, 1,000,209
-ratings, 90/10 split) on a 4 x 4 grid with k = 20.
+HBM: partition (block ids, exact block means, the dense centred blocks),
+Gram products, truncated eigen-solve, projection, held-out prediction and
+RMSE. The default workload is the Netflix-prize-shaped matrix (480,189
+users x 17,770 items, 100,480,507 ratings, 90/10 split) cut at rating-
+activity quantiles into a 32 x 8 grid of uneven blocks, k = 40, with the
+BF16 Gram and float32 eigen-solver of the batched form.
+
+The line's value is that fast form. Beside it ("forms") the same workload
+runs with the exact tensor-core Gram (float32 result) and on the plain FP32
+path (FP32 SIMT Gram, panel products and projection), and the
+MovieLens-1M-shaped medium matrix (4 x 4 grid, k = 20) runs as a second
+workload ("medium"). Every RMSE is compared with the FP64 oracle's value in
+the workload's fixture under tests/golden/.
 
 At N=1 the line also carries the served form ("served"): Poisson streams of
-factorise-then-predict requests through the continuous-batching server, at
-each --serve-rates rate, beside the same requests run one at a time; and the
-paper's own blocked SGD ("sgd", Algorithms 1-2): seconds per epoch on the
-same matrix, beside one epoch of the FP64 oracle.
+factorise-then-predict requests through the continuous-batching server at
+each --serve-rates rate, beside the same requests run one at a time; and
+the paper's own blocked SGD ("sgd", Algorithms 1-2): seconds per epoch on
+the medium matrix, beside one epoch of the FP64 oracle.
 
 Prints one JSON line (rank 0). Usage:
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -37,13 +46,37 @@ import synth  # noqa: E402
 
 FP32_LANES_PER_SM = 128
 SMS = 152
-# DRAM bytes (read + write) of one k_gram_tc launch, from the ncu capture
-# summarised in profiles/k_gram_tc_medium-4x4-k20.md; None until captured.
-GRAM_TC_TRAFFIC = {"medium-6040x3952-4x4-k20": 133.9e6}
-GRAM_BF16_TRAFFIC = {}
-# DRAM bytes of one k_gpanel_tc launch with every block running, from the
-# ncu capture summarised in profiles/k_gpanel_tc_medium-4x4-k20.md.
-PANEL_TRAFFIC = {"medium-6040x3952-4x4-k20": 67.94e6}
+PROFILES = os.path.join(ROOT, "profiles")
+CSRC = os.path.join(ROOT, "paper_1907_07410_gb300", "csrc")
+# kernel -> source file whose contents the ncu traffic figures belong to
+KERNEL_SOURCES = {"k_gpanel_tc": "kernels_panel_tc.cu",
+                  "k_gram_tc": "kernels_gram_tc.cu",
+                  "k_gram_bf16": "kernels_gram_tc.cu",
+                  "k_gram_tf32": "kernels_gram_tc.cu",
+                  "k_gram_f32": "kernels_gram.cu"}
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from
+    the ncu summaries under profiles/, if one was captured from the kernel's
+    current source. A summary records it in a line
+    ``traffic: <kernel> <workload> <bytes> <sha256 of the source file>``;
+    a figure taken from other source is stale and gives None."""
+    src = KERNEL_SOURCES.get(kernel)
+    if not src or not os.path.isdir(PROFILES):
+        return None
+    import hashlib
+    with open(os.path.join(CSRC, src), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    for name in sorted(os.listdir(PROFILES)):
+        with open(os.path.join(PROFILES, name)) as f:
+            for line in f:
+                parts = line.strip().strip("`").split()
+                if (len(parts) == 5 and parts[0] == "traffic:"
+                        and parts[1] == kernel and parts[2] == workload
+                        and parts[4] == sha):
+                    return float(parts[3])
+    return None
 
 
 def load_peaks():
@@ -139,83 +172,130 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def golden_rmse(w):
+def golden(w):
     path = os.path.join(ROOT, "tests", "golden", w.name + ".json")
     if os.path.exists(path):
         with open(path) as f:
-            return json.load(f)["rmse"]
+            return json.load(f)
     return None
 
 
-def oracle_sample(w, r, nblocks, threads, gridkw=None):
-    """The oracle (as it stands) on a bounded sample: partition of all the
-    ratings, factorisation of the `nblocks` blocks with the fewest cells
-    (lowest ids on ties), RMSE over their held-out ratings.
-    Returns (seconds, blocks)."""
+def bench_config(w, r):
+    """The workload as both arms name it (identical dicts)."""
+    return {"workload": w.name, "m": w.m, "n": w.n,
+            "nnz_train": int(r.u_train.size), "nnz_test": int(r.u_test.size),
+            "p": w.p, "q": w.q, "k": w.k, "grid": w.grid,
+            "l2": "flushed (256 MB write) before each step, untimed"}
+
+
+def jacobi_work(shape):
+    """One-sided Jacobi work of a block, m_b n_b s_b (flops per sweep / 6)."""
+    mb, nb = shape
+    return float(mb) * nb * min(mb, nb)
+
+
+def oracle_block_sample(w, r, count, max_work=2.0e9):
+    """A bounded, spread-out sample of the workload's blocks for timing the
+    oracle: of the blocks whose Jacobi work m_b n_b s_b is at most
+    `max_work` (the largest blocks take the oracle hours), `count` evenly
+    spaced in work order. Returns (oracle partition restricted to the
+    sample's ratings, sample ids, work per block of the whole grid)."""
     import oracle
+    gridkw = oracle_grid(w, r)
+    g = oracle.make_grid(w.m, w.n, w.p, w.q, **gridkw)
+    nb = w.p * w.q
+    work = [jacobi_work(g.block_shape(b)) for b in range(nb)]
+    ok = sorted((b for b in range(nb) if 0 < work[b] <= max_work),
+                key=lambda b: (work[b], b))
+    count = min(count, len(ok))
+    pick = sorted({ok[int(round(j * (len(ok) - 1) / max(count - 1, 1)))]
+                   for j in range(count)})
+    b_tr, _, _ = g.locate(r.u_train, r.i_train)
+    sel = np.isin(b_tr, pick)
+    part = oracle.partition(w.m, w.n, r.u_train[sel], r.i_train[sel],
+                            r.x_train[sel], w.p, w.q, **gridkw)
+    return part, pick, work
+
+
+def oracle_grid(w, r):
+    """Bounds and permutations of the workload's grid, from the oracle."""
+    if w.grid != "quantile":
+        return {}
+    import oracle
+    rp, rb = oracle.activity_quantile_cut(r.u_train, w.m, w.p)
+    cp, cb = oracle.activity_quantile_cut(r.i_train, w.n, w.q)
+    return dict(row_bounds=rb, col_bounds=cb, row_perm=rp, col_perm=cp)
+
+
+def oracle_sample(w, r, threads):
+    """The oracle (as it stands) on a bounded sample: FP64 Jacobi SVDs of
+    `threads` sampled blocks at once, one thread each, and the RMSE of their
+    held-out ratings. The measured rate (Jacobi work per second) is scaled
+    to the whole grid: value = blocks / (total work / rate)."""
+    import oracle
+    part, pick, work = oracle_block_sample(w, r, threads)
     t0 = time.perf_counter()
-    part = oracle.partition(w.m, w.n, r.u_train, r.i_train, r.x_train, w.p,
-                            w.q, **(gridkw or {}))
-    cells = [np.prod(part.grid.block_shape(b)) for b in range(w.p * w.q)]
-    ids = sorted(int(b) for b in
-                 np.argsort(cells, kind="stable")[:min(nblocks, w.p * w.q)])
-    model = oracle.factor(part, w.k, blocks=ids, threads=threads)
+    model = oracle.factor(part, w.k, blocks=pick, threads=threads)
     b, _, _ = part.grid.locate(r.u_test, r.i_test)
-    sel = np.isin(b, ids)
+    sel = np.isin(b, pick)
     if sel.any():
         oracle.rmse(model, r.u_test[sel], r.i_test[sel], r.x_test[sel])
-    return time.perf_counter() - t0, len(ids)
+    dt = time.perf_counter() - t0
+    done = sum(work[b] for b in pick)
+    nb = w.p * w.q
+    value = nb / (sum(work) / (done / dt))
+    return value, dt, pick, done / sum(work)
 
 
 def run_reference(args, w, r, rank):
     """Reference arm: the FP64 oracle on the host cores. A step is one block
-    of the workload (cycling through the grid): its FP64 Jacobi SVD and the
-    held-out RMSE of its ratings. Steps run on a pool of one thread per
-    core (the C routine releases the GIL), so the value is the oracle's
-    throughput on the whole host: timed blocks / wall time."""
+    of a bounded sample of the workload's blocks (cycling through it): its
+    FP64 Jacobi SVD and the held-out RMSE of its ratings. Steps run on a
+    pool of one thread per core (the C routine releases the GIL). The
+    sample's rate (Jacobi work per second of wall time) is scaled to the
+    whole grid, so the value is block-SVDs/s of the workload's own mix."""
     if rank != 0:
         return
     import concurrent.futures as cf
     import oracle
     oracle.build()           # once, before the worker threads use it
     cores = os.cpu_count() or 1
-    gridkw = host_grid(w, r)
     t0 = time.perf_counter()
-    part = oracle.partition(w.m, w.n, r.u_train, r.i_train, r.x_train, w.p,
-                            w.q, **(gridkw or {}))
+    part, pick, work = oracle_block_sample(w, r, 4 * cores, max_work=1.0e9)
     t_part = time.perf_counter() - t0
     b_te, _, _ = part.grid.locate(r.u_test, r.i_test)
-    nb = w.p * w.q
 
     def one(step):
-        b = step % nb
-        t = time.perf_counter()
+        b = pick[step % len(pick)]
         model = oracle.Model(part, w.k,
                              {b: oracle.factor_block(oracle.dense_block(part, b),
                                                      w.k)})
         sel = b_te == b
         if sel.any():
             oracle.rmse(model, r.u_test[sel], r.i_test[sel], r.x_test[sel])
-        return time.perf_counter() - t
+        return work[b]
     with cf.ThreadPoolExecutor(max_workers=cores) as ex:
         list(ex.map(one, range(args.warmup)))
         t0 = time.perf_counter()
-        per = list(ex.map(one, range(args.warmup, args.warmup + args.steps)))
+        done = sum(ex.map(one, range(args.warmup, args.warmup + args.steps)))
         wall = time.perf_counter() - t0
-    value = args.steps / wall
-    sample = ("per step: one block of the %d (cycling), FP64 Jacobi SVD of "
-              "its centred dense block and the RMSE of its held-out ratings; "
-              "steps on %d threads at once; the oracle partition of all %d "
-              "training ratings ran once first (%.2f s, not in the timing)"
-              % (nb, cores, r.u_train.size, t_part))
+    nb = w.p * w.q
+    raw = args.steps / wall
+    value = nb / (sum(work) / (done / wall))
+    sample = ("per step: one of %d sampled blocks (Jacobi work m_b n_b s_b <= "
+              "1e9, evenly spread in work order; cycling), its FP64 Jacobi "
+              "SVD and the RMSE of its held-out ratings; %d threads at once; "
+              "%.1f sampled blocks/s, scaled by Jacobi work to the whole "
+              "%d-block grid; oracle grid + partition of the sample's "
+              "ratings ran first (%.1f s, not in the timing)"
+              % (len(pick), cores, raw, nb, t_part))
     line = {
         "impl": "reference", "metric": "block SVDs/s", "value": value,
         "unit": "block-SVDs/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(per),
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "m": w.m, "n": w.n, "p": w.p,
-                   "q": w.q, "k": w.k},
+        "config": bench_config(w, r),
         "cpu_baseline": {"value": value, "unit": "block-SVDs/s",
                          "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "block-SVDs/s",
@@ -258,10 +338,13 @@ def poisson_run(srv, pool, rate, count, seed):
     return res, span
 
 
-def serve_leg(rates, workers=4, max_batch=64, budget=120e9):
+def serve_leg(rates, per_rate=None, workers=4, max_batch=64, budget=120e9):
     """The served form: Poisson streams of factorise-then-predict requests
     through the continuous-batching server at each rate, beside the same
-    requests run one at a time through one context."""
+    requests run one at a time through one context. `per_rate` requests per
+    rate (None: 2 s of traffic, 64 to 10,000). The predictions of a seeded
+    1% sample of each stream's requests are compared with the oracle's
+    fixture for the pool."""
     import paper_1907_07410_gb300 as bs
     from paper_1907_07410_gb300 import serve
     pool, qy = served_pool()
@@ -270,18 +353,36 @@ def serve_leg(rates, workers=4, max_batch=64, budget=120e9):
            "3-10% observed, k in {10,20,40}, 64 held-out queries each",
            "workers": workers, "max_batch": max_batch,
            "hbm_budget_gb": budget / 1e9, "sweep": []}
+    gpath = os.path.join(ROOT, "tests", "golden", "served-pool-%d.json" % P)
+    gold = None
+    if os.path.exists(gpath):
+        with open(gpath) as f:
+            gold = {q["index"]: np.array(q["yhat"])
+                    for q in json.load(f)["requests"]}
     served_y = [None] * P
+    sample_err, sample_diff, sample_n = [], 0.0, 0
     with serve.Server(workers=workers, max_batch=max_batch,
                       hbm_budget=budget) as srv:
         for f in [srv.submit(__import__("dataclasses").replace(q))
                   for q in pool * 2]:
             f.result(timeout=600)                  # warm-up: buffers, code
         for n, rate in enumerate(rates):
-            count = int(min(max(rate * 2.0, 64), 1500))
+            count = int(per_rate or min(max(rate * 2.0, 64), 10000))
             nb0 = len(srv.batches)
             res, span = poisson_run(srv, pool, rate, count, 1000 + n)
             for j, r in enumerate(res[:P]):
                 served_y[j] = r.yhat
+            if gold is not None:
+                rng = np.random.default_rng(2000 + n)
+                pick = rng.choice(count, max(1, count // 100), replace=False)
+                for j in sorted(pick.tolist()):
+                    pj = j % P
+                    if pj in gold:
+                        d = res[j].yhat.astype(np.float64) - gold[pj]
+                        sample_diff = max(sample_diff, float(np.max(np.abs(d))))
+                        sample_err.append(res[j].yhat.astype(np.float64)
+                                          - qy[pj])
+                        sample_n += 1
             sizes = [len(ids) for ids, _ in srv.batches[nb0:]]
             lat = serve.latency_percentiles(res)
             out["sweep"].append({
@@ -317,17 +418,21 @@ def serve_leg(rates, workers=4, max_batch=64, budget=120e9):
         err_1.astype(np.float64) ** 2)))
     out["max_abs_diff_served_vs_one"] = float(max(
         np.max(np.abs(served_y[j] - one_y[j])) for j in range(P)))
-    gpath = os.path.join(ROOT, "tests", "golden",
-                         "served-pool-%d.json" % P)
-    if os.path.exists(gpath):
-        with open(gpath) as f:
-            g = json.load(f)
-        ids = [q["index"] for q in g["requests"]]
+    if gold is not None:
+        ids = sorted(gold)
         e = np.concatenate([served_y[j] - qy[j] for j in ids])
+        eo = np.concatenate([gold[j] - qy[j] for j in ids])
         got = float(np.sqrt(np.mean(e.astype(np.float64) ** 2)))
-        out["rmse_oracle_subset"] = {
-            "requests": len(ids), "served": got, "oracle": g["rmse"],
-            "parity": abs(got - g["rmse"]) <= 1e-4}
+        want = float(np.sqrt(np.mean(eo ** 2)))
+        out["rmse_oracle_pool"] = {
+            "requests": len(ids), "served": got, "oracle": want,
+            "parity": abs(got - want) <= 1e-4}
+        if sample_n:
+            es = np.concatenate(sample_err)
+            out["oracle_sample"] = {
+                "requests": sample_n, "of": "a seeded 1% of each stream",
+                "max_abs_yhat_diff": sample_diff,
+                "rmse_served": float(np.sqrt(np.mean(es ** 2)))}
     return out
 
 
@@ -385,30 +490,193 @@ def sgd_leg(r, w, epochs=10, grids=(8, 64, 256)):
     return out
 
 
-def host_grid(w, r):
-    """Bounds and permutations of an activity-quantile grid (host side)."""
+def grid_bounds_of(w, r):
+    """Row and column bounds of the workload's grid, for counting the
+    method's work: the activity-quantile cut (from the library) or the
+    paper's equal blocks."""
     if w.grid != "quantile":
         return None
-    from paper_1907_07410_gb300 import grid
-    return grid.quantile_grid(r.u_train, r.i_train, w.m, w.n, w.p, w.q)
+    import paper_1907_07410_gb300 as bs
+    with bs.Context() as ctx:
+        kw = ctx.quantile_grid(w.m, w.n, r.u_train, r.i_train, w.p, w.q)
+    return kw
+
+
+def time_form(w, data, steps, warmup, flush, stream, **cfg):
+    """Warm up, then time `steps` steps of one form of the path. Returns the
+    per-step times, phases, RMSE, launches and the solver report."""
+    import torch
+    import paper_1907_07410_gb300 as bs
+    u_tr, i_tr, x_tr, u_te, i_te, x_te = data
+    ctx = bs.Context(stream=stream, profile=1, **cfg)
+    for _ in range(warmup):
+        ctx.partition(w.m, w.n, u_tr, i_tr, x_tr, w.p, w.q,
+                      **step_grid(ctx, w, u_tr, i_tr))
+        ctx.factor(w.k, warn=False)
+        ctx.rmse(u_te, i_te, x_te)
+    phases = {k: [] for k in bs.PHASES}
+    step_ms = []
+    launches0 = ctx.kernel_launches()
+    for _ in range(steps):
+        flush.fill_(1)                       # evict L2 between steps (untimed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.partition(w.m, w.n, u_tr, i_tr, x_tr, w.p, w.q,
+                      **step_grid(ctx, w, u_tr, i_tr))
+        part_ph = ctx.phase_times()["partition"]
+        status = ctx.factor(w.k, warn=False)
+        fac_ph = ctx.phase_times()
+        rm = ctx.rmse(u_te, i_te, x_te)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        ph = ctx.phase_times()
+        phases["partition"].append(part_ph)
+        for key in ("gram", "eigen", "project", "eigen_filter", "eigen_rr",
+                    "eigen_other"):
+            phases[key].append(fac_ph[key])
+        phases["predict"].append(ph["predict"])
+    return dict(ctx=ctx, step_ms=step_ms, rmse=rm, status=status,
+                launches=ctx.kernel_launches() - launches0,
+                phases={k: statistics.mean(v) for k, v in phases.items()},
+                report=ctx.factor_report(full=True),
+                gram_path=ctx.gram_path())
+
+
+def step_grid(ctx, w, u, i):
+    """The grid's bounds and permutations for partition(): the activity-
+    quantile cut (computed by the library, part of the step) for the
+    uneven workloads, the paper's equal blocks otherwise."""
+    if w.grid != "quantile":
+        return {}
+    return ctx.quantile_grid(w.m, w.n, u, i, w.p, w.q)
+
+
+GRAM_NAMES = {1: "fp32 simt", 2: "tensor cores, exact (bf16 planes)",
+              3: "tensor cores, tf32", 4: "tensor cores, bf16"}
+GRAM_KERNELS = {1: "k_gram_f32", 2: "k_gram_tc", 3: "k_gram_tf32",
+                4: "k_gram_bf16"}
+
+
+def gram_peak(gram_path, peaks, peak_kind):
+    """(bound, peak TFLOP/s, what the peak is) of a Gram kernel."""
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    if gram_path in (2, 4):
+        return "tensor", bf16, "bf16 dense, burst, of %s" % peak_kind
+    if gram_path == 3:
+        return "tensor", 0.5 * bf16, "0.5 x bf16 dense burst, of %s" % peak_kind
+    return "alu", fp32_alu_peak_tflops(peaks), (
+        "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % peaks.get("sm_max_mhz",
+                                                           2070.0))
+
+
+def step_roofline(w, r, shapes, keff, gram_path, step_s, peaks, peak_kind):
+    """The whole step against its roofline: the method's algorithmic flops
+    (Gram 2 m_b n_b s_b, projection 2 m_b n_b k, prediction 2 k per query)
+    and bytes (COO read 12 B per training rating, dense blocks written once
+    in float32, read once by the Gram in its operand type and once by the
+    projection in float32, 12 B plus two k-float factor rows per query).
+    The eigen-solver's iterations are not counted."""
+    cells = float(sum(s * L for (s, L) in shapes))
+    f_gram = gram_flops(shapes)
+    f_proj = 2.0 * sum(s * L * min(keff, s) for (s, L) in shapes)
+    f_pred = 2.0 * keff * r.u_test.size
+    gram_operand = {1: 4, 2: 4, 3: 4, 4: 2}.get(gram_path, 4)
+    by = (12.0 * r.u_train.size + cells * (4 + gram_operand + 4)
+          + r.u_test.size * (12.0 + 8.0 * keff))
+    bound, tc_peak, _ = gram_peak(gram_path, peaks, peak_kind)
+    flops = f_gram + f_proj + f_pred
+    t_tc = flops / (tc_peak * 1e12)
+    t_hbm = by / (peaks.get("hbm_gbs", 6800.0) * 1e9)
+    t_roof = max(t_tc, t_hbm)
+    return {"bound": (bound if t_tc >= t_hbm else "hbm"),
+            "roofline_ms": t_roof * 1e3, "measured_ms": step_s * 1e3,
+            "frac": t_roof / step_s, "algorithmic_flops": flops,
+            "algorithmic_bytes": by, "tensor_ms": t_tc * 1e3,
+            "hbm_ms": t_hbm * 1e3,
+            "note": "eigen-solver iterations excluded from the work; the "
+                    "exact Gram counts its float32 operand bytes"}
+
+
+def panel_roofline(w, shapes, rep, filter_ms, peaks, peak_kind):
+    """The eigen-solver's panel products G X (k_gpanel_tc): algorithmic
+    bytes per product = G once (4 s^2) + the panel in and out (4 s b each),
+    summed over the filter phase's products (the first product of each
+    block runs before the phase's events and is left out) and divided by
+    the phase's event time. b/2 flop per byte of G: far below the tensor
+    ridge, so the bound is bandwidth."""
+    want = w.k + max(8, w.k // 2)
+    bsub = 16 if want <= 16 else (32 if want <= 32 else 64)
+    pflops = pbytes = 0.0
+    nprod = 0
+    for (s_b, L_b), prods in zip(shapes, rep["products"]):
+        n_f = max(int(prods) - 1, 0)
+        b_b = min(bsub, s_b)
+        pflops += n_f * 2.0 * s_b * s_b * b_b
+        pbytes += n_f * (4.0 * s_b * s_b + 8.0 * s_b * b_b)
+        nprod += int(prods)
+    t = filter_ms * 1e-3
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    gbs = pbytes / t / 1e9 if t > 0 else 0.0
+    tf = pflops / t / 1e12 if t > 0 else 0.0
+    tf32 = 0.5 * peaks.get("bf16_tflops", 1900.0)
+    return {"kernel": "k_gpanel_tc", "bound": "hbm", "achieved": gbs,
+            "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+            "traffic": profiled_traffic("k_gpanel_tc", w.name),
+            "peak_source": "STREAM-style copy, of %s" % peak_kind,
+            "products": nprod, "algorithmic_bytes": pbytes,
+            "tensor_tflops": tf,
+            "tensor_frac_of_fp32_equivalent": tf / (tf32 / 3.0),
+            "note": "algorithmic bytes (G once, panel in and out) of the "
+                    "filter phase's block products over that phase's event "
+                    "time; tensor_tflops counts 2 s^2 b flops per product "
+                    "against one third of the tf32 peak (0.5 x measured "
+                    "bf16), as the kernel issues three tf32 products for "
+                    "float32 accuracy"}
+
+
+def form_summary(w, r, res, gold, steps):
+    total = sum(res["step_ms"])
+    g_rmse = gold["rmse"] if gold else None
+    rep = res["report"]
+    return {"value": w.p * w.q * steps / (total * 1e-3),
+            "ms_per_step": total / steps, "steps": steps,
+            "gram": GRAM_NAMES.get(res["gram_path"], "none"),
+            "rmse": res["rmse"], "rmse_oracle": g_rmse,
+            "rmse_parity": (g_rmse is not None
+                            and abs(res["rmse"] - g_rmse) <= 1e-4),
+            "converged_blocks": int(np.sum(rep["converged"])),
+            "phases_ms": res["phases"]}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default=synth.MEDIUM.name,
+    ap.add_argument("--workload", default=synth.LARGE.name,
                     choices=sorted(synth.WORKLOADS))
-    ap.add_argument("--precision", default="fp32",
+    ap.add_argument("--precision", default="bf16",
                     choices=("fp32", "tf32", "bf16"))
+    ap.add_argument("--forms", default="exact,plain",
+                    help="other forms timed beside the main one: exact "
+                         "(tensor-core exact Gram, float32 result), plain "
+                         "(FP32 SIMT Gram, panel products and projection); "
+                         "empty to skip")
+    ap.add_argument("--form-steps", type=int, default=3,
+                    help="timed steps of each other form")
+    ap.add_argument("--no-medium", action="store_true",
+                    help="skip the medium-matrix leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sgd", action="store_true",
                     help="skip the blocked-SGD leg (the paper's Algorithms 1-2)")
-    ap.add_argument("--serve-rates", default="50,500,5000",
+    ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000,5000",
                     help="Poisson rates (req/s) of the served-form leg; "
                          "empty to skip it")
+    ap.add_argument("--serve-requests", type=int, default=0,
+                    help="requests per rate (0: 2 s of traffic, 64 to 10000)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -437,60 +705,26 @@ def main():
         torch.cuda.synchronize()
 
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
-    gridkw = host_grid(w, r)
-    pkw = {}
-    if gridkw:
-        pkw = dict(row_bounds=gridkw["row_bounds"],
-                   col_bounds=gridkw["col_bounds"],
-                   row_perm=dev(gridkw["row_perm"]),
-                   col_perm=dev(gridkw["col_perm"]))
-    u_tr, i_tr, x_tr = dev(r.u_train), dev(r.i_train), dev(r.x_train)
-    u_te, i_te, x_te = dev(r.u_test), dev(r.i_test), dev(r.x_test)
     stream = torch.cuda.current_stream()
-    ctx = bs.Context(stream=stream, profile=1,
-                     precision={"fp32": bs.FP32, "tf32": bs.TF32,
-                                "bf16": bs.BF16}[args.precision])
-    nblocks = w.p * w.q
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    def device_data(rr):
+        return (dev(rr.u_train), dev(rr.i_train), dev(rr.x_train),
+                dev(rr.u_test), dev(rr.i_test), dev(rr.x_test))
 
-    def step():
-        ctx.partition(w.m, w.n, u_tr, i_tr, x_tr, w.p, w.q, **pkw)
-        ctx.factor(w.k)
-        return ctx.rmse(u_te, i_te, x_te)
+    data = device_data(r)
+    prec = {"fp32": bs.FP32, "tf32": bs.TF32, "bf16": bs.BF16}
+    nblocks = w.p * w.q
 
-    for _ in range(args.warmup):
-        rm = step()
-
-    # ---- device-resident timed region -----------------------------------
-    phases = {k: [] for k in bs.PHASES}
-    step_ms = []
-    launches0 = ctx.kernel_launches()
+    # ---- device-resident timed region (the main form) --------------------
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
-    for _ in range(args.steps):
-        flush.fill_(1)                       # evict L2 between steps (untimed)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.partition(w.m, w.n, u_tr, i_tr, x_tr, w.p, w.q, **pkw)
-        part_ph = ctx.phase_times()["partition"]
-        ctx.factor(w.k)
-        fac_ph = ctx.phase_times()
-        rm = ctx.rmse(u_te, i_te, x_te)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        ph = ctx.phase_times()
-        phases["partition"].append(part_ph)
-        for key in ("gram", "eigen", "project", "eigen_filter", "eigen_rr",
-                    "eigen_other"):
-            phases[key].append(fac_ph[key])
-        phases["predict"].append(ph["predict"])
+    main_res = time_form(w, data, args.steps, args.warmup, flush, stream,
+                         precision=prec[args.precision])
     barrier()
     clk = clocks.stop()
-    launches = ctx.kernel_launches() - launches0
-    total_ms = sum(step_ms)
+    ctx = main_res["ctx"]
+    total_ms = sum(main_res["step_ms"])
     if dist is not None:
         from paper_1907_07410_gb300 import dist as bdist
         total_ms = bdist.max_over_ranks(total_ms)
@@ -499,103 +733,57 @@ def main():
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
     h_u, h_i, h_x = pin(r.u_train), pin(r.i_train), pin(r.x_train)
     h_ut, h_it, h_xt = pin(r.u_test), pin(r.i_test), pin(r.x_test)
-    pkw_host = {}
-    if gridkw:
-        pkw_host = dict(row_bounds=gridkw["row_bounds"],
-                        col_bounds=gridkw["col_bounds"],
-                        row_perm=pin(gridkw["row_perm"]),
-                        col_perm=pin(gridkw["col_perm"]))
     e2e_ms = []
     barrier()
     for _ in range(args.steps):
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.partition(w.m, w.n, h_u, h_i, h_x, w.p, w.q, **pkw_host)
-        ctx.factor(w.k)
+        ctx.partition(w.m, w.n, h_u, h_i, h_x, w.p, w.q,
+                      **step_grid(ctx, w, h_u, h_i))
+        ctx.factor(w.k, warn=False)
         rm_e2e = ctx.rmse(h_ut, h_it, h_xt)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     barrier()
     e2e_total = sum(e2e_ms)
     if dist is not None:
         e2e_total = bdist.max_over_ranks(e2e_total)
+    ctx.close()
+
+    # ---- the other forms, the same workload ------------------------------
+    forms = {}
+    form_cfg = {"exact": dict(precision=bs.FP32),
+                "plain": dict(precision=bs.FP32, gram_path=1, panel_path=1),
+                "bf16": dict(precision=bs.BF16), "tf32": dict(precision=bs.TF32)}
+    for name in [f for f in args.forms.split(",") if f.strip()]:
+        res = time_form(w, data, args.form_steps, args.warmup, flush, stream,
+                        **form_cfg[name])
+        res["ctx"].close()
+        forms[name] = res
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
 
+    quant = w.grid == "quantile"
+    e2e_h2d = int(12 * (r.u_train.size + r.u_test.size)
+                  + (8 * r.u_train.size + 4 * (w.m + w.n) if quant else 0))
+    e2e_d2h = int(8 + (4 * (w.m + w.n) + 8 * (w.p + w.q + 2) if quant else 0))
     peaks, peak_kind = load_peaks()
-    shapes = block_shapes(w, gridkw)
+    gold = golden(w)
+    shapes = block_shapes(w, grid_bounds_of(w, r))
     gflops = gram_flops(shapes)
-    gram_ms = statistics.mean(phases["gram"])
-    achieved = gflops / (gram_ms * 1e-3) / 1e12
-    gram_path = ctx.gram_path()
-    if gram_path == 4:
-        roof = {"kernel": "k_gram_bf16", "bound": "tensor",
-                "peak": peaks.get("bf16_tflops", 1900.0),
-                "peak_source": "bf16 dense, burst, of %s" % peak_kind,
-                "traffic": GRAM_BF16_TRAFFIC.get(w.name)}
-    elif gram_path == 3:
-        # tf32 peak: the bf16 measurement scaled by the nominal ratio 1/2
-        roof = {"kernel": "k_gram_tf32", "bound": "tensor",
-                "peak": 0.5 * peaks.get("bf16_tflops", 1900.0),
-                "peak_source": "0.5 x bf16 dense burst, of %s" % peak_kind,
-                "traffic": None}
-    elif gram_path == 2:
-        roof = {"kernel": "k_gram_tc", "bound": "tensor",
-                "peak": peaks.get("bf16_tflops", 1900.0),
-                "peak_source": "bf16 dense, burst, of %s" % peak_kind,
-                "traffic": GRAM_TC_TRAFFIC.get(w.name)}
-    else:
-        roof = {"kernel": "k_gram_f32", "bound": "alu",
-                "peak": fp32_alu_peak_tflops(peaks),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz"
-                               % peaks.get("sm_max_mhz", 2070.0),
-                "traffic": None}
-    # the dominant kernel: panel products G X of the eigen-solver, counted
-    # per block by the library (the last timed step's factorisation). The
-    # first product of each block runs before the filter phase's events, so
-    # it is left out of both the work and the time. Its arithmetic intensity
-    # (2 s^2 b flops per 4 s^2 bytes of G, b/2 flop/B) is far below the
-    # tensor ridge, so its roofline is bandwidth: algorithmic bytes per
-    # product = G once (4 s^2) + the panel in and the panel out (4 s b each).
-    rep = ctx.factor_report(full=True)
-    bsub = 16 if w.k + max(8, w.k // 2) <= 16 else (
-        32 if w.k + max(8, w.k // 2) <= 32 else 64)
-    pflops = pbytes = 0.0
-    nprod = 0
-    for (s_b, L_b), prods in zip(shapes, rep["products"]):
-        n_f = max(int(prods) - 1, 0)
-        b_b = min(bsub, s_b)
-        pflops += n_f * 2.0 * s_b * s_b * b_b
-        pbytes += n_f * (4.0 * s_b * s_b + 8.0 * s_b * b_b)
-        nprod += int(prods)
-    t_filter = statistics.mean(phases["eigen_filter"]) * 1e-3
-    tf32_peak = 0.5 * peaks.get("bf16_tflops", 1900.0)
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    p_gbs = pbytes / t_filter / 1e9 if t_filter > 0 else 0.0
-    p_tf = pflops / t_filter / 1e12 if t_filter > 0 else 0.0
-    roof_panel = {
-        "kernel": "k_gpanel_tc", "bound": "hbm",
-        "achieved": p_gbs, "peak": hbm_peak, "unit": "GB/s",
-        "frac": p_gbs / hbm_peak,
-        "traffic": PANEL_TRAFFIC.get(w.name),
-        "peak_source": "STREAM-style copy, of %s" % peak_kind,
-        "products": nprod,
-        "algorithmic_bytes": pbytes,
-        "tensor_tflops": p_tf,
-        "tensor_frac_of_fp32_equivalent": p_tf / (tf32_peak / 3.0),
-        "note": "algorithmic bytes (G once, panel in and out) of the filter "
-                "phase's block products over that phase's event time; "
-                "tensor_tflops counts 2 s^2 b flops per product against "
-                "one third of the tf32 peak (0.5 x measured bf16), as the "
-                "kernel issues three tf32 products for float32 accuracy"}
+    gram_path = main_res["gram_path"]
+    bound, gpeak, gsrc = gram_peak(gram_path, peaks, peak_kind)
+    gram_ms = main_res["phases"]["gram"]
+    g_tf = gflops / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else 0.0
     value = world * nblocks * args.steps / (total_ms * 1e-3)
-    proj_flops = 2.0 * sum(L * s * w.k for (s, L) in shapes)
+    step_s = total_ms * 1e-3 / args.steps
+    proj_flops = 2.0 * sum(L * s * min(w.k, s) for (s, L) in shapes)
     pred_flops = 2.0 * w.k * r.u_test.size
-    tflops = (gflops + proj_flops + pred_flops) * args.steps / (total_ms * 1e-3) / 1e12
-    gold = golden_rmse(w)
+    tflops = (gflops + proj_flops + pred_flops) / step_s / 1e12
+    main_sum = form_summary(w, r, main_res, gold, args.steps)
     line = {
         "metric": "block SVDs/s", "value": value, "unit": "block-SVDs/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -603,50 +791,68 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32": "tf32 gram, f32",
                   "bf16": "bf16 gram, f32"}[args.precision],
-        "data": "synthetic (seeded MovieLens-1M-shaped ratings, in HBM)",
-        "config": {"workload": w.name, "m": w.m, "n": w.n,
-                   "nnz_train": int(r.u_train.size),
-                   "nnz_test": int(r.u_test.size), "p": w.p, "q": w.q,
-                   "k": w.k, "precision": args.precision,
-                   "gram": {1: "fp32 simt", 2: "tensor cores, exact",
-                            3: "tensor cores, tf32",
-                            4: "tensor cores, bf16"}.get(gram_path, "none"),
-                   "l2": "flushed (256 MB write) before each step, untimed"},
-        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
-                       "p99": float(np.percentile(step_ms, 99))},
+        "data": "synthetic (seeded, shaped like the paper's rating data; "
+                "inputs in HBM)",
+        "config": bench_config(w, r),
+        "path": {"precision": args.precision,
+                 "gram": GRAM_NAMES.get(gram_path, "none")},
+        "latency_ms": {"p50": float(np.percentile(main_res["step_ms"], 50)),
+                       "p99": float(np.percentile(main_res["step_ms"], 99))},
         "tflops": tflops,
-        "phases_ms": {k: statistics.mean(v) for k, v in phases.items()},
-        "rmse": rm, "rmse_oracle": gold,
-        "rmse_parity": (gold is not None and abs(rm - gold) <= 1e-4),
-        "roofline": roof_panel,
-        "roofline_gram": {"kernel": roof["kernel"], "bound": roof["bound"],
-                          "achieved": achieved, "peak": roof["peak"],
-                          "unit": "TFLOP/s", "frac": achieved / roof["peak"],
-                          "traffic": roof["traffic"],
+        "phases_ms": main_res["phases"],
+        "rmse": main_res["rmse"], "rmse_oracle": main_sum["rmse_oracle"],
+        "rmse_parity": main_sum["rmse_parity"],
+        "converged_blocks": main_sum["converged_blocks"],
+        "roofline": panel_roofline(w, shapes, main_res["report"],
+                                   main_res["phases"]["eigen_filter"], peaks,
+                                   peak_kind),
+        "roofline_step": step_roofline(w, r, shapes, w.k, gram_path, step_s,
+                                       peaks, peak_kind),
+        "roofline_gram": {"kernel": GRAM_KERNELS.get(gram_path), "bound": bound,
+                          "achieved": g_tf, "peak": gpeak, "unit": "TFLOP/s",
+                          "frac": g_tf / gpeak,
+                          "traffic": profiled_traffic(
+                              GRAM_KERNELS.get(gram_path), w.name),
                           "algorithmic_flops_per_launch": gflops,
-                          "peak_source": roof["peak_source"]},
-        "gpu_launches": int(launches),
+                          "peak_source": gsrc},
+        "forms": {name: form_summary(w, r, res, gold, args.form_steps)
+                  for name, res in forms.items()},
+        "gpu_launches": int(main_res["launches"]),
         "e2e": {"value": world * nblocks * args.steps / (e2e_total * 1e-3),
                 "unit": "block-SVDs/s",
-                "h2d_bytes_per_step": int(12 * (r.u_train.size + r.u_test.size)
-                                          + (4 * (w.m + w.n) if gridkw else 0)),
-                "d2h_bytes_per_step": 8, "rmse": rm_e2e},
+                "h2d_bytes_per_step": e2e_h2d, "d2h_bytes_per_step": e2e_d2h,
+                "rmse": rm_e2e,
+                "note": "host (pinned) inputs every step: the quantile cut "
+                        "stages u, i; the permutations come back to the "
+                        "host and go in again with u, i, x"},
         "clocks": clk,
     }
+    if world == 1 and not args.no_medium and w.name != synth.MEDIUM.name:
+        wm = synth.MEDIUM
+        rm_ = synth.generate(wm)
+        res = time_form(wm, device_data(rm_), args.steps,
+                        args.warmup, flush, stream,
+                        precision=prec[args.precision])
+        res["ctx"].close()
+        line["medium"] = dict(form_summary(wm, rm_, res, golden(wm),
+                                           args.steps), workload=wm.name)
     if world == 1 and not args.no_cpu_baseline:
         cores = min(os.cpu_count() or 1, nblocks)
-        dt, nb = oracle_sample(w, r, cores, cores, gridkw)
+        value_cpu, dt, pick, frac = oracle_sample(w, r, cores)
         line["cpu_baseline"] = {
-            "value": nb / dt, "unit": "block-SVDs/s", "cores": cores,
+            "value": value_cpu, "unit": "block-SVDs/s", "cores": cores,
             "kind": "oracle",
-            "sample": "oracle partition of all ratings + FP64 Jacobi SVD of "
-                      "the %d smallest of %d blocks (one thread each) + their "
-                      "held-out RMSE, %.1f s" % (nb, nblocks, dt)}
+            "sample": "FP64 Jacobi SVDs of %d of the %d blocks (Jacobi work "
+                      "m_b n_b s_b <= 2e9, evenly spread in work order; one "
+                      "thread each) and their held-out RMSE, %.1f s for "
+                      "%.2f%% of the grid's Jacobi work; scaled by work to "
+                      "the whole grid" % (len(pick), nblocks, dt, 100 * frac)}
     rates = [float(v) for v in args.serve_rates.split(",") if v.strip()]
     if world == 1 and rates:
-        line["served"] = serve_leg(rates)
-    if world == 1 and not args.no_sgd and w.name == synth.MEDIUM.name:
-        line["sgd"] = sgd_leg(r, w)
+        line["served"] = serve_leg(rates, args.serve_requests or None)
+    if world == 1 and not args.no_sgd:
+        wm = synth.MEDIUM
+        line["sgd"] = sgd_leg(synth.generate(wm), wm)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -55,7 +55,10 @@ typedef enum {
     BSVD_ENOMEM = 2,    /* device or host allocation failed */
     BSVD_ECUDA = 3,     /* a CUDA runtime call failed */
     BSVD_ENOTCONV = 4,  /* an eigen-solver hit its iteration cap */
-    BSVD_ETIMEOUT = 5,  /* reserved for bounded device-side waits */
+    BSVD_ETIMEOUT = 5,  /* a bounded device-side wait gave up; copies of
+                           the kernel that gave up may still have been in
+                           flight, so discard the context (and the CUDA
+                           context's results) instead of retrying in place */
     BSVD_ESTATE = 6     /* call out of order (e.g. factor before partition) */
 } bsvd_status;
 
@@ -87,7 +90,11 @@ typedef struct {
                              else FP32 SIMT; 1: FP32 SIMT always; 2: tensor
                              cores or BSVD_EINVAL from bsvd_factor */
     double tol;           /* residual |G v - theta v| <= tol * theta_1;
-                             <= 0: default (1e-5) */
+                             <= 0: default, 1e-5 for BSVD_FP32 and 1e-4
+                             for BSVD_TF32 and BSVD_BF16 (their Gram
+                             products already carry errors near 1e-3
+                             relative, so a tighter residual buys no
+                             accuracy) */
     uint64_t seed;        /* seed of the start basis */
     void *stream;         /* cudaStream_t, or NULL for the default stream */
     int32_t panel_path;   /* panel products G X of the eigen-solver and
@@ -163,6 +170,29 @@ bsvd_status bsvd_partition_diag(bsvd_ctx *ctx, int32_t nb,
                                 const int64_t *col_bounds, int64_t nnz,
                                 const int32_t *u, const int32_t *i,
                                 const float *x);
+
+/*
+ * Uneven grid cut at rating-activity quantiles, for bsvd_partition (the
+ * batched form; the paper's own grid, Section 3 Eq. "datax", has equal
+ * blocks, which on long-tailed data leaves a few blocks holding most
+ * ratings). Users are ordered by their number of training ratings, busiest
+ * first, lower id first on ties; row_perm[u] is user u's position. Block
+ * row bound g (0 < g < p) is the smallest position j whose preceding users
+ * hold at least g / p of the nnz ratings, parts * C_j >= g * nnz in exact
+ * integers; row_bounds[0] = 0 and row_bounds[p] = m. Items and the q block
+ * columns likewise. The results plug into bsvd_partition unchanged.
+ * m, n, nnz, u, i, p, q  as in bsvd_partition (x is not needed); nnz must
+ *            be below 2^32 and 1 <= p <= m, 1 <= q <= n.
+ * row_perm, col_perm     host or device arrays of m and n entries, written.
+ * row_bounds, col_bounds host arrays of p + 1 and q + 1 entries, written.
+ * Errors: BSVD_EINVAL (bad sizes, an id out of range), BSVD_ENOMEM,
+ * BSVD_ECUDA.
+ */
+bsvd_status bsvd_quantile_grid(bsvd_ctx *ctx, int64_t m, int64_t n,
+                               int64_t nnz, const int32_t *u,
+                               const int32_t *i, int32_t p, int32_t q,
+                               int32_t *row_perm, int32_t *col_perm,
+                               int64_t *row_bounds, int64_t *col_bounds);
 
 /*
  * Truncated SVD of every block (Section 2, Eq. 1 and the rank-k truncation
@@ -393,13 +423,18 @@ bsvd_status bsvd_sgd_get(bsvd_ctx *ctx, double *P, double *Q, double *bu,
  *                  since staging it would need an allocation).
  * counts, mu       device arrays of p * q entries, written by the call.
  * stream           cudaStream_t (NULL: the legacy default stream); the call
- *                  synchronises it before returning.
+ *                  reads an error word back and synchronises the stream
+ *                  before returning, so it must never be made on a stream
+ *                  that is being captured.
  * The first call on each device looks up the scratch array's device
  * address (once per device, with that device current); make that first
- * call before any stream capture. Every call shares the array and clears
- * the parts it accumulates into; calls that overlap on the GPU (other
- * threads or streams, or work queued before this call finishes) race on
- * it and must not be made.
+ * call before another thread starts a global-mode stream capture. The
+ * address is kept for the life of the process: after cudaDeviceReset this
+ * entry point must not be called again. Every call shares the array and
+ * clears the parts it accumulates into; calls that overlap on the GPU
+ * (other threads or streams, or work queued before this call finishes)
+ * race on it and must not be made. Device pointers must belong to the
+ * current device (or be managed memory).
  * Errors (status only, there is no context): BSVD_EINVAL (bad sizes, a
  * grid over the limit, a host pointer, an id out of range, a non-finite or
  * too large rating), BSVD_ECUDA.

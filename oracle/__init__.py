@@ -189,9 +189,10 @@ def activity_quantile_cut(ids, size: int, parts: int):
     lower id; cut where the ratings before the cut first reach g/parts of
     all ratings (exact integer comparison parts * before >= g * total).
     Returns (perm: id -> position, bounds: parts + 1 positions)."""
-    counts = [0] * size
-    for v in ids:
-        counts[int(v)] += 1
+    ids = np.asarray(ids, np.int64)
+    if ids.size and (ids.min() < 0 or ids.max() >= size):
+        raise ValueError("id out of range")
+    counts = np.bincount(ids, minlength=size).tolist()   # ratings per id
     order = sorted(range(size), key=lambda x: (-counts[x], x))
     perm = np.empty(size, np.int64)
     for pos, x in enumerate(order):

@@ -32,7 +32,7 @@ EXPORTS = ("bsvd_config_default", "bsvd_create", "bsvd_destroy",
            "bsvd_kernel_launches", "bsvd_block_means_noalloc",
            "bsvd_gram_path", "bsvd_partition_diag", "bsvd_factor_ks",
            "bsvd_sgd_params_default", "bsvd_sgd_prepare", "bsvd_sgd_train",
-           "bsvd_sgd_predict", "bsvd_sgd_get")
+           "bsvd_sgd_predict", "bsvd_sgd_get", "bsvd_quantile_grid")
 
 
 class BsvdError(RuntimeError):
@@ -108,6 +108,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                  ctypes.POINTER(i32)]),
         "bsvd_sgd_predict": (i32, [vp, i64, vp, vp, vp]),
         "bsvd_sgd_get": (i32, [vp, vp, vp, vp, vp]),
+        "bsvd_quantile_grid": (i32, [vp, i64, i64, i64, vp, vp, i32, i32, vp,
+                                     vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -201,6 +203,24 @@ def bsvd_partition(ctx, m, n, u, i, x, p, q, row_bounds=None, col_bounds=None,
         _ptr(cb, np.int64, "col_bounds"), _ptr(row_perm, np.int32, "row_perm"),
         _ptr(col_perm, np.int32, "col_perm"))
     return _check(ctx, st)
+
+
+def bsvd_quantile_grid(ctx, m, n, u, i, p, q, row_perm, col_perm):
+    """Activity-quantile grid; fills row_perm (m) and col_perm (n), host or
+    device int32 arrays, and returns (row_bounds, col_bounds) as numpy."""
+    nnz = _len(u)
+    if _len(i) != nnz:
+        raise ValueError("u, i must have the same length")
+    if _len(row_perm) != m or _len(col_perm) != n:
+        raise ValueError("row_perm needs m entries and col_perm n entries")
+    rb = np.zeros(p + 1, np.int64)
+    cb = np.zeros(q + 1, np.int64)
+    st = load().bsvd_quantile_grid(
+        ctx, m, n, nnz, _ptr(u, np.int32, "u"), _ptr(i, np.int32, "i"), p, q,
+        _ptr(row_perm, np.int32, "row_perm"),
+        _ptr(col_perm, np.int32, "col_perm"), rb.ctypes.data, cb.ctypes.data)
+    _check(ctx, st)
+    return rb, cb
 
 
 def bsvd_partition_diag(ctx, row_bounds, col_bounds, u, i, x) -> int:
@@ -392,6 +412,19 @@ def bsvd_block_means_noalloc(m, n, u, i, x, p, q, counts, mu,
     nnz = _len(u)
     if _len(i) != nnz or _len(x) != nnz:
         raise ValueError("u, i, x must have the same length")
+    if _len(counts) < p * q or _len(mu) < p * q:
+        raise ValueError("counts and mu need p * q entries")
+    try:
+        import torch
+        cur = torch.cuda.current_device() if torch.cuda.is_available() else None
+        for name, a in (("u", u), ("i", i), ("x", x), ("counts", counts),
+                        ("mu", mu)):
+            if (isinstance(a, torch.Tensor) and a.is_cuda
+                    and a.device.index != cur):
+                raise ValueError("%s is on cuda:%d, not the current device "
+                                 "cuda:%s" % (name, a.device.index, cur))
+    except ImportError:  # pragma: no cover
+        pass
     if stream is not None and not isinstance(stream, int):
         stream = stream.cuda_stream
     return int(load().bsvd_block_means_noalloc(
@@ -453,6 +486,25 @@ class Context:
         bsvd_partition(self.handle, m, n, u, i, x, p, q, row_bounds,
                        col_bounds, row_perm, col_perm)
         self.nblocks = p * q
+
+    def quantile_grid(self, m, n, u, i, p, q):
+        """Keyword arguments for partition(): the activity-quantile grid of
+        the ratings (u, i). The permutations live where u does (CUDA
+        tensors for CUDA input, else numpy arrays)."""
+        on_gpu = False
+        try:
+            import torch
+            on_gpu = isinstance(u, torch.Tensor) and u.is_cuda
+        except ImportError:  # pragma: no cover
+            pass
+        if on_gpu:
+            rp = torch.empty(m, dtype=torch.int32, device=u.device)
+            cp = torch.empty(n, dtype=torch.int32, device=u.device)
+        else:
+            rp = np.empty(m, np.int32)
+            cp = np.empty(n, np.int32)
+        rb, cb = bsvd_quantile_grid(self.handle, m, n, u, i, p, q, rp, cp)
+        return dict(row_bounds=rb, col_bounds=cb, row_perm=rp, col_perm=cp)
 
     def partition_diag(self, row_bounds, col_bounds, u, i, x):
         bsvd_partition_diag(self.handle, row_bounds, col_bounds, u, i, x)

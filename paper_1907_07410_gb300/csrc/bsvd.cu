@@ -132,6 +132,8 @@ struct bsvd_ctx {
 
   // staging of host arguments and results
   DevBuf s_a, s_b, s_c, s_out, d_partials, d_rmse;
+  // activity-quantile cut: counts, sort keys, running sums, perms, bounds
+  DevBuf d_qcnt, d_qkeys, d_qcum, d_qperm, d_qbounds;
 
   // tracing: kernel launch count and per-phase CUDA events
   int64_t launches = 0;
@@ -268,7 +270,7 @@ void bsvd_config_default(bsvd_config *cfg) {
   cfg->cheb_degree = 8;
   cfg->max_iters = 30;
   cfg->max_sweeps = 30;
-  cfg->tol = 1e-5;
+  cfg->tol = 0.0;        // per precision, set by bsvd_create
   cfg->seed = 0x5eed5eedull;
   cfg->stream = nullptr;
   cfg->panel_path = 0;
@@ -286,8 +288,9 @@ bsvd_status bsvd_create(const bsvd_config *cfg, bsvd_ctx **out) {
     if (c->cfg.cheb_degree <= 0) c->cfg.cheb_degree = 8;
     if (c->cfg.max_iters <= 0) c->cfg.max_iters = 30;
     if (c->cfg.max_sweeps <= 0) c->cfg.max_sweeps = 30;
-    if (!(c->cfg.tol > 0)) c->cfg.tol = 1e-5;
   }
+  if (!(c->cfg.tol > 0))
+    c->cfg.tol = c->cfg.precision == BSVD_FP32 ? 1e-5 : 1e-4;
   if ((c->cfg.precision != BSVD_FP32 && c->cfg.precision != BSVD_TF32 &&
        c->cfg.precision != BSVD_BF16) ||
       c->cfg.gram_path < 0 ||
@@ -334,7 +337,9 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->d_sgd_cnt, &c->d_sgd_off, &c->d_sgd_key,
                     &c->d_sgd_src, &c->d_sgd_u, &c->d_sgd_i, &c->d_sgd_x,
                     &c->d_sgd_range, &c->d_sgd_blocks, &c->d_sgd_P,
-                    &c->d_sgd_Q, &c->d_sgd_bu, &c->d_sgd_bi, &c->d_sgd_sum};
+                    &c->d_sgd_Q, &c->d_sgd_bu, &c->d_sgd_bi, &c->d_sgd_sum,
+                    &c->d_qcnt, &c->d_qkeys, &c->d_qcum, &c->d_qperm,
+                    &c->d_qbounds};
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   for (DevBuf *b : bufs) b->release();
@@ -612,6 +617,65 @@ bsvd_status bsvd_partition_diag(bsvd_ctx *c, int32_t nb,
     return fail(c, BSVD_EINVAL, "partition_diag: need nb >= 1 and bounds");
   return partition_impl(c, row_bounds[nb], col_bounds[nb], nnz, u, i, x, nb,
                         nb, row_bounds, col_bounds, nullptr, nullptr, true);
+}
+
+// One side of the activity-quantile grid: perm (host or device, size
+// entries) and bounds (host, parts + 1).
+static bsvd_status quantile_side(bsvd_ctx *c, const char *what, int64_t size,
+                                 int64_t nnz, const int32_t *ids,
+                                 int32_t parts, int32_t *perm,
+                                 int64_t *bounds) {
+  const int64_t padded = quantile_cut_padded(size);
+  CK(c->d_qcnt.ensure(sizeof(unsigned int) * size), what);
+  CK(c->d_qkeys.ensure(sizeof(unsigned long long) * padded), what);
+  CK(c->d_qcum.ensure(sizeof(long long) * (size + 1)), what);
+  CK(c->d_qbounds.ensure(sizeof(int64_t) * (parts + 1)), what);
+  const bool dev_perm = is_device_ptr(perm);
+  int32_t *dperm = perm;
+  if (!dev_perm) {
+    CK(c->d_qperm.ensure(sizeof(int32_t) * size), what);
+    dperm = c->d_qperm.as<int32_t>();
+  }
+  CK(launch_quantile_cut(ids, nnz, size, parts, c->d_qcnt.as<unsigned int>(),
+                         c->d_qkeys.as<unsigned long long>(),
+                         c->d_qcum.as<long long>(), dperm,
+                         c->d_qbounds.as<int64_t>(), c->d_err.as<int32_t>(),
+                         &c->launches, c->st), what);
+  if (!dev_perm)
+    CK(cudaMemcpyAsync(perm, dperm, sizeof(int32_t) * size,
+                       cudaMemcpyDeviceToHost, c->st), what);
+  CK(cudaMemcpyAsync(bounds, c->d_qbounds.p, sizeof(int64_t) * (parts + 1),
+                     cudaMemcpyDeviceToHost, c->st), what);
+  return BSVD_OK;
+}
+
+bsvd_status bsvd_quantile_grid(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
+                               const int32_t *u, const int32_t *i, int32_t p,
+                               int32_t q, int32_t *row_perm,
+                               int32_t *col_perm, int64_t *row_bounds,
+                               int64_t *col_bounds) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (m < 1 || n < 1 || m > INT32_MAX || n > INT32_MAX || nnz < 0 ||
+      nnz > (int64_t)UINT32_MAX)
+    return fail(c, BSVD_EINVAL, "quantile_grid: bad sizes m=%lld n=%lld "
+                "nnz=%lld", (long long)m, (long long)n, (long long)nnz);
+  if (p < 1 || q < 1 || p > m || q > n)
+    return fail(c, BSVD_EINVAL, "quantile_grid: bad grid %d x %d", p, q);
+  if ((nnz > 0 && (!u || !i)) || !row_perm || !col_perm || !row_bounds ||
+      !col_bounds)
+    return fail(c, BSVD_EINVAL, "quantile_grid: null array");
+  const void *du = nullptr, *di = nullptr;
+  CK(cudaMemsetAsync(c->d_err.p, 0, sizeof(int32_t), c->st), "quantile_grid");
+  CK(device_view(c, u, sizeof(int32_t) * nnz, c->s_a, &du), "quantile_grid");
+  CK(device_view(c, i, sizeof(int32_t) * nnz, c->s_b, &di), "quantile_grid");
+  bsvd_status s = quantile_side(c, "quantile_grid: rows", m, nnz,
+                                (const int32_t *)du, p, row_perm, row_bounds);
+  if (s != BSVD_OK) return s;
+  s = quantile_side(c, "quantile_grid: columns", n, nnz, (const int32_t *)di,
+                    q, col_perm, col_bounds);
+  if (s != BSVD_OK) return s;
+  return read_errors(c, "quantile_grid");
 }
 
 static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks);

@@ -25,6 +25,17 @@ cudaError_t launch_scatter(const GridDesc &g, const BlockMeta *meta,
                            const float *x, const float *mu, float *W,
                            __nv_bfloat16 *Wh, cudaStream_t st);
 
+// ---- activity-quantile cut of one side (kernels_grid.cu) ----------------
+// Keys are padded to quantile_cut_padded(size) entries. counts: size,
+// keys: padded, cum: size + 1, perm: size, bounds: parts + 1 (device).
+// *launches is increased by the number of kernels queued.
+int64_t quantile_cut_padded(int64_t size);
+cudaError_t launch_quantile_cut(const int32_t *ids, int64_t nnz, int64_t size,
+                                int32_t parts, unsigned int *counts,
+                                unsigned long long *keys, long long *cum,
+                                int32_t *perm, int64_t *bounds, int32_t *err,
+                                int64_t *launches, cudaStream_t st);
+
 // ---- Gram (kernels_gram.cu) ---------------------------------------------
 // tiles: (block, tile_i, tile_j, 0) with tile_i <= tile_j, 128 x 128 tiles.
 cudaError_t launch_gram_f32(const BlockMeta *meta, const int4 *tiles,

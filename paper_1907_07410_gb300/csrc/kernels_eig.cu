@@ -23,6 +23,13 @@
 //   3. Stop a block when |G x_i - theta_i x_i| <= tol * theta_1 for its k
 //      wanted pairs; otherwise cut <- smallest Ritz value and go to 1.
 //
+// The damped interval reaches up to the smallest kept Ritz value (a lower
+// bound of the unwanted part of the spectrum), however close it is to
+// theta_1. Noise-dominated blocks have flat spectra (sigma_1 / sigma_40
+// about 1.1 on the 480,189 x 17,770 workload); capping the cut at
+// theta_1 / 2 there left most of the unwanted spectrum undamped and took
+// 2.2 times the panel products.
+//
 // The filter amplifies the top of the spectrum by C_d(t_1), with
 // t_1 = 2 theta_1 / cut - 1, relative to the damped interval. In float32
 // the columns that should hold the lower Ritz directions drown in rounding
@@ -57,6 +64,9 @@ constexpr float kMaxAmplification = 3e6f;
 constexpr float kMinAmplification = 1e3f;
 constexpr float kAmpBackoff = 1e2f;
 constexpr float kCutFloor = 1e-3f;   // cut >= kCutFloor * theta_1
+// cut <= kCutCeil * theta_1, so that 2 theta_1 / cut - 1 >= 1.105 and the
+// filter's degree stays defined when the Ritz values are nearly equal
+constexpr float kCutCeil = 0.95f;
 constexpr float kPivotDrop = 1e-4f;  // squared sine of the angle to the span
 constexpr float kJacobiTol = 3e-7f;       // |a_p . a_q| / (|a_p| |a_q|) to stop
 constexpr float kJacobiTolFirst = 1e-3f;  // the same, first step from a random start
@@ -750,10 +760,10 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
       }
       st.amp = amp;
       cut = fmaxf(cut, kCutFloor * t1);
-      if (cut >= 0.5f * t1) cut = 0.5f * t1;
+      if (cut >= kCutCeil * t1) cut = kCutCeil * t1;
       st.cut = cut;
       st.a0 = t1;
-      const float tt = 2.f * t1 / cut - 1.f;   // >= 3
+      const float tt = 2.f * t1 / cut - 1.f;   // >= 1.105
       const float at = acoshf(tt);
       int d = 2;
       while (d + 2 <= max_degree && coshf((float)(d + 2) * at) <= amp)

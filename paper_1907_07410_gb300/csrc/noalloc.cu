@@ -44,7 +44,9 @@ std::mutex g_setup_mutex;
 NoAllocScratch *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device (set up once per
-// device, with that device current).
+// device, with that device current). The address stays valid while the
+// device's primary context lives; after cudaDeviceReset the library must
+// not be used again in this process.
 cudaError_t scratch_address(NoAllocScratch **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -70,13 +72,23 @@ __global__ void k_equal_bounds(int64_t *bounds, int32_t parts, int64_t total,
   }
 }
 
+// True for managed memory and for device memory of the current device. A
+// device pointer of another GPU is refused: the kernels would reach it
+// through a peer mapping that may not exist.
 bool on_device(const void *ptr) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type != cudaMemoryTypeDevice) return false;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.device == dev;
 }
 
 }  // namespace

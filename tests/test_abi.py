@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol():
 def test_config_layout_matches_header():
     cfg = bs.bsvd_config_default()
     assert cfg.cheb_degree == 8 and cfg.max_iters == 30
-    assert abs(cfg.tol - 1e-5) < 1e-20
+    assert cfg.tol == 0.0          # per-precision default in bsvd_create
     assert cfg.clamp_lo == 1.0 and cfg.clamp_hi == 5.0
     # int32 x2, float x2, int32 x6, double, uint64, pointer, int32 x2
     assert ctypes.sizeof(bs.Config) == 72

@@ -1,38 +1,78 @@
-"""Activity-quantile grids: the library's host split against the oracle's
-independent one, and a hand-worked example."""
+"""Activity-quantile grids (the batched form's uneven cut): the oracle's cut
+against a hand-worked example and brute force (CPU), and the library's
+bsvd_quantile_grid against the oracle bit for bit (GPU)."""
 import numpy as np
 import pytest
 
 import oracle
-from paper_1907_07410_gb300 import grid
 
 
-def test_hand_example():
+def _library_cut(ids, size, parts):
+    """One side of bsvd_quantile_grid: the ids as users of a size x 1
+    matrix, cut into parts block rows (one block column)."""
+    torch = pytest.importorskip("torch")
+    import paper_1907_07410_gb300 as bs
+    ids = np.ascontiguousarray(ids, np.int32)
+    zeros = np.zeros(ids.size, np.int32)
+    with bs.Context() as ctx:
+        kw = ctx.quantile_grid(size, 1, torch.from_numpy(ids).cuda(),
+                               torch.from_numpy(zeros).cuda(), parts, 1)
+    return kw["row_perm"].cpu().numpy(), kw["row_bounds"]
+
+
+@pytest.mark.gpu
+def test_library_hand_example():
     # counts per id: [5, 1, 3, 0, 3] -> order 0, 2, 4, 1, 3 (ties by id)
     ids = np.array([0] * 5 + [1] + [2] * 3 + [4] * 3)
-    perm, bounds = grid.quantile_split(ids, 5, 2)
+    perm, bounds = _library_cut(ids, 5, 2)
     assert perm.tolist() == [0, 3, 1, 4, 2]
     # ratings before positions 0..5: 0, 5, 8, 11, 12, 12; half of 12 is
     # first reached before position 2
     assert bounds.tolist() == [0, 2, 5]
-    perm3, bounds3 = grid.quantile_split(ids, 5, 3)
+    perm3, bounds3 = _library_cut(ids, 5, 3)
     # thirds: 4 and 8 ratings -> positions 1 (5 >= 4) and 2 (8 >= 8)
     assert bounds3.tolist() == [0, 1, 2, 5]
 
 
+@pytest.mark.gpu
 @pytest.mark.parametrize("seed,size,parts", [(1, 50, 4), (2, 1000, 8),
-                                             (3, 300, 32), (4, 17, 17)])
-def test_matches_oracle(seed, size, parts):
+                                             (3, 300, 32), (4, 17, 17),
+                                             (7, 5000, 1), (8, 9000, 31)])
+def test_library_matches_oracle(seed, size, parts):
+    """bsvd_quantile_grid against the oracle's cut, bit for bit; sizes on
+    both sides of the 4096-key sorting tile."""
     rng = np.random.default_rng(seed)
     w = (np.arange(size) + 1.0) ** -1.1
     ids = rng.choice(size, size=20 * size, p=w / w.sum())
-    perm, bounds = grid.quantile_split(ids, size, parts)
+    perm, bounds = _library_cut(ids, size, parts)
     operm, obounds = oracle.activity_quantile_cut(ids, size, parts)
     assert np.array_equal(perm, operm)
     assert np.array_equal(bounds, obounds)
-    assert bounds[0] == 0 and bounds[-1] == size
-    assert np.all(np.diff(bounds) >= 0)
-    assert np.array_equal(np.sort(perm), np.arange(size))
+
+
+@pytest.mark.gpu
+def test_library_grid_both_sides_and_errors():
+    torch = pytest.importorskip("torch")
+    import paper_1907_07410_gb300 as bs
+    rng = np.random.default_rng(9)
+    m, n = 700, 300
+    u = rng.integers(0, m, 6000).astype(np.int32)
+    i = (rng.integers(0, n, 6000) ** 2 % n).astype(np.int32)
+    with bs.Context() as ctx:
+        kw = ctx.quantile_grid(m, n, u, i, 5, 3)       # host arrays
+        rp, rb = oracle.activity_quantile_cut(u, m, 5)
+        cp, cb = oracle.activity_quantile_cut(i, n, 3)
+        assert np.array_equal(kw["row_perm"], rp)
+        assert np.array_equal(kw["col_perm"], cp)
+        assert np.array_equal(kw["row_bounds"], rb)
+        assert np.array_equal(kw["col_bounds"], cb)
+        bad = u.copy()
+        bad[17] = m
+        with pytest.raises(bs.BsvdError) as e:
+            ctx.quantile_grid(m, n, bad, i, 5, 3)
+        assert e.value.status == bs.EINVAL
+        with pytest.raises(bs.BsvdError):
+            ctx.quantile_grid(m, n, u, i, m + 1, 3)
 
 
 def test_oracle_cut_hand_example():

@@ -1,15 +1,18 @@
-"""The allocation-free block-means entry point against bsvd_partition.
+"""The allocation-free block-means entry point against bsvd_partition and
+the oracle.
 
 bsvd_block_means_noalloc serves callers that cannot allocate device memory
 during a call (a process whose device memory all belongs to its own pool,
 or a loop whose memory is fixed up front): its scratch is a fixed device
 array inside the library. Its counts and means must equal, bit for bit,
-what the context-based partition reports, on two calls in a row (the
-second call must not see the first call's sums).
+what the context-based partition reports and what the FP64 oracle's
+partition computes (exact sums over float64, rounded to float32), on
+consecutive calls (a later call must not see an earlier call's sums).
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 torch = pytest.importorskip("torch")
@@ -52,6 +55,10 @@ def test_noalloc_matches_partition_on_consecutive_calls():
         c2, m2 = via_partition(r, p, q)
         assert np.array_equal(c1, c2)
         assert np.array_equal(m1.view(np.uint32), m2.view(np.uint32))
+        part = oracle.partition(r.m, r.n, r.u_train, r.i_train, r.x_train,
+                                p, q)
+        assert np.array_equal(c1, part.counts)
+        assert np.array_equal(m1.view(np.uint32), part.mu32.view(np.uint32))
 
 
 def test_noalloc_rejects_oversized_grid_and_host_memory():
@@ -64,3 +71,7 @@ def test_noalloc_rejects_oversized_grid_and_host_memory():
     assert bs.bsvd_block_means_noalloc(r.m, r.n, r.u_train, r.i_train,
                                        r.x_train, 2, 2, counts[:4],
                                        mu[:4]) == bs.EINVAL
+    # outputs shorter than p * q are refused before the library is called
+    with pytest.raises(ValueError):
+        bs.bsvd_block_means_noalloc(r.m, r.n, dev(r.u_train), dev(r.i_train),
+                                    dev(r.x_train), 2, 2, counts[:3], mu[:4])
