@@ -23,8 +23,10 @@ the medium matrix, beside one epoch of the FP64 oracle.
 
 Prints one JSON line (rank 0). Usage:
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun each rank solves its own copy of the workload (weak scaling;
-no collective on the data path).
+Under torchrun the ranks share one workload (strong scaling): each holds and
+factorises its longest-processing-time share of the blocks, and the step's
+held-out RMSE is combined by one all-reduce of (sum of squared errors,
+count); the blocks need no other exchange.
 """
 from __future__ import annotations
 
@@ -293,7 +295,7 @@ def run_reference(args, w, r, rank):
         "impl": "reference", "metric": "block SVDs/s", "value": value,
         "unit": "block-SVDs/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": bench_config(w, r),
         "cpu_baseline": {"value": value, "unit": "block-SVDs/s",
@@ -502,18 +504,32 @@ def grid_bounds_of(w, r):
     return kw
 
 
-def time_form(w, data, steps, warmup, flush, stream, **cfg):
-    """Warm up, then time `steps` steps of one form of the path. Returns the
-    per-step times, phases, RMSE, launches and the solver report."""
+def step_rmse(ctx, u, i, y, sharded):
+    """The step's held-out RMSE: on one GPU the library's; across ranks each
+    rank's squared-error sum over its own blocks, combined by one
+    all-reduce of the sum and the count."""
+    if not sharded:
+        return ctx.rmse(u, i, y)
+    from paper_1907_07410_gb300 import dist as bdist
+    return bdist.sharded_rmse(ctx, u, i, y)
+
+
+def time_form(w, data, steps, warmup, flush, stream, owned=None, **cfg):
+    """Warm up, then time `steps` steps of one form of the path (this rank's
+    blocks only when `owned` is given). Returns the per-step times, phases,
+    RMSE, launches and the solver report."""
     import torch
     import paper_1907_07410_gb300 as bs
     u_tr, i_tr, x_tr, u_te, i_te, x_te = data
     ctx = bs.Context(stream=stream, profile=1, **cfg)
+    sharded = owned is not None
+    if sharded:
+        ctx.set_owned(owned)
     for _ in range(warmup):
         ctx.partition(w.m, w.n, u_tr, i_tr, x_tr, w.p, w.q,
                       **step_grid(ctx, w, u_tr, i_tr))
         ctx.factor(w.k, warn=False)
-        ctx.rmse(u_te, i_te, x_te)
+        step_rmse(ctx, u_te, i_te, x_te, sharded)
     phases = {k: [] for k in bs.PHASES}
     step_ms = []
     launches0 = ctx.kernel_launches()
@@ -527,7 +543,7 @@ def time_form(w, data, steps, warmup, flush, stream, **cfg):
         part_ph = ctx.phase_times()["partition"]
         status = ctx.factor(w.k, warn=False)
         fac_ph = ctx.phase_times()
-        rm = ctx.rmse(u_te, i_te, x_te)
+        rm = step_rmse(ctx, u_te, i_te, x_te, sharded)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -714,13 +730,19 @@ def main():
     data = device_data(r)
     prec = {"fp32": bs.FP32, "tf32": bs.TF32, "bf16": bs.BF16}
     nblocks = w.p * w.q
+    shapes = block_shapes(w, grid_bounds_of(w, r))
+    owned = None
+    if world > 1:
+        # this rank's share of the blocks (longest processing time first)
+        from paper_1907_07410_gb300 import dist as bdist
+        owned = bdist.owned_mask(bdist.block_costs(shapes), world, rank)
 
     # ---- device-resident timed region (the main form) --------------------
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
     main_res = time_form(w, data, args.steps, args.warmup, flush, stream,
-                         precision=prec[args.precision])
+                         owned, precision=prec[args.precision])
     barrier()
     clk = clocks.stop()
     ctx = main_res["ctx"]
@@ -742,7 +764,7 @@ def main():
         ctx.partition(w.m, w.n, h_u, h_i, h_x, w.p, w.q,
                       **step_grid(ctx, w, h_u, h_i))
         ctx.factor(w.k, warn=False)
-        rm_e2e = ctx.rmse(h_ut, h_it, h_xt)
+        rm_e2e = step_rmse(ctx, h_ut, h_it, h_xt, owned is not None)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     barrier()
     e2e_total = sum(e2e_ms)
@@ -757,7 +779,7 @@ def main():
                 "bf16": dict(precision=bs.BF16), "tf32": dict(precision=bs.TF32)}
     for name in [f for f in args.forms.split(",") if f.strip()]:
         res = time_form(w, data, args.form_steps, args.warmup, flush, stream,
-                        **form_cfg[name])
+                        owned, **form_cfg[name])
         res["ctx"].close()
         forms[name] = res
 
@@ -772,13 +794,13 @@ def main():
     e2e_d2h = int(8 + (4 * (w.m + w.n) + 8 * (w.p + w.q + 2) if quant else 0))
     peaks, peak_kind = load_peaks()
     gold = golden(w)
-    shapes = block_shapes(w, grid_bounds_of(w, r))
     gflops = gram_flops(shapes)
     gram_path = main_res["gram_path"]
     bound, gpeak, gsrc = gram_peak(gram_path, peaks, peak_kind)
     gram_ms = main_res["phases"]["gram"]
     g_tf = gflops / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else 0.0
-    value = world * nblocks * args.steps / (total_ms * 1e-3)
+    # the ranks share the workload's blocks: all of them per step
+    value = nblocks * args.steps / (total_ms * 1e-3)
     step_s = total_ms * 1e-3 / args.steps
     proj_flops = 2.0 * sum(L * s * min(w.k, s) for (s, L) in shapes)
     pred_flops = 2.0 * w.k * r.u_test.size
@@ -788,7 +810,7 @@ def main():
         "metric": "block SVDs/s", "value": value, "unit": "block-SVDs/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong", "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32": "tf32 gram, f32",
                   "bf16": "bf16 gram, f32"}[args.precision],
         "data": "synthetic (seeded, shaped like the paper's rating data; "
@@ -818,7 +840,7 @@ def main():
         "forms": {name: form_summary(w, r, res, gold, args.form_steps)
                   for name, res in forms.items()},
         "gpu_launches": int(main_res["launches"]),
-        "e2e": {"value": world * nblocks * args.steps / (e2e_total * 1e-3),
+        "e2e": {"value": nblocks * args.steps / (e2e_total * 1e-3),
                 "unit": "block-SVDs/s",
                 "h2d_bytes_per_step": e2e_h2d, "d2h_bytes_per_step": e2e_d2h,
                 "rmse": rm_e2e,

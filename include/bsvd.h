@@ -235,12 +235,45 @@ bsvd_status bsvd_predict(bsvd_ctx *ctx, int64_t nq, const int32_t *u,
  * Root mean squared error of the predictions for nq held-out ratings y
  * (Section 5, Table 1 "Test RMSE"): sqrt(sum (yhat - y)^2 / nq). The
  * squared errors are summed in float64 in a fixed order, so the result is
- * the same on every run. u, i, y: host or device arrays of nq entries;
- * nq >= 1. *out_rmse: host double.
+ * the same on every run. Every query counts, including those of blocks a
+ * shard does not hold (bsvd_set_owned), which predict the block mean; a
+ * shard reports its part with bsvd_sqerr instead. u, i, y: host or device
+ * arrays of nq entries; nq >= 1. *out_rmse: host double.
  * Errors: BSVD_ESTATE, BSVD_EINVAL.
  */
 bsvd_status bsvd_rmse(bsvd_ctx *ctx, int64_t nq, const int32_t *u,
                       const int32_t *i, const float *y, double *out_rmse);
+
+/*
+ * Restrict the context to a subset of the blocks, for sharding one matrix
+ * over several GPUs (Section 3's blocks are independent: a block's factors
+ * need only its own ratings, so each GPU can hold and factorise its own
+ * blocks). owned: host array of nblocks flags (nonzero: held), one per
+ * block of the next partition (p * q, or nb after bsvd_partition_diag);
+ * nblocks = 0 (owned may be NULL) holds every block again. The next
+ * partition still counts every block and computes every block mean, but
+ * stores dense blocks only for the held ones; bsvd_factor factorises only
+ * those (the others keep k_eff = 0, so their predictions are the block
+ * means). bsvd_sqerr then sums the squared errors of the held blocks'
+ * queries. Takes effect at the next partition (a mask of the wrong length
+ * is rejected there with BSVD_EINVAL); discards any partition and factors.
+ * Errors: BSVD_EINVAL.
+ */
+bsvd_status bsvd_set_owned(bsvd_ctx *ctx, int32_t nblocks,
+                           const uint8_t *owned);
+
+/*
+ * The held-out error of the blocks this context holds (see bsvd_set_owned;
+ * every block when no mask is set): *out_sum = sum of (yhat - y)^2 over the
+ * queries whose block is held, in float64 in a fixed order, and
+ * *out_count = the number of those queries. Summed over the shards, these
+ * give the RMSE of Section 5, sqrt(sum / count). u, i, y: host or device
+ * arrays of nq entries, nq >= 0. out_sum, out_count: host.
+ * Errors: BSVD_ESTATE (no factors), BSVD_EINVAL (an id out of range).
+ */
+bsvd_status bsvd_sqerr(bsvd_ctx *ctx, int64_t nq, const int32_t *u,
+                       const int32_t *i, const float *y, double *out_sum,
+                       int64_t *out_count);
 
 /*
  * Grid information after a partition: number of blocks and the count and
@@ -259,7 +292,11 @@ bsvd_status bsvd_block_stats(bsvd_ctx *ctx, int32_t *nblocks,
  *             pair (P_i, V_i) has the sign that makes the largest-|.|
  *             entry of V_i positive.
  *   dense     mb x nb, row-major float32: the centred dense block as
- *             stored on the device (needs only a partition).
+ *             stored on the device (needs only a partition). The BF16 form
+ *             (with the tensor-core panel path) stores only the bf16
+ *             rounding of each cell, so that is what it returns.
+ * A block another shard holds (bsvd_set_owned) reports keff = 0 and has
+ * no dense block (BSVD_EINVAL when dense is asked for).
  * Errors: BSVD_ESTATE, BSVD_EINVAL (b out of range).
  */
 bsvd_status bsvd_get_block(bsvd_ctx *ctx, int32_t b, int32_t *mb,

@@ -32,7 +32,8 @@ EXPORTS = ("bsvd_config_default", "bsvd_create", "bsvd_destroy",
            "bsvd_kernel_launches", "bsvd_block_means_noalloc",
            "bsvd_gram_path", "bsvd_partition_diag", "bsvd_factor_ks",
            "bsvd_sgd_params_default", "bsvd_sgd_prepare", "bsvd_sgd_train",
-           "bsvd_sgd_predict", "bsvd_sgd_get", "bsvd_quantile_grid")
+           "bsvd_sgd_predict", "bsvd_sgd_get", "bsvd_quantile_grid",
+           "bsvd_set_owned", "bsvd_sqerr")
 
 
 class BsvdError(RuntimeError):
@@ -110,6 +111,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "bsvd_sgd_get": (i32, [vp, vp, vp, vp, vp]),
         "bsvd_quantile_grid": (i32, [vp, i64, i64, i64, vp, vp, i32, i32, vp,
                                      vp, vp, vp]),
+        "bsvd_set_owned": (i32, [vp, i32, vp]),
+        "bsvd_sqerr": (i32, [vp, i64, vp, vp, vp,
+                             ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_int64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -269,6 +274,29 @@ def bsvd_rmse(ctx, u, i, y) -> float:
                           ctypes.byref(out))
     _check(ctx, st)
     return out.value
+
+
+def bsvd_set_owned(ctx, owned=None) -> int:
+    """Hold only the blocks flagged in `owned` (one entry per block of the
+    next partition); None holds all of them again."""
+    if owned is None:
+        return _check(ctx, load().bsvd_set_owned(ctx, 0, None))
+    mask = np.ascontiguousarray(np.asarray(owned) != 0, np.uint8)
+    return _check(ctx, load().bsvd_set_owned(ctx, mask.size, mask.ctypes.data))
+
+
+def bsvd_sqerr(ctx, u, i, y):
+    """(sum of squared errors, count) over the queries of held blocks."""
+    nq = _len(u)
+    if _len(i) != nq or _len(y) != nq:
+        raise ValueError("u, i, y must have the same length")
+    out = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    st = load().bsvd_sqerr(ctx, nq, _ptr(u, np.int32, "u"),
+                           _ptr(i, np.int32, "i"), _ptr(y, np.float32, "y"),
+                           ctypes.byref(out), ctypes.byref(cnt))
+    _check(ctx, st)
+    return out.value, cnt.value
 
 
 def bsvd_block_stats(ctx, nblocks: int):
@@ -529,6 +557,15 @@ class Context:
 
     def rmse(self, u, i, y):
         return bsvd_rmse(self.handle, u, i, y)
+
+    def set_owned(self, owned=None):
+        """Hold only the flagged blocks from the next partition on (multi-GPU
+        sharding); None holds every block."""
+        bsvd_set_owned(self.handle, owned)
+
+    def sqerr(self, u, i, y):
+        """(sum of squared errors, count) over the held blocks' queries."""
+        return bsvd_sqerr(self.handle, u, i, y)
 
     def block_stats(self):
         return bsvd_block_stats(self.handle, self.nblocks)

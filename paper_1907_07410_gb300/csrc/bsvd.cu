@@ -87,11 +87,16 @@ struct bsvd_ctx {
   bool diag = false;        // block-diagonal batch of independent blocks
   int64_t br = 0, bc = 0;
   std::vector<BlockMeta> meta;
+  // blocks this context holds (bsvd_set_owned); empty: all of them
+  std::vector<uint8_t> own;
   int64_t arena = 0;
   DevBuf d_rb, d_cb, d_rperm, d_cperm, d_seen, d_meta, d_counts, d_sums,
       d_maxabs, d_mu, d_W, d_err;
   // bf16 [Y; M] planes, per-block shift and delta, TMA maps (tensor Gram)
   bool tc_planes = false, tc_exact = false;
+  // the float32 arena W is written unless the BF16 form's tensor-core
+  // projection reads the bf16 copy instead
+  bool w32 = true;
   int32_t gram_used = 0;    // 1: FP32 SIMT, 2: exact tensor, 3: tf32, 4: bf16
   DevBuf d_VX, d_shift, d_delta, d_maps, d_flag;
   DevBuf d_wmaps;           // TMA maps over the float32 blocks (tf32 Gram)
@@ -114,6 +119,12 @@ struct bsvd_ctx {
   // tensor-core projection: 128-column tiles of W and one TMA map per block
   DevBuf d_pjtiles, d_pwmaps;
   int32_t n_pjtiles = 0;
+  // finalisation: per-tile column statistics of F_L and F_s, column flips
+  DevBuf d_lpart, d_spart, d_flip;
+  // the BF16 form's projection: maps over the bf16 blocks and over F_s's
+  // bf16 B form, and that B form
+  DevBuf d_pbmaps, d_fbmaps, d_FB;
+  std::vector<CUtensorMap> h_pbmaps, h_fbmaps;
   // the layout the uploaded tables and tensor maps were built for (see
   // factor_impl), and the solver's initial state kept on the device
   std::vector<unsigned char> fsig;
@@ -339,7 +350,8 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->d_sgd_range, &c->d_sgd_blocks, &c->d_sgd_P,
                     &c->d_sgd_Q, &c->d_sgd_bu, &c->d_sgd_bi, &c->d_sgd_sum,
                     &c->d_qcnt, &c->d_qkeys, &c->d_qcum, &c->d_qperm,
-                    &c->d_qbounds};
+                    &c->d_qbounds, &c->d_pbmaps, &c->d_fbmaps, &c->d_FB,
+                    &c->d_lpart, &c->d_spart, &c->d_flip};
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   for (DevBuf *b : bufs) b->release();
@@ -377,6 +389,10 @@ static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
     return fail(c, BSVD_EINVAL, "partition: bad row bounds");
   if (col_bounds && !bounds_ok(col_bounds, q, n))
     return fail(c, BSVD_EINVAL, "partition: bad column bounds");
+  if (!c->own.empty() && (int64_t)c->own.size() != (diag ? (int64_t)p : (int64_t)p * q))
+    return fail(c, BSVD_EINVAL, "partition: the owned-block mask has %lld "
+                "entries for %lld blocks", (long long)c->own.size(),
+                (long long)(diag ? (int64_t)p : (int64_t)p * q));
 
   c->parted = false;
   c->factored = false;
@@ -411,10 +427,13 @@ static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
       bm.L_pad = (int32_t)round_up(bm.L, kPad);
       bm.row0 = c->rb[bi];
       bm.col0 = c->cb[bj];
+      const int32_t b = diag ? bi : bi * q + bj;
+      bm.owned = c->own.empty() || c->own[b] ? 1 : 0;
       bm.w_off = off;
-      off += (int64_t)bm.s_pad * bm.L_pad;
       bm.s128 = (int32_t)round_up(bm.s, 128);
       bm.vx_off = vxoff;
+      if (!bm.owned) continue;   // another shard's block: no dense storage
+      off += (int64_t)bm.s_pad * bm.L_pad;
       // exact Gram: planes [Y; M]; bf16 Gram: one bf16 copy of W
       vxoff += (c->cfg.precision == BSVD_BF16 ? 1 : 2) * (int64_t)bm.s128 *
                bm.L_pad;
@@ -430,7 +449,9 @@ static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
   CK(c->d_sums.ensure(sizeof(long long) * nb), "partition");
   CK(c->d_maxabs.ensure(sizeof(unsigned int)), "partition");
   CK(c->d_mu.ensure(sizeof(float) * nb), "partition");
-  CK(c->d_W.ensure(sizeof(float) * std::max<int64_t>(off, 1)), "partition");
+  c->w32 = !(c->cfg.precision == BSVD_BF16 && c->cfg.panel_path == 0);
+  if (c->w32)
+    CK(c->d_W.ensure(sizeof(float) * std::max<int64_t>(off, 1)), "partition");
   CK(cudaMemcpyAsync(c->d_rb.p, c->rb.data(), sizeof(int64_t) * (p + 1),
                      cudaMemcpyHostToDevice, c->st), "partition");
   CK(cudaMemcpyAsync(c->d_cb.p, c->cb.data(), sizeof(int64_t) * (q + 1),
@@ -476,8 +497,9 @@ static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
      "partition");
   CK(cudaMemsetAsync(c->d_maxabs.p, 0, sizeof(unsigned int), c->st),
      "partition");
-  CK(cudaMemsetAsync(c->d_W.p, 0, sizeof(float) * std::max<int64_t>(off, 1),
-                     c->st), "partition");
+  if (c->w32)
+    CK(cudaMemsetAsync(c->d_W.p, 0, sizeof(float) * std::max<int64_t>(off, 1),
+                       c->st), "partition");
   const GridDesc g = c->grid();
   std::fill(c->phase_ms, c->phase_ms + 8, 0.0);
   mark(c, 0);
@@ -498,7 +520,8 @@ static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
   }
   CK(launch_scatter(g, c->d_meta.as<BlockMeta>(), nnz, (const int32_t *)du,
                     (const int32_t *)di, (const float *)dx,
-                    c->d_mu.as<float>(), c->d_W.as<float>(), wh, c->st),
+                    c->d_mu.as<float>(), c->w32 ? c->d_W.as<float>() : nullptr,
+                    wh, c->st),
      "partition: scatter");
   c->launches += nnz > 0 ? 3 : 1;
   // bf16 planes for the exact tensor-core Gram
@@ -543,7 +566,7 @@ static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
       std::memset(maps.data(), 0, sizeof(CUtensorMap) * nb);
       for (int32_t b = 0; b < nb; ++b) {
         const BlockMeta &bm = c->meta[b];
-        if (bm.s == 0) continue;
+        if (bm.s == 0 || !bm.owned) continue;
         cuuint64_t dims[2] = {(cuuint64_t)bm.L_pad,
                               (cuuint64_t)(plane_rows * bm.s128)};
         cuuint64_t strides[1] = {(cuuint64_t)bm.L_pad * 2};
@@ -574,7 +597,7 @@ static bsvd_status partition_impl(bsvd_ctx *c, int64_t m, int64_t n,
     std::memset(maps.data(), 0, sizeof(CUtensorMap) * nb);
     for (int32_t b = 0; b < nb; ++b) {
       const BlockMeta &bm = c->meta[b];
-      if (bm.s == 0) continue;
+      if (bm.s == 0 || !bm.owned) continue;
       cuuint64_t dims[2] = {(cuuint64_t)bm.L_pad, (cuuint64_t)bm.s_pad};
       cuuint64_t strides[1] = {(cuuint64_t)bm.L_pad * 4};
       cuuint32_t box[2] = {32, 128};
@@ -715,29 +738,44 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
   c->kp = (int32_t)std::max<int64_t>(4, round_up(k, 4));
   const int32_t B = c->bsub, kp = c->kp, nb = c->nblocks;
 
-  int64_t goff = 0, xoff = 0, fsoff = 0, floff = 0;
+  const bool proj16 = c->cfg.panel_path == 0 && c->cfg.precision == BSVD_BF16;
+  const bool g256 = c->cfg.precision == BSVD_BF16 ||
+                    c->cfg.precision == BSVD_TF32;
+  const int32_t kn = (int32_t)round_up(kp, 16);
+  int64_t goff = 0, xoff = 0, fsoff = 0, floff = 0, fboff = 0;
   std::vector<int4> gt;
   std::vector<int2> rt, lt, pt, pj;
   std::vector<SolverState> st0(nb);
   for (int32_t b = 0; b < nb; ++b) {
     BlockMeta &bm = c->meta[b];
-    bm.keff = std::min(ks ? ks[b] : k, bm.s);
+    bm.keff = bm.owned ? std::min(ks ? ks[b] : k, bm.s) : 0;
     bm.g_off = goff;
     bm.x_off = xoff;
     bm.fs_off = fsoff;
     bm.fl_off = floff;
-    goff += (int64_t)bm.s_pad * bm.s_pad;
-    xoff += (int64_t)bm.s_pad * B;
-    fsoff += (int64_t)bm.s_pad * kp;
-    floff += (int64_t)bm.L_pad * kp;
+    bm.fb_off = fboff;
+    if (bm.owned) {          // another shard's block takes no solver storage
+      if (proj16 && bm.s > 0) fboff += project_bf16_bform_elems(bm.s_pad, kn);
+      goff += (int64_t)bm.s_pad * bm.s_pad;
+      xoff += (int64_t)bm.s_pad * B;
+      fsoff += (int64_t)bm.s_pad * kp;
+      floff += (int64_t)bm.L_pad * kp;
+    }
     SolverState &s = st0[b];
     std::memset(&s, 0, sizeof s);
     s.bsub = std::min(B, bm.s);
     s.status = (bm.s == 0 || bm.keff == 0) ? kConverged : kRunning;
     bm.t0 = (int32_t)rt.size();
     bm.nt = 0;
-    if (bm.s == 0) continue;
-    const int32_t T = (bm.s_pad + 127) / 128;
+    bm.pt0 = (int32_t)pt.size();
+    bm.npt = 0;
+    bm.pj0 = (int32_t)pj.size();
+    bm.npj = 0;
+    if (bm.s == 0 || !bm.owned) continue;
+    // Gram tiles: 256 x 256 for the single-product tensor-core Grams,
+    // 128 x 128 for the exact four-product one and the FP32 SIMT one
+    const int32_t tsz = g256 ? 256 : 128;
+    const int32_t T = (bm.s_pad + tsz - 1) / tsz;
     for (int32_t ti = 0; ti < T; ++ti)
       for (int32_t tj = ti; tj < T; ++tj) gt.push_back(make_int4(b, ti, tj, 0));
     for (int32_t r = 0; r < bm.s_pad; r += 64) rt.push_back(make_int2(b, r));
@@ -745,6 +783,8 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     bm.nt = (int32_t)rt.size() - bm.t0;
     for (int32_t l = 0; l < bm.L; l += kProjCols) lt.push_back(make_int2(b, l));
     for (int32_t l = 0; l < bm.L; l += 128) pj.push_back(make_int2(b, l));
+    bm.npt = (int32_t)pt.size() - bm.pt0;
+    bm.npj = (int32_t)pj.size() - bm.pj0;
   }
   c->n_gtiles = (int32_t)gt.size();
   c->n_rowtiles = (int32_t)rt.size();
@@ -769,16 +809,28 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
   CK(c->d_rowtiles.ensure(sizeof(int2) * std::max<size_t>(rt.size(), 1)), "factor");
   CK(c->d_ltiles.ensure(sizeof(int2) * std::max<size_t>(lt.size(), 1)), "factor");
   CK(c->d_state0.ensure(sizeof(SolverState) * std::max(nb, 1)), "factor");
+  // 128-row tiles of F_s (panel products, finalisation) and of F_L
+  // (projection, finalisation), and the finalisation's partials and flips
+  CK(c->d_ptiles.ensure(sizeof(int2) * std::max<size_t>(pt.size(), 1)), "factor");
+  CK(c->d_pjtiles.ensure(sizeof(int2) * std::max<size_t>(pj.size(), 1)),
+     "factor");
+  CK(c->d_lpart.ensure(sizeof(ColPartial) * kp *
+                       std::max<size_t>(pj.size(), 1)), "factor");
+  CK(c->d_spart.ensure(sizeof(ColPartial) * kp *
+                       std::max<size_t>(pt.size(), 1)), "factor");
+  CK(c->d_flip.ensure((size_t)kp * std::max(nb, 1)), "factor");
   const bool tc_maps = panel_tc && !pt.empty();
   if (tc_maps) {
     CK(c->d_gmaps.ensure(sizeof(CUtensorMap) * nb), "factor");
     CK(c->d_XB.ensure(sizeof(float) * 2 * std::max<int64_t>(xoff, 1)), "factor");
     CK(c->d_ZB.ensure(sizeof(float) * 2 * std::max<int64_t>(xoff, 1)), "factor");
     CK(c->d_xmaps.ensure(sizeof(CUtensorMap) * 2 * nb), "factor");
-    CK(c->d_ptiles.ensure(sizeof(int2) * pt.size()), "factor");
     CK(c->d_pwmaps.ensure(sizeof(CUtensorMap) * std::max(nb, 1)), "factor");
-    CK(c->d_pjtiles.ensure(sizeof(int2) * std::max<size_t>(pj.size(), 1)),
-       "factor");
+    if (proj16) {
+      CK(c->d_pbmaps.ensure(sizeof(CUtensorMap) * std::max(nb, 1)), "factor");
+      CK(c->d_fbmaps.ensure(sizeof(CUtensorMap) * std::max(nb, 1)), "factor");
+      CK(c->d_FB.ensure(2 * std::max<int64_t>(fboff, 1)), "factor");
+    }
   }
   // The tile tables, the TMA maps and the initial solver state depend only
   // on the block layout (the metadata computed above, which includes every
@@ -799,7 +851,9 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     const void *ptrs[] = {c->d_G.p, c->d_W.p, c->d_XB.p, c->d_ZB.p,
                           c->d_gtiles.p, c->d_rowtiles.p, c->d_ltiles.p,
                           c->d_gmaps.p, c->d_xmaps.p, c->d_ptiles.p,
-                          c->d_pwmaps.p, c->d_pjtiles.p, c->d_state0.p};
+                          c->d_pwmaps.p, c->d_pjtiles.p, c->d_state0.p,
+                          c->d_VX.p, c->d_pbmaps.p, c->d_fbmaps.p, c->d_FB.p,
+                          c->d_lpart.p, c->d_spart.p, c->d_flip.p};
     put(ptrs, sizeof ptrs);
   }
   const bool same_layout = sig == c->fsig;
@@ -819,6 +873,12 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     if (!lt.empty())
       CK(cudaMemcpyAsync(c->d_ltiles.p, lt.data(), sizeof(int2) * lt.size(),
                          cudaMemcpyHostToDevice, c->st), "factor");
+    if (!pt.empty())
+      CK(cudaMemcpyAsync(c->d_ptiles.p, pt.data(), sizeof(int2) * pt.size(),
+                         cudaMemcpyHostToDevice, c->st), "factor");
+    if (!pj.empty())
+      CK(cudaMemcpyAsync(c->d_pjtiles.p, pj.data(), sizeof(int2) * pj.size(),
+                         cudaMemcpyHostToDevice, c->st), "factor");
   }
   if (nb > 0)
     CK(cudaMemcpyAsync(c->d_state.p, c->d_state0.p, sizeof(SolverState) * nb,
@@ -832,7 +892,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     std::memset(c->h_gmaps.data(), 0, sizeof(CUtensorMap) * nb);
     for (int32_t b = 0; b < nb; ++b) {
       const BlockMeta &bm = c->meta[b];
-      if (bm.s == 0) continue;
+      if (bm.s == 0 || !bm.owned) continue;
       cuuint64_t dims[2] = {(cuuint64_t)bm.s_pad, (cuuint64_t)bm.s_pad};
       cuuint64_t strides[1] = {(cuuint64_t)bm.s_pad * 4};
       cuuint32_t box[2] = {32, 128};
@@ -861,7 +921,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
       float *bform = h == 0 ? c->d_XB.as<float>() : c->d_ZB.as<float>();
       for (int32_t b = 0; b < nb; ++b) {
         const BlockMeta &bm = c->meta[b];
-        if (bm.s == 0) continue;
+        if (bm.s == 0 || !bm.owned) continue;
         cuuint64_t dims[2] = {32, (cuuint64_t)(bm.s_pad / 32) * 2 * B};
         cuuint64_t strides[1] = {128};
         cuuint32_t box[2] = {32, (cuuint32_t)(2 * B)};
@@ -881,17 +941,14 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     CK(cudaMemcpyAsync(c->d_xmaps.p, c->h_xmaps.data(),
                        sizeof(CUtensorMap) * 2 * nb, cudaMemcpyHostToDevice,
                        c->st), "factor");
-    CK(c->d_ptiles.ensure(sizeof(int2) * pt.size()), "factor");
-    CK(cudaMemcpyAsync(c->d_ptiles.p, pt.data(), sizeof(int2) * pt.size(),
-                       cudaMemcpyHostToDevice, c->st), "factor");
     // the tensor-core projection F_L = W^T F_s: one TMA map per block over
     // W (s_pad rows x L_pad columns, float32, boxes of 32 rows x 128
     // columns, plain layout) and 128-column tiles
     c->h_pwmaps.assign(nb, CUtensorMap());
     std::memset(c->h_pwmaps.data(), 0, sizeof(CUtensorMap) * nb);
-    for (int32_t b = 0; b < nb; ++b) {
+    for (int32_t b = 0; b < nb && !proj16; ++b) {
       const BlockMeta &bm = c->meta[b];
-      if (bm.s == 0 || bm.L == 0) continue;
+      if (bm.s == 0 || bm.L == 0 || !bm.owned) continue;
       cuuint64_t dims[2] = {(cuuint64_t)bm.L_pad, (cuuint64_t)bm.s_pad};
       cuuint64_t strides[1] = {(cuuint64_t)bm.L_pad * 4};
       cuuint32_t box[2] = {128, 32};
@@ -909,11 +966,50 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     CK(cudaMemcpyAsync(c->d_pwmaps.p, c->h_pwmaps.data(),
                        sizeof(CUtensorMap) * nb, cudaMemcpyHostToDevice,
                        c->st), "factor");
-    CK(c->d_pjtiles.ensure(sizeof(int2) * std::max<size_t>(pj.size(), 1)),
-       "factor");
-    if (!pj.empty())
-      CK(cudaMemcpyAsync(c->d_pjtiles.p, pj.data(), sizeof(int2) * pj.size(),
-                         cudaMemcpyHostToDevice, c->st), "factor");
+    if (proj16) {
+      // the BF16 form's projection: maps over the bf16 blocks (s128 rows x
+      // L_pad, boxes of 64 rows x 128 columns, plain layout) and over F_s's
+      // bf16 B form (rows of 64 values, 2 kn-row boxes, 128-byte swizzle)
+      c->h_pbmaps.assign(nb, CUtensorMap());
+      c->h_fbmaps.assign(nb, CUtensorMap());
+      std::memset(c->h_pbmaps.data(), 0, sizeof(CUtensorMap) * nb);
+      std::memset(c->h_fbmaps.data(), 0, sizeof(CUtensorMap) * nb);
+      for (int32_t b = 0; b < nb; ++b) {
+        const BlockMeta &bm = c->meta[b];
+        if (bm.s == 0 || bm.L == 0 || !bm.owned) continue;
+        cuuint64_t dims[2] = {(cuuint64_t)bm.L_pad, (cuuint64_t)bm.s128};
+        cuuint64_t strides[1] = {(cuuint64_t)bm.L_pad * 2};
+        cuuint32_t box[2] = {128, 64};
+        cuuint32_t es[2] = {1, 1};
+        CUresult r = enc(&c->h_pbmaps[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                         c->d_VX.as<__nv_bfloat16>() + bm.vx_off, dims, strides,
+                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+          return fail(c, BSVD_ECUDA, "factor: bf16 W tensor map %d failed (%d)",
+                      b, (int)r);
+        const int64_t rows = project_bf16_bform_elems(bm.s_pad, kn) / 64;
+        cuuint64_t fdims[2] = {64, (cuuint64_t)rows};
+        cuuint64_t fstrides[1] = {128};
+        cuuint32_t fbox[2] = {64, (cuuint32_t)(2 * kn)};
+        r = enc(&c->h_fbmaps[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                c->d_FB.as<__nv_bfloat16>() + bm.fb_off, fdims, fstrides, fbox,
+                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+          return fail(c, BSVD_ECUDA, "factor: F_s bf16 tensor map %d failed (%d)",
+                      b, (int)r);
+      }
+      CK(cudaMemcpyAsync(c->d_pbmaps.p, c->h_pbmaps.data(),
+                         sizeof(CUtensorMap) * nb, cudaMemcpyHostToDevice,
+                         c->st), "factor");
+      CK(cudaMemcpyAsync(c->d_fbmaps.p, c->h_fbmaps.data(),
+                         sizeof(CUtensorMap) * nb, cudaMemcpyHostToDevice,
+                         c->st), "factor");
+    }
   }
   c->fsig = std::move(sig);
   CK(cudaMemsetAsync(c->d_Fs.p, 0, sizeof(float) * std::max<int64_t>(fsoff, 1), c->st), "factor");
@@ -1063,7 +1159,19 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
       c->launches += (deg + 1) * (nrt > 0);
     }
     mark(c, 2);
-    if (panel_tc) {
+    if (proj16) {
+      // F_L from the bf16 blocks, F_s split into bf16 hi and lo
+      CK(launch_bform_fs16(e.meta, c->d_ptiles.as<int2>(), c->n_ptiles, e.Fs,
+                           kp, kn, c->d_FB.as<__nv_bfloat16>(), c->st),
+         "factor: bf16 B form of F_s");
+      CK(launch_project_bf16(e.meta, c->d_pjtiles.as<int2>(), c->n_pjtiles,
+                             c->d_pbmaps.as<CUtensorMap>(),
+                             c->d_fbmaps.as<CUtensorMap>(),
+                             c->d_FL.as<float>(), kp, kn,
+                             c->d_err.as<int32_t>(), c->st),
+         "factor: project (bf16 tensor cores)");
+      c->launches += (c->n_ptiles > 0);
+    } else if (panel_tc) {
       // F_s's split form goes into X's B-form buffer, free after the loop,
       // and is read through X's maps
       CK(launch_bform_fs(B, e.meta, c->d_ptiles.as<int2>(), c->n_ptiles, e.Fs,
@@ -1079,9 +1187,13 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
                         c->n_ltiles, c->d_W.as<float>(), e.Fs,
                         c->d_FL.as<float>(), kp, c->st), "factor: project");
     }
-    CK(launch_finalize(c->d_meta.as<BlockMeta>(), nb, e.Fs, c->d_FL.as<float>(),
-                       c->d_sigma.as<double>(), kp, k, c->st), "factor: finalize");
-    c->launches += (c->n_ltiles > 0) + (nb > 0);
+    CK(launch_finalize(c->d_meta.as<BlockMeta>(), nb, c->d_pjtiles.as<int2>(),
+                       c->n_pjtiles, c->d_ptiles.as<int2>(), c->n_ptiles, e.Fs,
+                       c->d_FL.as<float>(), c->d_sigma.as<double>(), kp,
+                       c->d_lpart.as<ColPartial>(), c->d_spart.as<ColPartial>(),
+                       c->d_flip.as<unsigned char>(), &c->launches, c->st),
+       "factor: finalize");
+    c->launches += (c->n_ltiles > 0);
     mark(c, 3);
     std::vector<SolverState> fin(nb);
     CK(cudaMemcpyAsync(fin.data(), c->d_state.p, sizeof(SolverState) * nb,
@@ -1162,8 +1274,8 @@ bsvd_status bsvd_rmse(bsvd_ctx *c, int64_t nq, const int32_t *u,
   CK(device_view(c, u, sizeof(int32_t) * nq, c->s_a, &du), "rmse");
   CK(device_view(c, i, sizeof(int32_t) * nq, c->s_b, &di), "rmse");
   CK(device_view(c, y, sizeof(float) * nq, c->s_c, &dy), "rmse");
-  CK(c->d_partials.ensure(sizeof(double) * kSqerrBlocks), "rmse");
-  CK(c->d_rmse.ensure(sizeof(double)), "rmse");
+  CK(c->d_partials.ensure(sizeof(double) * 2 * kSqerrBlocks), "rmse");
+  CK(c->d_rmse.ensure(2 * sizeof(double)), "rmse");
   mark(c, 4);
   CK(launch_sqerr(predict_args(c), nq, (const int32_t *)du,
                   (const int32_t *)di, (const float *)dy,
@@ -1178,6 +1290,53 @@ bsvd_status bsvd_rmse(bsvd_ctx *c, int64_t nq, const int32_t *u,
   if (s != BSVD_OK) return s;
   take(c, 4, 4, 5);
   *out_rmse = std::sqrt(sum / (double)nq);
+  return BSVD_OK;
+}
+
+bsvd_status bsvd_set_owned(bsvd_ctx *c, int32_t nblocks,
+                           const uint8_t *owned) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (nblocks < 0 || (nblocks > 0 && !owned))
+    return fail(c, BSVD_EINVAL, "set_owned: bad arguments");
+  c->own.assign(owned, owned + nblocks);
+  for (uint8_t &v : c->own) v = v ? 1 : 0;
+  c->parted = false;         // the next partition lays out the owned blocks
+  c->factored = false;
+  return BSVD_OK;
+}
+
+bsvd_status bsvd_sqerr(bsvd_ctx *c, int64_t nq, const int32_t *u,
+                       const int32_t *i, const float *y, double *out_sum,
+                       int64_t *out_count) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (!c->factored) return fail(c, BSVD_ESTATE, "sqerr: no factors");
+  if (nq < 0 || (nq > 0 && (!u || !i || !y)) || !out_sum || !out_count)
+    return fail(c, BSVD_EINVAL, "sqerr: bad arguments");
+  const void *du = u, *di = i, *dy = y;
+  CK(device_view(c, u, sizeof(int32_t) * nq, c->s_a, &du), "sqerr");
+  CK(device_view(c, i, sizeof(int32_t) * nq, c->s_b, &di), "sqerr");
+  CK(device_view(c, y, sizeof(float) * nq, c->s_c, &dy), "sqerr");
+  CK(c->d_partials.ensure(sizeof(double) * 2 * kSqerrBlocks), "sqerr");
+  CK(c->d_rmse.ensure(2 * sizeof(double)), "sqerr");
+  PredictArgs a = predict_args(c);
+  a.owned_only = 1;
+  mark(c, 4);
+  CK(launch_sqerr(a, nq, (const int32_t *)du, (const int32_t *)di,
+                  (const float *)dy, c->d_partials.as<double>(),
+                  c->d_rmse.as<double>(), c->d_err.as<int32_t>(), c->st),
+     "sqerr");
+  mark(c, 5);
+  c->launches += 2;
+  double res[2] = {0.0, 0.0};
+  CK(cudaMemcpyAsync(res, c->d_rmse.p, sizeof res, cudaMemcpyDeviceToHost,
+                     c->st), "sqerr");
+  bsvd_status s = read_errors(c, "sqerr");
+  if (s != BSVD_OK) return s;
+  take(c, 4, 4, 5);
+  *out_sum = res[0];
+  *out_count = (int64_t)res[1];
   return BSVD_OK;
 }
 
@@ -1207,6 +1366,9 @@ bsvd_status bsvd_get_block(bsvd_ctx *c, int32_t b, int32_t *mb, int32_t *nb,
   const BlockMeta &bm = c->meta[b];
   if ((sigma || P || V) && !c->factored)
     return fail(c, BSVD_ESTATE, "get_block: no factors");
+  if (dense && !bm.owned)
+    return fail(c, BSVD_EINVAL, "get_block: block %d is not held by this "
+                "context (bsvd_set_owned)", b);
   if (mb) *mb = bm.mb;
   if (nb) *nb = bm.nb;
   if (keff) *keff = c->factored ? bm.keff : 0;
@@ -1214,15 +1376,25 @@ bsvd_status bsvd_get_block(bsvd_ctx *c, int32_t b, int32_t *mb, int32_t *nb,
     CK(cudaMemcpyAsync(mu, c->d_mu.as<float>() + b, sizeof(float),
                        cudaMemcpyDeviceToHost, c->st), "get_block");
   std::vector<float> W;
-  if (dense) {
+  std::vector<__nv_bfloat16> Wh;
+  if (dense && c->w32) {
     W.resize((size_t)bm.s_pad * bm.L_pad);
     CK(cudaMemcpyAsync(W.data(), c->d_W.as<float>() + bm.w_off,
                        sizeof(float) * W.size(), cudaMemcpyDeviceToHost, c->st),
        "get_block");
+  } else if (dense) {
+    // the BF16 form keeps only the bf16 copy of its blocks
+    Wh.resize((size_t)bm.s_pad * bm.L_pad);
+    CK(cudaMemcpyAsync(Wh.data(), c->d_VX.as<__nv_bfloat16>() + bm.vx_off,
+                       sizeof(__nv_bfloat16) * Wh.size(),
+                       cudaMemcpyDeviceToHost, c->st), "get_block");
+    W.resize(Wh.size());
+    CK(cudaStreamSynchronize(c->st), "get_block");
+    for (size_t j = 0; j < Wh.size(); ++j) W[j] = __bfloat162float(Wh[j]);
   }
   std::vector<float> Fs, FL;
   std::vector<double> sg(c->kp);
-  if (c->factored && (sigma || P || V)) {
+  if (c->factored && bm.owned && (sigma || P || V)) {
     Fs.resize((size_t)bm.s_pad * c->kp);
     FL.resize((size_t)bm.L_pad * c->kp);
     CK(cudaMemcpyAsync(Fs.data(), c->d_Fs.as<float>() + bm.fs_off,
@@ -1272,6 +1444,9 @@ bsvd_status bsvd_reconstruct(bsvd_ctx *c, int32_t b, int32_t add_mean,
   if (b < 0 || b >= c->nblocks || !out)
     return fail(c, BSVD_EINVAL, "reconstruct: bad arguments");
   const BlockMeta &bm = c->meta[b];
+  if (!bm.owned)
+    return fail(c, BSVD_EINVAL, "reconstruct: block %d is not held by this "
+                "context (bsvd_set_owned)", b);
   const size_t cells = (size_t)bm.mb * bm.nb;
   if (cells == 0) return BSVD_OK;
   float mu = 0.f;

@@ -69,7 +69,7 @@ struct BlockMeta {
   int32_t keff;         // retained rank min(k, s) (set by factor)
   int32_t t0, nt;       // the block's 64-row tiles in the row-tile table
   int32_t s128;         // s rounded up to 128 (rows of each bf16 plane)
-  int32_t pad0;
+  int32_t owned;        // 1: this context holds the block (see set_owned)
   int64_t vx_off;       // bf16 planes offset: [Y; M], 2 s128 x L_pad
   int64_t row0, col0;   // first row / column position of the block
   int64_t w_off;        // W arena offset (floats)
@@ -77,6 +77,9 @@ struct BlockMeta {
   int64_t x_off;        // subspace panels offset, s_pad x bsub
   int64_t fs_off;       // F_s offset, s_pad x kp
   int64_t fl_off;       // F_L offset, L_pad x kp
+  int64_t fb_off;       // bf16 B form of F_s (BF16 form's projection)
+  int32_t pt0, npt;     // the block's 128-row tiles of F_s (panel tiles)
+  int32_t pj0, npj;     // the block's 128-row tiles of F_L (projection)
 };
 
 // Per-block state of the subspace iteration.

@@ -20,6 +20,7 @@ cudaError_t launch_means(int32_t nblocks, const unsigned long long *counts,
                          const long long *sums,
                          const unsigned int *maxabs_bits, float *mu,
                          int32_t *err, cudaStream_t st);
+// W (float32 arena) and Wh (bf16 copy) are each written when not null.
 cudaError_t launch_scatter(const GridDesc &g, const BlockMeta *meta,
                            int64_t nnz, const int32_t *u, const int32_t *i,
                            const float *x, const float *mu, float *W,
@@ -51,7 +52,9 @@ cudaError_t launch_gram_tc(const BlockMeta *meta, const int4 *tiles,
                            cudaStream_t st);
 
 // Single-pass tf32 Gram of the float32 blocks; maps: one TMA map per block
-// over W (s_pad x L_pad f32, 128 x 32 boxes, 128-byte swizzle).
+// over W (s_pad x L_pad f32, 128 x 32 boxes, 128-byte swizzle). This and
+// launch_gram_bf16 take tiles (block, tile_i, tile_j, 0), tile_i <= tile_j,
+// of 256 x 256.
 cudaError_t launch_gram_tf32(const BlockMeta *meta, const int4 *tiles,
                              int32_t ntiles, const CUtensorMap *maps, float *G,
                              int32_t *err, cudaStream_t st);
@@ -126,6 +129,23 @@ cudaError_t launch_project_tc(int32_t bsub, const BlockMeta *meta,
 cudaError_t launch_bform_fs(int32_t bsub, const BlockMeta *meta,
                             const int2 *tiles, int32_t ntiles, const float *Fs,
                             int32_t kp, float *out_bf, cudaStream_t st);
+// BF16 form: F_L = W_h^T F_s from the bf16 copy of the centred blocks (the
+// BF16 Gram's operand) with F_s split into bf16 hi and lo: tiles are (block,
+// first column l) pairs of 128 columns; wmaps one TMA map per block over
+// W_h (s128 rows x L_pad bf16, 128 x 64 boxes, plain layout); fmaps one per
+// block over F_s's bf16 B form (64-value rows, 2 kn-row boxes, 128-byte
+// swizzle), written by launch_bform_fs16 at fb_off. kn = kp rounded up to
+// 16 (16 .. 64).
+int64_t project_bf16_bform_elems(int32_t s_pad, int32_t kn);
+cudaError_t launch_project_bf16(const BlockMeta *meta, const int2 *tiles,
+                                int32_t ntiles, const CUtensorMap *wmaps,
+                                const CUtensorMap *fmaps, float *FL,
+                                int32_t kp, int32_t kn, int32_t *err,
+                                cudaStream_t st);
+// tiles: (block, first row) pairs of 128 rows of F_s.
+cudaError_t launch_bform_fs16(const BlockMeta *meta, const int2 *tiles,
+                              int32_t ntiles, const float *Fs, int32_t kp,
+                              int32_t kn, __nv_bfloat16 *out, cudaStream_t st);
 // B form of `in` for the blocks still running (tiles as above).
 cudaError_t launch_bform(int32_t bsub, const BlockMeta *meta,
                          const SolverState *state, const int2 *tiles,
@@ -152,15 +172,33 @@ cudaError_t launch_check(const EigBuffers &e, cudaStream_t st);
 cudaError_t launch_publish(const int32_t *running, int32_t *host, int32_t seq,
                            cudaStream_t st);
 
-// F_L = W^T F_s, then float64 norms (sigma) and sign canonicalisation.
+// F_L = W^T F_s on the FP32 SIMT pipes.
 // ltiles: (block, first column l) pairs, kProjCols columns each.
 constexpr int kProjCols = 64;
 cudaError_t launch_project(const BlockMeta *meta, const int2 *ltiles,
                            int32_t ntiles, const float *W, const float *Fs,
                            float *FL, int32_t kp, cudaStream_t st);
+
+// One tile's statistics of one factor column (kernels_finalize.cu).
+struct ColPartial {
+  double sq;        // float64 sum of squares over the tile's rows
+  float absmax;     // largest |value| (first row on ties)
+  float val;        // that value
+  int32_t idx;      // its row
+  int32_t pad;
+};
+// sigma_j = |F_L[:, j]| in float64 and the sign convention (the item-side
+// vector's largest-|.| entry positive), then the flips applied to F_s and
+// F_L. ltiles / stiles: (block, first row) pairs of 128 rows of F_L / F_s
+// (BlockMeta pj0, npj / pt0, npt index them); lpart, spart: nltiles * kp
+// and nstiles * kp partials; flip: nblocks * kp bytes.
 cudaError_t launch_finalize(const BlockMeta *meta, int32_t nblocks,
-                            float *Fs, float *FL, double *sigma, int32_t kp,
-                            int32_t k, cudaStream_t st);
+                            const int2 *ltiles, int32_t nltiles,
+                            const int2 *stiles, int32_t nstiles, float *Fs,
+                            float *FL, double *sigma, int32_t kp,
+                            ColPartial *lpart, ColPartial *spart,
+                            unsigned char *flip, int64_t *launches,
+                            cudaStream_t st);
 
 // ---- blocked SGD, the paper's Algorithms 1-2 (kernels_sgd.cu) -------------
 struct SgdRates {
@@ -205,12 +243,14 @@ struct PredictArgs {
   int32_t kp;
   int32_t clamp;
   float lo, hi;
+  int32_t owned_only = 0;   // squared errors: only blocks this context holds
 };
 cudaError_t launch_predict(const PredictArgs &a, int64_t nq, const int32_t *u,
                            const int32_t *i, float *yhat, int32_t *err,
                            cudaStream_t st);
 // Squared-error partial sums: one float64 per CTA of a fixed grid, then a
-// fixed-order final sum. partials must hold kSqerrBlocks doubles.
+// fixed-order final sum into out[0] and the number of queries summed into
+// out[1]. partials must hold 2 kSqerrBlocks doubles (sums, then counts).
 constexpr int kSqerrBlocks = 304;
 cudaError_t launch_sqerr(const PredictArgs &a, int64_t nq, const int32_t *u,
                          const int32_t *i, const float *y, double *partials,

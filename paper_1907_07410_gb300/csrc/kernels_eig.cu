@@ -915,92 +915,6 @@ k_project(const BlockMeta *__restrict__ meta, const int2 *__restrict__ ltiles,
   }
 }
 
-// sigma_j = |F_L[:, j]| (float64 across threads); then flip (F_s_j, F_L_j) so
-// the item-side vector's largest-|.| entry (lowest index on ties) is
-// positive. Thread t reads whole rows t, t + 256, ... (kp floats each).
-template <int KM, int NT>
-__global__ void __launch_bounds__(NT)
-k_finalize(const BlockMeta *__restrict__ meta, float *Fs, float *FL,
-           double *sigma, int kp) {
-  __shared__ double sq[NT / 32][KM];
-  __shared__ float bv[NT / 32][KM];
-  __shared__ int bi[NT / 32][KM];
-  __shared__ int flip[KM];
-  const int blk = blockIdx.x;
-  pdl_wait();
-  pdl_trigger();
-  const BlockMeta bm = meta[blk];
-  const int keff = bm.keff;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float *Fsb = Fs + bm.fs_off;
-  float *FLb = FL + bm.fl_off;
-  const float *vec = bm.trans ? Fsb : FLb;     // item-side vectors
-  const int len = bm.trans ? bm.s : bm.L;
-  // sums of squares, reduced per warp before the arg-max loop, so only
-  // two KM-wide arrays are live at a time
-  {
-    float part[KM];
-#pragma unroll
-    for (int j = 0; j < KM; ++j) part[j] = 0.f;
-    for (int l = threadIdx.x; l < bm.L; l += blockDim.x) {
-#pragma unroll
-      for (int j = 0; j < KM; ++j) {
-        const float v = j < kp ? FLb[(int64_t)l * kp + j] : 0.f;
-        part[j] = fmaf(v, v, part[j]);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < KM; ++j) {
-      double d = part[j];
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      if (lane == 0) sq[warp][j] = d;
-    }
-  }
-  {
-    float best[KM];
-    int bidx[KM];
-#pragma unroll
-    for (int j = 0; j < KM; ++j) { best[j] = -1.f; bidx[j] = 0x7fffffff; }
-    for (int a = threadIdx.x; a < len; a += blockDim.x) {
-#pragma unroll
-      for (int j = 0; j < KM; ++j) {
-        const float v = j < kp ? fabsf(vec[(int64_t)a * kp + j]) : 0.f;
-        if (v > best[j]) { best[j] = v; bidx[j] = a; }   // first index wins ties
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < KM; ++j) {
-      float b = best[j];
-      int ix = bidx[j];
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, b, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
-        if (ob > b || (ob == b && oi < ix)) { b = ob; ix = oi; }
-      }
-      if (lane == 0) { bv[warp][j] = b; bi[warp][j] = ix; }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < KM) {
-    const int j = threadIdx.x;
-    double s2 = 0.0;
-    float b = -1.f;
-    int ix = 0x7fffffff;
-    for (int w = 0; w < NT / 32; ++w) {
-      s2 += sq[w][j];
-      if (bv[w][j] > b || (bv[w][j] == b && bi[w][j] < ix)) { b = bv[w][j]; ix = bi[w][j]; }
-    }
-    const bool live = j < keff;
-    flip[j] = (live && ix < len && vec[(int64_t)ix * kp + j] < 0.f) ? 1 : 0;
-    if (j < kp) sigma[(int64_t)blk * kp + j] = live ? sqrt(s2) : 0.0;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < bm.s * kp; e += blockDim.x)
-    if (flip[e % kp]) Fsb[e] = -Fsb[e];
-  for (int e = threadIdx.x; e < bm.L * kp; e += blockDim.x)
-    if (flip[e % kp]) FLb[e] = -FLb[e];
-}
-
 template <int B>
 size_t rr_smem() { return sizeof(RRSmem<B>); }
 
@@ -1149,19 +1063,5 @@ cudaError_t launch_project(const BlockMeta *meta, const int2 *ltiles,
   });
 }
 
-cudaError_t launch_finalize(const BlockMeta *meta, int32_t nblocks,
-                            float *Fs, float *FL, double *sigma, int32_t kp,
-                            int32_t k, cudaStream_t st) {
-  (void)k;
-  if (nblocks <= 0) return cudaSuccess;
-  return by_kmax(kp, [&](auto km) {
-    constexpr int KM = decltype(km)::value;
-    // one CTA per block; more threads where the per-thread registers
-    // (3 KM) allow it
-    constexpr int NT = KM <= 32 ? 512 : 256;
-    return launch_pdl(k_finalize<KM, NT>, dim3(nblocks), dim3(NT), 0, st,
-                      meta, Fs, FL, sigma, kp);
-  });
-}
 
 }  // namespace bsvd

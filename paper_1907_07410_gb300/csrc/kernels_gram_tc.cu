@@ -194,18 +194,29 @@ k_gram_tc(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
 //   * k_gram_tf32 reads the float32 blocks, truncated to tf32 by the MMA
 //     (10-bit mantissa);
 //   * k_gram_bf16 reads a bf16 copy of the centred blocks (8-bit mantissa).
-// Both accumulate in f32. Same tiling and roles as k_gram_tc, with one
-// accumulator and 6 stages of {W_i, W_j} boxes of 128 rows x 128 bytes
-// (32 floats or 64 bf16). Either way a k-chunk is four MMAs of 32 bytes of
-// K each (K = 8 tf32 or K = 16 bf16), so the descriptor steps match.
+// Both accumulate in f32. Same roles as k_gram_tc (warp 0 TMA, warp 1 MMA,
+// all four warps in the epilogue), on the larger tiles below, with boxes of
+// 128 rows x 128 bytes (32 floats or 64 bf16). Either way a k-chunk is four
+// K slices of 32 bytes each (K = 8 tf32 or K = 16 bf16), so the descriptor
+// steps match.
 constexpr int KF = 32;                          // floats per k-chunk (128 B)
-constexpr int FSTAGES = 6;
-constexpr int FTILE_BYTES = TT * KF * 4;        // 16 KiB
-constexpr int FSTAGE_BYTES = 2 * FTILE_BYTES;
+constexpr int FTILE_BYTES = TT * KF * 4;        // 16 KiB: 128 rows x 128 B
 
-struct CtrlF {
-  uint64_t full[FSTAGES];
-  uint64_t empty[FSTAGES];
+// 256 x 256 output tiles: two 128-row halves of A (rows i0 .. i0+255) and
+// the 256 rows j0 .. j0+255 as B (N = 256), one accumulator of 256 columns
+// per half (all 512 tensor-memory columns). Per k-chunk the stage holds
+// four boxes of 128 rows x 128 bytes, [A0 | A1 | B0 | B1], 64 KiB, and the
+// MMA thread issues 8 MMAs (4 K slices x 2 halves): 128 flop per byte
+// loaded, twice the 128 x 128 tile's, so the loads no longer set the pace.
+// A diagonal tile (i0 = j0) loads A only and reads B from it: [A0 | A1]
+// is the same 256 rows, contiguous in shared memory.
+constexpr int G2T = 256;
+constexpr int G2STAGES = 3;
+constexpr int G2STAGE_BYTES = 4 * FTILE_BYTES;       // 64 KiB
+
+struct CtrlG2 {
+  uint64_t full[G2STAGES];
+  uint64_t empty[G2STAGES];
   uint64_t done;
   uint32_t tmem;
   int abort;
@@ -213,7 +224,8 @@ struct CtrlF {
   int consumed;
 };
 
-constexpr size_t kSmemBytesF = FSTAGES * FSTAGE_BYTES + sizeof(CtrlF) + 1024;
+constexpr size_t kSmemBytesG2 =
+    G2STAGES * G2STAGE_BYTES + sizeof(CtrlG2) + 1024;
 
 template <bool kBf16>
 __device__ __forceinline__ void
@@ -223,19 +235,19 @@ gram_single(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
   extern __shared__ unsigned char smem_raw[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  CtrlF &ct = *reinterpret_cast<CtrlF *>(base + FSTAGES * FSTAGE_BYTES);
+  CtrlG2 &ct = *reinterpret_cast<CtrlG2 *>(base + G2STAGES * G2STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int4 tl = tiles[blockIdx.x];
   const BlockMeta bm = meta[tl.x];
   const CUtensorMap *map = maps + tl.x;
   const bool diag = tl.y == tl.z;
-  const int yi = tl.y * TT, yj = tl.z * TT;
+  const int yi = tl.y * G2T, yj = tl.z * G2T;
   constexpr int kElems = kBf16 ? 64 : KF;        // elements per k-chunk
   const int nk = (bm.L_pad + kElems - 1) / kElems;
 
-  if (warp == 0) tc::tmem_alloc(&ct.tmem, 128);
+  if (warp == 0) tc::tmem_alloc(&ct.tmem, 512);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < FSTAGES; ++s) {
+    for (int s = 0; s < G2STAGES; ++s) {
       tc::mbar_init(&ct.full[s], 1);
       tc::mbar_init(&ct.empty[s], 1);
     }
@@ -251,29 +263,33 @@ gram_single(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
   const uint32_t taddr = ct.tmem;
 
   if (warp == 0 && lane == 0) {
-    const uint32_t bytes = (diag ? 1 : 2) * FTILE_BYTES;
+    const uint32_t bytes = (diag ? 2 : 4) * FTILE_BYTES;
     for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % FSTAGES;
-      const uint32_t ph = (kc / FSTAGES) & 1;
+      const int s = kc % G2STAGES;
+      const uint32_t ph = (kc / G2STAGES) & 1;
       if (!tc::mbar_wait(&ct.empty[s], ph ^ 1, kSpin) ||
           *reinterpret_cast<volatile int *>(&ct.abort)) {
         atomicOr(err, kErrTimeout);
         ct.abort = 1;
         break;
       }
-      unsigned char *buf = base + s * FSTAGE_BYTES;
+      unsigned char *buf = base + s * G2STAGE_BYTES;
       const int x = kc * kElems;
       tc::mbar_expect_tx(&ct.full[s], bytes);
       tc::tma_load_2d(buf, map, x, yi, &ct.full[s]);
-      if (!diag) tc::tma_load_2d(buf + FTILE_BYTES, map, x, yj, &ct.full[s]);
+      tc::tma_load_2d(buf + FTILE_BYTES, map, x, yi + TT, &ct.full[s]);
+      if (!diag) {
+        tc::tma_load_2d(buf + 2 * FTILE_BYTES, map, x, yj, &ct.full[s]);
+        tc::tma_load_2d(buf + 3 * FTILE_BYTES, map, x, yj + TT, &ct.full[s]);
+      }
       ct.issued = kc + 1;
     }
   } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc =
-        kBf16 ? tc::idesc_bf16_f32(TT, TT) : tc::idesc_tf32_f32(TT, TT);
+    constexpr uint32_t idesc = kBf16 ? tc::idesc_bf16_f32(TT, G2T)
+                                     : tc::idesc_tf32_f32(TT, G2T);
     for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % FSTAGES;
-      const uint32_t ph = (kc / FSTAGES) & 1;
+      const int s = kc % G2STAGES;
+      const uint32_t ph = (kc / G2STAGES) & 1;
       if (!tc::mbar_wait(&ct.full[s], ph, kSpin) ||
           *reinterpret_cast<volatile int *>(&ct.abort)) {
         atomicOr(err, kErrTimeout);
@@ -282,16 +298,22 @@ gram_single(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
       }
       ct.consumed = kc + 1;
       tc::fence_after_sync();
-      unsigned char *buf = base + s * FSTAGE_BYTES;
-      const uint64_t dwi = tc::sdesc_kmajor_sw128(tc::smem_u32(buf));
-      const uint64_t dwj = diag ? dwi : tc::sdesc_kmajor_sw128(tc::smem_u32(buf + FTILE_BYTES));
+      unsigned char *buf = base + s * G2STAGE_BYTES;
+      const uint64_t da0 = tc::sdesc_kmajor_sw128(tc::smem_u32(buf));
+      const uint64_t da1 =
+          tc::sdesc_kmajor_sw128(tc::smem_u32(buf + FTILE_BYTES));
+      const uint64_t db =
+          diag ? da0 : tc::sdesc_kmajor_sw128(tc::smem_u32(buf + 2 * FTILE_BYTES));
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {          // 32 bytes of K per MMA
         const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
-        if constexpr (kBf16)
-          tc::mma_bf16(taddr, dwi + 2 * kk, dwj + 2 * kk, idesc, acc);
-        else
-          tc::mma_tf32(taddr, dwi + 2 * kk, dwj + 2 * kk, idesc, acc);
+        if constexpr (kBf16) {
+          tc::mma_bf16(taddr, da0 + 2 * kk, db + 2 * kk, idesc, acc);
+          tc::mma_bf16(taddr + G2T, da1 + 2 * kk, db + 2 * kk, idesc, acc);
+        } else {
+          tc::mma_tf32(taddr, da0 + 2 * kk, db + 2 * kk, idesc, acc);
+          tc::mma_tf32(taddr + G2T, da1 + 2 * kk, db + 2 * kk, idesc, acc);
+        }
       }
       tc::mma_commit(&ct.empty[s]);
     }
@@ -305,23 +327,27 @@ gram_single(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
   if (ready && !*reinterpret_cast<volatile int *>(&ct.abort)) {
     tc::fence_after_sync();
     const int sp = bm.s_pad;
-    const int gi = yi + warp * 32 + lane;
     float *Gb = G + bm.g_off;
     const uint32_t lrow = (uint32_t)(warp * 32) << 16;
 #pragma unroll 1
-    for (int c0 = 0; c0 < TT; c0 += 32) {
-      float a[32];
-      tc::tmem_ld32(taddr + lrow + c0, a);
-      const int gj0 = yj + c0;
-      if (gj0 >= sp) continue;
-      if (gi < sp) {
-        float4 *dst = reinterpret_cast<float4 *>(Gb + (int64_t)gi * sp + gj0);
+    for (int h = 0; h < 2; ++h) {
+      const int gi = yi + h * TT + warp * 32 + lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < G2T; c0 += 32) {
+        float a[32];
+        tc::tmem_ld32(taddr + lrow + h * G2T + c0, a);
+        const int gj0 = yj + c0;
+        if (gj0 >= sp) continue;
+        if (gi < sp) {
+          float4 *dst = reinterpret_cast<float4 *>(Gb + (int64_t)gi * sp + gj0);
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          dst[j] = make_float4(a[4 * j], a[4 * j + 1], a[4 * j + 2], a[4 * j + 3]);
-        if (!diag) {
+          for (int j = 0; j < 8; ++j)
+            dst[j] = make_float4(a[4 * j], a[4 * j + 1], a[4 * j + 2],
+                                 a[4 * j + 3]);
+          if (!diag) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) Gb[(int64_t)(gj0 + j) * sp + gi] = a[j];
+            for (int j = 0; j < 32; ++j) Gb[(int64_t)(gj0 + j) * sp + gi] = a[j];
+          }
         }
       }
     }
@@ -330,10 +356,10 @@ gram_single(const BlockMeta *__restrict__ meta, const int4 *__restrict__ tiles,
   __syncthreads();
   if (threadIdx.x == 0 && ct.abort) {
     for (int kc = ct.consumed; kc < ct.issued; ++kc)
-      tc::mbar_wait(&ct.full[kc % FSTAGES], (kc / FSTAGES) & 1, kSpin);
+      tc::mbar_wait(&ct.full[kc % G2STAGES], (kc / G2STAGES) & 1, kSpin);
   }
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(taddr, 128);
+  if (warp == 0) tc::tmem_dealloc(taddr, 512);
 }
 
 __global__ void __launch_bounds__(128, 1)
@@ -356,11 +382,12 @@ cudaError_t launch_gram_bf16(const BlockMeta *meta, const int4 *tiles,
                              int32_t ntiles, const CUtensorMap *maps, float *G,
                              int32_t *err, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
+  static_assert(kSmemBytesG2 <= 227 * 1024, "shared memory");
   cudaError_t e = cudaFuncSetAttribute(
       k_gram_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)kSmemBytesF);
+      (int)kSmemBytesG2);
   if (e != cudaSuccess) return e;
-  k_gram_bf16<<<ntiles, 128, kSmemBytesF, st>>>(meta, tiles, maps, G, err);
+  k_gram_bf16<<<ntiles, 128, kSmemBytesG2, st>>>(meta, tiles, maps, G, err);
   return cudaGetLastError();
 }
 
@@ -370,9 +397,9 @@ cudaError_t launch_gram_tf32(const BlockMeta *meta, const int4 *tiles,
   if (ntiles <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(
       k_gram_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)kSmemBytesF);
+      (int)kSmemBytesG2);
   if (e != cudaSuccess) return e;
-  k_gram_tf32<<<ntiles, 128, kSmemBytesF, st>>>(meta, tiles, maps, G, err);
+  k_gram_tf32<<<ntiles, 128, kSmemBytesG2, st>>>(meta, tiles, maps, G, err);
   return cudaGetLastError();
 }
 

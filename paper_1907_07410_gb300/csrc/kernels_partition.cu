@@ -146,9 +146,10 @@ k_scatter(GridDesc g, const BlockMeta *__restrict__ meta, int64_t nnz,
     int32_t blk, r, c, a, l;
     if (!locate(g, u[t], it[t], &blk, &r, &c)) continue;   // flagged in pass 1
     const BlockMeta &bm = meta[blk];
+    if (!bm.owned) continue;                 // another shard's block
     to_w(bm, r, c, &a, &l);
     const float w = __fsub_rn(x[t], mu[blk]);
-    W[bm.w_off + (int64_t)a * bm.L_pad + l] = w;
+    if (W) W[bm.w_off + (int64_t)a * bm.L_pad + l] = w;
     // bf16 copy for the bf16 Gram: s128 x L_pad per block at vx_off
     if (Wh) Wh[bm.vx_off + (int64_t)a * bm.L_pad + l] = __float2bfloat16_rn(w);
   }
@@ -179,6 +180,7 @@ k_scatter_planes(GridDesc g, const BlockMeta *__restrict__ meta, int64_t nnz,
     int32_t blk, r, c, a, l;
     if (!locate(g, u[t], it[t], &blk, &r, &c)) continue;   // flagged in pass 1
     const BlockMeta &bm = meta[blk];
+    if (!bm.owned) continue;                 // another shard's block
     to_w(bm, r, c, &a, &l);
     const float y = __fsub_rn(x[t], shift[blk]);
     // exact in bf16, and every Gram partial sum below 2^24 in f32:

@@ -53,38 +53,67 @@ k_predict(PredictArgs a, int64_t nq, const int32_t *__restrict__ u,
   }
 }
 
+// With a.owned_only, queries in blocks this context does not hold are
+// skipped; the CTA's count of summed queries goes to counts.
 __global__ void __launch_bounds__(256)
 k_sqerr(PredictArgs a, int64_t nq, const int32_t *__restrict__ u,
         const int32_t *__restrict__ it, const float *__restrict__ y,
-        double *__restrict__ partials, int32_t *err) {
+        double *__restrict__ partials, long long *__restrict__ counts,
+        int32_t *err) {
   __shared__ double red[256];
+  __shared__ long long cnt[256];
   double acc = 0.0;
+  long long n = 0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nq;
        t += (int64_t)gridDim.x * blockDim.x) {
+    if (a.owned_only) {
+      int32_t blk, r, c;
+      if (locate(a.g, u[t], it[t], &blk, &r, &c) && !a.meta[blk].owned)
+        continue;
+    }
     float yh;
     if (!predict_one(a, u[t], it[t], &yh)) { atomicOr(err, kErrIndex); continue; }
     const double d = (double)yh - (double)y[t];
     acc = fma(d, d, acc);
+    ++n;
   }
   red[threadIdx.x] = acc;
+  cnt[threadIdx.x] = n;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    if (threadIdx.x < w) {
+      red[threadIdx.x] += red[threadIdx.x + w];
+      cnt[threadIdx.x] += cnt[threadIdx.x + w];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = red[0];
+    counts[blockIdx.x] = cnt[0];
+  }
 }
 
+// out[0] = sum of the partial sums (fixed tree); out[1] = their count, as
+// a float64 holding an exact integer below 2^53.
 __global__ void __launch_bounds__(512)
-k_sum_partials(const double *__restrict__ partials, int n, double *out) {
+k_sum_partials(const double *__restrict__ partials,
+               const long long *__restrict__ counts, int n, double *out) {
   __shared__ double red[512];
+  __shared__ long long cnt[512];
   red[threadIdx.x] = threadIdx.x < n ? partials[threadIdx.x] : 0.0;
+  cnt[threadIdx.x] = threadIdx.x < n ? counts[threadIdx.x] : 0;
   __syncthreads();
   for (int w = 256; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    if (threadIdx.x < w) {
+      red[threadIdx.x] += red[threadIdx.x + w];
+      cnt[threadIdx.x] += cnt[threadIdx.x + w];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = red[0];
+  if (threadIdx.x == 0) {
+    out[0] = red[0];
+    out[1] = (double)cnt[0];
+  }
 }
 
 __global__ void __launch_bounds__(256)
@@ -127,8 +156,9 @@ cudaError_t launch_sqerr(const PredictArgs &a, int64_t nq, const int32_t *u,
                          const int32_t *i, const float *y, double *partials,
                          double *out, int32_t *err, cudaStream_t st) {
   static_assert(kSqerrBlocks <= 512, "final sum is one CTA of 512");
-  k_sqerr<<<kSqerrBlocks, 256, 0, st>>>(a, nq, u, i, y, partials, err);
-  k_sum_partials<<<1, 512, 0, st>>>(partials, kSqerrBlocks, out);
+  long long *counts = reinterpret_cast<long long *>(partials + kSqerrBlocks);
+  k_sqerr<<<kSqerrBlocks, 256, 0, st>>>(a, nq, u, i, y, partials, counts, err);
+  k_sum_partials<<<1, 512, 0, st>>>(partials, counts, kSqerrBlocks, out);
   return cudaGetLastError();
 }
 

@@ -1,11 +1,14 @@
 """Multi-GPU helpers for the block-SVD path (host side).
 
 Blocks are independent on this path: a block's factorisation needs only its
-own ratings. So blocks shard across ranks with no data exchange. The only
-cross-rank reductions are the held-out error (the RMSE of Section 5 sums
-squared errors over every block's held-out ratings) and the benchmark's
-max-over-ranks time. Everything here uses torch.distributed collectives on
-whatever backend the caller initialised (NCCL on GPUs, gloo on CPUs).
+own ratings. So blocks shard across ranks with no data exchange: each rank
+holds its longest-processing-time share of the blocks (bsvd_set_owned), and
+the library partitions and factorises only those. The only cross-rank
+reductions are the held-out error (the RMSE of Section 5 sums squared
+errors over every block's held-out ratings: one all-reduce of the sum and
+the count) and the benchmark's max-over-ranks time. Everything here uses
+torch.distributed collectives on whatever backend the caller initialised
+(NCCL on GPUs, gloo on CPUs).
 """
 from __future__ import annotations
 
@@ -38,6 +41,13 @@ def assign_blocks(costs, world: int) -> list:
     return [sorted(p) for p in parts]
 
 
+def owned_mask(costs, world: int, rank: int):
+    """This rank's blocks under assign_blocks, as a 0/1 list (one flag per
+    block) for Context.set_owned."""
+    mine = set(assign_blocks(costs, world)[rank])
+    return [1 if b in mine else 0 for b in range(len(costs))]
+
+
 def _device(group=None):
     backend = torch.distributed.get_backend(group)
     return torch.device("cuda", torch.cuda.current_device()) \
@@ -62,3 +72,11 @@ def rmse_from_parts(sqerr_sum: float, count: int, group=None) -> float:
     if total == 0:
         raise ValueError("RMSE of an empty set")
     return math.sqrt(float(s.item()) / total)
+
+
+def sharded_rmse(ctx, u, i, y, group=None) -> float:
+    """RMSE over all ranks' held-out ratings: each rank sums the squared
+    errors of the queries in its own blocks (Context.sqerr), then one
+    all-reduce combines the sums and the counts."""
+    s, n = ctx.sqerr(u, i, y)
+    return rmse_from_parts(s, n, group)

@@ -84,3 +84,72 @@ def test_assign_blocks_balances_and_covers():
     assert max(loads) <= (4 / 3 - 1 / 9) * max(sum(costs) / 3, max(costs)) + 1e-9
     with pytest.raises(ValueError):
         bdist.assign_blocks(costs, 0)
+
+
+def _gpu_worker(rank, world, port, out):
+    """One shard on cuda:0: the library holds and factorises this rank's
+    LPT share of the uneven workload's 32 blocks."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import paper_1907_07410_gb300 as bs
+        torch.cuda.set_device(0)
+        w = synth.UNEVEN
+        r = synth.generate(w)
+        ctx = bs.Context()
+        kw = ctx.quantile_grid(w.m, w.n, r.u_train, r.i_train, w.p, w.q)
+        rb, cb = kw["row_bounds"], kw["col_bounds"]
+        shapes = [(min(rb[b // w.q + 1] - rb[b // w.q],
+                       cb[b % w.q + 1] - cb[b % w.q]),
+                   max(rb[b // w.q + 1] - rb[b // w.q],
+                       cb[b % w.q + 1] - cb[b % w.q]))
+                  for b in range(w.p * w.q)]
+        mask = bdist.owned_mask(bdist.block_costs(shapes), world, rank)
+        ctx.set_owned(mask)
+        ctx.partition(w.m, w.n, r.u_train, r.i_train, r.x_train, w.p, w.q,
+                      **kw)
+        assert ctx.factor(w.k) == bs.OK
+        rmse = bdist.sharded_rmse(ctx, r.u_test, r.i_test, r.x_test)
+        mine = [b for b in range(w.p * w.q) if mask[b]]
+        sig = {b: ctx.get_block(b)["sigma"].tolist() for b in mine}
+        other = next(b for b in range(w.p * w.q) if not mask[b])
+        out[rank] = (mine, rmse, sig, ctx.get_block(other)["keff"])
+        ctx.close()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_sharded_library_on_one_gpu_with_gloo():
+    """Two gloo ranks share cuda:0, each factorising its own blocks through
+    libbsvd (no kernel of one rank waits on the other). Every block lands on
+    exactly one rank, each block's singular values equal the single-process
+    run's bit for bit, and the combined RMSE equals the single-process RMSE
+    within 1e-12."""
+    import paper_1907_07410_gb300 as bs
+    world = 2
+    port = _free_port()
+    manager = mp.get_context("spawn").Manager()
+    out = manager.dict()
+    mp.start_processes(_gpu_worker, args=(world, port, out), nprocs=world,
+                       join=True, start_method="spawn")
+    w = synth.UNEVEN
+    r = synth.generate(w)
+    ctx = bs.Context()
+    kw = ctx.quantile_grid(w.m, w.n, r.u_train, r.i_train, w.p, w.q)
+    ctx.partition(w.m, w.n, r.u_train, r.i_train, r.x_train, w.p, w.q, **kw)
+    assert ctx.factor(w.k) == bs.OK
+    want = ctx.rmse(r.u_test, r.i_test, r.x_test)
+    s_all, n_all = ctx.sqerr(r.u_test, r.i_test, r.x_test)
+    assert n_all == r.u_test.size
+    assert abs(np.sqrt(s_all / n_all) - want) <= 1e-15 * want
+    blocks = sorted(out[0][0] + out[1][0])
+    assert blocks == list(range(w.p * w.q))
+    for rank in range(world):
+        mine, rmse, sig, keff_other = out[rank]
+        assert abs(rmse - want) <= 1e-12
+        assert keff_other == 0
+        for b in mine:
+            assert sig[b] == ctx.get_block(b)["sigma"].tolist(), b
+    ctx.close()
