@@ -96,8 +96,17 @@ def fp32_alu_peak_tflops(peaks):
 
 
 def gram_flops(blocks):
-    """Algorithmic Gram work: 2 m_b n_b s_b flop per block (s = min side)."""
+    """Gram work as the survey counts it: 2 m_b n_b s_b flop per block
+    (s = min side), both triangles of the symmetric product."""
     return float(sum(2.0 * L * s * s for (s, L) in blocks))
+
+
+def gram_flops_min(blocks):
+    """The Gram's least dense work: its s (s + 1) / 2 distinct entries, 2 L
+    flop each (G is symmetric, and the kernels compute one triangle). The
+    rooflines use this count, so that no kernel can beat its bound by
+    exploiting the symmetry."""
+    return float(sum(float(L) * s * (s + 1) for (s, L) in blocks))
 
 
 def grid_bounds(w, gridkw):
@@ -554,6 +563,8 @@ def time_form(w, data, steps, warmup, flush, stream, owned=None, **cfg):
             phases[key].append(fac_ph[key])
         phases["predict"].append(ph["predict"])
     return dict(ctx=ctx, step_ms=step_ms, rmse=rm, status=status,
+                loop={1: "host-driven", 2: "CUDA graph, device-driven"}.get(
+                    ctx.loop_form(), "none"),
                 launches=ctx.kernel_launches() - launches0,
                 phases={k: statistics.mean(v) for k, v in phases.items()},
                 report=ctx.factor_report(full=True),
@@ -595,7 +606,7 @@ def step_roofline(w, r, shapes, keff, gram_path, step_s, peaks, peak_kind):
     projection in float32, 12 B plus two k-float factor rows per query).
     The eigen-solver's iterations are not counted."""
     cells = float(sum(s * L for (s, L) in shapes))
-    f_gram = gram_flops(shapes)
+    f_gram = gram_flops_min(shapes)
     f_proj = 2.0 * sum(s * L * min(keff, s) for (s, L) in shapes)
     f_pred = 2.0 * keff * r.u_test.size
     gram_operand = {1: 4, 2: 4, 3: 4, 4: 2}.get(gram_path, 4)
@@ -611,23 +622,25 @@ def step_roofline(w, r, shapes, keff, gram_path, step_s, peaks, peak_kind):
             "frac": t_roof / step_s, "algorithmic_flops": flops,
             "algorithmic_bytes": by, "tensor_ms": t_tc * 1e3,
             "hbm_ms": t_hbm * 1e3,
-            "note": "eigen-solver iterations excluded from the work; the "
-                    "exact Gram counts its float32 operand bytes"}
+            "note": "the Gram counted as its s(s+1)/2 distinct entries "
+                    "(2 L flop each); eigen-solver iterations excluded from "
+                    "the work; the exact Gram counts its float32 operand "
+                    "bytes"}
 
 
 def panel_roofline(w, shapes, rep, filter_ms, peaks, peak_kind):
     """The eigen-solver's panel products G X (k_gpanel_tc): algorithmic
     bytes per product = G once (4 s^2) + the panel in and out (4 s b each),
-    summed over the filter phase's products (the first product of each
-    block runs before the phase's events and is left out) and divided by
-    the phase's event time. b/2 flop per byte of G: far below the tensor
-    ridge, so the bound is bandwidth."""
+    summed over every product of every block and divided by the products'
+    own device time (the library sums each launch's span, first CTA start
+    to last CTA end, with the GPU's timer). b/2 flop per byte of G: far
+    below the tensor ridge, so the bound is bandwidth."""
     want = w.k + max(8, w.k // 2)
     bsub = 16 if want <= 16 else (32 if want <= 32 else 64)
     pflops = pbytes = 0.0
     nprod = 0
     for (s_b, L_b), prods in zip(shapes, rep["products"]):
-        n_f = max(int(prods) - 1, 0)
+        n_f = int(prods)
         b_b = min(bsub, s_b)
         pflops += n_f * 2.0 * s_b * s_b * b_b
         pbytes += n_f * (4.0 * s_b * s_b + 8.0 * s_b * b_b)
@@ -644,9 +657,9 @@ def panel_roofline(w, shapes, rep, filter_ms, peaks, peak_kind):
             "products": nprod, "algorithmic_bytes": pbytes,
             "tensor_tflops": tf,
             "tensor_frac_of_fp32_equivalent": tf / (tf32 / 3.0),
-            "note": "algorithmic bytes (G once, panel in and out) of the "
-                    "filter phase's block products over that phase's event "
-                    "time; tensor_tflops counts 2 s^2 b flops per product "
+            "note": "algorithmic bytes (G once, panel in and out) of all "
+                    "block products over the products' summed device time; "
+                    "tensor_tflops counts 2 s^2 b flops per product "
                     "against one third of the tf32 peak (0.5 x measured "
                     "bf16), as the kernel issues three tf32 products for "
                     "float32 accuracy"}
@@ -659,6 +672,7 @@ def form_summary(w, r, res, gold, steps):
     return {"value": w.p * w.q * steps / (total * 1e-3),
             "ms_per_step": total / steps, "steps": steps,
             "gram": GRAM_NAMES.get(res["gram_path"], "none"),
+            "eigen_loop": res["loop"],
             "rmse": res["rmse"], "rmse_oracle": g_rmse,
             "rmse_parity": (g_rmse is not None
                             and abs(res["rmse"] - g_rmse) <= 1e-4),
@@ -685,6 +699,9 @@ def main():
                     help="timed steps of each other form")
     ap.add_argument("--no-medium", action="store_true",
                     help="skip the medium-matrix leg")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default eigen-solver schedule instead of "
+                         "the autotuner's choice for this workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sgd", action="store_true",
                     help="skip the blocked-SGD leg (the paper's Algorithms 1-2)")
@@ -737,12 +754,23 @@ def main():
         from paper_1907_07410_gb300 import dist as bdist
         owned = bdist.owned_mask(bdist.block_costs(shapes), world, rank)
 
+    # ---- the solver schedule for this workload (autotuner, cached) -------
+    tuned = {"params": {}, "note": "default schedule (--no-autotune)"}
+    if not args.no_autotune and world == 1:
+        from paper_1907_07410_gb300 import autotune
+        with bs.Context() as gctx:
+            gkw = step_grid(gctx, w, data[0], data[1])
+        tuned = autotune.tune(w.m, w.n, w.p, w.q, w.k, *data, shapes,
+                              precision=prec[args.precision], grid=gkw,
+                              stream=stream)
+
     # ---- device-resident timed region (the main form) --------------------
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
     main_res = time_form(w, data, args.steps, args.warmup, flush, stream,
-                         owned, precision=prec[args.precision])
+                         owned, precision=prec[args.precision],
+                         **tuned["params"])
     barrier()
     clk = clocks.stop()
     ctx = main_res["ctx"]
@@ -795,16 +823,17 @@ def main():
     peaks, peak_kind = load_peaks()
     gold = golden(w)
     gflops = gram_flops(shapes)
+    gflops_min = gram_flops_min(shapes)
     gram_path = main_res["gram_path"]
     bound, gpeak, gsrc = gram_peak(gram_path, peaks, peak_kind)
     gram_ms = main_res["phases"]["gram"]
-    g_tf = gflops / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else 0.0
+    g_tf = gflops_min / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else 0.0
     # the ranks share the workload's blocks: all of them per step
     value = nblocks * args.steps / (total_ms * 1e-3)
     step_s = total_ms * 1e-3 / args.steps
     proj_flops = 2.0 * sum(L * s * min(w.k, s) for (s, L) in shapes)
     pred_flops = 2.0 * w.k * r.u_test.size
-    tflops = (gflops + proj_flops + pred_flops) / step_s / 1e12
+    tflops = (gflops_min + proj_flops + pred_flops) / step_s / 1e12
     main_sum = form_summary(w, r, main_res, gold, args.steps)
     line = {
         "metric": "block SVDs/s", "value": value, "unit": "block-SVDs/s",
@@ -817,7 +846,10 @@ def main():
                 "inputs in HBM)",
         "config": bench_config(w, r),
         "path": {"precision": args.precision,
-                 "gram": GRAM_NAMES.get(gram_path, "none")},
+                 "gram": GRAM_NAMES.get(gram_path, "none"),
+                 "eigen_loop": main_res["loop"],
+                 "schedule": tuned["params"] or "default"},
+        "autotune": {k: v for k, v in tuned.items() if k != "trials"},
         "latency_ms": {"p50": float(np.percentile(main_res["step_ms"], 50)),
                        "p99": float(np.percentile(main_res["step_ms"], 99))},
         "tflops": tflops,
@@ -835,8 +867,12 @@ def main():
                           "frac": g_tf / gpeak,
                           "traffic": profiled_traffic(
                               GRAM_KERNELS.get(gram_path), w.name),
-                          "algorithmic_flops_per_launch": gflops,
-                          "peak_source": gsrc},
+                          "algorithmic_flops_per_launch": gflops_min,
+                          "full_product_flops": gflops,
+                          "peak_source": gsrc,
+                          "note": "algorithmic flops: the symmetric Gram's "
+                                  "distinct entries, L s (s+1) per block "
+                                  "(half of 2 L s^2 plus the diagonal)"},
         "forms": {name: form_summary(w, r, res, gold, args.form_steps)
                   for name, res in forms.items()},
         "gpu_launches": int(main_res["launches"]),
@@ -852,12 +888,19 @@ def main():
     if world == 1 and not args.no_medium and w.name != synth.MEDIUM.name:
         wm = synth.MEDIUM
         rm_ = synth.generate(wm)
-        res = time_form(wm, device_data(rm_), args.steps,
-                        args.warmup, flush, stream,
-                        precision=prec[args.precision])
+        dm = device_data(rm_)
+        mparams = {}
+        if not args.no_autotune:
+            from paper_1907_07410_gb300 import autotune
+            mparams = autotune.tune(wm.m, wm.n, wm.p, wm.q, wm.k, *dm,
+                                    block_shapes(wm), stream=stream,
+                                    precision=prec[args.precision])["params"]
+        res = time_form(wm, dm, args.steps, args.warmup, flush, stream,
+                        precision=prec[args.precision], **mparams)
         res["ctx"].close()
         line["medium"] = dict(form_summary(wm, rm_, res, golden(wm),
-                                           args.steps), workload=wm.name)
+                                           args.steps), workload=wm.name,
+                              schedule=mparams or "default")
     if world == 1 and not args.no_cpu_baseline:
         cores = min(os.cpu_count() or 1, nblocks)
         value_cpu, dt, pick, frac = oracle_sample(w, r, cores)

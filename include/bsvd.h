@@ -101,7 +101,13 @@ typedef struct {
                              the projection F_L = W^T F_s:
                              0: tensor cores (three tf32 passes, float32
                              accuracy); 1: FP32 SIMT */
-    int32_t reserved;     /* must be 0 */
+    int32_t loop;         /* eigen loop: 0 (default) device-driven from
+                             the second bsvd_factor of a block layout on
+                             (one CUDA graph whose loop a kernel ends; the
+                             first factorisation of a layout runs the
+                             host-driven loop, since a layout seen once
+                             may never repeat); 1 always host-driven
+                             (per-step phase times); 2 always the graph */
 } bsvd_config;
 
 /* Fill *cfg with the defaults listed above. */
@@ -353,6 +359,13 @@ int64_t bsvd_kernel_launches(const bsvd_ctx *ctx);
  * bf16), 0 none yet (or k = 0), -1 for a NULL context.
  */
 int32_t bsvd_gram_path(const bsvd_ctx *ctx);
+
+/*
+ * How the last bsvd_factor ran its eigen loop: 1 host-driven, 2 one CUDA
+ * graph with the loop decided on the device (see bsvd_config.loop), 0 no
+ * factorisation yet, -1 for a NULL context.
+ */
+int32_t bsvd_loop_form(const bsvd_ctx *ctx);
 
 /*
  * ---- The paper's own method: blocked SGD (Algorithms 1-2) ----------------

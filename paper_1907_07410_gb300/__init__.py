@@ -33,7 +33,7 @@ EXPORTS = ("bsvd_config_default", "bsvd_create", "bsvd_destroy",
            "bsvd_gram_path", "bsvd_partition_diag", "bsvd_factor_ks",
            "bsvd_sgd_params_default", "bsvd_sgd_prepare", "bsvd_sgd_train",
            "bsvd_sgd_predict", "bsvd_sgd_get", "bsvd_quantile_grid",
-           "bsvd_set_owned", "bsvd_sqerr")
+           "bsvd_set_owned", "bsvd_sqerr", "bsvd_loop_form")
 
 
 class BsvdError(RuntimeError):
@@ -51,7 +51,7 @@ class Config(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("gram_path", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("panel_path", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("loop", ctypes.c_int32)]
 
 
 class SgdParams(ctypes.Structure):
@@ -112,6 +112,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "bsvd_quantile_grid": (i32, [vp, i64, i64, i64, vp, vp, i32, i32, vp,
                                      vp, vp, vp]),
         "bsvd_set_owned": (i32, [vp, i32, vp]),
+        "bsvd_loop_form": (i32, [vp]),
         "bsvd_sqerr": (i32, [vp, i64, vp, vp, vp,
                              ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_int64)]),
@@ -375,6 +376,10 @@ def bsvd_gram_path(ctx) -> int:
     return int(load().bsvd_gram_path(ctx))
 
 
+def bsvd_loop_form(ctx) -> int:
+    return int(load().bsvd_loop_form(ctx))
+
+
 PHASES = ("partition", "gram", "eigen", "project", "predict", "eigen_filter",
           "eigen_rr", "eigen_other")
 
@@ -590,6 +595,11 @@ class Context:
 
     def gram_path(self) -> int:
         return bsvd_gram_path(self.handle)
+
+    def loop_form(self) -> int:
+        """1: the last factor ran its eigen loop from the host; 2: as one
+        CUDA graph decided on the device."""
+        return bsvd_loop_form(self.handle)
 
     # ---- the paper's blocked SGD (Algorithms 1-2) ------------------------
     def sgd_prepare(self, u, i, x):

@@ -121,6 +121,21 @@ struct bsvd_ctx {
   int32_t n_pjtiles = 0;
   // finalisation: per-tile column statistics of F_L and F_s, column flips
   DevBuf d_lpart, d_spart, d_flip;
+  // the persistent panel products' tile counter, and the CTAs they launch
+  DevBuf d_pctl;
+  int32_t nsm = 1;
+  // panel products' device time: [0] summed launch durations (ns), [1] the
+  // running launch's start; the graph loop's step counter
+  DevBuf d_ptime, d_loopctl;
+  // the device-driven form: the captured graph, the layout key it was built
+  // for, the key of this and of the previous factorisation, kernel counts
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap = nullptr, side = nullptr, side2 = nullptr;  // capture
+  std::vector<unsigned char> gkey_now, gkey_prev, gkey_exec;
+  bool graph_failed = false, capturing = false;
+  std::string graph_err;     // why the graph could not be built
+  int64_t graph_static_launches = 0, graph_loop_launches = 0;
+  int32_t last_graph = 0;   // last factor's loop: 0 none, 1 host, 2 graph
   // the BF16 form's projection: maps over the bf16 blocks and over F_s's
   // bf16 B form, and that B form
   DevBuf d_pbmaps, d_fbmaps, d_FB;
@@ -238,7 +253,11 @@ bsvd_status read_errors(bsvd_ctx *c, const char *what) {
 
 // Phase events: mark(i) records event i on the stream when profiling.
 void mark(bsvd_ctx *c, int i) {
-  if (c->cfg.profile && c->ev[i]) cudaEventRecord(c->ev[i], c->st);
+  if (!c->cfg.profile || !c->ev[i]) return;
+  if (c->capturing)   // an event-record node of the graph
+    cudaEventRecordWithFlags(c->ev[i], c->st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(c->ev[i], c->st);
 }
 
 // After a synchronised call: phase_ms[ph] = time between events a and b.
@@ -266,6 +285,195 @@ int32_t subspace_width(int32_t k, int32_t oversample) {
   return 64;
 }
 
+// The panel products' device timer: no time summed yet, no launch running.
+cudaError_t reset_ptime(bsvd_ctx *c) {
+  cudaError_t e = cudaMemsetAsync(c->d_ptime.p, 0, sizeof(unsigned long long),
+                                  c->st);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(c->d_ptime.as<unsigned long long>() + 1, 0xFF,
+                         sizeof(unsigned long long), c->st);
+}
+
+// Capture one factorisation into c->gexec: pre, then a conditional WHILE
+// node whose body is one Rayleigh-Ritz step, k_loopctl (which sets the
+// condition from the number of blocks still iterating) and one full-degree
+// filter, then post. The body is captured on a second stream into the
+// node's body graph. Kernel counts: graph_static_launches per graph launch
+// outside the loop, graph_loop_launches per loop step.
+template <class Pre, class Rr, class Step, class Prod, class Post>
+cudaError_t build_graph(bsvd_ctx *c, Pre &pre, Rr &rr, Step &fstep,
+                        Prod &fprod, Post &post) {
+  cudaGraph_t g = nullptr;
+  cudaError_t r = cudaGraphCreate(&g, 0);
+  if (r != cudaSuccess) return r;
+  // capture on the context's own streams (the caller's stream may be the
+  // legacy default stream, which cannot be captured); the graph is then
+  // launched on the caller's stream
+  for (cudaStream_t *sp : {&c->cap, &c->side, &c->side2}) {
+    if (!*sp) {
+      r = cudaStreamCreateWithFlags(sp, cudaStreamNonBlocking);
+      if (r != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return r;
+      }
+    }
+  }
+  const cudaStream_t user_st = c->st;
+  const cudaStream_t st = c->cap;
+  c->st = st;
+  const int64_t l0 = c->launches;
+  int64_t l1 = 0, l2 = 0;
+  c->capturing = true;
+  // the first failing step names itself in graph_err
+  auto note = [&](const char *what, cudaError_t e) {
+    if (e != cudaSuccess && c->graph_err.empty())
+      c->graph_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e;
+  };
+  r = note("begin capture", cudaStreamBeginCaptureToGraph(
+                                st, g, nullptr, nullptr, 0,
+                                cudaStreamCaptureModeThreadLocal));
+  const bool main_open = r == cudaSuccess;
+  if (r == cudaSuccess) r = note("Gram and start", pre());
+  if (r == cudaSuccess)
+    r = note("loop counter", cudaMemsetAsync(c->d_loopctl.p, 0,
+                                              2 * sizeof(int32_t), st));
+  if (r == cudaSuccess) {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaGraph_t cg = nullptr;
+    r = note("capture info", cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg,
+                                                      &deps, nullptr, &nd));
+    cudaGraphConditionalHandle h = 0;
+    if (r == cudaSuccess)
+      r = note("conditional handle",
+               cudaGraphConditionalHandleCreate(&h, cg, 1,
+                                                cudaGraphCondAssignDefault));
+    // zeroed storage: the struct's union has no default constructor
+    alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+    std::memset(npbuf, 0, sizeof npbuf);
+    cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(npbuf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t cnode = nullptr;
+    if (r == cudaSuccess)
+      r = note("conditional node",
+               cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &np));
+    if (r == cudaSuccess)
+      r = note("capture dependencies",
+               cudaStreamUpdateCaptureDependencies(
+                   st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    if (r == cudaSuccess) {
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      c->st = c->side;
+      l1 = c->launches;
+      r = note("begin body capture",
+               cudaStreamBeginCaptureToGraph(c->side, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+      if (r == cudaSuccess) {
+        // filter steps 3 .. cheb_degree each sit in an IF node that
+        // k_loopctl opens when some running block's degree reaches the step
+        const int deg = c->cfg.cheb_degree;
+        LoopHandles lh;
+        std::memset(&lh, 0, sizeof lh);
+        lh.first = 3;
+        lh.n = deg >= 3 ? deg - 2 : 0;
+        cudaError_t rb = cudaSuccess;
+        for (int j = 0; j < lh.n && rb == cudaSuccess; ++j)
+          rb = note("step handle", cudaGraphConditionalHandleCreate(
+                                       &lh.h[j], body, 0,
+                                       cudaGraphCondAssignDefault));
+        if (rb == cudaSuccess) rb = note("Rayleigh-Ritz step", rr());
+        if (rb == cudaSuccess) {
+          rb = note("loop control",
+                    launch_loopctl(c->d_running.as<int32_t>(),
+                                   c->d_loopctl.as<int32_t>(),
+                                   c->cfg.max_iters + 2, h, lh, c->side));
+          ++c->launches;
+        }
+        for (int j = 1; j <= std::min(deg, 2) && rb == cudaSuccess; ++j)
+          rb = note("filter step", fstep(j));
+        for (int j = 3; j <= deg && rb == cudaSuccess; ++j) {
+          cudaStreamCaptureStatus bs;
+          const cudaGraphNode_t *bdeps = nullptr;
+          size_t bnd = 0;
+          cudaGraph_t bg = nullptr;
+          rb = note("body capture info",
+                    cudaStreamGetCaptureInfo(c->side, &bs, nullptr, &bg, &bdeps,
+                                             nullptr, &bnd));
+          alignas(cudaGraphNodeParams) unsigned char ibuf[sizeof(cudaGraphNodeParams)];
+          std::memset(ibuf, 0, sizeof ibuf);
+          cudaGraphNodeParams &ip = *reinterpret_cast<cudaGraphNodeParams *>(ibuf);
+          ip.type = cudaGraphNodeTypeConditional;
+          ip.conditional.handle = lh.h[j - 3];
+          ip.conditional.type = cudaGraphCondTypeIf;
+          ip.conditional.size = 1;
+          cudaGraphNode_t inode = nullptr;
+          if (rb == cudaSuccess)
+            rb = note("step node",
+                      cudaGraphAddNode(&inode, bg, bdeps, nullptr, bnd, &ip));
+          if (rb == cudaSuccess)
+            rb = note("body dependencies",
+                      cudaStreamUpdateCaptureDependencies(
+                          c->side, &inode, nullptr, 1,
+                          cudaStreamSetCaptureDependencies));
+          if (rb == cudaSuccess) {
+            const cudaStream_t body_st = c->st;
+            c->st = c->side2;
+            rb = note("begin step capture",
+                      cudaStreamBeginCaptureToGraph(
+                          c->side2, ip.conditional.phGraph_out[0], nullptr,
+                          nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            if (rb == cudaSuccess) {
+              const cudaError_t rs = note("filter step", fstep(j));
+              cudaGraph_t sout = nullptr;
+              const cudaError_t re2 = note(
+                  "end step capture", cudaStreamEndCapture(c->side2, &sout));
+              rb = rs != cudaSuccess ? rs : re2;
+            }
+            c->st = body_st;
+          }
+        }
+        if (rb == cudaSuccess) rb = note("product", fprod());
+        cudaGraph_t bout = nullptr;
+        const cudaError_t re =
+            note("end body capture", cudaStreamEndCapture(c->side, &bout));
+        r = rb != cudaSuccess ? rb : re;
+      }
+      l2 = c->launches;
+      c->st = st;
+    }
+  }
+  if (r == cudaSuccess) r = note("projection", post());
+  c->st = user_st;
+  if (main_open) {
+    cudaGraph_t gout = nullptr;
+    const cudaError_t re = note("end capture", cudaStreamEndCapture(st, &gout));
+    if (r == cudaSuccess) r = re;
+  }
+  c->capturing = false;
+  if (r != cudaSuccess && c->graph_err.empty())
+    c->graph_err = std::string("capture: ") + cudaGetErrorString(r);
+  if (r == cudaSuccess) {
+    r = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (r != cudaSuccess)
+      c->graph_err = std::string("instantiate: ") + cudaGetErrorString(r);
+  }
+  cudaGraphDestroy(g);
+  const int64_t l3 = c->launches;
+  c->launches = l0;                 // captured, not run
+  // the filter steps inside IF nodes are counted as the loop opens them
+  const int64_t cond = c->cfg.cheb_degree >= 3
+                           ? (int64_t)(c->cfg.cheb_degree - 2) * (c->n_rowtiles > 0)
+                           : 0;
+  c->graph_loop_launches = l2 - l1 - cond;
+  c->graph_static_launches = (l3 - l0) - (l2 - l1);
+  return r;
+}
+
 }  // namespace
 
 extern "C" {
@@ -285,7 +493,7 @@ void bsvd_config_default(bsvd_config *cfg) {
   cfg->seed = 0x5eed5eedull;
   cfg->stream = nullptr;
   cfg->panel_path = 0;
-  cfg->reserved = 0;
+  cfg->loop = 0;
 }
 
 bsvd_status bsvd_create(const bsvd_config *cfg, bsvd_ctx **out) {
@@ -306,7 +514,7 @@ bsvd_status bsvd_create(const bsvd_config *cfg, bsvd_ctx **out) {
        c->cfg.precision != BSVD_BF16) ||
       c->cfg.gram_path < 0 ||
       c->cfg.gram_path > 2 || c->cfg.panel_path < 0 ||
-      c->cfg.panel_path > 1 || c->cfg.reserved != 0 ||
+      c->cfg.panel_path > 1 || c->cfg.loop < 0 || c->cfg.loop > 2 ||
       c->cfg.cheb_degree % 2 != 0 ||
       c->cfg.cheb_degree > 64 || (c->cfg.clamp && !(c->cfg.clamp_lo <= c->cfg.clamp_hi))) {
     delete c;
@@ -314,6 +522,8 @@ bsvd_status bsvd_create(const bsvd_config *cfg, bsvd_ctx **out) {
   }
   c->st = static_cast<cudaStream_t>(c->cfg.stream);
   if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount,
+                             c->device) != cudaSuccess ||
       c->d_err.ensure(sizeof(int32_t)) != cudaSuccess ||
       cudaMemsetAsync(c->d_err.p, 0, sizeof(int32_t), c->st) != cudaSuccess ||
       cudaStreamSynchronize(c->st) != cudaSuccess) {
@@ -351,9 +561,14 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->d_sgd_Q, &c->d_sgd_bu, &c->d_sgd_bi, &c->d_sgd_sum,
                     &c->d_qcnt, &c->d_qkeys, &c->d_qcum, &c->d_qperm,
                     &c->d_qbounds, &c->d_pbmaps, &c->d_fbmaps, &c->d_FB,
-                    &c->d_lpart, &c->d_spart, &c->d_flip};
+                    &c->d_lpart, &c->d_spart, &c->d_flip, &c->d_pctl,
+                    &c->d_ptime, &c->d_loopctl};
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->side2) cudaStreamDestroy(c->side2);
   for (DevBuf *b : bufs) b->release();
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
@@ -703,6 +918,7 @@ bsvd_status bsvd_quantile_grid(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
 
 static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks);
 
+
 bsvd_status bsvd_factor(bsvd_ctx *c, int32_t k) {
   return factor_impl(c, k, nullptr);
 }
@@ -733,6 +949,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
                 "offsets from their block's rounded mean");
   c->factored = false;
   c->any_capped = false;
+  c->last_graph = 0;
   c->k = k;
   c->bsub = subspace_width(k, c->cfg.oversample);
   c->kp = (int32_t)std::max<int64_t>(4, round_up(k, 4));
@@ -819,6 +1036,10 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
   CK(c->d_spart.ensure(sizeof(ColPartial) * kp *
                        std::max<size_t>(pt.size(), 1)), "factor");
   CK(c->d_flip.ensure((size_t)kp * std::max(nb, 1)), "factor");
+  CK(c->d_pctl.ensure(2 * sizeof(int32_t)), "factor");
+  CK(cudaMemsetAsync(c->d_pctl.p, 0, 2 * sizeof(int32_t), c->st), "factor");
+  CK(c->d_ptime.ensure(2 * sizeof(unsigned long long)), "factor");
+  CK(c->d_loopctl.ensure(2 * sizeof(int32_t)), "factor");
   const bool tc_maps = panel_tc && !pt.empty();
   if (tc_maps) {
     CK(c->d_gmaps.ensure(sizeof(CUtensorMap) * nb), "factor");
@@ -1048,9 +1269,11 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
                                 (in == e.X ? 0 : (size_t)nb);
         float *out_bf = out == e.X ? c->d_XB.as<float>() : c->d_ZB.as<float>();
         return launch_gpanel_tc(B, e.meta, e.state, c->d_ptiles.as<int2>(),
-                                c->n_ptiles, c->d_gmaps.as<CUtensorMap>(), xm,
-                                in, in2, out, out_bf, mode, step,
-                                c->d_err.as<int32_t>(), c->st);
+                                c->n_ptiles, c->nsm, c->d_pctl.as<int32_t>(),
+                                c->d_ptime.as<unsigned long long>(),
+                                c->d_gmaps.as<CUtensorMap>(), xm, in, in2, out,
+                                out_bf, mode, step, c->d_err.as<int32_t>(),
+                                c->st);
       }
       return launch_gpanel(e, rtd, nrt, mode, step, deg, in, in2, out, c->st);
     };
@@ -1064,137 +1287,229 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
 
     std::fill(c->phase_ms + 1, c->phase_ms + 4, 0.0);
     std::fill(c->phase_ms + 5, c->phase_ms + 8, 0.0);
-    mark(c, 0);
     c->gram_used = c->cfg.precision == BSVD_TF32   ? 3
                    : c->cfg.precision == BSVD_BF16 ? 4
                    : (c->tc_planes && c->tc_exact) ? 2
                                                    : 1;
-    if (c->gram_used == 4) {
-      CK(launch_gram_bf16(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
-                          c->n_gtiles, c->d_maps.as<CUtensorMap>(), e.G,
-                          c->d_err.as<int32_t>(), c->st),
-         "factor: gram (bf16 tensor cores)");
-    } else if (c->gram_used == 3) {
-      CK(launch_gram_tf32(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
-                          c->n_gtiles, c->d_wmaps.as<CUtensorMap>(), e.G,
-                          c->d_err.as<int32_t>(), c->st),
-         "factor: gram (tf32 tensor cores)");
-    } else if (c->gram_used == 2) {
-      CK(launch_gram_tc(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
-                        c->n_gtiles, c->d_maps.as<CUtensorMap>(),
-                        c->d_delta.as<float>(), e.G, c->d_err.as<int32_t>(),
-                        c->st), "factor: gram (tensor cores)");
-    } else {
-      CK(launch_gram_f32(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
-                         c->n_gtiles, c->d_W.as<float>(), e.G, c->st),
-         "factor: gram");
-    }
-    mark(c, 1);
-    CK(launch_init_panels(e, rtd, nrt, c->st), "factor: init");
-    CK(bform_x(), "factor: B form");
-    CK(panel(0, 0, 0, e.X, nullptr, e.Z), "factor: G X");
-    c->launches += (c->n_gtiles > 0) + 2 * (nrt > 0);
-    for (int it = 0; it <= c->cfg.max_iters + 1; ++it) {
-      mark(c, 6);
-      CK(launch_small_gram(e, rtd, nrt, c->st), "factor: rr gram");
-      CK(launch_rr_solve(e, c->st), "factor: rr solve");
-      CK(launch_rotate(e, rtd, nrt, c->st), "factor: rotate");
+    // The device work of one factorisation, in four parts: the Gram, the
+    // start basis and its first product (pre); one Rayleigh-Ritz step (rr);
+    // one Chebyshev filter of degree deg and the product that follows it
+    // (filter); the projection and the finalisation (post). Each returns
+    // the first error and counts its kernels in c->launches.
+    auto pre = [&]() -> cudaError_t {
+      cudaError_t r = cudaSuccess;
+      mark(c, 0);
+      if (c->gram_used == 4)
+        r = launch_gram_bf16(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
+                             c->n_gtiles, c->d_maps.as<CUtensorMap>(), e.G,
+                             c->d_err.as<int32_t>(), c->st);
+      else if (c->gram_used == 3)
+        r = launch_gram_tf32(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
+                             c->n_gtiles, c->d_wmaps.as<CUtensorMap>(), e.G,
+                             c->d_err.as<int32_t>(), c->st);
+      else if (c->gram_used == 2)
+        r = launch_gram_tc(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
+                           c->n_gtiles, c->d_maps.as<CUtensorMap>(),
+                           c->d_delta.as<float>(), e.G, c->d_err.as<int32_t>(),
+                           c->st);
+      else
+        r = launch_gram_f32(c->d_meta.as<BlockMeta>(), c->d_gtiles.as<int4>(),
+                            c->n_gtiles, c->d_W.as<float>(), e.G, c->st);
+      if (r != cudaSuccess) return r;
+      mark(c, 1);
+      if ((r = launch_init_panels(e, rtd, nrt, c->st)) != cudaSuccess) return r;
+      if ((r = bform_x()) != cudaSuccess) return r;
+      if ((r = panel(0, 0, 0, e.X, nullptr, e.Z)) != cudaSuccess) return r;
+      c->launches += (c->n_gtiles > 0) + 2 * (nrt > 0);
+      return cudaSuccess;
+    };
+    auto rr = [&]() -> cudaError_t {
+      cudaError_t r;
+      if ((r = launch_small_gram(e, rtd, nrt, c->st)) != cudaSuccess) return r;
+      if ((r = launch_rr_solve(e, c->st)) != cudaSuccess) return r;
+      if ((r = launch_rotate(e, rtd, nrt, c->st)) != cudaSuccess) return r;
       // k_rotate clears the running counters that k_check fills
-      if (nrt == 0)
-        CK(cudaMemsetAsync(e.running, 0, 2 * sizeof(int32_t), c->st), "factor");
-      CK(launch_check(e, c->st), "factor: check");
-      mark(c, 7);
+      if (nrt == 0 &&
+          (r = cudaMemsetAsync(e.running, 0, 2 * sizeof(int32_t), c->st)) !=
+              cudaSuccess)
+        return r;
+      if ((r = launch_check(e, c->st)) != cudaSuccess) return r;
       c->launches += 2 + 2 * (nrt > 0);
-      // The counters reach the host through mapped pinned memory, written
-      // by k_publish; this thread polls the sequence word. That avoids a
-      // copy and a stream synchronisation per step. If the word does not
-      // arrive within kPollMs (an error, or a very slow step), the stream
-      // synchronisation below waits and reports any error.
-      if (!c->h_run) {
-        CK(cudaHostAlloc(&c->h_run, 4 * sizeof(int32_t), cudaHostAllocMapped),
-           "factor");
-        c->h_run[2] = 0;
-        CK(cudaHostGetDevicePointer(&c->d_run_host, c->h_run, 0), "factor");
+      return cudaSuccess;
+    };
+    // Chebyshev filter of even degree: Y_1 -> Z, Y_2 -> X, ..., Y_d -> X;
+    // step j reads Y_{j-1}, Y_{j-2} and overwrites Y_{j-2} with Y_j. A block
+    // whose own degree is lower skips the later steps, so its Y_d is in X.
+    auto fstep = [&](int j) -> cudaError_t {
+      const bool even = j % 2 == 0;
+      const float *in = even ? e.Z : e.X;
+      const float *in2 = j == 1 ? nullptr : (even ? e.X : e.Z);
+      float *out = even ? e.X : e.Z;
+      c->launches += (nrt > 0);
+      return panel(j == 1 ? 1 : 2, j, 0, in, in2, out);
+    };
+    auto fprod = [&]() -> cudaError_t {
+      c->launches += (nrt > 0);
+      return panel(0, 0, 0, e.X, nullptr, e.Z);
+    };
+    auto filter = [&](int deg) -> cudaError_t {
+      cudaError_t r;
+      for (int j = 1; j <= deg; ++j)
+        if ((r = fstep(j)) != cudaSuccess) return r;
+      return fprod();
+    };
+    auto post = [&]() -> cudaError_t {
+      cudaError_t r;
+      mark(c, 2);
+      if (proj16) {
+        // F_L from the bf16 blocks, F_s split into bf16 hi and lo
+        if ((r = launch_bform_fs16(e.meta, c->d_ptiles.as<int2>(), c->n_ptiles,
+                                   e.Fs, kp, kn, c->d_FB.as<__nv_bfloat16>(),
+                                   c->st)) != cudaSuccess)
+          return r;
+        if ((r = launch_project_bf16(e.meta, c->d_pjtiles.as<int2>(),
+                                     c->n_pjtiles, c->d_pbmaps.as<CUtensorMap>(),
+                                     c->d_fbmaps.as<CUtensorMap>(),
+                                     c->d_FL.as<float>(), kp, kn,
+                                     c->d_err.as<int32_t>(), c->st)) !=
+            cudaSuccess)
+          return r;
+        c->launches += (c->n_ptiles > 0);
+      } else if (panel_tc) {
+        // F_s's split form goes into X's B-form buffer, free after the loop,
+        // and is read through X's maps
+        if ((r = launch_bform_fs(B, e.meta, c->d_ptiles.as<int2>(),
+                                 c->n_ptiles, e.Fs, kp, c->d_XB.as<float>(),
+                                 c->st)) != cudaSuccess)
+          return r;
+        if ((r = launch_project_tc(B, e.meta, c->d_pjtiles.as<int2>(),
+                                   c->n_pjtiles, c->d_pwmaps.as<CUtensorMap>(),
+                                   c->d_xmaps.as<CUtensorMap>(),
+                                   c->d_FL.as<float>(), kp,
+                                   c->d_err.as<int32_t>(), c->st)) !=
+            cudaSuccess)
+          return r;
+        c->launches += (c->n_ptiles > 0);
+      } else {
+        if ((r = launch_project(c->d_meta.as<BlockMeta>(),
+                                c->d_ltiles.as<int2>(), c->n_ltiles,
+                                c->d_W.as<float>(), e.Fs, c->d_FL.as<float>(),
+                                kp, c->st)) != cudaSuccess)
+          return r;
       }
-      const int32_t seq = ++c->run_seq;
-      CK(launch_publish(e.running, c->d_run_host, seq, c->st), "factor: publish");
-      ++c->launches;
-      {
-        volatile int32_t *hr = c->h_run;
-        const auto t0 = std::chrono::steady_clock::now();
-        bool seen = false;
-        for (uint32_t spin = 0;; ++spin) {
-          if (hr[2] == seq) { seen = true; break; }
-          if ((spin & 1023u) == 0 &&
-              std::chrono::steady_clock::now() - t0 >
-                  std::chrono::milliseconds(kPollMs))
-            break;
+      if ((r = launch_finalize(c->d_meta.as<BlockMeta>(), nb,
+                               c->d_pjtiles.as<int2>(), c->n_pjtiles,
+                               c->d_ptiles.as<int2>(), c->n_ptiles, e.Fs,
+                               c->d_FL.as<float>(), c->d_sigma.as<double>(), kp,
+                               c->d_lpart.as<ColPartial>(),
+                               c->d_spart.as<ColPartial>(),
+                               c->d_flip.as<unsigned char>(), &c->launches,
+                               c->st)) != cudaSuccess)
+        return r;
+      c->launches += (c->n_ltiles > 0);
+      mark(c, 3);
+      return cudaSuccess;
+    };
+
+    // Device-driven form: the same kernels captured once per layout into a
+    // CUDA graph whose eigen loop is a conditional WHILE node; k_loopctl
+    // decides on the device whether another step runs, so no step waits on
+    // the host. The first factorisation of a layout runs the host-driven
+    // loop below (a layout seen once may never repeat, and capturing costs
+    // about as much as a run); from the second on, the graph.
+    {
+      std::vector<unsigned char> key = c->fsig;
+      const int64_t extra[4] = {c->gram_used, k, B, kp};
+      const unsigned char *eb = reinterpret_cast<const unsigned char *>(extra);
+      key.insert(key.end(), eb, eb + sizeof extra);
+      const void *bufs[] = {c->d_meta.p, c->d_state.p, c->d_G.p, c->d_X.p,
+                            c->d_Z.p, c->d_SH.p, c->d_RP.p, c->d_T.p,
+                            c->d_theta.p, c->d_Fs.p, c->d_FL.p, c->d_sigma.p,
+                            c->d_running.p, c->d_err.p, c->d_maps.p,
+                            c->d_delta.p, c->d_wmaps.p, c->d_pctl.p,
+                            c->d_ptime.p, c->d_loopctl.p};
+      const unsigned char *pb = reinterpret_cast<const unsigned char *>(bufs);
+      key.insert(key.end(), pb, pb + sizeof bufs);
+      c->gkey_now.swap(key);
+    }
+    const bool key_seen = c->gkey_now == c->gkey_prev;
+    const int loop = c->cfg.loop;
+    const bool want_graph = loop == 2 || (loop == 0 && key_seen);
+    bool ran_graph = false;
+    if (want_graph && !c->graph_failed) {
+      if (!c->gexec || c->gkey_now != c->gkey_exec) {
+        if (c->gexec) {
+          cudaGraphExecDestroy(c->gexec);
+          c->gexec = nullptr;
         }
-        if (!seen) CK(cudaStreamSynchronize(c->st), "factor");
-        std::atomic_thread_fence(std::memory_order_acquire);
+        c->graph_err.clear();
+        if (build_graph(c, pre, rr, fstep, fprod, post) != cudaSuccess) {
+          cudaGetLastError();
+          c->graph_failed = true;     // keep to the host-driven loop
+          if (loop == 2)
+            return fail(c, BSVD_ECUDA, "factor: the eigen loop's graph could "
+                        "not be built (%s)", c->graph_err.c_str());
+        } else {
+          c->gkey_exec = c->gkey_now;
+        }
       }
-      const int32_t run_deg[2] = {c->h_run[0], c->h_run[1]};
-      if (c->cfg.profile) {
-        float ms = 0.f;
-        if (it > 0 && cudaEventElapsedTime(&ms, c->ev[8], c->ev[9]) == cudaSuccess)
-          c->phase_ms[5] += ms;
-        if (cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]) == cudaSuccess)
-          c->phase_ms[6] += ms;
-        cudaGetLastError();
+      if (c->gexec) {
+        CK(reset_ptime(c), "factor");
+        CK(cudaGraphLaunch(c->gexec, c->st), "factor: graph");
+        c->launches += c->graph_static_launches;
+        ran_graph = true;
       }
-      if (run_deg[0] == 0) break;
-      const int deg = std::min(c->cfg.cheb_degree, std::max(2, run_deg[1]));
-      // Chebyshev filter of even degree: Y_1 -> Z, Y_2 -> X, ..., Y_d -> X
-      // step j reads Y_{j-1}, Y_{j-2} and overwrites Y_{j-2} with Y_j
-      mark(c, 8);
-      for (int j = 1; j <= deg; ++j) {
-        const bool even = j % 2 == 0;
-        const float *in = even ? e.Z : e.X;
-        const float *in2 = j == 1 ? nullptr : (even ? e.X : e.Z);
-        float *out = even ? e.X : e.Z;
-        CK(panel(j == 1 ? 1 : 2, j, deg, in, in2, out), "factor: filter");
-      }
-      CK(panel(0, 0, 0, e.X, nullptr, e.Z), "factor: G X");
-      mark(c, 9);
-      c->launches += (deg + 1) * (nrt > 0);
     }
-    mark(c, 2);
-    if (proj16) {
-      // F_L from the bf16 blocks, F_s split into bf16 hi and lo
-      CK(launch_bform_fs16(e.meta, c->d_ptiles.as<int2>(), c->n_ptiles, e.Fs,
-                           kp, kn, c->d_FB.as<__nv_bfloat16>(), c->st),
-         "factor: bf16 B form of F_s");
-      CK(launch_project_bf16(e.meta, c->d_pjtiles.as<int2>(), c->n_pjtiles,
-                             c->d_pbmaps.as<CUtensorMap>(),
-                             c->d_fbmaps.as<CUtensorMap>(),
-                             c->d_FL.as<float>(), kp, kn,
-                             c->d_err.as<int32_t>(), c->st),
-         "factor: project (bf16 tensor cores)");
-      c->launches += (c->n_ptiles > 0);
-    } else if (panel_tc) {
-      // F_s's split form goes into X's B-form buffer, free after the loop,
-      // and is read through X's maps
-      CK(launch_bform_fs(B, e.meta, c->d_ptiles.as<int2>(), c->n_ptiles, e.Fs,
-                         kp, c->d_XB.as<float>(), c->st), "factor: B form of F_s");
-      CK(launch_project_tc(B, e.meta, c->d_pjtiles.as<int2>(), c->n_pjtiles,
-                           c->d_pwmaps.as<CUtensorMap>(),
-                           c->d_xmaps.as<CUtensorMap>(), c->d_FL.as<float>(),
-                           kp, c->d_err.as<int32_t>(), c->st),
-         "factor: project (tensor cores)");
-      c->launches += (c->n_ptiles > 0);
-    } else {
-      CK(launch_project(c->d_meta.as<BlockMeta>(), c->d_ltiles.as<int2>(),
-                        c->n_ltiles, c->d_W.as<float>(), e.Fs,
-                        c->d_FL.as<float>(), kp, c->st), "factor: project");
+    if (!ran_graph) {
+      CK(reset_ptime(c), "factor");
+      CK(pre(), "factor: Gram and start");
+      for (int it = 0; it <= c->cfg.max_iters + 1; ++it) {
+        mark(c, 6);
+        CK(rr(), "factor: Rayleigh-Ritz");
+        mark(c, 7);
+        // The counters reach the host through mapped pinned memory, written
+        // by k_publish; this thread polls the sequence word. That avoids a
+        // copy and a stream synchronisation per step. If the word does not
+        // arrive within kPollMs (an error, or a very slow step), the stream
+        // synchronisation below waits and reports any error.
+        if (!c->h_run) {
+          CK(cudaHostAlloc(&c->h_run, 4 * sizeof(int32_t), cudaHostAllocMapped),
+             "factor");
+          c->h_run[2] = 0;
+          CK(cudaHostGetDevicePointer(&c->d_run_host, c->h_run, 0), "factor");
+        }
+        const int32_t seq = ++c->run_seq;
+        CK(launch_publish(e.running, c->d_run_host, seq, c->st),
+           "factor: publish");
+        ++c->launches;
+        {
+          volatile int32_t *hr = c->h_run;
+          const auto t0 = std::chrono::steady_clock::now();
+          bool seen = false;
+          for (uint32_t spin = 0;; ++spin) {
+            if (hr[2] == seq) { seen = true; break; }
+            if ((spin & 1023u) == 0 &&
+                std::chrono::steady_clock::now() - t0 >
+                    std::chrono::milliseconds(kPollMs))
+              break;
+          }
+          if (!seen) CK(cudaStreamSynchronize(c->st), "factor");
+          std::atomic_thread_fence(std::memory_order_acquire);
+        }
+        const int32_t run_deg[2] = {c->h_run[0], c->h_run[1]};
+        if (c->cfg.profile) {
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]) == cudaSuccess)
+            c->phase_ms[6] += ms;
+          cudaGetLastError();
+        }
+        if (run_deg[0] == 0) break;
+        CK(filter(std::min(c->cfg.cheb_degree, std::max(2, run_deg[1]))),
+           "factor: filter");
+      }
+      CK(post(), "factor: projection");
     }
-    CK(launch_finalize(c->d_meta.as<BlockMeta>(), nb, c->d_pjtiles.as<int2>(),
-                       c->n_pjtiles, c->d_ptiles.as<int2>(), c->n_ptiles, e.Fs,
-                       c->d_FL.as<float>(), c->d_sigma.as<double>(), kp,
-                       c->d_lpart.as<ColPartial>(), c->d_spart.as<ColPartial>(),
-                       c->d_flip.as<unsigned char>(), &c->launches, c->st),
-       "factor: finalize");
-    c->launches += (c->n_ltiles > 0);
-    mark(c, 3);
+    c->gkey_prev = c->gkey_now;
     std::vector<SolverState> fin(nb);
     CK(cudaMemcpyAsync(fin.data(), c->d_state.p, sizeof(SolverState) * nb,
                        cudaMemcpyDeviceToHost, c->st), "factor");
@@ -1204,7 +1519,28 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     take(c, 1, 0, 1);
     take(c, 2, 1, 2);
     take(c, 3, 2, 3);
-    // host time inside the eigen phase: what neither products nor RR cover
+    {
+      // the panel products' own time (summed over launches on the device),
+      // and in graph form the loop's kernel count
+      unsigned long long pt[2] = {0, 0};
+      int32_t loops[2] = {0, 0};
+      CK(cudaMemcpyAsync(pt, c->d_ptime.p, sizeof pt, cudaMemcpyDeviceToHost,
+                         c->st), "factor");
+      if (ran_graph)
+        CK(cudaMemcpyAsync(loops, c->d_loopctl.p, sizeof loops,
+                           cudaMemcpyDeviceToHost, c->st), "factor");
+      CK(cudaStreamSynchronize(c->st), "factor");
+      c->phase_ms[5] = (double)pt[0] * 1e-6;
+      // loop steps times their unconditional kernels, plus the filter
+      // steps the loop control opened
+      if (ran_graph)
+        c->launches += (int64_t)loops[0] * c->graph_loop_launches +
+                       (int64_t)loops[1] * (c->n_rowtiles > 0 ? 1 : 0);
+      c->last_graph = ran_graph ? 2 : 1;
+    }
+    // in graph form the Rayleigh-Ritz kernels are not timed on their own:
+    // what the eigen phase spends outside the products
+    if (ran_graph) c->phase_ms[6] = std::max(0.0, c->phase_ms[2] - c->phase_ms[5]);
     c->phase_ms[7] = std::max(0.0, c->phase_ms[2] - c->phase_ms[5] - c->phase_ms[6]);
   }
   CK(cudaStreamSynchronize(c->st), "factor");
@@ -1507,6 +1843,8 @@ int64_t bsvd_kernel_launches(const bsvd_ctx *c) {
 }
 
 int32_t bsvd_gram_path(const bsvd_ctx *c) { return c ? c->gram_used : -1; }
+
+int32_t bsvd_loop_form(const bsvd_ctx *c) { return c ? c->last_graph : -1; }
 
 // ---- blocked SGD (Algorithms 1-2) ----------------------------------------
 

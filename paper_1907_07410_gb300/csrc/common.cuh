@@ -34,6 +34,13 @@ __device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// The GPU's global nanosecond timer.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // x rounded to the nearest value with 10 mantissa bits, ties away from 0
 // (exact in tf32): the "hi" part of the split x = hi + lo that the tensor-
 // core kernels use, lo = x - hi exactly.

@@ -107,9 +107,16 @@ struct EigBuffers {
 // 2 x_off: for each 32-row chunk, bsub rows of hi(P) then bsub rows of
 // lo(P), 32 floats each (hi = P rounded to 10 mantissa bits, lo = P - hi).
 // out_bf (optional) receives the B form of `out`.
+// Persistent: nctas CTAs (one per SM) take the tiles of the running blocks
+// from the counter ctl[0] (ctl: 2 ints, zero before the first launch; the
+// kernel leaves them zero). ptime[0] gains the launch's span in ns (first
+// CTA start to last CTA end); ptime[1] must hold ~0 before the first launch
+// (the kernel leaves it so).
 cudaError_t launch_gpanel_tc(int32_t bsub, const BlockMeta *meta,
                              SolverState *state, const int2 *tiles,
-                             int32_t ntiles, const CUtensorMap *gmaps,
+                             int32_t ntiles, int32_t nctas, int32_t *ctl,
+                             unsigned long long *ptime,
+                             const CUtensorMap *gmaps,
                              const CUtensorMap *xmaps, const float *in,
                              const float *in2, float *out, float *out_bf,
                              int mode, int step, int32_t *err,
@@ -166,6 +173,18 @@ cudaError_t launch_rr_solve(const EigBuffers &e, cudaStream_t st);
 cudaError_t launch_rotate(const EigBuffers &e, const int2 *rowtiles,
                           int32_t ntiles, cudaStream_t st);
 cudaError_t launch_check(const EigBuffers &e, cudaStream_t st);
+// The IF nodes of filter steps first .. first + n - 1.
+struct LoopHandles {
+  cudaGraphConditionalHandle h[62];
+  int32_t first, n;
+};
+// The device-driven loop's decisions, after a Rayleigh-Ritz step: one more
+// step while blocks are still iterating and ++count[0] < max; filter step
+// first + j runs when some running block's degree (running[1]) reaches it.
+// count[1] sums the steps opened.
+cudaError_t launch_loopctl(const int32_t *running, int32_t *count,
+                           int32_t max, cudaGraphConditionalHandle handle,
+                           const LoopHandles &steps, cudaStream_t st);
 // Copies running[0..1] to host-mapped memory `host` (device pointer), then
 // writes `seq` to host[2], so a host thread that sees seq in host[2] reads
 // the counters of this step.

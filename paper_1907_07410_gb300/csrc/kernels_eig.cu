@@ -1032,6 +1032,31 @@ __global__ void k_publish(const int32_t *__restrict__ running,
   host[2] = seq;
 }
 
+__global__ void k_loopctl(const int32_t *__restrict__ running,
+                          int32_t *count, int32_t max,
+                          cudaGraphConditionalHandle handle, LoopHandles steps) {
+  pdl_wait();
+  if (threadIdx.x == 0) {
+    const int32_t it = ++count[0];
+    const bool any = running[0] > 0;
+    cudaGraphSetConditional(handle, (any && it < max) ? 1u : 0u);
+    int32_t opened = 0;
+    for (int j = 0; j < steps.n; ++j) {
+      const bool go = any && running[1] >= steps.first + j;
+      cudaGraphSetConditional(steps.h[j], go ? 1u : 0u);
+      opened += go;
+    }
+    count[1] += opened;
+  }
+}
+
+cudaError_t launch_loopctl(const int32_t *running, int32_t *count,
+                           int32_t max, cudaGraphConditionalHandle handle,
+                           const LoopHandles &steps, cudaStream_t st) {
+  k_loopctl<<<1, 32, 0, st>>>(running, count, max, handle, steps);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_publish(const int32_t *running, int32_t *host, int32_t seq,
                            cudaStream_t st) {
   return launch_pdl(k_publish, dim3(1), dim3(1), 0, st, running,

@@ -102,12 +102,18 @@ struct PanelTc {
   static_assert(STAGES <= kMaxStages && STAGES >= kSlots, "ring sizes");
 };
 
+constexpr int kTq = 4;                   // tile-index ring of the products
+
 struct PanelCtrl {
   uint64_t full[kMaxStages];    // G tile and rows of `in` landed (TMA bytes)
   uint64_t empty[kMaxStages];   // the stage's MMAs completed
   uint64_t ready[kSlots];       // A slot written (the 8 converter warps)
   uint64_t afree[kSlots];       // the MMAs reading the A slot completed
-  uint64_t done;                // every MMA completed
+  uint64_t done;                // a tile's MMAs completed (one phase a tile)
+  uint64_t accfree;             // the epilogue read the accumulators (4 warps)
+  uint64_t tfull[kTq];          // tile index published (the producer)
+  uint64_t tempty[kTq];         // tile index read (warps 1-9)
+  int tq[kTq];                  // tile indices, -1 ends the launch
   uint32_t tmem;
   int abort;
   int issued;                   // stages whose loads were issued
@@ -156,10 +162,29 @@ __device__ __forceinline__ void acc_sum(uint32_t taddr, uint32_t col,
   }
 }
 
+// True when tile `t`'s block takes part in this product: still iterating,
+// and (for a filter step) its own filter reaches this step.
+__device__ __forceinline__ bool tile_active(const SolverState *state, int2 t,
+                                            int mode, int step) {
+  const SolverState &st = state[t.x];
+  return st.status == kRunning && !(mode >= 1 && step > st.degree);
+}
+
+// Persistent: one CTA per SM. CTA i starts with tile i (if its block is
+// still iterating), then takes tiles from gridDim.x on from a shared
+// counter (ctl[0]; ctl[1] counts finished CTAs, and the last one resets
+// both for the next launch). A claimed tile of an idle block moves the
+// counter past the rest of that block. Warp 0 claims tiles, publishes their
+// indices in a small ring (tq) and loads their stages; the stage, A-slot and
+// tile counters run on across tiles, so a CTA sets up its barriers and
+// tensor memory once per launch and the loads of the next tile overlap the
+// epilogue of the last. The MMA warp starts a tile only after the epilogue
+// warps have read the previous tile's accumulators (accfree).
 template <int B>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
-            const int2 *__restrict__ tiles, const CUtensorMap *__restrict__ gmaps,
+            const int2 *__restrict__ tiles, int ntiles, int *ctl,
+            unsigned long long *ptime, const CUtensorMap *__restrict__ gmaps,
             const CUtensorMap *__restrict__ xmaps, const float *in,
             const float *in2, float *out, float *out_bf, int mode, int step,
             int32_t *err) {
@@ -170,19 +195,6 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   PanelCtrl &ct = *reinterpret_cast<PanelCtrl *>(base + S * L::STAGE);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int2 t = tiles[blockIdx.x];
-  const SolverState st = state[t.x];
-  // uniform over the CTA, before any barrier or TMEM is touched
-  if (st.status != kRunning) return;
-  if (mode >= 1 && step > st.degree) return;
-  const BlockMeta bm = meta[t.x];
-  const int sp = bm.s_pad, row0 = t.y;
-  if (row0 == 0 && threadIdx.x == 0) atomicAdd(&state[t.x].products, 1);
-  // s_pad is a multiple of 32: a last half stage reads zeros past s_pad
-  const int nk = (sp + PK - 1) / PK;
-  const float *inb = in + bm.x_off;
-  float alpha, beta, gamma;
-  cheb_coeffs(st, mode, step, &alpha, &beta, &gamma);
 
   auto g_tile = [&](int s) { return base + s * L::STAGE; };
   auto b_op = [&](int s) { return base + s * L::STAGE + G_BYTES; };
@@ -197,7 +209,12 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
       tc::mbar_init(&ct.ready[a], kConv);
       tc::mbar_init(&ct.afree[a], 1);
     }
+    for (int q = 0; q < kTq; ++q) {
+      tc::mbar_init(&ct.tfull[q], 1);
+      tc::mbar_init(&ct.tempty[q], 9);
+    }
     tc::mbar_init(&ct.done, 1);
+    tc::mbar_init(&ct.accfree, 4);
     ct.abort = 0;
     ct.issued = 0;
     ct.consumed = 0;
@@ -206,193 +223,291 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  // everything above reads only what kernels before the previous one wrote
-  // (tiles, meta, the solver state); the panels need the previous product
+  // everything below reads what the previous kernels wrote: the solver
+  // state (which blocks run), the panels and the tile counter's reset
   pdl_wait();
+  if (threadIdx.x == 0) atomicMin(&ptime[1], globaltimer_ns());
   const uint32_t taddr = ct.tmem;
   const uint32_t aslots = taddr + L::ACC_COLS;    // A slot a at +128 a
   volatile int *abort_flag = &ct.abort;
 
+  // consumers (warps 1-9): the next tile index from the ring, -1 at the end
+  auto next_tile = [&](int &got, int &idx) -> bool {
+    const int q = got % kTq;
+    const bool ok = __all_sync(
+        0xffffffffu,
+        tc::mbar_wait(&ct.tfull[q], (got / kTq) & 1, kSpinP) && !*abort_flag);
+    if (!ok) {
+      if (lane == 0) atomicOr(err, kErrTimeout);
+      ct.abort = 1;
+      return false;
+    }
+    idx = *reinterpret_cast<volatile int *>(&ct.tq[q]);
+    __syncwarp();
+    if (lane == 0) tc::mbar_arrive(&ct.tempty[q]);
+    ++got;
+    return idx >= 0;
+  };
+
   if (warp == 0) {
     // the whole warp runs the loop (warp-uniform addresses); one lane issues
-    const CUtensorMap *map = gmaps + t.x;
-    const CUtensorMap *xmap = xmaps + t.x;
-    for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % S;
-      const uint32_t ph = (kc / S) & 1;
-      const bool ok = __all_sync(
-          0xffffffffu,
-          tc::mbar_wait(&ct.empty[s], ph ^ 1, kSpinP) && !*abort_flag);
+    int g = 0, pub = 0;
+    const int first = (int)gridDim.x;     // tiles below this: one per CTA
+    for (;;) {
+      int idx = -1;
+      if (lane == 0) {
+        // the CTA's own tile first, with no atomic; then the counter, which
+        // numbers the tiles from gridDim.x on
+        if (pub == 0 && (int)blockIdx.x < ntiles &&
+            tile_active(state, tiles[blockIdx.x], mode, step)) {
+          idx = (int)blockIdx.x;
+        } else {
+          for (;;) {
+            const int i = first + atomicAdd(&ctl[0], 1);
+            if (i >= ntiles) break;
+            const int2 ti = tiles[i];
+            if (tile_active(state, ti, mode, step)) { idx = i; break; }
+            // the block is idle: move the counter past its other tiles (a
+            // block's tiles are consecutive in the list)
+            const BlockMeta &bx = meta[ti.x];
+            atomicMax(&ctl[0], bx.pt0 + bx.npt - first);
+          }
+        }
+      }
+      idx = __shfl_sync(0xffffffffu, idx, 0);
+      const int q = pub % kTq;
+      bool ok = __all_sync(0xffffffffu,
+                           tc::mbar_wait(&ct.tempty[q], ((pub / kTq) & 1) ^ 1,
+                                         kSpinP) && !*abort_flag);
       if (!ok) {
         if (lane == 0) atomicOr(err, kErrTimeout);
         ct.abort = 1;
         break;
       }
-      if (tc::elect_one()) {
-        const int k0 = kc * PK;
-        tc::mbar_expect_tx(&ct.full[s], G_BYTES + L::BOP_BYTES);
-        tc::tma_load_2d(g_tile(s), map, k0, row0, &ct.full[s]);
-        tc::tma_load_2d(g_tile(s) + G_HALF, map, k0 + PH, row0, &ct.full[s]);
-        // B-form chunks 2 kc and 2 kc + 1 (past the last: zero fill)
-        tc::tma_load_2d(b_op(s), xmap, 0, 2 * kc * 2 * B, &ct.full[s]);
-        tc::tma_load_2d(b_op(s) + L::BOP_HALF, xmap, 0, (2 * kc + 1) * 2 * B,
-                        &ct.full[s]);
-        ct.issued = kc + 1;
+      if (lane == 0) {
+        ct.tq[q] = idx;
+        tc::mbar_arrive(&ct.tfull[q]);
       }
       __syncwarp();
+      ++pub;
+      if (idx < 0) break;
+      const int2 t = tiles[idx];
+      const BlockMeta bm = meta[t.x];
+      if (t.y == 0 && lane == 0) atomicAdd(&state[t.x].products, 1);
+      // s_pad is a multiple of 32: a last half stage reads zeros past s_pad
+      const int nk = (bm.s_pad + PK - 1) / PK;
+      const CUtensorMap *map = gmaps + t.x;
+      const CUtensorMap *xmap = xmaps + t.x;
+      for (int kc = 0; kc < nk; ++kc, ++g) {
+        const int s = g % S;
+        const uint32_t ph = (g / S) & 1;
+        ok = __all_sync(0xffffffffu,
+                        tc::mbar_wait(&ct.empty[s], ph ^ 1, kSpinP) &&
+                            !*abort_flag);
+        if (!ok) {
+          if (lane == 0) atomicOr(err, kErrTimeout);
+          ct.abort = 1;
+          break;
+        }
+        if (tc::elect_one()) {
+          const int k0 = kc * PK;
+          tc::mbar_expect_tx(&ct.full[s], G_BYTES + L::BOP_BYTES);
+          tc::tma_load_2d(g_tile(s), map, k0, t.y, &ct.full[s]);
+          tc::tma_load_2d(g_tile(s) + G_HALF, map, k0 + PH, t.y, &ct.full[s]);
+          // B-form chunks 2 kc and 2 kc + 1 (past the last: zero fill)
+          tc::tma_load_2d(b_op(s), xmap, 0, 2 * kc * 2 * B, &ct.full[s]);
+          tc::tma_load_2d(b_op(s) + L::BOP_HALF, xmap, 0,
+                          (2 * kc + 1) * 2 * B, &ct.full[s]);
+          ct.issued = g + 1;
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
     }
   } else if (warp == 1) {
     // the whole warp runs the loop (warp-uniform descriptors); one lane issues
     constexpr uint32_t idesc2 = tc::idesc_tf32_f32(PT, 2 * B);
     constexpr uint32_t idesc1 = tc::idesc_tf32_f32(PT, B);
-    for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % S, a = kc % kSlots;
-      const bool ok = __all_sync(
-          0xffffffffu, tc::mbar_wait(&ct.ready[a], (kc / kSlots) & 1, kSpinP) &&
-                           !*abort_flag);
+    int got = 0, idx = -1, gm = 0, tl = 0;
+    while (next_tile(got, idx)) {
+      const BlockMeta bm = meta[tiles[idx].x];
+      const int nk = (bm.s_pad + PK - 1) / PK;
+      bool ok = true;
+      if (tl > 0) {
+        // the previous tile's accumulators have been read
+        ok = __all_sync(0xffffffffu,
+                        tc::mbar_wait(&ct.accfree, (tl - 1) & 1, kSpinP) &&
+                            !*abort_flag);
+      }
+      for (int kc = 0; ok && kc < nk; ++kc, ++gm) {
+        const int s = gm % S, a = gm % kSlots;
+        ok = __all_sync(0xffffffffu,
+                        tc::mbar_wait(&ct.ready[a], (gm / kSlots) & 1, kSpinP) &&
+                            !*abort_flag);
+        if (!ok) break;
+        tc::fence_after_sync();
+        const uint64_t db0 = tc::sdesc_kmajor_sw128(tc::smem_u32(b_op(s)));
+        const uint64_t db1 =
+            tc::sdesc_kmajor_sw128(tc::smem_u32(b_op(s) + L::BOP_HALF));
+        const uint32_t ahi = aslots + 2 * PK * a, alo = ahi + PK;
+        if (tc::elect_one()) {
+          // K slice 8 kc + kk goes to accumulator kk mod R; the first R
+          // slices of a tile start their accumulators
+#pragma unroll
+          for (int kk = 0; kk < PK / 8; ++kk) {
+            const uint32_t d = taddr + 2 * B * (kk % L::R);
+            const uint64_t db = (kk < 4 ? db0 : db1) + 2 * (kk & 3);
+            const uint32_t acc = (kc > 0 || kk >= L::R) ? 1u : 0u;
+            // [G_hi in_hi | G_hi in_lo], then G_lo in_hi onto the cross half
+            tc::mma_tf32_ta(d, ahi + 8 * kk, db, idesc2, acc);
+            tc::mma_tf32_ta(d + B, alo + 8 * kk, db, idesc1, 1u);
+          }
+          tc::mma_commit(&ct.empty[s]);
+          tc::mma_commit(&ct.afree[a]);
+        }
+        __syncwarp();
+      }
       if (!ok) {
         if (lane == 0) atomicOr(err, kErrTimeout);
         ct.abort = 1;
         break;
       }
-      tc::fence_after_sync();
-      const uint64_t db0 = tc::sdesc_kmajor_sw128(tc::smem_u32(b_op(s)));
-      const uint64_t db1 =
-          tc::sdesc_kmajor_sw128(tc::smem_u32(b_op(s) + L::BOP_HALF));
-      const uint32_t ahi = aslots + 2 * PK * a, alo = ahi + PK;
-      if (tc::elect_one()) {
-        // K slice 8 kc + kk goes to accumulator kk mod R; the first R
-        // slices start their accumulators
-#pragma unroll
-        for (int kk = 0; kk < PK / 8; ++kk) {
-          const uint32_t d = taddr + 2 * B * (kk % L::R);
-          const uint64_t db = (kk < 4 ? db0 : db1) + 2 * (kk & 3);
-          const uint32_t acc = (kc > 0 || kk >= L::R) ? 1u : 0u;
-          // [G_hi in_hi | G_hi in_lo], then G_lo in_hi onto the cross half
-          tc::mma_tf32_ta(d, ahi + 8 * kk, db, idesc2, acc);
-          tc::mma_tf32_ta(d + B, alo + 8 * kk, db, idesc1, 1u);
-        }
-        tc::mma_commit(&ct.empty[s]);
-        tc::mma_commit(&ct.afree[a]);
-      }
+      if (tc::elect_one()) tc::mma_commit(&ct.done);
       __syncwarp();
+      ++tl;
     }
-    if (tc::elect_one()) tc::mma_commit(&ct.done);
-    __syncwarp();
   } else {
     // converters: warps 2-9. Warp w may touch TMEM lanes 32 (w mod 4) ..
     // +31, so two warps share each lane quarter: warps 2-5 split the first
-    // 32-float half of a stage's K range, warps 6-9 the second.
+    // 32-float half of a stage's K range, warps 6-9 the second. Warps 2-5
+    // also run each tile's epilogue.
     const int cid = threadIdx.x - 64;
     const int q = warp & 3;
     const int kh = (warp - 2) >> 2;
     const int r = q * 32 + lane;                  // G tile row of this thread
     const uint32_t lrow = (uint32_t)(q * 32) << 16;
-    for (int kc = 0; kc < nk; ++kc) {
-      const int s = kc % S, a = kc % kSlots;
-      const uint32_t ph = (kc / S) & 1;
-      // warp-uniform: every lane breaks, or none does
-      bool ok = tc::mbar_wait(&ct.full[s], ph, kSpinP);
-      if constexpr (L::kWaitSlot)
-        ok = ok && tc::mbar_wait(&ct.afree[a], ((kc / kSlots) & 1) ^ 1, kSpinP);
-      ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+    int got = 0, idx = -1, gc = 0, tl = 0;
+    while (next_tile(got, idx)) {
+      const int2 t = tiles[idx];
+      const BlockMeta bm = meta[t.x];
+      const int nk = (bm.s_pad + PK - 1) / PK;
+      bool ok = true;
+      for (int kc = 0; kc < nk; ++kc, ++gc) {
+        const int s = gc % S, a = gc % kSlots;
+        const uint32_t ph = (gc / S) & 1;
+        // warp-uniform: every lane breaks, or none does
+        ok = tc::mbar_wait(&ct.full[s], ph, kSpinP);
+        if constexpr (L::kWaitSlot)
+          ok = ok &&
+               tc::mbar_wait(&ct.afree[a], ((gc / kSlots) & 1) ^ 1, kSpinP);
+        ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+        if (!ok) break;
+        if (cid == 0) ct.consumed = gc + 1;
+        tc::fence_after_sync();
+        // this thread's row of its half of the G tile, split into hi and lo
+        {
+          const unsigned char *gt = g_tile(s) + kh * G_HALF;
+          float h[32], l[32];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float4 v = *reinterpret_cast<const float4 *>(gt + sw128(r, c));
+            const float4 vh = hi4(v), vl = sub4(v, vh);
+            h[4 * c + 0] = vh.x; h[4 * c + 1] = vh.y;
+            h[4 * c + 2] = vh.z; h[4 * c + 3] = vh.w;
+            l[4 * c + 0] = vl.x; l[4 * c + 1] = vl.y;
+            l[4 * c + 2] = vl.z; l[4 * c + 3] = vl.w;
+          }
+          const uint32_t ta = aslots + lrow + 2 * PK * a + PH * kh;
+          tc::tmem_st32(ta, h);
+          tc::tmem_st32(ta + PK, l);
+        }
+        tc::tmem_wait_st();
+        // order the tensor-memory stores before the MMAs
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&ct.ready[a]);
+      }
       if (!ok) {
         if (lane == 0) atomicOr(err, kErrTimeout);
         ct.abort = 1;
         break;
       }
-      if (cid == 0) ct.consumed = kc + 1;
-      tc::fence_after_sync();
-      // this thread's row of its half of the G tile, split into hi and lo
-      {
-        const unsigned char *g = g_tile(s) + kh * G_HALF;
-        float h[32], l[32];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const float4 v = *reinterpret_cast<const float4 *>(g + sw128(r, c));
-          const float4 vh = hi4(v), vl = sub4(v, vh);
-          h[4 * c + 0] = vh.x; h[4 * c + 1] = vh.y;
-          h[4 * c + 2] = vh.z; h[4 * c + 3] = vh.w;
-          l[4 * c + 0] = vl.x; l[4 * c + 1] = vl.y;
-          l[4 * c + 2] = vl.z; l[4 * c + 3] = vl.w;
+      if (warp < 6) {
+        // the tile's epilogue
+        ok = __all_sync(0xffffffffu,
+                        tc::mbar_wait(&ct.done, tl & 1, kSpinP) && !*abort_flag);
+        if (!ok) {
+          if (lane == 0) atomicOr(err, kErrTimeout);
+          ct.abort = 1;
+          break;
         }
-        const uint32_t ta = aslots + lrow + 2 * PK * a + PH * kh;
-        tc::tmem_st32(ta, h);
-        tc::tmem_st32(ta + PK, l);
+        tc::fence_after_sync();
+        const SolverState st = state[t.x];
+        float alpha, beta, gamma;
+        cheb_coeffs(st, mode, step, &alpha, &beta, &gamma);
+        const int sp = bm.s_pad;
+        const int rr = t.y + r;                  // output row
+        const float *inb = in + bm.x_off;
+        const float *in2b = in2 ? in2 + bm.x_off : nullptr;
+        float *outb = out + bm.x_off;
+        // B form of `out`: chunk rr / 32, position rr mod 32 (lanes of a
+        // warp hold 32 consecutive rows of one chunk: coalesced 128 bytes)
+        float *bfb = out_bf ? out_bf + 2 * bm.x_off +
+                                  (int64_t)(rr >> 5) * 2 * B * 32 + (rr & 31)
+                            : nullptr;
+        // a thread's row of `out` (and of in, in2) is contiguous: 16-byte
+        // accesses, 4 columns each
+        auto finish = [&](const float *main, const float *cross, int c0,
+                          int ncol) {
+          const int64_t o0 = (int64_t)rr * B + c0;
+#pragma unroll
+          for (int c4 = 0; c4 < ncol / 4; ++c4) {
+            float y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              y[u] = alpha * (main[4 * c4 + u] + cross[4 * c4 + u]);
+            if (beta != 0.f) {
+              const float4 x = *reinterpret_cast<const float4 *>(inb + o0 + 4 * c4);
+              y[0] = fmaf(beta, x.x, y[0]); y[1] = fmaf(beta, x.y, y[1]);
+              y[2] = fmaf(beta, x.z, y[2]); y[3] = fmaf(beta, x.w, y[3]);
+            }
+            if (gamma != 0.f) {
+              const float4 x = *reinterpret_cast<const float4 *>(in2b + o0 + 4 * c4);
+              y[0] = fmaf(gamma, x.x, y[0]); y[1] = fmaf(gamma, x.y, y[1]);
+              y[2] = fmaf(gamma, x.z, y[2]); y[3] = fmaf(gamma, x.w, y[3]);
+            }
+            *reinterpret_cast<float4 *>(outb + o0 + 4 * c4) =
+                make_float4(y[0], y[1], y[2], y[3]);
+            if (bfb) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int c = c0 + 4 * c4 + u;
+                const float yh = hi1(y[u]);
+                bfb[c * 32] = yh;
+                bfb[(B + c) * 32] = __fsub_rn(y[u], yh);
+              }
+            }
+          }
+        };
+#pragma unroll 1
+        for (int c0 = 0; c0 < B; c0 += 16) {
+          float v[16], w[16];
+          acc_sum<B>(taddr + lrow, c0, v);        // main halves
+          acc_sum<B>(taddr + lrow, B + c0, w);    // cross halves
+          if (rr < sp) finish(v, w, c0, 16);
+        }
+        // the accumulators may be overwritten by the next tile's MMAs
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&ct.accfree);
       }
-      tc::tmem_wait_st();
-      // order the tensor-memory stores before the MMAs
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&ct.ready[a]);
+      ++tl;
     }
   }
   __syncwarp();
-
-  // the next product may be scheduled now; it waits for this grid to
+  // the next kernel may be scheduled now; it waits for this grid to
   // complete before it reads a panel
   pdl_trigger();
-  if (warp >= 2 && warp < 6) {
-    const bool ready =
-        __all_sync(0xffffffffu, tc::mbar_wait(&ct.done, 0, kSpinP));
-    if (!ready && lane == 0) atomicOr(err, kErrTimeout);
-    // tcgen05.ld is warp-collective: decide for the whole warp
-    const bool go = __all_sync(0xffffffffu, ready && !*abort_flag);
-    if (go) {
-      tc::fence_after_sync();
-      const int q = warp & 3;                 // TMEM lane quarter of this warp
-      const int r = row0 + q * 32 + lane;     // output row
-      const uint32_t lrow = (uint32_t)(q * 32) << 16;
-      const float *in2b = in2 ? in2 + bm.x_off : nullptr;
-      float *outb = out + bm.x_off;
-      // B form of `out`: chunk r / 32, position r mod 32 (lanes of a warp
-      // hold 32 consecutive rows of one chunk: coalesced rows of 128 bytes)
-      float *bfb = out_bf ? out_bf + 2 * bm.x_off + (int64_t)(r >> 5) * 2 * B * 32 +
-                                (r & 31)
-                          : nullptr;
-      // a thread's row of `out` (and of in, in2) is contiguous: 16-byte
-      // accesses, 4 columns each
-      auto finish = [&](const float *main, const float *cross, int c0,
-                        int ncol) {
-        const int64_t o0 = (int64_t)r * B + c0;
-#pragma unroll
-        for (int c4 = 0; c4 < ncol / 4; ++c4) {
-          float y[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            y[u] = alpha * (main[4 * c4 + u] + cross[4 * c4 + u]);
-          if (beta != 0.f) {
-            const float4 x = *reinterpret_cast<const float4 *>(inb + o0 + 4 * c4);
-            y[0] = fmaf(beta, x.x, y[0]); y[1] = fmaf(beta, x.y, y[1]);
-            y[2] = fmaf(beta, x.z, y[2]); y[3] = fmaf(beta, x.w, y[3]);
-          }
-          if (gamma != 0.f) {
-            const float4 x = *reinterpret_cast<const float4 *>(in2b + o0 + 4 * c4);
-            y[0] = fmaf(gamma, x.x, y[0]); y[1] = fmaf(gamma, x.y, y[1]);
-            y[2] = fmaf(gamma, x.z, y[2]); y[3] = fmaf(gamma, x.w, y[3]);
-          }
-          *reinterpret_cast<float4 *>(outb + o0 + 4 * c4) =
-              make_float4(y[0], y[1], y[2], y[3]);
-          if (bfb) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int c = c0 + 4 * c4 + u;
-              const float yh = hi1(y[u]);
-              bfb[c * 32] = yh;
-              bfb[(B + c) * 32] = __fsub_rn(y[u], yh);
-            }
-          }
-        }
-      };
-#pragma unroll 1
-      for (int c0 = 0; c0 < B; c0 += 16) {
-        float v[16], w[16];
-        acc_sum<B>(taddr + lrow, c0, v);        // main halves
-        acc_sum<B>(taddr + lrow, B + c0, w);    // cross halves
-        if (r < sp) finish(v, w, c0, 16);
-      }
-    }
-  }
   tc::fence_before_sync();
   __syncthreads();
   if (threadIdx.x == 0 && ct.abort) {
@@ -400,13 +515,30 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
     for (int kc = ct.consumed; kc < ct.issued; ++kc)
       tc::mbar_wait(&ct.full[kc % S], (kc / S) & 1, kSpinP);
   }
+  if (threadIdx.x == 0) {
+    // the last CTA out resets the tile counter for the next launch
+    __threadfence();
+    if (atomicAdd(&ctl[1], 1) == (int)gridDim.x - 1) {
+      // and adds this launch's span (first start to last end) to ptime[0]
+      // (the two dies' timers may differ by a little: a negative span of a
+      // very short launch counts as 0)
+      const unsigned long long t0 = atomicAdd(&ptime[1], 0ull);
+      const unsigned long long t1 = globaltimer_ns();
+      if (t1 > t0 && t0 != ~0ull) atomicAdd(&ptime[0], t1 - t0);
+      atomicExch(&ptime[1], ~0ull);
+      atomicExch(&ctl[0], 0);
+      atomicExch(&ctl[1], 0);
+      __threadfence();
+    }
+  }
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(taddr, kTmemCols);
 }
 
 template <int B>
 cudaError_t launch_b(const BlockMeta *meta, SolverState *state,
-                     const int2 *tiles, int32_t ntiles,
+                     const int2 *tiles, int32_t ntiles, int32_t nctas, int *ctl,
+                     unsigned long long *ptime,
                      const CUtensorMap *gmaps, const CUtensorMap *xmaps,
                      const float *in, const float *in2, float *out,
                      float *out_bf, int mode, int step, int32_t *err,
@@ -418,9 +550,10 @@ cudaError_t launch_b(const BlockMeta *meta, SolverState *state,
   if (e != cudaSuccess) return e;
   // programmatic dependent launch: this grid's prologue may overlap the end
   // of the previous kernel in the stream (see pdl_wait)
-  return launch_pdl(k_gpanel_tc<B>, dim3((unsigned)ntiles), dim3(kThreads),
-                    panel_tc_smem<B>(), st, meta, state, tiles, gmaps, xmaps,
-                    in, in2, out, out_bf, mode, step, err);
+  return launch_pdl(k_gpanel_tc<B>, dim3((unsigned)nctas), dim3(kThreads),
+                    panel_tc_smem<B>(), st, meta, state, tiles, (int)ntiles,
+                    ctl, ptime, gmaps, xmaps, in, in2, out, out_bf, mode, step,
+                    err);
 }
 
 // F_L = W^T F_s on the tensor cores, with the panel product's data path and
@@ -686,19 +819,26 @@ k_bform(const BlockMeta *__restrict__ meta, const SolverState *__restrict__ stat
 
 cudaError_t launch_gpanel_tc(int32_t bsub, const BlockMeta *meta,
                              SolverState *state, const int2 *tiles,
-                             int32_t ntiles, const CUtensorMap *gmaps,
+                             int32_t ntiles, int32_t nctas, int32_t *ctl,
+                             unsigned long long *ptime,
+                             const CUtensorMap *gmaps,
                              const CUtensorMap *xmaps, const float *in,
                              const float *in2, float *out, float *out_bf,
                              int mode, int step, int32_t *err,
                              cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
+  nctas = nctas < ntiles ? nctas : ntiles;
+  if (nctas < 1) nctas = 1;
   switch (bsub) {
-    case 16: return launch_b<16>(meta, state, tiles, ntiles, gmaps, xmaps, in,
-                                 in2, out, out_bf, mode, step, err, st);
-    case 32: return launch_b<32>(meta, state, tiles, ntiles, gmaps, xmaps, in,
-                                 in2, out, out_bf, mode, step, err, st);
-    case 64: return launch_b<64>(meta, state, tiles, ntiles, gmaps, xmaps, in,
-                                 in2, out, out_bf, mode, step, err, st);
+    case 16: return launch_b<16>(meta, state, tiles, ntiles, nctas, ctl, ptime,
+                                 gmaps, xmaps, in, in2, out, out_bf, mode, step,
+                                 err, st);
+    case 32: return launch_b<32>(meta, state, tiles, ntiles, nctas, ctl, ptime,
+                                 gmaps, xmaps, in, in2, out, out_bf, mode, step,
+                                 err, st);
+    case 64: return launch_b<64>(meta, state, tiles, ntiles, nctas, ctl, ptime,
+                                 gmaps, xmaps, in, in2, out, out_bf, mode, step,
+                                 err, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -378,3 +378,40 @@ def test_sign_convention_matches_oracle():
                 assert np.max(np.abs(col - f.V[:, j])) <= 1e-3, (b, j)
                 checked += 1
     assert checked >= 8
+
+
+@pytest.mark.parametrize("workload", [synth.SMALL, synth.MEDIUM_8x8])
+def test_device_driven_loop_matches_host_loop(workload):
+    """The eigen loop captured in one CUDA graph (a conditional WHILE node
+    that a kernel ends) gives bit-identical factors to the host-driven loop:
+    loop = 0 runs the host loop on a layout's first factorisation and the
+    graph from the second on; loop = 2 always the graph; loop = 1 never."""
+    w = workload
+    r = synth.generate(w)
+
+    def run(loop, times):
+        ctx = bs.Context(loop=loop)
+        forms = []
+        for _ in range(times):
+            ctx.partition(r.m, r.n, dev(r.u_train), dev(r.i_train),
+                          dev(r.x_train), w.p, w.q)
+            assert ctx.factor(w.k) == bs.OK
+            forms.append(ctx.loop_form())
+        sig = [ctx.get_block(b)["sigma"] for b in range(w.p * w.q)]
+        y = ctx.predict(r.u_test, r.i_test)
+        rm = ctx.rmse(r.u_test, r.i_test, r.x_test)
+        iters, _ = ctx.factor_report()
+        ctx.close()
+        return forms, sig, y, rm, iters
+
+    f1, s1, y1, rm1, it1 = run(1, 1)
+    f0, s0, y0, rm0, it0 = run(0, 3)
+    f2, s2, y2, rm2, it2 = run(2, 1)
+    assert f1 == [1] and f0 == [1, 2, 2] and f2 == [2]
+    for a, b in zip(s1, s0):
+        assert np.array_equal(a, b)
+    for a, b in zip(s1, s2):
+        assert np.array_equal(a, b)
+    assert np.array_equal(y1, y0) and np.array_equal(y1, y2)
+    assert rm1 == rm0 == rm2
+    assert np.array_equal(it1, it0) and np.array_equal(it1, it2)
