@@ -58,12 +58,14 @@ KERNEL_SOURCES = {"k_gpanel_tc": "kernels_panel_tc.cu",
                   "k_gram_f32": "kernels_gram.cu"}
 
 
-def profiled_traffic(kernel, workload):
-    """DRAM bytes (read + write) per launch of `kernel` on `workload` from
-    the ncu summaries under profiles/, if one was captured from the kernel's
-    current source. A summary records it in a line
-    ``traffic: <kernel> <workload> <bytes> <sha256 of the source file>``;
-    a figure taken from other source is stale and gives None."""
+def profiled_traffic_ratio(kernel):
+    """DRAM bytes (read + write) over algorithmic bytes of one launch of
+    `kernel`, from the ncu summaries under profiles/, if one was captured
+    from the kernel's current source. A summary records it in a line
+    ``traffic_ratio: <kernel> <ratio> <sha256 of the source file>``; a
+    figure taken from other source is stale and gives None. The captures
+    run on a workload small enough for a multi-pass ncu capture; the bench
+    scales the ratio by its own launches' algorithmic bytes."""
     src = KERNEL_SOURCES.get(kernel)
     if not src or not os.path.isdir(PROFILES):
         return None
@@ -74,10 +76,9 @@ def profiled_traffic(kernel, workload):
         with open(os.path.join(PROFILES, name)) as f:
             for line in f:
                 parts = line.strip().strip("`").split()
-                if (len(parts) == 5 and parts[0] == "traffic:"
-                        and parts[1] == kernel and parts[2] == workload
-                        and parts[4] == sha):
-                    return float(parts[3])
+                if (len(parts) == 4 and parts[0] == "traffic_ratio:"
+                        and parts[1] == kernel and parts[3] == sha):
+                    return float(parts[2])
     return None
 
 
@@ -567,7 +568,8 @@ def time_form(w, data, steps, warmup, flush, stream, owned=None, **cfg):
                     ctx.loop_form(), "none"),
                 launches=ctx.kernel_launches() - launches0,
                 phases={k: statistics.mean(v) for k, v in phases.items()},
-                report=ctx.factor_report(full=True),
+                report=dict(ctx.factor_report(full=True),
+                            launches=ctx.panel_launches()),
                 gram_path=ctx.gram_path())
 
 
@@ -650,9 +652,12 @@ def panel_roofline(w, shapes, rep, filter_ms, peaks, peak_kind):
     gbs = pbytes / t / 1e9 if t > 0 else 0.0
     tf = pflops / t / 1e12 if t > 0 else 0.0
     tf32 = 0.5 * peaks.get("bf16_tflops", 1900.0)
+    ratio = profiled_traffic_ratio("k_gpanel_tc")
+    nlaunch = max(int(rep.get("launches", 0)), 1)
     return {"kernel": "k_gpanel_tc", "bound": "hbm", "achieved": gbs,
             "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-            "traffic": profiled_traffic("k_gpanel_tc", w.name),
+            "traffic": (ratio * pbytes / nlaunch if ratio else None),
+            "traffic_ratio": ratio, "launches": nlaunch,
             "peak_source": "STREAM-style copy, of %s" % peak_kind,
             "products": nprod, "algorithmic_bytes": pbytes,
             "tensor_tflops": tf,
@@ -699,6 +704,11 @@ def main():
                     help="timed steps of each other form")
     ap.add_argument("--no-medium", action="store_true",
                     help="skip the medium-matrix leg")
+    ap.add_argument("--loop", default="tuned",
+                    choices=("tuned", "host", "graph"),
+                    help="eigen loop form: the autotuner's choice, or forced "
+                         "host-driven (ncu cannot profile kernels inside a "
+                         "graph with conditional nodes) or graph")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default eigen-solver schedule instead of "
                          "the autotuner's choice for this workload")
@@ -768,9 +778,11 @@ def main():
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
+    params = dict(tuned["params"])
+    if args.loop != "tuned":
+        params["loop"] = {"host": 1, "graph": 2}[args.loop]
     main_res = time_form(w, data, args.steps, args.warmup, flush, stream,
-                         owned, precision=prec[args.precision],
-                         **tuned["params"])
+                         owned, precision=prec[args.precision], **params)
     barrier()
     clk = clocks.stop()
     ctx = main_res["ctx"]
@@ -806,8 +818,11 @@ def main():
                 "plain": dict(precision=bs.FP32, gram_path=1, panel_path=1),
                 "bf16": dict(precision=bs.BF16), "tf32": dict(precision=bs.TF32)}
     for name in [f for f in args.forms.split(",") if f.strip()]:
+        fcfg = dict(form_cfg[name])
+        if args.loop != "tuned":
+            fcfg["loop"] = {"host": 1, "graph": 2}[args.loop]
         res = time_form(w, data, args.form_steps, args.warmup, flush, stream,
-                        owned, **form_cfg[name])
+                        owned, **fcfg)
         res["ctx"].close()
         forms[name] = res
 
@@ -828,6 +843,10 @@ def main():
     bound, gpeak, gsrc = gram_peak(gram_path, peaks, peak_kind)
     gram_ms = main_res["phases"]["gram"]
     g_tf = gflops_min / (gram_ms * 1e-3) / 1e12 if gram_ms > 0 else 0.0
+    # the Gram's algorithmic bytes: its operand read once, G written once
+    opnd = {1: 4, 2: 4, 3: 4, 4: 2}.get(gram_path, 4) * (2 if gram_path == 2 else 1)
+    gram_bytes = float(sum(opnd * s * L + 4.0 * s * s for (s, L) in shapes))
+    gram_ratio = profiled_traffic_ratio(GRAM_KERNELS.get(gram_path))
     # the ranks share the workload's blocks: all of them per step
     value = nblocks * args.steps / (total_ms * 1e-3)
     step_s = total_ms * 1e-3 / args.steps
@@ -848,7 +867,7 @@ def main():
         "path": {"precision": args.precision,
                  "gram": GRAM_NAMES.get(gram_path, "none"),
                  "eigen_loop": main_res["loop"],
-                 "schedule": tuned["params"] or "default"},
+                 "schedule": params or "default"},
         "autotune": {k: v for k, v in tuned.items() if k != "trials"},
         "latency_ms": {"p50": float(np.percentile(main_res["step_ms"], 50)),
                        "p99": float(np.percentile(main_res["step_ms"], 99))},
@@ -865,8 +884,9 @@ def main():
         "roofline_gram": {"kernel": GRAM_KERNELS.get(gram_path), "bound": bound,
                           "achieved": g_tf, "peak": gpeak, "unit": "TFLOP/s",
                           "frac": g_tf / gpeak,
-                          "traffic": profiled_traffic(
-                              GRAM_KERNELS.get(gram_path), w.name),
+                          "traffic": (gram_ratio * gram_bytes
+                                      if gram_ratio else None),
+                          "traffic_ratio": gram_ratio,
                           "algorithmic_flops_per_launch": gflops_min,
                           "full_product_flops": gflops,
                           "peak_source": gsrc,

@@ -339,8 +339,11 @@ bsvd_status bsvd_factor_report(bsvd_ctx *ctx, int32_t *iters,
  *   ms[0] partition (count, means, scatter)   ms[1] Gram products
  *   ms[2] subspace iteration (eigen-solve)    ms[3] projection and norms
  *   ms[4] prediction / squared-error sum
- *   ms[5] inside ms[2]: Chebyshev filters and panel products
- *   ms[6] inside ms[2]: Rayleigh-Ritz kernels (Grams, solve, rotate, check)
+ *   ms[5] inside ms[2]: the tensor-core panel products' own device time
+ *         (each launch's span, first CTA start to last CTA end, summed on
+ *         the device; 0 on the FP32 SIMT panel path)
+ *   ms[6] inside ms[2]: Rayleigh-Ritz kernels (Grams, solve, rotate,
+ *         check); with the loop in a graph, the rest of ms[2]
  *   ms[7] the rest of ms[2] (start basis, host round trips between steps)
  * Phases the last calls did not run read as 0. ms: host array of 8.
  */
@@ -366,6 +369,13 @@ int32_t bsvd_gram_path(const bsvd_ctx *ctx);
  * factorisation yet, -1 for a NULL context.
  */
 int32_t bsvd_loop_form(const bsvd_ctx *ctx);
+
+/*
+ * Launches of the tensor-core panel products G X in the last bsvd_factor
+ * (counted on the device, so also inside a graph), -1 for a NULL context.
+ * Their summed device time is bsvd_phase_times' ms[5].
+ */
+int64_t bsvd_panel_launches(const bsvd_ctx *ctx);
 
 /*
  * ---- The paper's own method: blocked SGD (Algorithms 1-2) ----------------

@@ -33,7 +33,8 @@ EXPORTS = ("bsvd_config_default", "bsvd_create", "bsvd_destroy",
            "bsvd_gram_path", "bsvd_partition_diag", "bsvd_factor_ks",
            "bsvd_sgd_params_default", "bsvd_sgd_prepare", "bsvd_sgd_train",
            "bsvd_sgd_predict", "bsvd_sgd_get", "bsvd_quantile_grid",
-           "bsvd_set_owned", "bsvd_sqerr", "bsvd_loop_form")
+           "bsvd_set_owned", "bsvd_sqerr", "bsvd_loop_form",
+           "bsvd_panel_launches")
 
 
 class BsvdError(RuntimeError):
@@ -113,6 +114,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                      vp, vp, vp]),
         "bsvd_set_owned": (i32, [vp, i32, vp]),
         "bsvd_loop_form": (i32, [vp]),
+        "bsvd_panel_launches": (i64, [vp]),
         "bsvd_sqerr": (i32, [vp, i64, vp, vp, vp,
                              ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_int64)]),
@@ -380,6 +382,10 @@ def bsvd_loop_form(ctx) -> int:
     return int(load().bsvd_loop_form(ctx))
 
 
+def bsvd_panel_launches(ctx) -> int:
+    return int(load().bsvd_panel_launches(ctx))
+
+
 PHASES = ("partition", "gram", "eigen", "project", "predict", "eigen_filter",
           "eigen_rr", "eigen_other")
 
@@ -595,6 +601,10 @@ class Context:
 
     def gram_path(self) -> int:
         return bsvd_gram_path(self.handle)
+
+    def panel_launches(self) -> int:
+        """Tensor-core panel-product launches in the last factor."""
+        return bsvd_panel_launches(self.handle)
 
     def loop_form(self) -> int:
         """1: the last factor ran its eigen loop from the host; 2: as one

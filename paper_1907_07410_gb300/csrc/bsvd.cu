@@ -136,6 +136,7 @@ struct bsvd_ctx {
   std::string graph_err;     // why the graph could not be built
   int64_t graph_static_launches = 0, graph_loop_launches = 0;
   int32_t last_graph = 0;   // last factor's loop: 0 none, 1 host, 2 graph
+  int64_t panel_launches = 0;   // tensor-core panel products, last factor
   // the BF16 form's projection: maps over the bf16 blocks and over F_s's
   // bf16 B form, and that B form
   DevBuf d_pbmaps, d_fbmaps, d_FB;
@@ -287,8 +288,8 @@ int32_t subspace_width(int32_t k, int32_t oversample) {
 
 // The panel products' device timer: no time summed yet, no launch running.
 cudaError_t reset_ptime(bsvd_ctx *c) {
-  cudaError_t e = cudaMemsetAsync(c->d_ptime.p, 0, sizeof(unsigned long long),
-                                  c->st);
+  cudaError_t e = cudaMemsetAsync(c->d_ptime.p, 0,
+                                  3 * sizeof(unsigned long long), c->st);
   if (e != cudaSuccess) return e;
   return cudaMemsetAsync(c->d_ptime.as<unsigned long long>() + 1, 0xFF,
                          sizeof(unsigned long long), c->st);
@@ -950,6 +951,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
   c->factored = false;
   c->any_capped = false;
   c->last_graph = 0;
+  c->panel_launches = 0;
   c->k = k;
   c->bsub = subspace_width(k, c->cfg.oversample);
   c->kp = (int32_t)std::max<int64_t>(4, round_up(k, 4));
@@ -984,7 +986,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     s.status = (bm.s == 0 || bm.keff == 0) ? kConverged : kRunning;
     bm.t0 = (int32_t)rt.size();
     bm.nt = 0;
-    bm.pt0 = (int32_t)pt.size();
+    bm.pt0 = 0;
     bm.npt = 0;
     bm.pj0 = (int32_t)pj.size();
     bm.npj = 0;
@@ -996,12 +998,29 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     for (int32_t ti = 0; ti < T; ++ti)
       for (int32_t tj = ti; tj < T; ++tj) gt.push_back(make_int4(b, ti, tj, 0));
     for (int32_t r = 0; r < bm.s_pad; r += 64) rt.push_back(make_int2(b, r));
-    for (int32_t r = 0; r < bm.s_pad; r += 128) pt.push_back(make_int2(b, r));
     bm.nt = (int32_t)rt.size() - bm.t0;
     for (int32_t l = 0; l < bm.L; l += kProjCols) lt.push_back(make_int2(b, l));
     for (int32_t l = 0; l < bm.L; l += 128) pj.push_back(make_int2(b, l));
-    bm.npt = (int32_t)pt.size() - bm.pt0;
     bm.npj = (int32_t)pj.size() - bm.pj0;
+  }
+  // 128-row tiles of the panel products, the blocks in decreasing order of
+  // s (each tile reduces over s columns of G, so its cost grows with s),
+  // ties by block index. The persistent products claim tiles in table
+  // order: the longest start first and the shortest fill the end of each
+  // launch. A block's tiles stay contiguous.
+  {
+    std::vector<int32_t> order(nb);
+    for (int32_t b = 0; b < nb; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return c->meta[a].s > c->meta[b].s;
+    });
+    for (int32_t b : order) {
+      BlockMeta &bm = c->meta[b];
+      bm.pt0 = (int32_t)pt.size();
+      if (bm.s > 0 && bm.owned)
+        for (int32_t r = 0; r < bm.s_pad; r += 128) pt.push_back(make_int2(b, r));
+      bm.npt = (int32_t)pt.size() - bm.pt0;
+    }
   }
   c->n_gtiles = (int32_t)gt.size();
   c->n_rowtiles = (int32_t)rt.size();
@@ -1014,7 +1033,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
   CK(c->d_X.ensure(sizeof(float) * std::max<int64_t>(xoff, 1)), "factor");
   CK(c->d_Z.ensure(sizeof(float) * std::max<int64_t>(xoff, 1)), "factor");
   CK(c->d_SH.ensure(sizeof(float) * 2 * B * B * std::max<int64_t>(rt.size(), 1)), "factor");
-  CK(c->d_RP.ensure(sizeof(float) * 2 * B * std::max<int64_t>(rt.size(), 1)), "factor");
+  CK(c->d_RP.ensure(sizeof(double) * 2 * B * std::max<int64_t>(rt.size(), 1)), "factor");
   CK(c->d_T.ensure(sizeof(float) * B * B * (int64_t)nb), "factor");
   CK(c->d_theta.ensure(sizeof(float) * B * (int64_t)nb), "factor");
   CK(c->d_state.ensure(sizeof(SolverState) * nb), "factor");
@@ -1038,7 +1057,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
   CK(c->d_flip.ensure((size_t)kp * std::max(nb, 1)), "factor");
   CK(c->d_pctl.ensure(2 * sizeof(int32_t)), "factor");
   CK(cudaMemsetAsync(c->d_pctl.p, 0, 2 * sizeof(int32_t), c->st), "factor");
-  CK(c->d_ptime.ensure(2 * sizeof(unsigned long long)), "factor");
+  CK(c->d_ptime.ensure(3 * sizeof(unsigned long long)), "factor");
   CK(c->d_loopctl.ensure(2 * sizeof(int32_t)), "factor");
   const bool tc_maps = panel_tc && !pt.empty();
   if (tc_maps) {
@@ -1245,7 +1264,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     e.X = c->d_X.as<float>();
     e.Z = c->d_Z.as<float>();
     e.SH = c->d_SH.as<float>();
-    e.RP = c->d_RP.as<float>();
+    e.RP = c->d_RP.as<double>();
     e.T = c->d_T.as<float>();
     e.theta = c->d_theta.as<float>();
     e.Fs = c->d_Fs.as<float>();
@@ -1522,7 +1541,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     {
       // the panel products' own time (summed over launches on the device),
       // and in graph form the loop's kernel count
-      unsigned long long pt[2] = {0, 0};
+      unsigned long long pt[3] = {0, 0, 0};
       int32_t loops[2] = {0, 0};
       CK(cudaMemcpyAsync(pt, c->d_ptime.p, sizeof pt, cudaMemcpyDeviceToHost,
                          c->st), "factor");
@@ -1531,6 +1550,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
                            cudaMemcpyDeviceToHost, c->st), "factor");
       CK(cudaStreamSynchronize(c->st), "factor");
       c->phase_ms[5] = (double)pt[0] * 1e-6;
+      c->panel_launches = (int64_t)pt[2];
       // loop steps times their unconditional kernels, plus the filter
       // steps the loop control opened
       if (ran_graph)
@@ -1845,6 +1865,10 @@ int64_t bsvd_kernel_launches(const bsvd_ctx *c) {
 int32_t bsvd_gram_path(const bsvd_ctx *c) { return c ? c->gram_used : -1; }
 
 int32_t bsvd_loop_form(const bsvd_ctx *c) { return c ? c->last_graph : -1; }
+
+int64_t bsvd_panel_launches(const bsvd_ctx *c) {
+  return c ? c->panel_launches : -1;
+}
 
 // ---- blocked SGD (Algorithms 1-2) ----------------------------------------
 

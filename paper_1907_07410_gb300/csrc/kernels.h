@@ -86,7 +86,7 @@ struct EigBuffers {
   float *X;          // panels, s_pad x bsub per block
   float *Z;          // G X panels
   float *SH;         // per row tile: partial S (bsub^2) then H (bsub^2)
-  float *RP;         // per row tile: partial residual^2 and norm^2 (2 bsub)
+  double *RP;        // per row tile: partial residual^2 and norm^2 (2 bsub)
   float *T;          // per block: bsub^2 transform
   float *theta;      // per block: bsub Ritz values, descending
   float *Fs;         // s_pad x kp per block
@@ -110,8 +110,8 @@ struct EigBuffers {
 // Persistent: nctas CTAs (one per SM) take the tiles of the running blocks
 // from the counter ctl[0] (ctl: 2 ints, zero before the first launch; the
 // kernel leaves them zero). ptime[0] gains the launch's span in ns (first
-// CTA start to last CTA end); ptime[1] must hold ~0 before the first launch
-// (the kernel leaves it so).
+// CTA start to last CTA end), ptime[2] counts launches; ptime[1] must hold
+// ~0 before the first launch (the kernel leaves it so).
 cudaError_t launch_gpanel_tc(int32_t bsub, const BlockMeta *meta,
                              SolverState *state, const int2 *tiles,
                              int32_t ntiles, int32_t nctas, int32_t *ctl,

@@ -624,7 +624,7 @@ k_rotate(const BlockMeta *__restrict__ meta,
          const SolverState *__restrict__ state,
          const int2 *__restrict__ rowtiles, const float *__restrict__ T,
          const float *__restrict__ theta, float *X, float *Z,
-         float *__restrict__ RP, uint64_t seed, int32_t *running,
+         double *__restrict__ RP, uint64_t seed, int32_t *running,
          float *__restrict__ XB) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float (*Ts)[B + 1] = reinterpret_cast<float (*)[B + 1]>(smem_raw);
@@ -652,12 +652,13 @@ k_rotate(const BlockMeta *__restrict__ meta,
   }
   __syncthreads();
   // column j handled by threads j, j + B, ... (256 / B row groups)
+  // the residual and norm sums are float64 (the convergence test's norms)
   constexpr int G = 256 / B;
-  __shared__ float r2s[G][B], x2s[G][B];
+  __shared__ double r2s[G][B], x2s[G][B];
   const int j = threadIdx.x % B, grp = threadIdx.x / B;
   const bool refill = (st.refill >> j) & 1ull;
   const float tj = th[j];
-  float r2 = 0.f, x2 = 0.f;
+  double r2 = 0.0, x2 = 0.0;
   for (int r = grp; r < rows; r += G) {
     float ax = 0.f, az = 0.f;
 #pragma unroll 8
@@ -674,9 +675,9 @@ k_rotate(const BlockMeta *__restrict__ meta,
     Xb[(int64_t)r * B + j] = ax;
     Zb[(int64_t)r * B + j] = az;
     Os[r][j] = ax;
-    const float d = az - tj * ax;
-    r2 = fmaf(d, d, r2);
-    x2 = fmaf(ax, ax, x2);
+    const double d = (double)az - (double)tj * (double)ax;
+    r2 = fma(d, d, r2);
+    x2 = fma((double)ax, (double)ax, x2);
   }
   r2s[grp][j] = r2;
   x2s[grp][j] = x2;
@@ -698,9 +699,9 @@ k_rotate(const BlockMeta *__restrict__ meta,
     }
   }
   if (threadIdx.x < B) {
-    float a = 0.f, b = 0.f;
+    double a = 0.0, b = 0.0;
     for (int g = 0; g < G; ++g) { a += r2s[g][threadIdx.x]; b += x2s[g][threadIdx.x]; }
-    float *rp = RP + (int64_t)blockIdx.x * 2 * B;
+    double *rp = RP + (int64_t)blockIdx.x * 2 * B;
     rp[threadIdx.x] = a;
     rp[B + threadIdx.x] = b;
   }
@@ -710,10 +711,10 @@ k_rotate(const BlockMeta *__restrict__ meta,
 template <int B>
 __global__ void __launch_bounds__(256)
 k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
-        const float *__restrict__ X, const float *__restrict__ RP,
+        const float *__restrict__ X, const double *__restrict__ RP,
         const float *__restrict__ theta, float *__restrict__ Fs, int kp,
         int max_iters, int max_degree, float tol, int32_t *running) {
-  __shared__ float r2[B], x2[B];
+  __shared__ double r2[B], x2[B];
   __shared__ int s_done;
   const int blk = blockIdx.x;
   pdl_wait();
@@ -724,10 +725,10 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   const int n = st.bsub, s = bm.s, keff = bm.keff;
   const float *th = theta + (int64_t)blk * B;
   if (threadIdx.x < B) {
-    float a = 0.f, b = 0.f;
+    double a = 0.0, b = 0.0;
 #pragma unroll 8
     for (int t = 0; t < bm.nt; ++t) {
-      const float *rp = RP + (int64_t)(bm.t0 + t) * 2 * B;
+      const double *rp = RP + (int64_t)(bm.t0 + t) * 2 * B;
       a += rp[threadIdx.x];
       b += rp[B + threadIdx.x];
     }
@@ -736,17 +737,23 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    // The convergence test, in float64: |G x_j - theta_j x_j| / |x_j| <=
+    // tol theta_1 for the wanted pairs. For orthonormal Ritz vectors it
+    // also bounds the off-diagonal entries |x_i^T G x_j| = |x_i^T r_j| of
+    // the Rayleigh quotient matrix by the same amount.
     const float t1 = th[0];
-    float worst = 0.f;
-    for (int j = 0; j < keff && j < n; ++j) worst = fmaxf(worst, sqrtf(r2[j]));
+    double worst = 0.0;
+    for (int j = 0; j < keff && j < n; ++j)
+      worst = fmax(worst, x2[j] > 0.0 ? sqrt(r2[j] / x2[j]) : sqrt(r2[j]));
     const unsigned long long wanted =
         keff >= 64 ? ~0ull : ((1ull << keff) - 1ull);
     st.iters += 1;
     st.theta1 = t1;
-    st.resid = t1 > 0.f ? worst / t1 : 0.f;
+    st.resid = t1 > 0.f ? (float)(worst / (double)t1) : 0.f;
     const bool refilled_wanted = (st.refill & wanted) != 0ull;
     const bool conv = !refilled_wanted &&
-                      ((s <= B) || !(t1 > 1e-30f) || (worst <= tol * t1));
+                      ((s <= B) || !(t1 > 1e-30f) ||
+                       (worst <= (double)tol * (double)t1));
     if (conv || st.iters >= max_iters) {
       st.status = conv ? kConverged : kCapped;
       s_done = 1;
@@ -777,14 +784,18 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   }
   __syncthreads();
   if (!s_done) return;
+  // unit columns: one float64 reciprocal norm per column
+  __shared__ float inv[B];
+  if (threadIdx.x < B) {
+    const double nn = x2[threadIdx.x];
+    inv[threadIdx.x] = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
+  }
+  __syncthreads();
   const float *Xb = X + bm.x_off;
   for (int e = threadIdx.x; e < s * kp; e += blockDim.x) {
     const int r = e / kp, j = e % kp;
     float v = 0.f;
-    if (j < keff && j < n) {
-      const float nn = x2[j];
-      v = nn > 0.f ? Xb[(int64_t)r * B + j] / sqrtf(nn) : 0.f;
-    }
+    if (j < keff && j < n) v = Xb[(int64_t)r * B + j] * inv[j];
     Fs[bm.fs_off + (int64_t)r * kp + j] = v;
   }
 }
@@ -1014,7 +1025,7 @@ cudaError_t launch_check(const EigBuffers &e, cudaStream_t st) {
   return by_width(e.bsub, [&](auto w) {
     constexpr int B = decltype(w)::value;
     return launch_pdl(k_check<B>, dim3(e.nblocks), dim3(256), 0, st, e.meta,
-                      e.state, (const float *)e.X, (const float *)e.RP,
+                      e.state, (const float *)e.X, (const double *)e.RP,
                       (const float *)e.theta, e.Fs, e.kp, e.max_iters,
                       e.max_degree, e.tol, e.running);
   });

@@ -525,6 +525,7 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
       const unsigned long long t0 = atomicAdd(&ptime[1], 0ull);
       const unsigned long long t1 = globaltimer_ns();
       if (t1 > t0 && t0 != ~0ull) atomicAdd(&ptime[0], t1 - t0);
+      atomicAdd(&ptime[2], 1ull);          // launches
       atomicExch(&ptime[1], ~0ull);
       atomicExch(&ctl[0], 0);
       atomicExch(&ctl[1], 0);

@@ -77,8 +77,14 @@ LARGE = Workload("large-480189x17770-32x8-k40", 480_189, 17_770, 100_480_507,
 UNEVEN = Workload("uneven-20000x3000-8x4-k40", 20_000, 3_000, 1_500_000, 40,
                   1.2, 0.9, 8, 4, 40, 4, grid="quantile")
 
+# The large workload's generator at a tenth of its ratings, for kernel
+# profiles that must fit a few GB of device memory (blocks up to about
+# 30,000 x 5,000; every Gram and dense copy still exceeds the 129 MB L2).
+MID = Workload("mid-120000x8000-16x4-k40", 120_000, 8_000, 12_000_000, 40,
+               1.2, 0.9, 16, 4, 40, 5, grid="quantile")
+
 WORKLOADS = {w.name: w for w in (SMALL, MEDIUM, MEDIUM_8x8, MEDIUM_16x16,
-                                 LARGE, UNEVEN)}
+                                 LARGE, UNEVEN, MID)}
 
 
 @dataclasses.dataclass
