@@ -105,7 +105,7 @@ struct bsvd_ctx {
   bool factored = false;
   int32_t k = 0, bsub = 0, kp = 4;
   DevBuf d_G, d_X, d_Z, d_SH, d_RP, d_T, d_theta, d_state, d_Fs, d_FL, d_sigma,
-      d_running, d_gtiles, d_rowtiles, d_ltiles;
+      d_running, d_gtiles, d_rowtiles, d_ltiles, d_finv, d_chunks;
   int32_t n_gtiles = 0, n_rowtiles = 0, n_ltiles = 0;
   // tensor-core panel products: 128-row tiles and one TMA map per block of G
   DevBuf d_ptiles, d_gmaps, d_xmaps;
@@ -119,6 +119,7 @@ struct bsvd_ctx {
   // tensor-core projection: 128-column tiles of W and one TMA map per block
   DevBuf d_pjtiles, d_pwmaps;
   int32_t n_pjtiles = 0;
+  int32_t n_chunks = 0;      // kChunkRows-row chunks of the panels
   // finalisation: per-tile column statistics of F_L and F_s, column flips
   DevBuf d_lpart, d_spart, d_flip;
   // the persistent panel products' tile counter, and the CTAs they launch
@@ -563,7 +564,7 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->d_qcnt, &c->d_qkeys, &c->d_qcum, &c->d_qperm,
                     &c->d_qbounds, &c->d_pbmaps, &c->d_fbmaps, &c->d_FB,
                     &c->d_lpart, &c->d_spart, &c->d_flip, &c->d_pctl,
-                    &c->d_ptime, &c->d_loopctl};
+                    &c->d_ptime, &c->d_loopctl, &c->d_finv, &c->d_chunks};
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -963,7 +964,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
   const int32_t kn = (int32_t)round_up(kp, 16);
   int64_t goff = 0, xoff = 0, fsoff = 0, floff = 0, fboff = 0;
   std::vector<int4> gt;
-  std::vector<int2> rt, lt, pt, pj;
+  std::vector<int2> rt, lt, pt, pj, ch;
   std::vector<SolverState> st0(nb);
   for (int32_t b = 0; b < nb; ++b) {
     BlockMeta &bm = c->meta[b];
@@ -990,6 +991,8 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     bm.npt = 0;
     bm.pj0 = (int32_t)pj.size();
     bm.npj = 0;
+    bm.ch0 = (int32_t)ch.size();
+    bm.nch = 0;
     if (bm.s == 0 || !bm.owned) continue;
     // Gram tiles: 256 x 256 for the single-product tensor-core Grams,
     // 128 x 128 for the exact four-product one and the FP32 SIMT one
@@ -999,6 +1002,8 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
       for (int32_t tj = ti; tj < T; ++tj) gt.push_back(make_int4(b, ti, tj, 0));
     for (int32_t r = 0; r < bm.s_pad; r += 64) rt.push_back(make_int2(b, r));
     bm.nt = (int32_t)rt.size() - bm.t0;
+    for (int32_t r = 0; r < bm.s; r += kChunkRows) ch.push_back(make_int2(b, r));
+    bm.nch = (int32_t)ch.size() - bm.ch0;
     for (int32_t l = 0; l < bm.L; l += kProjCols) lt.push_back(make_int2(b, l));
     for (int32_t l = 0; l < bm.L; l += 128) pj.push_back(make_int2(b, l));
     bm.npj = (int32_t)pj.size() - bm.pj0;
@@ -1027,15 +1032,18 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
   c->n_ltiles = (int32_t)lt.size();
   c->n_ptiles = (int32_t)pt.size();
   c->n_pjtiles = (int32_t)pj.size();
+  c->n_chunks = (int32_t)ch.size();
   const bool panel_tc = c->cfg.panel_path == 0;
 
   CK(c->d_G.ensure(sizeof(float) * std::max<int64_t>(goff, 1)), "factor");
   CK(c->d_X.ensure(sizeof(float) * std::max<int64_t>(xoff, 1)), "factor");
   CK(c->d_Z.ensure(sizeof(float) * std::max<int64_t>(xoff, 1)), "factor");
-  CK(c->d_SH.ensure(sizeof(float) * 2 * B * B * std::max<int64_t>(rt.size(), 1)), "factor");
+  CK(c->d_SH.ensure(sizeof(float) * 2 * B * B * std::max<int64_t>(ch.size(), 1)), "factor");
+  CK(c->d_chunks.ensure(sizeof(int2) * std::max<size_t>(ch.size(), 1)), "factor");
   CK(c->d_RP.ensure(sizeof(double) * 2 * B * std::max<int64_t>(rt.size(), 1)), "factor");
   CK(c->d_T.ensure(sizeof(float) * B * B * (int64_t)nb), "factor");
   CK(c->d_theta.ensure(sizeof(float) * B * (int64_t)nb), "factor");
+  CK(c->d_finv.ensure(sizeof(float) * B * (int64_t)nb), "factor");
   CK(c->d_state.ensure(sizeof(SolverState) * nb), "factor");
   CK(c->d_Fs.ensure(sizeof(float) * std::max<int64_t>(fsoff, 1)), "factor");
   CK(c->d_FL.ensure(sizeof(float) * std::max<int64_t>(floff, 1)), "factor");
@@ -1093,7 +1101,8 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
                           c->d_gmaps.p, c->d_xmaps.p, c->d_ptiles.p,
                           c->d_pwmaps.p, c->d_pjtiles.p, c->d_state0.p,
                           c->d_VX.p, c->d_pbmaps.p, c->d_fbmaps.p, c->d_FB.p,
-                          c->d_lpart.p, c->d_spart.p, c->d_flip.p};
+                          c->d_lpart.p, c->d_spart.p, c->d_flip.p,
+                          c->d_chunks.p};
     put(ptrs, sizeof ptrs);
   }
   const bool same_layout = sig == c->fsig;
@@ -1118,6 +1127,9 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
                          cudaMemcpyHostToDevice, c->st), "factor");
     if (!pj.empty())
       CK(cudaMemcpyAsync(c->d_pjtiles.p, pj.data(), sizeof(int2) * pj.size(),
+                         cudaMemcpyHostToDevice, c->st), "factor");
+    if (!ch.empty())
+      CK(cudaMemcpyAsync(c->d_chunks.p, ch.data(), sizeof(int2) * ch.size(),
                          cudaMemcpyHostToDevice, c->st), "factor");
   }
   if (nb > 0)
@@ -1268,6 +1280,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     e.T = c->d_T.as<float>();
     e.theta = c->d_theta.as<float>();
     e.Fs = c->d_Fs.as<float>();
+    e.Finv = c->d_finv.as<float>();
     e.running = c->d_running.as<int32_t>();
     // k_rotate keeps X's B form current for the tensor-core products
     e.XB = panel_tc ? c->d_XB.as<float>() : nullptr;
@@ -1344,7 +1357,9 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     };
     auto rr = [&]() -> cudaError_t {
       cudaError_t r;
-      if ((r = launch_small_gram(e, rtd, nrt, c->st)) != cudaSuccess) return r;
+      if ((r = launch_small_gram(e, c->d_chunks.as<int2>(), c->n_chunks,
+                                 c->st)) != cudaSuccess)
+        return r;
       if ((r = launch_rr_solve(e, c->st)) != cudaSuccess) return r;
       if ((r = launch_rotate(e, rtd, nrt, c->st)) != cudaSuccess) return r;
       // k_rotate clears the running counters that k_check fills
@@ -1380,6 +1395,10 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     auto post = [&]() -> cudaError_t {
       cudaError_t r;
       mark(c, 2);
+      if ((r = launch_publish_fs(e, c->d_ptiles.as<int2>(), c->n_ptiles,
+                                 c->st)) != cudaSuccess)
+        return r;
+      c->launches += (c->n_ptiles > 0);
       if (proj16) {
         // F_L from the bf16 blocks, F_s split into bf16 hi and lo
         if ((r = launch_bform_fs16(e.meta, c->d_ptiles.as<int2>(), c->n_ptiles,
@@ -1446,7 +1465,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
                             c->d_theta.p, c->d_Fs.p, c->d_FL.p, c->d_sigma.p,
                             c->d_running.p, c->d_err.p, c->d_maps.p,
                             c->d_delta.p, c->d_wmaps.p, c->d_pctl.p,
-                            c->d_ptime.p, c->d_loopctl.p};
+                            c->d_ptime.p, c->d_loopctl.p, c->d_finv.p};
       const unsigned char *pb = reinterpret_cast<const unsigned char *>(bufs);
       key.insert(key.end(), pb, pb + sizeof bufs);
       c->gkey_now.swap(key);

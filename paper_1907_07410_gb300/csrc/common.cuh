@@ -87,7 +87,11 @@ struct BlockMeta {
   int64_t fb_off;       // bf16 B form of F_s (BF16 form's projection)
   int32_t pt0, npt;     // the block's 128-row tiles of F_s (panel tiles)
   int32_t pj0, npj;     // the block's 128-row tiles of F_L (projection)
+  int32_t ch0, nch;     // the block's kChunkRows-row chunks (small Grams)
 };
+
+// rows of the panels per chunk of the Rayleigh-Ritz small Grams
+constexpr int kChunkRows = 512;
 
 // Per-block state of the subspace iteration.
 struct SolverState {

@@ -85,11 +85,12 @@ struct EigBuffers {
   float *G;          // s_pad x s_pad Gram per block
   float *X;          // panels, s_pad x bsub per block
   float *Z;          // G X panels
-  float *SH;         // per row tile: partial S (bsub^2) then H (bsub^2)
+  float *SH;         // per chunk: partial S (bsub^2) then H (bsub^2)
   double *RP;        // per row tile: partial residual^2 and norm^2 (2 bsub)
   float *T;          // per block: bsub^2 transform
   float *theta;      // per block: bsub Ritz values, descending
   float *Fs;         // s_pad x kp per block
+  float *Finv;       // per block: bsub reciprocal column norms of X (done)
   int32_t *running;  // [0] blocks still iterating, [1] their largest degree
   float *XB = nullptr;  // the B form of X for the tensor-core products, or null
   int32_t bsub, kp, k;
@@ -167,12 +168,16 @@ cudaError_t launch_gpanel(const EigBuffers &e, const int2 *rowtiles,
                           int32_t ntiles, int32_t mode, int32_t step,
                           int32_t degree, const float *in, const float *in2,
                           float *out, cudaStream_t st);
-cudaError_t launch_small_gram(const EigBuffers &e, const int2 *rowtiles,
-                              int32_t ntiles, cudaStream_t st);
+cudaError_t launch_small_gram(const EigBuffers &e, const int2 *chunks,
+                              int32_t nchunks, cudaStream_t st);
 cudaError_t launch_rr_solve(const EigBuffers &e, cudaStream_t st);
 cudaError_t launch_rotate(const EigBuffers &e, const int2 *rowtiles,
                           int32_t ntiles, cudaStream_t st);
 cudaError_t launch_check(const EigBuffers &e, cudaStream_t st);
+// F_s of every finished block from X and Finv, over 128-row tiles
+// (block, first row) of F_s.
+cudaError_t launch_publish_fs(const EigBuffers &e, const int2 *tiles,
+                              int32_t ntiles, cudaStream_t st);
 // The IF nodes of filter steps first .. first + n - 1.
 struct LoopHandles {
   cudaGraphConditionalHandle h[62];

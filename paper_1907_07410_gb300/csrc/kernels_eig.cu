@@ -60,6 +60,7 @@ namespace bsvd {
 namespace {
 
 constexpr int TR = 64;       // panel rows per CTA
+static_assert(kChunkRows % 32 == 0, "chunks are whole 32-row passes");
 constexpr float kMaxAmplification = 3e6f;
 constexpr float kMinAmplification = 1e3f;
 constexpr float kAmpBackoff = 1e2f;
@@ -274,51 +275,99 @@ size_t panel_smem() {
   return a > r ? a : r;
 }
 
-// Partial S = X^T X and H = X^T Z over the 64 rows of one row tile, for
-// every tile of every running block; k_rr_solve sums a block's tiles in a
-// fixed order, so the totals do not depend on scheduling.
+// N consecutive floats (N = 1, 2 or 4; p aligned to 4 N bytes) in one load
+template <int N>
+__device__ __forceinline__ void ld_vec(const float *p, float (&v)[N]) {
+  if constexpr (N == 4) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else if constexpr (N == 2) {
+    const float2 q = *reinterpret_cast<const float2 *>(p);
+    v[0] = q.x; v[1] = q.y;
+  } else {
+    v[0] = p[0];
+  }
+}
+
+// The same N floats to global memory in one store
+template <int N>
+__device__ __forceinline__ void st_vec(float *p, const float (&v)[N]) {
+  if constexpr (N == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (N == 2) {
+    *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+  } else {
+    p[0] = v[0];
+  }
+}
+
+// Partial S = X^T X and H = X^T Z over one chunk of up to kChunkRows rows,
+// for every chunk of every running block; k_rr_solve sums a block's chunks
+// in a fixed order, so the totals do not depend on scheduling. The 256
+// threads form a 16 x 16 grid over the b x b outputs, each thread a TI x TI
+// register tile (TI = b / 16): per row, three 16-byte shared loads (its
+// slices of the X row for i and j, and of the Z row for j) feed 2 TI^2
+// fused multiply-adds. The rows are added in order, 32 at a time staged in
+// shared memory.
 template <int B>
 __global__ void __launch_bounds__(256)
 k_small_gram(const BlockMeta *__restrict__ meta,
              const SolverState *__restrict__ state,
-             const int2 *__restrict__ rowtiles, const float *__restrict__ X,
+             const int2 *__restrict__ chunks, const float *__restrict__ X,
              const float *__restrict__ Z, float *__restrict__ SHp) {
   pdl_wait();
   pdl_trigger();
-  constexpr int PER = (B * B + 255) / 256;
-  __shared__ float Xs[TR][B + 1];
-  __shared__ float Zs[TR][B + 1];
-  const int2 t = rowtiles[blockIdx.x];
+  constexpr int TI = B / 16;
+  constexpr int SR = 32;                   // rows staged per pass
+  __shared__ __align__(16) float Xs[SR][B];
+  __shared__ __align__(16) float Zs[SR][B];
+  const int2 t = chunks[blockIdx.x];
   if (state[t.x].status != kRunning) return;
   const BlockMeta bm = meta[t.x];
-  const int rows = min(TR, bm.s - t.y);
+  const int rows = min(kChunkRows, bm.s - t.y);
   const float *Xb = X + bm.x_off + (int64_t)t.y * B;
   const float *Zb = Z + bm.x_off + (int64_t)t.y * B;
-  for (int e = threadIdx.x; e < TR * B; e += 256) {
-    const int rr = e / B, c = e % B;
-    const bool ok = rr < rows;
-    Xs[rr][c] = ok ? Xb[e] : 0.f;
-    Zs[rr][c] = ok ? Zb[e] : 0.f;
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  float sa[TI][TI], ha[TI][TI];
+#pragma unroll
+  for (int a = 0; a < TI; ++a)
+#pragma unroll
+    for (int b = 0; b < TI; ++b) sa[a][b] = ha[a][b] = 0.f;
+  for (int r0 = 0; r0 < rows; r0 += SR) {
+    const int nr = min(SR, rows - r0);
+    __syncthreads();                       // the last pass has read Xs, Zs
+    for (int e4 = threadIdx.x; e4 < nr * (B / 4); e4 += 256) {
+      const int64_t o = (int64_t)r0 * B + 4 * e4;
+      reinterpret_cast<float4 *>(&Xs[0][0])[e4] =
+          *reinterpret_cast<const float4 *>(Xb + o);
+      reinterpret_cast<float4 *>(&Zs[0][0])[e4] =
+          *reinterpret_cast<const float4 *>(Zb + o);
+    }
+    __syncthreads();
+    for (int rr = 0; rr < nr; ++rr) {
+      float xi[TI], xj[TI], zj[TI];
+      ld_vec(&Xs[rr][TI * ti], xi);
+      ld_vec(&Xs[rr][TI * tj], xj);
+      ld_vec(&Zs[rr][TI * tj], zj);
+#pragma unroll
+      for (int a = 0; a < TI; ++a)
+#pragma unroll
+        for (int b = 0; b < TI; ++b) {
+          sa[a][b] = fmaf(xi[a], xj[b], sa[a][b]);
+          ha[a][b] = fmaf(xi[a], zj[b], ha[a][b]);
+        }
+    }
   }
-  __syncthreads();
   float *S = SHp + (int64_t)blockIdx.x * 2 * B * B;
   float *H = S + B * B;
 #pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int idx = threadIdx.x + 256 * q;
-    if (idx < B * B) {
-      const int i = idx / B, j = idx % B;
-      float sa = 0.f, ha = 0.f;
-#pragma unroll 16
-      for (int rr = 0; rr < TR; ++rr) {
-        const float xi = Xs[rr][i];
-        sa = fmaf(xi, Xs[rr][j], sa);
-        ha = fmaf(xi, Zs[rr][j], ha);
-      }
-      S[idx] = sa;
-      H[idx] = ha;
+  for (int a = 0; a < TI; ++a)
+#pragma unroll
+    for (int b = 0; b < TI; ++b) {
+      const int idx = (TI * ti + a) * B + TI * tj + b;
+      S[idx] = sa[a][b];
+      H[idx] = ha[a][b];
     }
-  }
 }
 
 // Round-robin pairings for cyclic Jacobi on ne (even) indices: round r pairs
@@ -452,14 +501,14 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   const int ne = n + (n & 1), np = ne / 2;
   const long long c0 = clock64();
   build_pairs(ne, sm.pairs);
-  // 1. sum the row-tile partials in tile order
-  const float *part = SHp + (int64_t)bm.t0 * 2 * B * B;
+  // 1. sum the chunk partials in chunk order
+  const float *part = SHp + (int64_t)bm.ch0 * 2 * B * B;
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
     float s = 0.f, h = 0.f;
-    // unrolled so the loads run ahead; the adds stay in tile order
+    // unrolled so the loads run ahead; the adds stay in chunk order
 #pragma unroll 8
-    for (int t = 0; t < bm.nt; ++t) {
+    for (int t = 0; t < bm.nch; ++t) {
       s += part[(int64_t)t * 2 * B * B + i * B + j];
       h += part[(int64_t)t * 2 * B * B + B * B + i * B + j];
     }
@@ -615,9 +664,16 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   }
 }
 
-// X <- X T and Z <- Z T on one row tile, in place; refilled columns get
+// X <- X T and Z <- Z T on one 64-row tile, in place; refilled columns get
 // fresh random values (and Z = 0 until the next product). Writes the tile's
-// partial |Z_j - theta_j X_j|^2 and |X_j|^2 for every column j.
+// partial |Z_j - theta_j X_j|^2 and |X_j|^2 for every column j: each
+// thread's four rows in float32 (one rounding for the residual entry, one
+// per square and add), then float64 over the threads in a fixed order.
+// The 256 threads form a 16 x 16 grid over the tile's 64 rows x b columns,
+// each thread 4 rows x TJ = b / 16 columns in registers. X and Z are staged
+// transposed (column l of the tile is row l of XT, ZT), so for each l one
+// 16-byte load of XT, of ZT and of T's row l feed 8 TJ fused multiply-adds;
+// every output is still the sum over l in ascending order.
 template <int B>
 __global__ void __launch_bounds__(256)
 k_rotate(const BlockMeta *__restrict__ meta,
@@ -626,15 +682,20 @@ k_rotate(const BlockMeta *__restrict__ meta,
          const float *__restrict__ theta, float *X, float *Z,
          double *__restrict__ RP, uint64_t seed, int32_t *running,
          float *__restrict__ XB) {
+  constexpr int TJ = B / 16;
+  constexpr int LD = TR + 4;                 // XT, ZT rows: 16-byte multiples
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float (*Ts)[B + 1] = reinterpret_cast<float (*)[B + 1]>(smem_raw);
+  float (*Ts)[B] = reinterpret_cast<float (*)[B]>(smem_raw);
+  float (*XT)[LD] = reinterpret_cast<float (*)[LD]>(smem_raw +
+                                                     sizeof(float) * B * B);
+  float (*ZT)[LD] = XT + B;
+  // the new X rows for the B form, over XT and ZT once they are read
+  float (*Os)[B + 1] = reinterpret_cast<float (*)[B + 1]>(&XT[0][0]);
+  __shared__ double r2s[16][B], x2s[16][B];
   pdl_wait();
   pdl_trigger();
   // k_check, next in the stream, counts the blocks still running here
   if (blockIdx.x == 0 && threadIdx.x < 2) running[threadIdx.x] = 0;
-  float (*Xs)[B + 1] = Ts + B;
-  float (*Zs)[B + 1] = Xs + TR;
-  float (*Os)[B + 1] = Zs + TR;    // the new X rows, for the B form
   const int2 t = rowtiles[blockIdx.x];
   const SolverState st = state[t.x];
   if (st.status != kRunning) return;
@@ -644,43 +705,70 @@ k_rotate(const BlockMeta *__restrict__ meta,
   const float *th = theta + (int64_t)t.x * B;
   float *Xb = X + bm.x_off + (int64_t)t.y * B;
   float *Zb = Z + bm.x_off + (int64_t)t.y * B;
-  for (int e = threadIdx.x; e < B * B; e += blockDim.x)
-    Ts[e / B][e % B] = Tb[e];
-  for (int e = threadIdx.x; e < rows * B; e += blockDim.x) {
-    Xs[e / B][e % B] = Xb[e];
-    Zs[e / B][e % B] = Zb[e];
+  for (int e4 = threadIdx.x; e4 < B * B / 4; e4 += blockDim.x)
+    reinterpret_cast<float4 *>(&Ts[0][0])[e4] =
+        reinterpret_cast<const float4 *>(Tb)[e4];
+  for (int e = threadIdx.x; e < TR * B; e += blockDim.x) {
+    const int r = e / B, l = e % B;
+    const bool ok = r < rows;
+    XT[l][r] = ok ? Xb[e] : 0.f;
+    ZT[l][r] = ok ? Zb[e] : 0.f;
   }
   __syncthreads();
-  // column j handled by threads j, j + B, ... (256 / B row groups)
-  // the residual and norm sums are float64 (the convergence test's norms)
-  constexpr int G = 256 / B;
-  __shared__ double r2s[G][B], x2s[G][B];
-  const int j = threadIdx.x % B, grp = threadIdx.x / B;
-  const bool refill = (st.refill >> j) & 1ull;
-  const float tj = th[j];
-  double r2 = 0.0, x2 = 0.0;
-  for (int r = grp; r < rows; r += G) {
-    float ax = 0.f, az = 0.f;
-#pragma unroll 8
-    for (int l = 0; l < B; ++l) {
-      const float tl = Ts[l][j];
-      ax = fmaf(Xs[r][l], tl, ax);
-      az = fmaf(Zs[r][l], tl, az);
-    }
-    if (refill) {
-      ax = hash_uniform(seed ^ (0x51ED270Bull * (uint64_t)(st.iters + 1)),
-                        (uint64_t)t.x, (uint64_t)(t.y + r) * B + j);
-      az = 0.f;
-    }
-    Xb[(int64_t)r * B + j] = ax;
-    Zb[(int64_t)r * B + j] = az;
-    Os[r][j] = ax;
-    const double d = (double)az - (double)tj * (double)ax;
-    r2 = fma(d, d, r2);
-    x2 = fma((double)ax, (double)ax, x2);
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+  float ax[4][TJ], az[4][TJ];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < TJ; ++b) ax[a][b] = az[a][b] = 0.f;
+#pragma unroll 4
+  for (int l = 0; l < B; ++l) {
+    float xv[4], zv[4], tv[TJ];
+    ld_vec(&XT[l][4 * tr], xv);
+    ld_vec(&ZT[l][4 * tr], zv);
+    ld_vec(&Ts[l][TJ * tc], tv);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < TJ; ++b) {
+        ax[a][b] = fmaf(xv[a], tv[b], ax[a][b]);
+        az[a][b] = fmaf(zv[a], tv[b], az[a][b]);
+      }
   }
-  r2s[grp][j] = r2;
-  x2s[grp][j] = x2;
+  __syncthreads();                           // XT, ZT read: Os may reuse them
+#pragma unroll
+  for (int b = 0; b < TJ; ++b) {
+    const int j = TJ * tc + b;
+    const bool refill = (st.refill >> j) & 1ull;
+    const float tj = th[j];
+    float pr2 = 0.f, px2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int r = 4 * tr + a;
+      if (refill) {
+        ax[a][b] = hash_uniform(
+            seed ^ (0x51ED270Bull * (uint64_t)(st.iters + 1)), (uint64_t)t.x,
+            (uint64_t)(t.y + r) * B + j);
+        az[a][b] = 0.f;
+      }
+      if (r < rows) {
+        const float d = fmaf(-tj, ax[a][b], az[a][b]);
+        pr2 = fmaf(d, d, pr2);
+        px2 = fmaf(ax[a][b], ax[a][b], px2);
+        Os[r][j] = ax[a][b];
+      }
+    }
+    r2s[tr][j] = (double)pr2;
+    x2s[tr][j] = (double)px2;
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int r = 4 * tr + a;
+    if (r < rows) {
+      st_vec(Xb + (int64_t)r * B + TJ * tc, ax[a]);
+      st_vec(Zb + (int64_t)r * B + TJ * tc, az[a]);
+    }
+  }
   __syncthreads();
   if (XB) {
     // the B form of X for the tensor-core products that follow: for each
@@ -700,20 +788,22 @@ k_rotate(const BlockMeta *__restrict__ meta,
   }
   if (threadIdx.x < B) {
     double a = 0.0, b = 0.0;
-    for (int g = 0; g < G; ++g) { a += r2s[g][threadIdx.x]; b += x2s[g][threadIdx.x]; }
+    for (int g = 0; g < 16; ++g) { a += r2s[g][threadIdx.x]; b += x2s[g][threadIdx.x]; }
     double *rp = RP + (int64_t)blockIdx.x * 2 * B;
     rp[threadIdx.x] = a;
     rp[B + threadIdx.x] = b;
   }
 }
 
-// Residuals, convergence, next filter; copies F_s when a block is done.
+// Residuals, convergence, next filter. When a block is done, its columns'
+// float32 reciprocal norms go to Finv (k_publish_fs normalises X into F_s
+// after the loop, spread over row tiles).
 template <int B>
 __global__ void __launch_bounds__(256)
 k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
-        const float *__restrict__ X, const double *__restrict__ RP,
-        const float *__restrict__ theta, float *__restrict__ Fs, int kp,
-        int max_iters, int max_degree, float tol, int32_t *running) {
+        const double *__restrict__ RP, const float *__restrict__ theta,
+        float *__restrict__ Finv, int max_iters, int max_degree, float tol,
+        int32_t *running) {
   __shared__ double r2[B], x2[B];
   __shared__ int s_done;
   const int blk = blockIdx.x;
@@ -785,19 +875,40 @@ k_check(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   __syncthreads();
   if (!s_done) return;
   // unit columns: one float64 reciprocal norm per column
-  __shared__ float inv[B];
   if (threadIdx.x < B) {
     const double nn = x2[threadIdx.x];
-    inv[threadIdx.x] = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
+    Finv[(int64_t)blk * B + threadIdx.x] =
+        nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
   }
-  __syncthreads();
-  const float *Xb = X + bm.x_off;
-  for (int e = threadIdx.x; e < s * kp; e += blockDim.x) {
-    const int r = e / kp, j = e % kp;
-    float v = 0.f;
-    if (j < keff && j < n) v = Xb[(int64_t)r * B + j] * inv[j];
-    Fs[bm.fs_off + (int64_t)r * kp + j] = v;
-  }
+}
+
+// F_s = the first keff columns of X, each scaled by its reciprocal norm
+// (zero elsewhere), for one 128-row tile of a finished block. Thread t takes
+// column t mod kp of the rows t / kp, t / kp + G, ... (G = blockDim / kp),
+// so a CTA writes consecutive floats of F_s. A block that never reached a
+// Rayleigh-Ritz step (keff = 0) gets zeros.
+template <int B>
+__global__ void __launch_bounds__(256)
+k_publish_fs(const BlockMeta *__restrict__ meta,
+             const SolverState *__restrict__ state,
+             const int2 *__restrict__ tiles, const float *__restrict__ X,
+             const float *__restrict__ Finv, float *__restrict__ Fs, int kp) {
+  pdl_wait();
+  pdl_trigger();
+  const int2 t = tiles[blockIdx.x];
+  const BlockMeta bm = meta[t.x];
+  const SolverState st = state[t.x];
+  const int G = (int)blockDim.x / kp;
+  const int j = (int)threadIdx.x % kp, g = (int)threadIdx.x / kp;
+  if (g >= G) return;
+  const int rows = min(128, bm.s - t.y);
+  const bool live = st.iters > 0 && st.status != kRunning && j < bm.keff &&
+                    j < st.bsub;
+  const float inv = live ? Finv[(int64_t)t.x * B + j] : 0.f;
+  const float *Xb = X + bm.x_off + (int64_t)t.y * B;
+  float *Fb = Fs + bm.fs_off + (int64_t)t.y * kp;
+  for (int r = g; r < rows; r += G)
+    Fb[(int64_t)r * kp + j] = live ? Xb[(int64_t)r * B + j] * inv : 0.f;
 }
 
 // Asynchronous 4-byte global -> shared copy (no register staging); with
@@ -930,7 +1041,8 @@ template <int B>
 size_t rr_smem() { return sizeof(RRSmem<B>); }
 
 template <int B>
-size_t rot_smem() { return sizeof(float) * (B + 3 * TR) * (B + 1); }
+size_t rot_smem() { return sizeof(float) * (B * B + 2 * B * (TR + 4)); }
+static_assert(TR * (16 + 1) <= 2 * 16 * (TR + 4), "Os fits over XT and ZT");
 
 template <int B>
 cudaError_t set_attrs() {
@@ -984,13 +1096,13 @@ cudaError_t launch_gpanel(const EigBuffers &e, const int2 *rowtiles,
   });
 }
 
-cudaError_t launch_small_gram(const EigBuffers &e, const int2 *rowtiles,
-                              int32_t ntiles, cudaStream_t st) {
-  if (ntiles <= 0) return cudaSuccess;
+cudaError_t launch_small_gram(const EigBuffers &e, const int2 *chunks,
+                              int32_t nchunks, cudaStream_t st) {
+  if (nchunks <= 0) return cudaSuccess;
   return by_width(e.bsub, [&](auto w) {
     constexpr int B = decltype(w)::value;
-    return launch_pdl(k_small_gram<B>, dim3(ntiles), dim3(256), 0, st, e.meta,
-                      e.state, rowtiles, (const float *)e.X,
+    return launch_pdl(k_small_gram<B>, dim3(nchunks), dim3(256), 0, st, e.meta,
+                      e.state, chunks, (const float *)e.X,
                       (const float *)e.Z, e.SH);
   });
 }
@@ -1025,9 +1137,22 @@ cudaError_t launch_check(const EigBuffers &e, cudaStream_t st) {
   return by_width(e.bsub, [&](auto w) {
     constexpr int B = decltype(w)::value;
     return launch_pdl(k_check<B>, dim3(e.nblocks), dim3(256), 0, st, e.meta,
-                      e.state, (const float *)e.X, (const double *)e.RP,
-                      (const float *)e.theta, e.Fs, e.kp, e.max_iters,
-                      e.max_degree, e.tol, e.running);
+                      e.state, (const double *)e.RP, (const float *)e.theta,
+                      e.Finv, e.max_iters, e.max_degree, e.tol, e.running);
+  });
+}
+
+cudaError_t launch_publish_fs(const EigBuffers &e, const int2 *tiles,
+                              int32_t ntiles, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (e.kp <= 0 || e.kp > 256) return cudaErrorInvalidValue;
+  const int threads = (256 / e.kp) * e.kp;
+  return by_width(e.bsub, [&](auto w) {
+    constexpr int B = decltype(w)::value;
+    return launch_pdl(k_publish_fs<B>, dim3(ntiles), dim3(threads), 0, st,
+                      e.meta, (const SolverState *)e.state, tiles,
+                      (const float *)e.X, (const float *)e.Finv, e.Fs,
+                      (int)e.kp);
   });
 }
 

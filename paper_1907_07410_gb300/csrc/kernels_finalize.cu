@@ -20,15 +20,14 @@
 #include <float.h>
 #include <limits.h>
 
-#include <type_traits>
-
 #include "kernels.h"
 
 namespace bsvd {
 
 namespace {
 
-constexpr int CT = 128;            // rows per tile, one per thread
+constexpr int CT = 128;            // rows per tile
+constexpr int kStatThreads = 256;  // at most; a multiple of kp is launched
 
 // Fold (value, row) candidates: larger |value| wins, then the lower row.
 __device__ __forceinline__ void pick(float &a, float &v, int &i, float a2,
@@ -41,66 +40,54 @@ __device__ __forceinline__ void pick(float &a, float &v, int &i, float a2,
 }
 
 // side 0: tiles of F_L (rows l < L); side 1: tiles of F_s (rows a < s).
-template <int KM>
-__global__ void __launch_bounds__(CT)
+// Thread t takes column j = t mod kp of the tile's rows g, g + G, ...
+// (g = t / kp, G = blockDim / kp), so the CTA reads consecutive floats and
+// each thread keeps one column's running sum and extreme entry; the G
+// partials of a column are then folded in the order g = 0, 1, ...
+__global__ void __launch_bounds__(kStatThreads)
 k_colstats(const BlockMeta *__restrict__ meta, const int2 *__restrict__ tiles,
            const float *__restrict__ Fs, const float *__restrict__ FL, int kp,
            int side, ColPartial *__restrict__ out) {
-  __shared__ double ssq[CT / 32][KM];
-  __shared__ float sabs[CT / 32][KM], sval[CT / 32][KM];
-  __shared__ int sidx[CT / 32][KM];
+  __shared__ double ssq[kStatThreads];
+  __shared__ float sabs[kStatThreads], sval[kStatThreads];
+  __shared__ int sidx[kStatThreads];
   pdl_wait();
   pdl_trigger();
   const int2 t = tiles[blockIdx.x];
   const BlockMeta bm = meta[t.x];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = t.y + threadIdx.x;
+  const int G = (int)blockDim.x / kp;
+  const int j = (int)threadIdx.x % kp, g = (int)threadIdx.x / kp;
   const int len = side == 0 ? bm.L : bm.s;
+  const int rows = bm.owned ? min(CT, len - t.y) : 0;
   const float *src = (side == 0 ? FL + bm.fl_off : Fs + bm.fs_off) +
-                     (int64_t)row * kp;
-  float v[KM];
-#pragma unroll
-  for (int j = 0; j < KM; ++j) v[j] = 0.f;
-  if (bm.owned && row < len) {
-#pragma unroll
-    for (int j4 = 0; j4 < KM / 4; ++j4) {
-      if (4 * j4 < kp) {
-        const float4 q = *reinterpret_cast<const float4 *>(src + 4 * j4);
-        v[4 * j4] = q.x; v[4 * j4 + 1] = q.y;
-        v[4 * j4 + 2] = q.z; v[4 * j4 + 3] = q.w;
-      }
+                     (int64_t)t.y * kp + j;
+  double sq = 0.0;
+  float a = -1.f, val = 0.f;
+  int idx = INT_MAX;
+  if (g < G) {
+#pragma unroll 4
+    for (int r = g; r < rows; r += G) {
+      const float v = src[(int64_t)r * kp];
+      sq = fma((double)v, (double)v, sq);
+      pick(a, val, idx, fabsf(v), v, t.y + r);
     }
-  }
-#pragma unroll
-  for (int j = 0; j < KM; ++j) {
-    double sq = (double)v[j] * (double)v[j];
-    float a = fabsf(v[j]), val = v[j];
-    int idx = row < len ? row : INT_MAX;
-    for (int o = 16; o > 0; o >>= 1) {
-      sq += __shfl_xor_sync(0xffffffffu, sq, o);
-      const float a2 = __shfl_xor_sync(0xffffffffu, a, o);
-      const float v2 = __shfl_xor_sync(0xffffffffu, val, o);
-      const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-      pick(a, val, idx, a2, v2, i2);
-    }
-    if (lane == 0) {
-      ssq[warp][j] = sq;
-      sabs[warp][j] = a;
-      sval[warp][j] = val;
-      sidx[warp][j] = idx;
-    }
+    ssq[threadIdx.x] = sq;
+    sabs[threadIdx.x] = a;
+    sval[threadIdx.x] = val;
+    sidx[threadIdx.x] = idx;
   }
   __syncthreads();
   if (threadIdx.x < kp) {
-    const int j = threadIdx.x;
-    double sq = 0.0;
-    float a = -1.f, val = 0.f;
-    int idx = INT_MAX;
-    for (int w = 0; w < CT / 32; ++w) {
-      sq += ssq[w][j];
-      pick(a, val, idx, sabs[w][j], sval[w][j], sidx[w][j]);
+    sq = 0.0;
+    a = -1.f;
+    val = 0.f;
+    idx = INT_MAX;
+    for (int q = 0; q < G; ++q) {
+      const int o = q * kp + (int)threadIdx.x;
+      sq += ssq[o];
+      pick(a, val, idx, sabs[o], sval[o], sidx[o]);
     }
-    ColPartial &p = out[(int64_t)blockIdx.x * kp + j];
+    ColPartial &p = out[(int64_t)blockIdx.x * kp + threadIdx.x];
     p.sq = sq;
     p.absmax = a;
     p.val = val;
@@ -142,8 +129,8 @@ k_colcombine(const BlockMeta *__restrict__ meta,
   }
 }
 
-template <int KM>
-__global__ void __launch_bounds__(CT)
+// Negates the flipped columns of one tile, with k_colstats' thread layout.
+__global__ void __launch_bounds__(kStatThreads)
 k_colflip(const BlockMeta *__restrict__ meta, const int2 *__restrict__ tiles,
           float *__restrict__ M, int kp, int side,
           const unsigned char *__restrict__ flip) {
@@ -151,15 +138,14 @@ k_colflip(const BlockMeta *__restrict__ meta, const int2 *__restrict__ tiles,
   pdl_trigger();
   const int2 t = tiles[blockIdx.x];
   const BlockMeta bm = meta[t.x];
-  if (!bm.owned) return;
-  const int row = t.y + threadIdx.x;
+  const int G = (int)blockDim.x / kp;
+  const int j = (int)threadIdx.x % kp, g = (int)threadIdx.x / kp;
+  if (!bm.owned || g >= G || !flip[(int64_t)t.x * kp + j]) return;
   const int len = side == 0 ? bm.L : bm.s;
-  if (row >= len) return;
-  float *dst = M + (side == 0 ? bm.fl_off : bm.fs_off) + (int64_t)row * kp;
-  const unsigned char *f = flip + (int64_t)t.x * kp;
-#pragma unroll
-  for (int j = 0; j < KM; ++j)
-    if (j < kp && f[j]) dst[j] = -dst[j];
+  const int rows = min(CT, len - t.y);
+  float *dst = M + (side == 0 ? bm.fl_off : bm.fs_off) + (int64_t)t.y * kp + j;
+#pragma unroll 4
+  for (int r = g; r < rows; r += G) dst[(int64_t)r * kp] = -dst[(int64_t)r * kp];
 }
 
 }  // namespace
@@ -173,46 +159,34 @@ cudaError_t launch_finalize(const BlockMeta *meta, int32_t nblocks,
                             cudaStream_t st) {
   if (nblocks <= 0) return cudaSuccess;
   if (kp > 56 || kp % 4 != 0) return cudaErrorInvalidValue;
-  auto go = [&](auto km) -> cudaError_t {
-    constexpr int KM = decltype(km)::value;
-    cudaError_t e = cudaSuccess;
-    if (nltiles > 0) {
-      e = launch_pdl(k_colstats<KM>, dim3(nltiles), dim3(CT), 0, st, meta,
-                     ltiles, (const float *)Fs, (const float *)FL, (int)kp, 0,
-                     lpart);
-      if (e != cudaSuccess) return e;
-    }
-    if (nstiles > 0) {
-      e = launch_pdl(k_colstats<KM>, dim3(nstiles), dim3(CT), 0, st, meta,
-                     stiles, (const float *)Fs, (const float *)FL, (int)kp, 1,
-                     spart);
-      if (e != cudaSuccess) return e;
-    }
-    e = launch_pdl(k_colcombine, dim3(nblocks), dim3(64), 0, st, meta,
-                   (const ColPartial *)lpart, (const ColPartial *)spart,
-                   (int)kp, sigma, flip);
+  const int threads = (kStatThreads / kp) * kp;
+  cudaError_t e = cudaSuccess;
+  if (nltiles > 0) {
+    e = launch_pdl(k_colstats, dim3(nltiles), dim3(threads), 0, st, meta,
+                   ltiles, (const float *)Fs, (const float *)FL, (int)kp, 0,
+                   lpart);
     if (e != cudaSuccess) return e;
-    if (nltiles > 0) {
-      e = launch_pdl(k_colflip<KM>, dim3(nltiles), dim3(CT), 0, st, meta,
-                     ltiles, FL, (int)kp, 0, (const unsigned char *)flip);
-      if (e != cudaSuccess) return e;
-    }
-    if (nstiles > 0)
-      e = launch_pdl(k_colflip<KM>, dim3(nstiles), dim3(CT), 0, st, meta,
-                     stiles, Fs, (int)kp, 1, (const unsigned char *)flip);
-    if (launches) *launches += 1 + 2 * ((nltiles > 0) + (nstiles > 0));
-    return e;
-  };
-  switch ((kp + 7) / 8) {
-    case 1: return go(std::integral_constant<int, 8>());
-    case 2: return go(std::integral_constant<int, 16>());
-    case 3: return go(std::integral_constant<int, 24>());
-    case 4: return go(std::integral_constant<int, 32>());
-    case 5: return go(std::integral_constant<int, 40>());
-    case 6: return go(std::integral_constant<int, 48>());
-    case 7: return go(std::integral_constant<int, 56>());
-    default: return cudaErrorInvalidValue;
   }
+  if (nstiles > 0) {
+    e = launch_pdl(k_colstats, dim3(nstiles), dim3(threads), 0, st, meta,
+                   stiles, (const float *)Fs, (const float *)FL, (int)kp, 1,
+                   spart);
+    if (e != cudaSuccess) return e;
+  }
+  e = launch_pdl(k_colcombine, dim3(nblocks), dim3(64), 0, st, meta,
+                 (const ColPartial *)lpart, (const ColPartial *)spart, (int)kp,
+                 sigma, flip);
+  if (e != cudaSuccess) return e;
+  if (nltiles > 0) {
+    e = launch_pdl(k_colflip, dim3(nltiles), dim3(threads), 0, st, meta,
+                   ltiles, FL, (int)kp, 0, (const unsigned char *)flip);
+    if (e != cudaSuccess) return e;
+  }
+  if (nstiles > 0)
+    e = launch_pdl(k_colflip, dim3(nstiles), dim3(threads), 0, st, meta,
+                   stiles, Fs, (int)kp, 1, (const unsigned char *)flip);
+  if (launches) *launches += 1 + 2 * ((nltiles > 0) + (nstiles > 0));
+  return e;
 }
 
 }  // namespace bsvd
