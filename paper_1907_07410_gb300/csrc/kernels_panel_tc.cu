@@ -21,9 +21,12 @@
 // converts a panel written by another kernel.
 //
 // Data path, per stage of 64 floats of K:
-//   * warp 0: TMA loads into a ring of stages: the G tile (128 rows x 64
-//     floats, as two 32-float boxes) and the two matching B-form chunks
-//     (2b rows x 32 floats each), all with 128-byte swizzling;
+//   * TMA loads of the G tile (128 rows x 64 floats, as two 32-float boxes)
+//     and the two matching B-form chunks (2b rows x 32 floats each), all
+//     with 128-byte swizzling. The panel products keep them in two rings,
+//     each with its own producer warp (warp 0 for G, warp 14 for the B
+//     form), and release a G stage as soon as the converters have read it;
+//     the projection loads both into one ring from warp 0;
 //   * warps 2-9 (converters, two per TMEM lane quarter, one per 32-float
 //     half of the stage): each thread reads one row of its half of the G
 //     tile, splits it in registers and stores hi and lo into a
@@ -40,7 +43,8 @@
 //     apply the Chebyshev step and write `out` while the next tile's MMAs
 //     run. (When the converter warps ran the epilogue as well, the MMA warp
 //     waited for it about 300 cycles per stage on the 480,189 x 17,770
-//     workload, and the products ran at 0.74 of HBM; now 0.79.)
+//     workload, and the products ran at 0.74 of HBM; 0.79 with these
+//     warps, 0.82 with the two rings.)
 // Warps 0 and 1 run their loops as whole warps, so addresses and
 // descriptors stay warp-uniform, and one elected lane issues. Measured on
 // GB300 (clock stamps per stage), a single lane running the same loop took
@@ -86,7 +90,10 @@ constexpr int PT = 128;                  // G rows per CTA (MMA M)
 constexpr int PK = 64;                   // floats of K per stage
 constexpr int PH = 32;                   // floats per 128-byte swizzle row
 constexpr int kThreads = 320;            // 10 warps (projection)
-constexpr int kPThreads = 448;           // 14 warps (panel products)
+constexpr int kPConv = 8;                // panel products: converter warps
+constexpr int kBWarp = 2 + kPConv + 4;   // their B-stage producer warp
+constexpr int kPThreads = 32 * (kBWarp + 1);  // 15 warps
+constexpr int kMaxGS = 6, kMaxBS = 4;    // the products' G and B rings
 constexpr int kConv = 8;                 // converter warps (2..9)
 constexpr int kMaxStages = 4;
 constexpr int kSlots = 2;                // A slots in tensor memory
@@ -169,6 +176,11 @@ __device__ __forceinline__ void acc_sum(uint32_t taddr, uint32_t col,
   }
 }
 
+// A converter thread's hi or lo values into its TMEM lane (32 columns)
+__device__ __forceinline__ void tmem_st_row(uint32_t ta, const float (&v)[32]) {
+  tc::tmem_st32(ta, v);
+}
+
 // True when tile `t`'s block takes part in this product: still iterating,
 // and (for a filter step) its own filter reaches this step.
 __device__ __forceinline__ bool tile_active(const SolverState *state, int2 t,
@@ -177,16 +189,60 @@ __device__ __forceinline__ bool tile_active(const SolverState *state, int2 t,
   return st.status == kRunning && !(mode >= 1 && step > st.degree);
 }
 
+// The persistent products keep G and the panel's B form in separate rings.
+// A G stage (128 rows x 64 floats, from HBM) is released as soon as the
+// converter warps have read it into registers, before its MMAs run; a B
+// stage (from L2: every row tile of a block reads the same panel) when its
+// MMAs complete. Each ring has its own producer warp, so G's loads run up to
+// GS stages ahead of the conversions whatever the MMAs are doing.
+template <int B>
+struct PanelRings {
+  static constexpr int BOP_HALF = 2 * B * 128;      // one B-form chunk
+  static constexpr int BOP_BYTES = 2 * BOP_HALF;
+  static constexpr int GS = B >= 64 ? 4 : (B >= 32 ? 5 : 6);
+  static constexpr int BS = B >= 64 ? 3 : 4;
+  static constexpr int R = PanelTc<B>::R;
+  static constexpr int ACC_COLS = PanelTc<B>::ACC_COLS;
+  static constexpr int B_OFF = GS * G_BYTES;         // the B ring follows G's
+  static constexpr int RINGS = B_OFF + BS * BOP_BYTES;
+  static_assert(BOP_BYTES % 1024 == 0, "stage regions stay 1024-byte aligned");
+  static_assert(GS <= kMaxGS && BS <= kMaxBS && BS >= 2, "ring sizes");
+};
+
+struct PanelRingCtrl {
+  uint64_t gfull[kMaxGS];       // G stage landed (TMA bytes)
+  uint64_t gempty[kMaxGS];      // G stage read by the converter warps
+  uint64_t bfull[kMaxBS];       // B stage landed (TMA bytes)
+  uint64_t bempty[kMaxBS];      // the B stage's MMAs completed
+  uint64_t ready[kSlots];       // A slot written (the converter warps)
+  uint64_t afree[kSlots];       // the MMAs reading the A slot completed
+  uint64_t done;                // a tile's MMAs completed (one phase a tile)
+  uint64_t accfree;             // the epilogue read the accumulators (4 warps)
+  uint64_t tfull[kTq];          // tile index published (warp 0)
+  uint64_t tempty[kTq];         // tile index read (the other warps)
+  int tq[kTq];                  // tile indices, -1 ends the launch
+  uint32_t tmem;
+  int abort;
+  int gissued, gconsumed;       // G stages issued / seen to land
+  int bissued, bconsumed;       // B stages issued / seen to land
+};
+
+template <int B>
+constexpr size_t panel_ring_smem() {
+  return PanelRings<B>::RINGS + sizeof(PanelRingCtrl) + 1024;
+}
+
 // Persistent: one CTA per SM. CTA i starts with tile i (if its block is
 // still iterating), then takes tiles from gridDim.x on from a shared
 // counter (ctl[0]; ctl[1] counts finished CTAs, and the last one resets
 // both for the next launch). A claimed tile of an idle block moves the
 // counter past the rest of that block. Warp 0 claims tiles, publishes their
-// indices in a small ring (tq) and loads their stages; the stage, A-slot and
-// tile counters run on across tiles, so a CTA sets up its barriers and
-// tensor memory once per launch and the loads of the next tile overlap the
-// epilogue of the last. The MMA warp starts a tile only after the epilogue
-// warps have read the previous tile's accumulators (accfree).
+// indices in a small ring (tq) and loads their G stages; warp kBWarp loads
+// the matching B stages; warps 2 + kPConv .. + 3 run the epilogue. The stage, A-slot and tile counters run on across
+// tiles, so a CTA sets up its barriers and tensor memory once per launch
+// and the loads of the next tile overlap the epilogue of the last. The MMA
+// warp starts a tile only after the epilogue warps have read the previous
+// tile's accumulators (accfree).
 template <int B>
 __global__ void __launch_bounds__(kPThreads, 1)
 k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
@@ -195,36 +251,40 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
             const CUtensorMap *__restrict__ xmaps, const float *in,
             const float *in2, float *out, float *out_bf, int mode, int step,
             int32_t *err) {
-  using L = PanelTc<B>;
-  constexpr int S = L::STAGES;
+  using L = PanelRings<B>;
+  constexpr int GS = L::GS, BS = L::BS;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  PanelCtrl &ct = *reinterpret_cast<PanelCtrl *>(base + S * L::STAGE);
+  PanelRingCtrl &ct = *reinterpret_cast<PanelRingCtrl *>(base + L::RINGS);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  auto g_tile = [&](int s) { return base + s * L::STAGE; };
-  auto b_op = [&](int s) { return base + s * L::STAGE + G_BYTES; };
+  auto g_tile = [&](int s) { return base + s * G_BYTES; };
+  auto b_op = [&](int s) { return base + L::B_OFF + s * L::BOP_BYTES; };
 
   if (warp == 0) tc::tmem_alloc(&ct.tmem, kTmemCols);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      tc::mbar_init(&ct.full[s], 1);
-      tc::mbar_init(&ct.empty[s], 1);
+    for (int s = 0; s < GS; ++s) {
+      tc::mbar_init(&ct.gfull[s], 1);
+      tc::mbar_init(&ct.gempty[s], kPConv);
+    }
+    for (int s = 0; s < BS; ++s) {
+      tc::mbar_init(&ct.bfull[s], 1);
+      tc::mbar_init(&ct.bempty[s], 1);
     }
     for (int a = 0; a < kSlots; ++a) {
-      tc::mbar_init(&ct.ready[a], kConv);
+      tc::mbar_init(&ct.ready[a], kPConv);
       tc::mbar_init(&ct.afree[a], 1);
     }
     for (int q = 0; q < kTq; ++q) {
       tc::mbar_init(&ct.tfull[q], 1);
-      tc::mbar_init(&ct.tempty[q], 13);    // MMA, converters, epilogue
+      tc::mbar_init(&ct.tempty[q], 6 + kPConv);  // MMA, converters, epilogue, B loads
     }
     tc::mbar_init(&ct.done, 1);
     tc::mbar_init(&ct.accfree, 4);
     ct.abort = 0;
-    ct.issued = 0;
-    ct.consumed = 0;
+    ct.gissued = ct.gconsumed = 0;
+    ct.bissued = ct.bconsumed = 0;
     tc::mbar_init_fence();
   }
   tc::fence_before_sync();
@@ -238,15 +298,18 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
   const uint32_t aslots = taddr + L::ACC_COLS;    // A slot a at +128 a
   volatile int *abort_flag = &ct.abort;
 
-  // consumers (warps 1-9): the next tile index from the ring, -1 at the end
+  auto give_up = [&]() {
+    if (lane == 0) atomicOr(err, kErrTimeout);
+    ct.abort = 1;
+  };
+  // the warps other than 0: the next tile index from the ring, -1 at the end
   auto next_tile = [&](int &got, int &idx) -> bool {
     const int q = got % kTq;
     const bool ok = __all_sync(
         0xffffffffu,
         tc::mbar_wait(&ct.tfull[q], (got / kTq) & 1, kSpinP) && !*abort_flag);
     if (!ok) {
-      if (lane == 0) atomicOr(err, kErrTimeout);
-      ct.abort = 1;
+      give_up();
       return false;
     }
     idx = *reinterpret_cast<volatile int *>(&ct.tq[q]);
@@ -257,7 +320,8 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
   };
 
   if (warp == 0) {
-    // the whole warp runs the loop (warp-uniform addresses); one lane issues
+    // tiles and G stages; the whole warp runs the loop (warp-uniform
+    // addresses) and one lane issues
     int g = 0, pub = 0;
     const int first = (int)gridDim.x;     // tiles below this: one per CTA
     for (;;) {
@@ -287,8 +351,7 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
                            tc::mbar_wait(&ct.tempty[q], ((pub / kTq) & 1) ^ 1,
                                          kSpinP) && !*abort_flag);
       if (!ok) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
-        ct.abort = 1;
+        give_up();
         break;
       }
       if (lane == 0) {
@@ -304,32 +367,55 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
       // s_pad is a multiple of 32: a last half stage reads zeros past s_pad
       const int nk = (bm.s_pad + PK - 1) / PK;
       const CUtensorMap *map = gmaps + t.x;
-      const CUtensorMap *xmap = xmaps + t.x;
       for (int kc = 0; kc < nk; ++kc, ++g) {
-        const int s = g % S;
-        const uint32_t ph = (g / S) & 1;
+        const int s = g % GS;
         ok = __all_sync(0xffffffffu,
-                        tc::mbar_wait(&ct.empty[s], ph ^ 1, kSpinP) &&
-                            !*abort_flag);
+                        tc::mbar_wait(&ct.gempty[s], ((g / GS) & 1) ^ 1,
+                                      kSpinP) && !*abort_flag);
         if (!ok) {
-          if (lane == 0) atomicOr(err, kErrTimeout);
-          ct.abort = 1;
+          give_up();
           break;
         }
         if (tc::elect_one()) {
           const int k0 = kc * PK;
-          tc::mbar_expect_tx(&ct.full[s], G_BYTES + L::BOP_BYTES);
-          tc::tma_load_2d(g_tile(s), map, k0, t.y, &ct.full[s]);
-          tc::tma_load_2d(g_tile(s) + G_HALF, map, k0 + PH, t.y, &ct.full[s]);
-          // B-form chunks 2 kc and 2 kc + 1 (past the last: zero fill)
-          tc::tma_load_2d(b_op(s), xmap, 0, 2 * kc * 2 * B, &ct.full[s]);
-          tc::tma_load_2d(b_op(s) + L::BOP_HALF, xmap, 0,
-                          (2 * kc + 1) * 2 * B, &ct.full[s]);
-          ct.issued = g + 1;
+          tc::mbar_expect_tx(&ct.gfull[s], G_BYTES);
+          tc::tma_load_2d(g_tile(s), map, k0, t.y, &ct.gfull[s]);
+          tc::tma_load_2d(g_tile(s) + G_HALF, map, k0 + PH, t.y, &ct.gfull[s]);
+          ct.gissued = g + 1;
         }
         __syncwarp();
       }
       if (!ok) break;
+    }
+  } else if (warp == kBWarp) {
+    // B stages: the B-form chunks 2 kc and 2 kc + 1 of the tile's panel
+    // (past the last: zero fill)
+    int got = 0, idx = -1, gb = 0;
+    while (next_tile(got, idx)) {
+      const int2 t = tiles[idx];
+      const BlockMeta bm = meta[t.x];
+      const int nk = (bm.s_pad + PK - 1) / PK;
+      const CUtensorMap *xmap = xmaps + t.x;
+      bool ok = true;
+      for (int kc = 0; kc < nk; ++kc, ++gb) {
+        const int s = gb % BS;
+        ok = __all_sync(0xffffffffu,
+                        tc::mbar_wait(&ct.bempty[s], ((gb / BS) & 1) ^ 1,
+                                      kSpinP) && !*abort_flag);
+        if (!ok) break;
+        if (tc::elect_one()) {
+          tc::mbar_expect_tx(&ct.bfull[s], L::BOP_BYTES);
+          tc::tma_load_2d(b_op(s), xmap, 0, 2 * kc * 2 * B, &ct.bfull[s]);
+          tc::tma_load_2d(b_op(s) + L::BOP_HALF, xmap, 0,
+                          (2 * kc + 1) * 2 * B, &ct.bfull[s]);
+          ct.bissued = gb + 1;
+        }
+        __syncwarp();
+      }
+      if (!ok) {
+        give_up();
+        break;
+      }
     }
   } else if (warp == 1) {
     // the whole warp runs the loop (warp-uniform descriptors); one lane issues
@@ -347,11 +433,14 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
                             !*abort_flag);
       }
       for (int kc = 0; ok && kc < nk; ++kc, ++gm) {
-        const int s = gm % S, a = gm % kSlots;
-        ok = __all_sync(0xffffffffu,
-                        tc::mbar_wait(&ct.ready[a], (gm / kSlots) & 1, kSpinP) &&
-                            !*abort_flag);
+        const int s = gm % BS, a = gm % kSlots;
+        ok = __all_sync(
+            0xffffffffu,
+            tc::mbar_wait(&ct.bfull[s], (gm / BS) & 1, kSpinP) &&
+                tc::mbar_wait(&ct.ready[a], (gm / kSlots) & 1, kSpinP) &&
+                !*abort_flag);
         if (!ok) break;
+        if (lane == 0) ct.bconsumed = gm + 1;
         tc::fence_after_sync();
         const uint64_t db0 = tc::sdesc_kmajor_sw128(tc::smem_u32(b_op(s)));
         const uint64_t db1 =
@@ -369,27 +458,28 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
             tc::mma_tf32_ta(d, ahi + 8 * kk, db, idesc2, acc);
             tc::mma_tf32_ta(d + B, alo + 8 * kk, db, idesc1, 1u);
           }
-          tc::mma_commit(&ct.empty[s]);
+          tc::mma_commit(&ct.bempty[s]);
           tc::mma_commit(&ct.afree[a]);
         }
         __syncwarp();
       }
       if (!ok) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
-        ct.abort = 1;
+        give_up();
         break;
       }
       if (tc::elect_one()) tc::mma_commit(&ct.done);
       __syncwarp();
       ++tl;
     }
-  } else if (warp < 2 + kConv) {
-    // converters: warps 2-9. Warp w may touch TMEM lanes 32 (w mod 4) ..
-    // +31, so two warps share each lane quarter: warps 2-5 split the first
-    // 32-float half of a stage's K range, warps 6-9 the second.
+  } else if (warp < 2 + kPConv) {
+    // converters: warps 2 .. 2 + kPConv - 1. Warp w may touch TMEM lanes
+    // 32 (w mod 4) .. +31, so kPConv / 4 warps share each lane quarter, one
+    // per CF-float part kq of a stage's 64-float K range (warps 2-5 kq = 0,
+    // 6-9 kq = 1, ...).
+    constexpr int CF = 4 * PK / kPConv;           // floats per converter
     const int cid = threadIdx.x - 64;
     const int q = warp & 3;
-    const int kh = (warp - 2) >> 2;
+    const int kq = (warp - 2) >> 2;
     const int r = q * 32 + lane;                  // G tile row of this thread
     const uint32_t lrow = (uint32_t)(q * 32) << 16;
     int got = 0, idx = -1, gc = 0, tl = 0;
@@ -399,34 +489,44 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
       const int nk = (bm.s_pad + PK - 1) / PK;
       bool ok = true;
       for (int kc = 0; kc < nk; ++kc, ++gc) {
-        const int s = gc % S, a = gc % kSlots;
-        const uint32_t ph = (gc / S) & 1;
+        const int s = gc % GS, a = gc % kSlots;
         // warp-uniform: every lane breaks, or none does
-        ok = tc::mbar_wait(&ct.full[s], ph, kSpinP);
-        if constexpr (L::kWaitSlot)
-          ok = ok &&
-               tc::mbar_wait(&ct.afree[a], ((gc / kSlots) & 1) ^ 1, kSpinP);
-        ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+        ok = __all_sync(0xffffffffu,
+                        tc::mbar_wait(&ct.gfull[s], (gc / GS) & 1, kSpinP) &&
+                            !*abort_flag);
         if (!ok) break;
-        if (cid == 0) ct.consumed = gc + 1;
+        if (cid == 0) ct.gconsumed = gc + 1;
         tc::fence_after_sync();
-        // this thread's row of its half of the G tile, split into hi and lo
+        // this thread's row of its part of the G tile (CF floats of the
+        // 32-float box kq CF / 32, from chunk (kq CF mod 32) / 4), split
+        // into hi and lo
+        float h[CF], l[CF];
         {
-          const unsigned char *gt = g_tile(s) + kh * G_HALF;
-          float h[32], l[32];
+          const unsigned char *gt = g_tile(s) + ((kq * CF) / PH) * G_HALF;
+          const int c0 = ((kq * CF) % PH) / 4;
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const float4 v = *reinterpret_cast<const float4 *>(gt + sw128(r, c));
+          for (int c = 0; c < CF / 4; ++c) {
+            const float4 v =
+                *reinterpret_cast<const float4 *>(gt + sw128(r, c0 + c));
             const float4 vh = hi4(v), vl = sub4(v, vh);
             h[4 * c + 0] = vh.x; h[4 * c + 1] = vh.y;
             h[4 * c + 2] = vh.z; h[4 * c + 3] = vh.w;
             l[4 * c + 0] = vl.x; l[4 * c + 1] = vl.y;
             l[4 * c + 2] = vl.z; l[4 * c + 3] = vl.w;
           }
-          const uint32_t ta = aslots + lrow + 2 * PK * a + PH * kh;
-          tc::tmem_st32(ta, h);
-          tc::tmem_st32(ta + PK, l);
         }
+        // the stage's values are in registers: release it to the G loads
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&ct.gempty[s]);
+        // the A slot's previous MMAs have completed
+        ok = __all_sync(0xffffffffu,
+                        tc::mbar_wait(&ct.afree[a], ((gc / kSlots) & 1) ^ 1,
+                                      kSpinP) && !*abort_flag);
+        if (!ok) break;
+        tc::fence_after_sync();
+        const uint32_t ta = aslots + lrow + 2 * PK * a + CF * kq;
+        tmem_st_row(ta, h);
+        tmem_st_row(ta + PK, l);
         tc::tmem_wait_st();
         // order the tensor-memory stores before the MMAs
         tc::fence_before_sync();
@@ -434,8 +534,7 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
         if (lane == 0) tc::mbar_arrive(&ct.ready[a]);
       }
       if (!ok) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
-        ct.abort = 1;
+        give_up();
         break;
       }
       ++tl;
@@ -528,9 +627,11 @@ k_gpanel_tc(const BlockMeta *__restrict__ meta, SolverState *state,
   tc::fence_before_sync();
   __syncthreads();
   if (threadIdx.x == 0 && ct.abort) {
-    // drain G tiles that were issued but never seen to land
-    for (int kc = ct.consumed; kc < ct.issued; ++kc)
-      tc::mbar_wait(&ct.full[kc % S], (kc / S) & 1, kSpinP);
+    // drain stages that were issued but never seen to land
+    for (int g = ct.gconsumed; g < ct.gissued; ++g)
+      tc::mbar_wait(&ct.gfull[g % GS], (g / GS) & 1, kSpinP);
+    for (int g = ct.bconsumed; g < ct.bissued; ++g)
+      tc::mbar_wait(&ct.bfull[g % BS], (g / BS) & 1, kSpinP);
   }
   if (threadIdx.x == 0) {
     // the last CTA out resets the tile counter for the next launch
@@ -561,15 +662,15 @@ cudaError_t launch_b(const BlockMeta *meta, SolverState *state,
                      const float *in, const float *in2, float *out,
                      float *out_bf, int mode, int step, int32_t *err,
                      cudaStream_t st) {
-  static_assert(panel_tc_smem<B>() <= 227 * 1024, "shared memory");
+  static_assert(panel_ring_smem<B>() <= 227 * 1024, "shared memory");
   cudaError_t e = cudaFuncSetAttribute(
       k_gpanel_tc<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)panel_tc_smem<B>());
+      (int)panel_ring_smem<B>());
   if (e != cudaSuccess) return e;
   // programmatic dependent launch: this grid's prologue may overlap the end
   // of the previous kernel in the stream (see pdl_wait)
   return launch_pdl(k_gpanel_tc<B>, dim3((unsigned)nctas), dim3(kPThreads),
-                    panel_tc_smem<B>(), st, meta, state, tiles, (int)ntiles,
+                    panel_ring_smem<B>(), st, meta, state, tiles, (int)ntiles,
                     ctl, ptime, gmaps, xmaps, in, in2, out, out_bf, mode, step,
                     err);
 }
