@@ -1285,6 +1285,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     // k_rotate keeps X's B form current for the tensor-core products
     e.XB = panel_tc ? c->d_XB.as<float>() : nullptr;
     e.bsub = B; e.kp = kp; e.k = k; e.nblocks = nb;
+    e.nsm = c->nsm;
     e.max_iters = c->cfg.max_iters;
     e.max_sweeps = c->cfg.max_sweeps;
     e.max_degree = c->cfg.cheb_degree;

@@ -95,6 +95,7 @@ struct EigBuffers {
   float *XB = nullptr;  // the B form of X for the tensor-core products, or null
   int32_t bsub, kp, k;
   int32_t nblocks;
+  int32_t nsm = 152;   // SMs of the device
   int32_t max_iters, max_sweeps;
   int32_t max_degree;  // cap on the per-block Chebyshev degree (even)
   float tol;

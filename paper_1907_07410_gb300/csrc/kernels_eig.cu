@@ -69,7 +69,10 @@ constexpr float kCutFloor = 1e-3f;   // cut >= kCutFloor * theta_1
 // filter's degree stays defined when the Ritz values are nearly equal
 constexpr float kCutCeil = 0.95f;
 constexpr float kPivotDrop = 1e-4f;  // squared sine of the angle to the span
-constexpr float kJacobiTol = 3e-7f;       // |a_p . a_q| / (|a_p| |a_q|) to stop
+// |a_p . a_q| / (|a_p| |a_q|) to stop. Float32 dot products of 64 terms
+// carry rounding near 5e-7 of |a_p| |a_q|, so a bar much below that is
+// met only by chance and costs sweeps (3e-7 took about 5 a step at b = 64).
+constexpr float kJacobiTol = 1e-6f;
 constexpr float kJacobiTolFirst = 1e-3f;  // the same, first step from a random start
 
 // hardware approximations (PTX .approx instructions, flush-to-zero)
@@ -391,18 +394,22 @@ __device__ __forceinline__ void build_pairs(int ne, unsigned short *tab) {
 // numerically orthogonal, |a_p.a_q| <= tol |a_p| |a_q|. Then A V = U S with
 // orthonormal U, and for a PSD A the columns of V are its eigenvectors and
 // the column norms |A v_j| its eigenvalues.
-// Round-robin ordering gives np disjoint pairs per round. Warp w takes the
-// pairs w, w + nwarps, ... (one pair per warp when the block has np warps);
-// lane l holds rows l and l + 32 of the two columns. The three dot products
-// are xor-butterfly warp sums: each step adds the same two operands in
-// every lane, so all lanes hold bitwise equal sums and apply the same
-// rotation. One block-wide barrier per round.
+// Round-robin ordering gives np disjoint pairs per round. Each half-warp
+// takes one pair (a warp two: pairs 2w + h, 2 (w + nwarps) + h, ...), lane
+// l of the half holding rows l, l + 16, ... of the two columns. The three
+// dot products are xor-butterfly sums over the half-warp: each step adds
+// the same two operands in every lane, so the 16 lanes hold bitwise equal
+// sums and apply the same rotation. The loop is issue-bound (one warp per
+// pair took about 1600 cycles a round at b = 64: 32 warps' shuffles and
+// address arithmetic), so two pairs per warp halve the instructions per
+// round. One block-wide barrier per round.
 template <int B>
 __device__ int onesided_jacobi(float (*Ac)[B + 1], float (*Vc)[B + 1], int n,
                                int max_sweeps, const unsigned short *pairs,
                                int *flag, float tol) {
-  constexpr int RPL = (B + 31) / 32;        // rows per lane
+  constexpr int RPL = (B + 15) / 16;        // rows per lane
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int hl = lane & 15, half = lane >> 4;
   const int nwarps = blockDim.x >> 5;
   const int ne = n + (n & 1), np = ne / 2;
   int sweep = 0;
@@ -411,27 +418,30 @@ __device__ int onesided_jacobi(float (*Ac)[B + 1], float (*Vc)[B + 1], int n,
     __syncthreads();
     for (int round = 0; round < ne - 1; ++round) {
       const unsigned short *pr = pairs + round * np;
-      for (int i = warp; i < np; i += nwarps) {
-        const int p = pr[i] & 255, q = pr[i] >> 8;
-        if (p >= n || q >= n) continue;
+      // warp-uniform trip count: both halves run the shuffles
+      for (int w2 = warp; 2 * w2 < np; w2 += nwarps) {
+        const int i = 2 * w2 + half;
+        const bool has = i < np;
+        const int p = has ? (pr[i] & 255) : 0, q = has ? (pr[i] >> 8) : 0;
+        const bool valid = has && p < n && q < n;
         float a[RPL], b[RPL];
         float al = 0.f, be = 0.f, ga = 0.f;
 #pragma unroll
         for (int h = 0; h < RPL; ++h) {
-          const int r = lane + 32 * h;
-          a[h] = r < n ? Ac[p][r] : 0.f;
-          b[h] = r < n ? Ac[q][r] : 0.f;
+          const int r = hl + 16 * h;
+          a[h] = (valid && r < n) ? Ac[p][r] : 0.f;
+          b[h] = (valid && r < n) ? Ac[q][r] : 0.f;
           al = fmaf(a[h], a[h], al);
           be = fmaf(b[h], b[h], be);
           ga = fmaf(a[h], b[h], ga);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = 8; o > 0; o >>= 1) {
           al += __shfl_xor_sync(0xffffffffu, al, o);
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (!(ga * ga > (tol * tol) * (al * be))) continue;
+        if (!valid || !(ga * ga > (tol * tol) * (al * be))) continue;
         // The angle only has to be close to the optimal one (any rotation
         // near it still converges), so t uses the hardware's approximate
         // reciprocal and square root; what must be accurate is c^2 + s^2 = 1,
@@ -446,10 +456,10 @@ __device__ int onesided_jacobi(float (*Ac)[B + 1], float (*Vc)[B + 1], int n,
         c = c * fmaf(-0.5f * x, c * c, 1.5f);
         const float s = t * c;
         if (s == 0.f) continue;
-        if (lane == 0) *flag = 1;
+        if (hl == 0) *flag = 1;
 #pragma unroll
         for (int h = 0; h < RPL; ++h) {
-          const int r = lane + 32 * h;
+          const int r = hl + 16 * h;
           if (r < n) {
             Ac[p][r] = c * a[h] - s * b[h];
             Ac[q][r] = s * a[h] + c * b[h];
@@ -484,6 +494,12 @@ struct RRSmem {
   int flag;
 };
 
+// Launched with 1024 threads, or with 512 (enough for the Jacobi's b / 4
+// warps at b = 64) when there are more blocks than SMs: two such CTAs share
+// an SM (at most 64 registers a thread either way), so 256 blocks run in
+// one wave instead of two. Measured on GB300, two CTAs on one SM each take
+// about 1.4 times as long as one alone, so with fewer blocks than SMs the
+// wider CTA is faster.
 template <int B>
 __global__ void __launch_bounds__(1024, 1)
 k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
@@ -498,6 +514,7 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   const BlockMeta bm = meta[blk];
   const int n = state[blk].bsub;
   const int tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = (int)blockDim.x >> 5;
   const int ne = n + (n & 1), np = ne / 2;
   const long long c0 = clock64();
   build_pairs(ne, sm.pairs);
@@ -556,21 +573,14 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
       sm.key[j] = ljj;          // L's diagonal; S[j][j] stays readable
     }
     __syncthreads();
-    // trailing triangle j < l <= i < n, one entry per thread
-    const int m = n - 1 - j;
-    for (int e = tid; e < m * (m + 1) / 2; e += blockDim.x) {
-      // e -> (ii, ll) with 0 <= ll <= ii < m, row-major over the triangle
-      int ii = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
-      while (ii * (ii + 1) / 2 > e) --ii;
-      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
-      const int ll = e - ii * (ii + 1) / 2;
-      const int i = j + 1 + ii, l = j + 1 + ll;
-      sm.S[i][l] = fmaf(-sm.S[i][j], sm.S[l][j], sm.S[i][l]);
-    }
-    // rows below j of L^-1, columns 0 .. j
-    for (int e = tid; e < m * (j + 1); e += blockDim.x) {
-      const int i = j + 1 + e / (j + 1), c = e % (j + 1);
-      sm.Li[i][c] = fmaf(-sm.S[i][j], sm.Li[j][c], sm.Li[i][c]);
+    // trailing triangle j < l <= i < n: a warp per row, lanes over l
+    for (int i = j + 1 + wid; i < n; i += nw) {
+      const float sij = sm.S[i][j];
+      for (int l = j + 1 + lane; l <= i; l += 32)
+        sm.S[i][l] = fmaf(-sij, sm.S[l][j], sm.S[i][l]);
+      // the row of L^-1, columns 0 .. j
+      for (int c = lane; c <= j; c += 32)
+        sm.Li[i][c] = fmaf(-sij, sm.Li[j][c], sm.Li[i][c]);
     }
     __syncthreads();
   }
@@ -613,7 +623,8 @@ k_rr_solve(const BlockMeta *__restrict__ meta, SolverState *__restrict__ state,
   // and what the next filter needs is the Ritz values (accurate to second
   // order in the off-diagonal) and the subspace, not an accurate basis of
   // it. So its columns only need to be orthogonal to 1e-3; every later
-  // step goes to 3e-7. Convergence is still decided by the residual test.
+  // step goes to kJacobiTol. Convergence is still decided by the residual
+  // test.
   const float tol =
       (state[blk].iters == 0 && n < bm.s) ? kJacobiTolFirst : kJacobiTol;
   const int sweeps = onesided_jacobi<B>(sm.A, sm.V, n, max_sweeps, sm.pairs,
@@ -1112,7 +1123,7 @@ cudaError_t launch_rr_solve(const EigBuffers &e, cudaStream_t st) {
     constexpr int B = decltype(w)::value;
     cudaError_t err = set_attrs<B>();
     if (err != cudaSuccess) return err;
-    constexpr int threads = (B / 2) * 32 > 256 ? (B / 2) * 32 : 256;
+    const int threads = B < 32 ? 256 : (e.nblocks > e.nsm ? 512 : 1024);
     return launch_pdl(k_rr_solve<B>, dim3(e.nblocks), dim3(threads),
                       rr_smem<B>(), st, e.meta, e.state, (const float *)e.SH,
                       e.T, e.theta, e.max_sweeps);
