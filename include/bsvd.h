@@ -312,8 +312,12 @@ bsvd_status bsvd_get_block(bsvd_ctx *ctx, int32_t b, int32_t *mb,
 /*
  * Rank-k reconstruction of block b (the low-rank matrix of Section 2):
  * out[r * nb + c] = (add_mean ? mu_b : 0) + P[r,:] . V[c,:], for the
- * mb x nb block. out: host or device array of mb * nb floats.
- * Errors: BSVD_ESTATE, BSVD_EINVAL.
+ * mb x nb block, computed on the tensor cores in 128 x 128 tiles (three
+ * tf32 products of the factors' hi and lo parts: float32-level accuracy).
+ * out: host or device array of mb * nb floats, owned by the caller.
+ * Errors: BSVD_ESTATE (no factors), BSVD_EINVAL (b out of range, a block
+ * another shard holds), BSVD_ETIMEOUT (a device-side wait gave up: discard
+ * the context).
  */
 bsvd_status bsvd_reconstruct(bsvd_ctx *ctx, int32_t b, int32_t add_mean,
                              float *out);

@@ -584,9 +584,19 @@ class Context:
     def get_block(self, b, want_factors=True, want_dense=False):
         return bsvd_get_block(self.handle, b, want_factors, want_dense)
 
-    def reconstruct(self, b, add_mean=True):
+    def reconstruct(self, b, add_mean=True, out=None):
+        """Block b's rank-k reconstruction (mb x nb). `out`: an optional
+        float32 device tensor of mb * nb entries to write into (returned);
+        else a new host array."""
         info = bsvd_get_block(self.handle, b, want_factors=False)
-        out = np.zeros((info["mb"], info["nb"]), np.float32)
+        cells = info["mb"] * info["nb"]
+        if out is None:
+            out = np.zeros((info["mb"], info["nb"]), np.float32)
+        else:
+            have = int(out.numel()) if hasattr(out, "numel") else int(np.size(out))
+            if have < cells:
+                raise ValueError("out holds %d entries, the block has %d"
+                                 % (have, cells))
         bsvd_reconstruct(self.handle, b, out, add_mean)
         return out
 

@@ -1836,15 +1836,15 @@ bsvd_status bsvd_reconstruct(bsvd_ctx *c, int32_t b, int32_t add_mean,
     CK(c->s_out.ensure(sizeof(float) * cells), "reconstruct");
     dst = c->s_out.as<float>();
   }
-  CK(launch_reconstruct(c->d_meta.as<BlockMeta>(), b, c->d_Fs.as<float>(),
-                        c->d_FL.as<float>(), c->kp, mu, dst, c->st),
+  CK(launch_reconstruct(c->d_meta.as<BlockMeta>(), bm, b, c->d_Fs.as<float>(),
+                        c->d_FL.as<float>(), c->kp, mu, dst,
+                        c->d_err.as<int32_t>(), c->st),
      "reconstruct");
   c->launches += 1;
   if (!dev_out)
     CK(cudaMemcpyAsync(out, dst, sizeof(float) * cells, cudaMemcpyDeviceToHost,
                        c->st), "reconstruct");
-  CK(cudaStreamSynchronize(c->st), "reconstruct");
-  return BSVD_OK;
+  return read_errors(c, "reconstruct");
 }
 
 bsvd_status bsvd_factor_report(bsvd_ctx *c, int32_t *iters,

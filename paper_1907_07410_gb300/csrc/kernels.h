@@ -280,8 +280,13 @@ constexpr int kSqerrBlocks = 304;
 cudaError_t launch_sqerr(const PredictArgs &a, int64_t nq, const int32_t *u,
                          const int32_t *i, const float *y, double *partials,
                          double *out, int32_t *err, cudaStream_t st);
-cudaError_t launch_reconstruct(const BlockMeta *meta, int32_t b,
-                               const float *Fs, const float *FL, int32_t kp,
-                               float mu, float *out, cudaStream_t st);
+// Rank-k reconstruction of block b on the tensor cores
+// (kernels_reconstruct_tc.cu): out (mb x nb, row-major, device) = mu +
+// P V^T from the block's factors; `host` is the block's metadata on the host
+// (for the grid). A timed-out wait sets kErrTimeout in *err.
+cudaError_t launch_reconstruct(const BlockMeta *meta, const BlockMeta &host,
+                               int32_t b, const float *Fs, const float *FL,
+                               int32_t kp, float mu, float *out, int32_t *err,
+                               cudaStream_t st);
 
 }  // namespace bsvd

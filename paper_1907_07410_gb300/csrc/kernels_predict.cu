@@ -116,25 +116,6 @@ k_sum_partials(const double *__restrict__ partials,
   }
 }
 
-__global__ void __launch_bounds__(256)
-k_reconstruct(const BlockMeta *__restrict__ meta, int32_t b,
-              const float *__restrict__ Fs, const float *__restrict__ FL,
-              int32_t kp, float mu, float *__restrict__ out) {
-  const BlockMeta bm = meta[b];
-  const int64_t total = (int64_t)bm.mb * bm.nb;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t r = (int32_t)(e / bm.nb), c = (int32_t)(e % bm.nb);
-    int32_t wa, wl;
-    to_w(bm, r, c, &wa, &wl);
-    const float *fs = Fs + bm.fs_off + (int64_t)wa * kp;
-    const float *fl = FL + bm.fl_off + (int64_t)wl * kp;
-    float dot = 0.f;
-    for (int j = 0; j < bm.keff; ++j) dot = fmaf(fs[j], fl[j], dot);
-    out[e] = mu + dot;
-  }
-}
-
 int grid_for(int64_t n) {
   int64_t g = (n + 255) / 256;
   if (g < 1) g = 1;
@@ -159,13 +140,6 @@ cudaError_t launch_sqerr(const PredictArgs &a, int64_t nq, const int32_t *u,
   long long *counts = reinterpret_cast<long long *>(partials + kSqerrBlocks);
   k_sqerr<<<kSqerrBlocks, 256, 0, st>>>(a, nq, u, i, y, partials, counts, err);
   k_sum_partials<<<1, 512, 0, st>>>(partials, counts, kSqerrBlocks, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_reconstruct(const BlockMeta *meta, int32_t b,
-                               const float *Fs, const float *FL, int32_t kp,
-                               float mu, float *out, cudaStream_t st) {
-  k_reconstruct<<<152 * 4, 256, 0, st>>>(meta, b, Fs, FL, kp, mu, out);
   return cudaGetLastError();
 }
 

@@ -415,3 +415,46 @@ def test_device_driven_loop_matches_host_loop(workload):
     assert np.array_equal(y1, y0) and np.array_equal(y1, y2)
     assert rm1 == rm0 == rm2
     assert np.array_equal(it1, it0) and np.array_equal(it1, it2)
+
+
+def test_reconstruction_on_tensor_cores_matches_factors():
+    """bsvd_reconstruct (128 x 128 tiles, three tf32 products of the factors'
+    hi and lo parts) against mu + P V^T computed in float64 from the block's
+    own factors, element by element: blocks of both orientations with
+    ragged tails across several tiles, host and device outputs, with and
+    without the mean. (check_factors holds reconstructions to the
+    oracle's.)"""
+    w = synth.UNEVEN
+    r = synth.generate(w)
+    ctx = bs.Context()
+    kw = ctx.quantile_grid(w.m, w.n, dev(r.u_train), dev(r.i_train), w.p, w.q)
+    ctx.partition(w.m, w.n, dev(r.u_train), dev(r.i_train), dev(r.x_train),
+                  w.p, w.q, **kw)
+    assert ctx.factor(w.k) == bs.OK
+    shapes = [(b, ctx.get_block(b, want_factors=False)) for b in range(w.p * w.q)]
+    tall = [b for b, g in shapes if g["mb"] > g["nb"] and g["mb"] % 128]
+    wide = [b for b, g in shapes if g["mb"] < g["nb"] and g["nb"] % 128]
+    big = max(range(w.p * w.q), key=lambda b: shapes[b][1]["mb"] * shapes[b][1]["nb"])
+    picked = sorted({big, tall[0], wide[0]} if tall and wide else {big})
+    assert len(picked) >= 2
+    for b in picked:
+        g = ctx.get_block(b)
+        P = g["P"].astype(np.float64)
+        V = g["V"].astype(np.float64)
+        ref = P @ V.T
+        scale = np.abs(P) @ np.abs(V).T      # the dot products' magnitude
+        got0 = ctx.reconstruct(b, add_mean=False).astype(np.float64)
+        assert got0.shape == (g["mb"], g["nb"])
+        assert np.all(np.abs(got0 - ref) <= 4e-6 * scale + 1e-7), b
+        got1 = ctx.reconstruct(b, add_mean=True).astype(np.float64)
+        mu = float(np.float32(g["mu"]))
+        assert np.all(np.abs(got1 - (ref + mu)) <=
+                      4e-6 * scale + 1e-6 * abs(mu) + 1e-7), b
+        out = torch.full((g["mb"] * g["nb"],), float("nan"),
+                         dtype=torch.float32, device="cuda")
+        ctx.reconstruct(b, add_mean=True, out=out)
+        assert np.array_equal(out.cpu().numpy().reshape(g["mb"], g["nb"]),
+                              got1.astype(np.float32)), b
+    with pytest.raises(ValueError):
+        ctx.reconstruct(picked[0], out=torch.zeros(3, device="cuda"))
+    ctx.close()
