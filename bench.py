@@ -688,8 +688,8 @@ def form_summary(w, r, res, gold, steps):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default=synth.LARGE.name,
                     choices=sorted(synth.WORKLOADS))
@@ -701,7 +701,7 @@ def main():
                          "(FP32 SIMT Gram, panel products and projection); "
                          "empty to skip")
     ap.add_argument("--form-steps", type=int, default=3,
-                    help="timed steps of each other form")
+                    help="timed steps of each other form (after 3 warm-up steps)")
     ap.add_argument("--no-medium", action="store_true",
                     help="skip the medium-matrix leg")
     ap.add_argument("--loop", default="tuned",
@@ -821,7 +821,7 @@ def main():
         fcfg = dict(form_cfg[name])
         if args.loop != "tuned":
             fcfg["loop"] = {"host": 1, "graph": 2}[args.loop]
-        res = time_form(w, data, args.form_steps, args.warmup, flush, stream,
+        res = time_form(w, data, args.form_steps, 3, flush, stream,
                         owned, **fcfg)
         res["ctx"].close()
         forms[name] = res

@@ -1927,7 +1927,9 @@ bsvd_status bsvd_sgd_prepare(bsvd_ctx *c, int64_t nnz, const int32_t *u,
   CK(device_view(c, i, sizeof(int32_t) * nnz, c->s_b, &di), "sgd_prepare");
   CK(device_view(c, x, sizeof(float) * nnz, c->s_c, &dx), "sgd_prepare");
   const size_t n1 = (size_t)std::max<int64_t>(nnz, 1);
-  CK(c->d_sgd_cnt.ensure(sizeof(unsigned long long) * nbuckets), "sgd_prepare");
+  // bucket counts, then (from the sort on) the list of large buckets
+  CK(c->d_sgd_cnt.ensure(sizeof(unsigned long long) * (nbuckets + 1)),
+     "sgd_prepare");
   CK(c->d_sgd_off.ensure(sizeof(int64_t) * (nbuckets + 1)), "sgd_prepare");
   CK(c->d_sgd_key.ensure(sizeof(int64_t) * n1), "sgd_prepare");
   CK(c->d_sgd_src.ensure(sizeof(int64_t) * n1), "sgd_prepare");
@@ -1942,7 +1944,7 @@ bsvd_status bsvd_sgd_prepare(bsvd_ctx *c, int64_t nnz, const int32_t *u,
                       c->d_sgd_i.as<int32_t>(), c->d_sgd_x.as<float>(),
                       c->d_sgd_range.as<int64_t>(), c->d_err.as<int32_t>(),
                       c->st), "sgd_prepare");
-  c->launches += nnz > 0 ? 6 : 2;
+  c->launches += nnz > 0 ? 7 : 2;
   bsvd_status s = read_errors(c, "sgd_prepare");
   if (s != BSVD_OK) return s;
   // the diagonal schedule (Figure 2): blocks sharing no block row or column

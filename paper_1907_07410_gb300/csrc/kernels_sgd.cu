@@ -91,13 +91,25 @@ k_sgd_fill(GridDesc g, int64_t nnz, const int32_t *__restrict__ u,
   }
 }
 
-// One thread per bucket: insertion sort by key (local column, input index).
+// Buckets are sorted by key (local column, then input index; the keys are
+// distinct). One thread per bucket sorts a small bucket by insertion; a
+// bucket of more than kSortSmall ratings is appended to a list (big[1..],
+// count in big[0]) for k_sgd_sort_big. The list's order depends on
+// scheduling, the sorted buckets do not.
+constexpr int64_t kSortSmall = 64;
+constexpr int kSortTile = 16384;       // keys of a shared-memory bitonic sort
+
 __global__ void __launch_bounds__(256)
 k_sgd_sort(int64_t nbuckets, const int64_t *__restrict__ off,
-           int64_t *__restrict__ key, int64_t *__restrict__ src) {
+           int64_t *__restrict__ key, int64_t *__restrict__ src,
+           unsigned long long *__restrict__ big) {
   for (int64_t bk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
        bk < nbuckets; bk += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = off[bk], b = off[bk + 1];
+    if (b - a > kSortSmall) {
+      big[1 + atomicAdd(&big[0], 1ull)] = (unsigned long long)bk;
+      continue;
+    }
     for (int64_t e = a + 1; e < b; ++e) {
       const int64_t kv = key[e], sv = src[e];
       int64_t d = e - 1;
@@ -109,6 +121,60 @@ k_sgd_sort(int64_t nbuckets, const int64_t *__restrict__ off,
       key[d + 1] = kv;
       src[d + 1] = sv;
     }
+  }
+}
+
+// One CTA per listed bucket (grid-stride over the list): a bitonic sort of
+// its keys in shared memory, padded with all-ones keys to a power of two;
+// the input index is the key's low 40 bits, so src is rewritten from the
+// sorted keys. A bucket of more than kSortTile ratings (more than that many
+// of one user's items in one block column) is sorted by insertion in
+// global memory by one thread: correct, slow, and not met by the workloads
+// here.
+__global__ void __launch_bounds__(1024)
+k_sgd_sort_big(const int64_t *__restrict__ off,
+               const unsigned long long *__restrict__ big,
+               int64_t *__restrict__ key, int64_t *__restrict__ src) {
+  extern __shared__ unsigned long long sk[];
+  const unsigned long long nbig = big[0];
+  for (unsigned long long li = blockIdx.x; li < nbig; li += gridDim.x) {
+    const int64_t bk = (int64_t)big[1 + li];
+    const int64_t a = off[bk], n = off[bk + 1] - a;
+    if (n > kSortTile) {
+      if (threadIdx.x == 0) {
+        for (int64_t e = a + 1; e < a + n; ++e) {
+          const int64_t kv = key[e];
+          int64_t d = e - 1;
+          while (d >= a && key[d] > kv) { key[d + 1] = key[d]; --d; }
+          key[d + 1] = kv;
+        }
+        for (int64_t e = a; e < a + n; ++e) src[e] = key[e] & ((1ll << 40) - 1);
+      }
+      __syncthreads();
+      continue;
+    }
+    int p2 = 1;
+    while (p2 < n) p2 <<= 1;
+    for (int t = threadIdx.x; t < p2; t += blockDim.x)
+      sk[t] = t < n ? (unsigned long long)key[a + t] : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= p2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = threadIdx.x; t < p2; t += blockDim.x) {
+          const int o = t ^ j;
+          if (o > t) {
+            const unsigned long long x = sk[t], y = sk[o];
+            const bool up = (t & k) == 0;
+            if ((x > y) == up) { sk[t] = y; sk[o] = x; }
+          }
+        }
+        __syncthreads();
+      }
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      key[a + t] = (int64_t)sk[t];
+      src[a + t] = (int64_t)(sk[t] & ((1ull << 40) - 1));
+    }
+    __syncthreads();
   }
 }
 
@@ -314,7 +380,17 @@ cudaError_t launch_sgd_order(const GridDesc &g, int32_t nblocks, int64_t nnz,
   if (e != cudaSuccess) return e;
   if (nnz > 0) {
     k_sgd_fill<<<sgd_grid(nnz), 256, 0, st>>>(g, nnz, u, i, off, cnt, key, src);
-    k_sgd_sort<<<sgd_grid(nbuckets), 256, 0, st>>>(nbuckets, off, key, src);
+    // the bucket counts are no longer needed: cnt holds the big-bucket list
+    e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_sgd_sort<<<sgd_grid(nbuckets), 256, 0, st>>>(nbuckets, off, key, src,
+                                                   cnt);
+    e = cudaFuncSetAttribute(k_sgd_sort_big,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(unsigned long long) * kSortTile));
+    if (e != cudaSuccess) return e;
+    k_sgd_sort_big<<<152 * 2, 1024, sizeof(unsigned long long) * kSortTile,
+                     st>>>(off, cnt, key, src);
     k_sgd_gather<<<sgd_grid(nnz), 256, 0, st>>>(nnz, src, u, i, x, su, si, sx);
   }
   k_sgd_ranges<<<(nblocks + 255) / 256, 256, 0, st>>>(g, nblocks, off, range);
