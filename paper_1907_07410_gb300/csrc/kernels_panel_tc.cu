@@ -44,7 +44,9 @@
 //     run. (When the converter warps ran the epilogue as well, the MMA warp
 //     waited for it about 300 cycles per stage on the 480,189 x 17,770
 //     workload, and the products ran at 0.74 of HBM; 0.79 with these
-//     warps, 0.82 with the two rings.)
+//     warps, 0.82 with the two rings, 0.83 with three G stages and four B
+//     stages at b = 64: measured against four and three, five and two,
+//     and two and five, the B ring's depth mattered more.)
 // Warps 0 and 1 run their loops as whole warps, so addresses and
 // descriptors stay warp-uniform, and one elected lane issues. Measured on
 // GB300 (clock stamps per stage), a single lane running the same loop took
@@ -199,8 +201,8 @@ template <int B>
 struct PanelRings {
   static constexpr int BOP_HALF = 2 * B * 128;      // one B-form chunk
   static constexpr int BOP_BYTES = 2 * BOP_HALF;
-  static constexpr int GS = B >= 64 ? 4 : (B >= 32 ? 5 : 6);
-  static constexpr int BS = B >= 64 ? 3 : 4;
+  static constexpr int GS = B >= 64 ? 3 : (B >= 32 ? 5 : 6);
+  static constexpr int BS = 4;
   static constexpr int R = PanelTc<B>::R;
   static constexpr int ACC_COLS = PanelTc<B>::ACC_COLS;
   static constexpr int B_OFF = GS * G_BYTES;         // the B ring follows G's
