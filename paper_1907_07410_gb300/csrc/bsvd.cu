@@ -511,7 +511,9 @@ bsvd_status bsvd_create(const bsvd_config *cfg, bsvd_ctx **out) {
     if (c->cfg.max_sweeps <= 0) c->cfg.max_sweeps = 30;
   }
   if (!(c->cfg.tol > 0))
-    c->cfg.tol = c->cfg.precision == BSVD_FP32 ? 1e-5 : 1e-4;
+    c->cfg.tol = c->cfg.precision == BSVD_FP32   ? 1e-5
+                 : c->cfg.precision == BSVD_TF32 ? 1e-4
+                                                 : 5e-4;
   if ((c->cfg.precision != BSVD_FP32 && c->cfg.precision != BSVD_TF32 &&
        c->cfg.precision != BSVD_BF16) ||
       c->cfg.gram_path < 0 ||
