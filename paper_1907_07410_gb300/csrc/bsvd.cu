@@ -1029,6 +1029,13 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
       bm.npt = (int32_t)pt.size() - bm.pt0;
     }
   }
+  // Gram tiles longest first (a tile's work grows with its block's L):
+  // CTAs start in launch order, so the last ones to start are the short
+  // tiles and the launch does not end on one long tile. Each tile writes
+  // its own part of G, so the order changes nothing in the result.
+  std::stable_sort(gt.begin(), gt.end(), [&](const int4 &x, const int4 &y) {
+    return c->meta[x.x].L_pad > c->meta[y.x].L_pad;
+  });
   c->n_gtiles = (int32_t)gt.size();
   c->n_rowtiles = (int32_t)rt.size();
   c->n_ltiles = (int32_t)lt.size();
