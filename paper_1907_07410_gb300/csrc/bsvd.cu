@@ -991,7 +991,7 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     bm.nt = 0;
     bm.pt0 = 0;
     bm.npt = 0;
-    bm.pj0 = (int32_t)pj.size();
+    bm.pj0 = 0;
     bm.npj = 0;
     bm.ch0 = (int32_t)ch.size();
     bm.nch = 0;
@@ -1007,14 +1007,13 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     for (int32_t r = 0; r < bm.s; r += kChunkRows) ch.push_back(make_int2(b, r));
     bm.nch = (int32_t)ch.size() - bm.ch0;
     for (int32_t l = 0; l < bm.L; l += kProjCols) lt.push_back(make_int2(b, l));
-    for (int32_t l = 0; l < bm.L; l += 128) pj.push_back(make_int2(b, l));
-    bm.npj = (int32_t)pj.size() - bm.pj0;
   }
-  // 128-row tiles of the panel products, the blocks in decreasing order of
-  // s (each tile reduces over s columns of G, so its cost grows with s),
-  // ties by block index. The persistent products claim tiles in table
-  // order: the longest start first and the shortest fill the end of each
-  // launch. A block's tiles stay contiguous.
+  // 128-row tiles of the panel products (over F_s) and of the projection
+  // (over F_L), the blocks in decreasing order of s: a tile of either
+  // reduces over s, so its cost grows with s. The persistent products claim
+  // tiles in table order and the projection's CTAs start in it, so the
+  // longest tiles start first and the shortest fill the end of each
+  // launch. A block's tiles stay contiguous; ties keep the block order.
   {
     std::vector<int32_t> order(nb);
     for (int32_t b = 0; b < nb; ++b) order[b] = b;
@@ -1024,9 +1023,13 @@ static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks) {
     for (int32_t b : order) {
       BlockMeta &bm = c->meta[b];
       bm.pt0 = (int32_t)pt.size();
-      if (bm.s > 0 && bm.owned)
+      bm.pj0 = (int32_t)pj.size();
+      if (bm.s > 0 && bm.owned) {
         for (int32_t r = 0; r < bm.s_pad; r += 128) pt.push_back(make_int2(b, r));
+        for (int32_t l = 0; l < bm.L; l += 128) pj.push_back(make_int2(b, l));
+      }
       bm.npt = (int32_t)pt.size() - bm.pt0;
+      bm.npj = (int32_t)pj.size() - bm.pj0;
     }
   }
   // Gram tiles longest first (a tile's work grows with its block's L):
