@@ -26,13 +26,29 @@ __device__ __forceinline__ bool predict_one(const PredictArgs &a, int32_t u,
         a.Fs + bm.fs_off + (int64_t)wa * a.kp);
     const float4 *fl = reinterpret_cast<const float4 *>(
         a.FL + bm.fl_off + (int64_t)wl * a.kp);
+    // both rows' loads in chunks of 5 float4s, each chunk's loads issued
+    // before its products (in column order)
+    constexpr int kChunk = 5;
+    const int n4 = a.kp / 4;
     float dot = 0.f;
-    for (int j = 0; j < a.kp / 4; ++j) {
-      const float4 p = __ldg(fs + j), q = __ldg(fl + j);
-      dot = fmaf(p.x, q.x, dot);
-      dot = fmaf(p.y, q.y, dot);
-      dot = fmaf(p.z, q.z, dot);
-      dot = fmaf(p.w, q.w, dot);
+    for (int j0 = 0; j0 < n4; j0 += kChunk) {
+      float4 p[kChunk], q[kChunk];
+#pragma unroll
+      for (int j = 0; j < kChunk; ++j) {
+        if (j0 + j < n4) {
+          p[j] = __ldg(fs + j0 + j);
+          q[j] = __ldg(fl + j0 + j);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kChunk; ++j) {
+        if (j0 + j < n4) {
+          dot = fmaf(p[j].x, q[j].x, dot);
+          dot = fmaf(p[j].y, q[j].y, dot);
+          dot = fmaf(p[j].z, q[j].z, dot);
+          dot = fmaf(p[j].w, q[j].w, dot);
+        }
+      }
     }
     y += dot;
   }
