@@ -10,27 +10,32 @@
 // contiguous (K-major, as the MMA wants both operands); P is F_s when the
 // Gram side is the users, else F_L.
 //
-// A CTA (4 warps) computes a 128 x 64 tile of out (two CTAs per SM):
-//   * the threads load the tile's 128 rows of P and 64 rows of V (kp
-//     floats each),
-//     split every value x into hi = x rounded to 10 mantissa bits and
-//     lo = x - hi, and write hi and lo of both operands into shared memory
-//     in the 128-byte-swizzled K-major layout (two 32-float atoms along K,
-//     zeros past kp and past the block's edge), then fence them for the
-//     tensor core's proxy;
-//   * one elected thread issues, per K = 8 slice, P_hi V_hi, P_hi V_lo and
-//     P_lo V_hi (kind::tf32, M = 128, N = 64) into one tensor-memory
-//     accumulator: the dropped lo x lo term is below 2^-21 relative, as in
-//     the panel products;
-//   * each warp reads its 32 rows of the accumulator, adds mu and stores the
-//     tile into shared memory (over the operands, which the MMAs no longer
-//     read); the CTA then writes the tile's rows to global memory with
-//     consecutive threads on consecutive columns.
+// Persistent: one CTA per SM walks a contiguous run of 128 x 64 output
+// tiles (row-major, so consecutive tiles share their 128 rows of P) with
+// a group of four loading warps and one of twelve writing warps:
+//   * warps 0-3 load: the strip's 128 rows of P when the strip changes and
+//     the tile's 64 rows of V (kp floats each), split every value x into
+//     hi = x rounded to 10 mantissa bits and lo = x - hi, and write both
+//     into shared memory in the 128-byte-swizzled K-major layout (two
+//     32-float atoms along K, zeros past kp and past the block's edge);
+//     one elected thread then issues, per K = 8 slice, P_hi V_hi, P_hi V_lo
+//     and P_lo V_hi (kind::tf32, M = 128, N = 64) into one of two
+//     tensor-memory accumulators: the dropped lo x lo term is below 2^-21
+//     relative, as in the panel products;
+//   * warps 4-7 read: each reads its 32 rows of the finished accumulator
+//     (and frees it), adds mu and fills a shared-memory tile; warps 4-15
+//     then write the tile's rows to global memory with consecutive threads
+//     on consecutive columns. (With the four readers alone writing, the
+//     stores in flight limited the kernel to 1.1 TB/s on a 92,840 x 4,619
+//     block; twelve writers reach 1.9 TB/s. 16-byte stores along the rows
+//     changed nothing.)
+// V rows and accumulators are double-buffered, so the next tile's loads
+// and MMAs run while the last one's rows are written. Every wait is an
+// mbarrier wait with a bound (no named barriers); a timeout sets
+// kErrTimeout and both groups stop.
 // The contraction is at most 56 long, so the kernel is bound by writing
 // out (4 bytes per cell against 2k flops); the tensor cores only keep the
-// arithmetic off that path. The one wait (the MMAs' completion) is bounded;
-// a timeout sets kErrTimeout, skips the tile's output and frees the tensor
-// memory.
+// arithmetic off that path.
 #include "kernels.h"
 #include "tc_ptx.cuh"
 
@@ -41,17 +46,28 @@ namespace {
 constexpr int RT = 128;                       // tile rows (MMA M)
 constexpr int CT = 64;                        // tile columns (MMA N)
 constexpr int RK = 64;                        // K padded to two swizzle atoms
-constexpr int kRThreads = 128;
+constexpr int kRThreads = 512;                // 4 loading, 12 writing warps
+constexpr int kRWriters = 12;                 // warps 4-15 write out rows
 constexpr uint32_t kRSpin = 1u << 22;         // mbarrier polls before giving up
 constexpr int A_ATOM = RT * 128;              // 16 KiB: 128 rows x 32 floats
 constexpr int B_ATOM = CT * 128;              // 8 KiB: 64 rows x 32 floats
 constexpr int A_BYTES = 2 * A_ATOM;           // one part of P, K = 64
 constexpr int B_BYTES = 2 * B_ATOM;           // one part of V
-constexpr int OPS = 2 * A_BYTES + 2 * B_BYTES;
-// A_hi, A_lo, B_hi, B_lo, then the barrier and the TMEM address
-constexpr int kRSmem = OPS + 64 + 1024;
-static_assert(RT * (CT + 1) * 4 <= OPS, "the output tile fits");
-static_assert(kRSmem <= 113 * 1024, "two CTAs per SM");
+constexpr int B_OFF = 2 * A_BYTES;            // V buffers (hi, lo) x 2
+constexpr int T_OFF = B_OFF + 4 * B_BYTES;    // the output tile
+constexpr int T_BYTES = (RT * (CT + 1) * 4 + 1023) / 1024 * 1024;
+constexpr int C_OFF = T_OFF + T_BYTES;        // the control block
+
+struct RCtrl {
+  uint64_t mma[2];      // the tile's MMAs completed (buffer b)
+  uint64_t tfree[2];    // the writers read accumulator b (4 warps)
+  uint64_t loaded[2];   // V (and P) rows of buffer b written (4 warps)
+  uint64_t tfull;       // the output tile filled (warps 4-7)
+  uint64_t tdone;       // the output tile written out (warps 4-15)
+  uint32_t tmem;
+  int abort;
+};
+constexpr int kRSmem = C_OFF + (int)sizeof(RCtrl) + 1024;
 
 __device__ __forceinline__ uint32_t swz(int r, int c) {
   return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
@@ -61,9 +77,9 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Row `row` (< rows, else zeros) of a kp-column factor into the hi and lo
-// parts of an operand: 16-byte chunk q of the row (4 floats of K) goes to
-// atom q / 8, chunk q mod 8 of the swizzled 128-byte row.
+// Row r (a row past the block's edge when !valid: zeros) of a kp-column
+// factor into the hi and lo parts of an operand: 16-byte chunk q of the row
+// (4 floats of K) goes to atom q / 8, chunk q mod 8 of the swizzled row.
 __device__ __forceinline__ void put_row(unsigned char *hi, unsigned char *lo,
                                         int atom, int r, const float *src,
                                         bool valid, int kp) {
@@ -81,7 +97,7 @@ __device__ __forceinline__ void put_row(unsigned char *hi, unsigned char *lo,
   }
 }
 
-__global__ void __launch_bounds__(kRThreads, 2)
+__global__ void __launch_bounds__(kRThreads, 1)
 k_reconstruct_tc(const BlockMeta *__restrict__ meta, int32_t b,
                  const float *__restrict__ Fs, const float *__restrict__ FL,
                  int32_t kp, float mu, float *__restrict__ out,
@@ -90,80 +106,187 @@ k_reconstruct_tc(const BlockMeta *__restrict__ meta, int32_t b,
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char *a_hi = base, *a_lo = base + A_BYTES;
-  unsigned char *b_hi = base + 2 * A_BYTES, *b_lo = b_hi + B_BYTES;
-  uint64_t *done = reinterpret_cast<uint64_t *>(base + OPS);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(base + OPS + 8);
-  float (*tile)[CT + 1] = reinterpret_cast<float (*)[CT + 1]>(base);
+  auto b_hi = [&](int buf) { return base + B_OFF + buf * 2 * B_BYTES; };
+  auto b_lo = [&](int buf) { return b_hi(buf) + B_BYTES; };
+  float (*tile)[CT + 1] = reinterpret_cast<float (*)[CT + 1]>(base + T_OFF);
+  RCtrl &ct = *reinterpret_cast<RCtrl *>(base + C_OFF);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const BlockMeta bm = meta[b];
-  const int r0 = blockIdx.y * RT, c0 = blockIdx.x * CT;
   // P (rows r of out) and V (columns c) in the library's storage
   const float *P = bm.trans ? FL + bm.fl_off : Fs + bm.fs_off;
   const float *V = bm.trans ? Fs + bm.fs_off : FL + bm.fl_off;
+  const int nct = (bm.nb + CT - 1) / CT;
+  const int64_t units = (int64_t)((bm.mb + RT - 1) / RT) * nct;
+  const int64_t per = (units + gridDim.x - 1) / gridDim.x;
+  const int64_t u0 = (int64_t)blockIdx.x * per;
+  const int64_t u1 = u0 + per < units ? u0 + per : units;
+  const int ntile = u1 > u0 ? (int)(u1 - u0) : 0;
 
-  if (warp == 0) tc::tmem_alloc(tslot, CT);
+  if (warp == 0) tc::tmem_alloc(&ct.tmem, 2 * CT);
   if (threadIdx.x == 0) {
-    tc::mbar_init(done, 1);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&ct.mma[i], 1);
+      tc::mbar_init(&ct.tfree[i], 4);
+      tc::mbar_init(&ct.loaded[i], 4);
+    }
+    tc::mbar_init(&ct.tfull, 4);
+    tc::mbar_init(&ct.tdone, kRWriters);
+    ct.abort = 0;
     tc::mbar_init_fence();
   }
-  {
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = ct.tmem;
+  volatile int *abort_flag = &ct.abort;
+  auto give_up = [&]() {
+    if (lane == 0) atomicOr(err, kErrTimeout);
+    ct.abort = 1;
+  };
+
+  if (warp < 4) {
+    // loading warps: thread t takes row t of P and, t < 64, row t of V
     const int t = threadIdx.x;
-    const int r = r0 + t, c = c0 + t;
-    put_row(a_hi, a_lo, A_ATOM, t, P + (int64_t)r * kp, r < bm.mb, kp);
-    if (t < CT)
-      put_row(b_hi, b_lo, B_ATOM, t, V + (int64_t)c * kp, c < bm.nb, kp);
-  }
-  fence_async_smem();
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t taddr = *tslot;
-  const int nks = (kp + 7) / 8;                   // K = 8 slices in use
-  if (warp == 0) {
+    const int nks = (kp + 7) / 8;                 // K = 8 slices in use
     constexpr uint32_t idesc = tc::idesc_tf32_f32(RT, CT);
-    if (tc::elect_one()) {
-      for (int kk = 0; kk < nks; ++kk) {
-        const uint32_t oa = (uint32_t)((kk >> 2) * A_ATOM);
-        const uint32_t ob = (uint32_t)((kk >> 2) * B_ATOM);
-        const uint64_t adh = tc::sdesc_kmajor_sw128(tc::smem_u32(a_hi + oa)) + 2 * (kk & 3);
-        const uint64_t adl = tc::sdesc_kmajor_sw128(tc::smem_u32(a_lo + oa)) + 2 * (kk & 3);
-        const uint64_t bdh = tc::sdesc_kmajor_sw128(tc::smem_u32(b_hi + ob)) + 2 * (kk & 3);
-        const uint64_t bdl = tc::sdesc_kmajor_sw128(tc::smem_u32(b_lo + ob)) + 2 * (kk & 3);
-        tc::mma_tf32(taddr, adh, bdh, idesc, kk > 0 ? 1u : 0u);
-        tc::mma_tf32(taddr, adh, bdl, idesc, 1u);
-        tc::mma_tf32(taddr, adl, bdh, idesc, 1u);
+    int64_t strip = -1;
+    for (int j = 0; j < ntile; ++j) {
+      const int64_t u = u0 + j;
+      const int64_t su = u / nct;
+      const int cu = (int)(u % nct);
+      const int buf = j & 1;
+      const uint32_t par = (j >> 1) & 1;
+      // buffer j mod 2 is free once the MMAs of tile j - 2 completed and
+      // the writers read their accumulator
+      bool ok = tc::mbar_wait(&ct.mma[buf], par ^ 1, kRSpin) &&
+                tc::mbar_wait(&ct.tfree[buf], par ^ 1, kRSpin);
+      // P is rewritten for a new strip once the last MMAs that read it
+      // (tile j - 1's) completed
+      if (ok && su != strip && j > 0)
+        ok = tc::mbar_wait(&ct.mma[(j - 1) & 1], ((j - 1) >> 1) & 1, kRSpin);
+      ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+      if (!ok) {
+        give_up();
+        break;
       }
-      tc::mma_commit(done);
+      if (su != strip) {
+        const int64_t r = su * RT + t;
+        put_row(a_hi, a_lo, A_ATOM, t, P + r * kp, r < bm.mb, kp);
+        strip = su;
+      }
+      if (t < CT) {
+        const int c = cu * CT + t;
+        put_row(b_hi(buf), b_lo(buf), B_ATOM, t, V + (int64_t)c * kp,
+                c < bm.nb, kp);
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&ct.loaded[buf]);
+      if (warp == 0) {
+        ok = __all_sync(0xffffffffu,
+                        tc::mbar_wait(&ct.loaded[buf], par, kRSpin) &&
+                            !*abort_flag);
+        if (!ok) {
+          give_up();
+          break;
+        }
+        tc::fence_after_sync();
+        if (tc::elect_one()) {
+          const uint32_t d = taddr + (uint32_t)(buf * CT);
+          for (int kk = 0; kk < nks; ++kk) {
+            const uint32_t oa = (uint32_t)((kk >> 2) * A_ATOM);
+            const uint32_t ob = (uint32_t)((kk >> 2) * B_ATOM);
+            const uint32_t k2 = 2 * (kk & 3);
+            const uint64_t adh = tc::sdesc_kmajor_sw128(tc::smem_u32(a_hi + oa)) + k2;
+            const uint64_t adl = tc::sdesc_kmajor_sw128(tc::smem_u32(a_lo + oa)) + k2;
+            const uint64_t bdh = tc::sdesc_kmajor_sw128(tc::smem_u32(b_hi(buf) + ob)) + k2;
+            const uint64_t bdl = tc::sdesc_kmajor_sw128(tc::smem_u32(b_lo(buf) + ob)) + k2;
+            tc::mma_tf32(d, adh, bdh, idesc, kk > 0 ? 1u : 0u);
+            tc::mma_tf32(d, adh, bdl, idesc, 1u);
+            tc::mma_tf32(d, adl, bdh, idesc, 1u);
+          }
+          tc::mma_commit(&ct.mma[buf]);
+        }
+        __syncwarp();
+      }
     }
-    __syncwarp();
-  }
-  const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(done, 0, kRSpin));
-  if (!ok && lane == 0) atomicOr(err, kErrTimeout);
-  const bool all_ok = __syncthreads_and(ok ? 1 : 0);
-  tc::fence_after_sync();
-  if (all_ok) {
-    // warp w holds rows 32 w .. 32 w + 31 of the accumulator
-    const int rr = warp * 32 + lane;
-    const uint32_t lrow = (uint32_t)(warp * 32) << 16;
-#pragma unroll 1
-    for (int cc = 0; cc < CT; cc += 32) {
-      float v[32];
-      tc::tmem_ld32(taddr + lrow + cc, v);
+  } else {
+    // writing warps: warps 4-7 read TMEM lanes 32 (w mod 4) .. + 31 into
+    // the output tile, then warps 4-15 write its rows out
+    const bool reader = warp < 8;
+    const int q = warp & 3;
+    const int rr = q * 32 + lane;                 // tile row of a reader thread
+    const uint32_t lrow = (uint32_t)(q * 32) << 16;
+    for (int j = 0; j < ntile; ++j) {
+      const int64_t u = u0 + j;
+      const int64_t r0 = (u / nct) * RT;
+      const int c0 = (int)(u % nct) * CT;
+      const int buf = j & 1;
+      const uint32_t par = (j >> 1) & 1;
+      bool ok = true;
+      if (reader) {
+        ok = __all_sync(
+            0xffffffffu,
+            tc::mbar_wait(&ct.mma[buf], par, kRSpin) && !*abort_flag);
+        if (!ok) {
+          give_up();
+          break;
+        }
+        tc::fence_after_sync();
+        float v[CT];
+        {
+          float w[32];
+          tc::tmem_ld32(taddr + lrow + (uint32_t)(buf * CT), w);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) tile[rr][cc + j] = mu + v[j];
+          for (int c = 0; c < 32; ++c) v[c] = w[c];
+          tc::tmem_ld32(taddr + lrow + (uint32_t)(buf * CT + 32), w);
+#pragma unroll
+          for (int c = 0; c < 32; ++c) v[32 + c] = w[c];
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&ct.tfree[buf]);
+        // the output tile is free once the last tile's rows were written
+        ok = __all_sync(
+            0xffffffffu,
+            tc::mbar_wait(&ct.tdone, (j & 1) ^ 1, kRSpin) && !*abort_flag);
+        if (!ok) {
+          give_up();
+          break;
+        }
+#pragma unroll
+        for (int c = 0; c < CT; ++c) tile[rr][c] = mu + v[c];
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&ct.tfull);
+      }
+      ok = __all_sync(
+          0xffffffffu,
+          tc::mbar_wait(&ct.tfull, j & 1, kRSpin) && !*abort_flag);
+      if (!ok) {
+        give_up();
+        break;
+      }
+      const int nr = (int)(bm.mb - r0 < RT ? bm.mb - r0 : RT);
+      const int nc = bm.nb - c0 < CT ? bm.nb - c0 : CT;
+      for (int r = warp - 4; r < nr; r += kRWriters) {
+        float *dst = out + (r0 + r) * (int64_t)bm.nb + c0;
+        for (int c = lane; c < nc; c += 32) dst[c] = tile[r][c];
+      }
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&ct.tdone);
     }
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (all_ok) {
-    const int nr = min(RT, bm.mb - r0), nc = min(CT, bm.nb - c0);
-    for (int r = warp; r < nr; r += kRThreads / 32) {
-      float *dst = out + (int64_t)(r0 + r) * bm.nb + c0;
-      for (int c = lane; c < nc; c += 32) dst[c] = tile[r][c];
+  if (threadIdx.x == 0 && ct.abort) {
+    // MMAs issued but never seen to finish: wait (bounded) before freeing
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_wait(&ct.mma[i], 0, kRSpin);
+      tc::mbar_wait(&ct.mma[i], 1, kRSpin);
     }
   }
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(taddr, CT);
+  if (warp == 0) tc::tmem_dealloc(taddr, 2 * CT);
 }
 
 }  // namespace
@@ -174,13 +297,18 @@ cudaError_t launch_reconstruct(const BlockMeta *meta, const BlockMeta &host,
                                cudaStream_t st) {
   if (host.mb <= 0 || host.nb <= 0) return cudaSuccess;
   if (kp <= 0 || kp > RK || kp % 4 != 0) return cudaErrorInvalidValue;
-  const int64_t gy = (host.mb + RT - 1) / RT, gx = (host.nb + CT - 1) / CT;
-  if (gy > 65535 || gx > 0x7fffffff) return cudaErrorInvalidValue;
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t units = (int64_t)((host.mb + RT - 1) / RT) *
+                        ((host.nb + CT - 1) / CT);
+  const int grid = (int)(units < nsm ? units : nsm);
+  static_assert(kRSmem <= 227 * 1024, "shared memory");
   cudaError_t e = cudaFuncSetAttribute(
       k_reconstruct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kRSmem);
   if (e != cudaSuccess) return e;
-  k_reconstruct_tc<<<dim3((unsigned)gx, (unsigned)gy), kRThreads, kRSmem,
-                     st>>>(meta, b, Fs, FL, kp, mu, out, err);
+  k_reconstruct_tc<<<grid, kRThreads, kRSmem, st>>>(meta, b, Fs, FL, kp, mu,
+                                                   out, err);
   return cudaGetLastError();
 }
 
