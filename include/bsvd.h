@@ -203,6 +203,24 @@ bsvd_status bsvd_quantile_grid(bsvd_ctx *ctx, int64_t m, int64_t n,
                                int64_t *row_bounds, int64_t *col_bounds);
 
 /*
+ * bsvd_quantile_grid followed by bsvd_partition in one call, for the
+ * batched form: the activity-quantile grid of (u, i) (same rule as
+ * bsvd_quantile_grid) and the partition of (u, i, x) on it. Host ratings
+ * are uploaded once (x while the grid is being cut), and the permutations
+ * stay on the device.
+ * m, n, nnz, u, i, x, p, q  as in bsvd_partition (u, i, x host or device);
+ *            nnz must be below 2^32 and 1 <= p <= m, 1 <= q <= n.
+ * row_bounds, col_bounds    host arrays of p + 1 and q + 1 entries that
+ *            receive the grid's bounds, or NULL.
+ * Errors: as bsvd_quantile_grid and bsvd_partition.
+ */
+bsvd_status bsvd_partition_quantile(bsvd_ctx *ctx, int64_t m, int64_t n,
+                                    int64_t nnz, const int32_t *u,
+                                    const int32_t *i, const float *x,
+                                    int32_t p, int32_t q, int64_t *row_bounds,
+                                    int64_t *col_bounds);
+
+/*
  * Truncated SVD of every block (Section 2, Eq. 1 and the rank-k truncation
  * after it): keep the k_eff = min(k, min(m_b, n_b)) largest singular values
  * of each centred block B_b and their singular vectors.

@@ -33,6 +33,7 @@ EXPORTS = ("bsvd_config_default", "bsvd_create", "bsvd_destroy",
            "bsvd_gram_path", "bsvd_partition_diag", "bsvd_factor_ks",
            "bsvd_sgd_params_default", "bsvd_sgd_prepare", "bsvd_sgd_train",
            "bsvd_sgd_predict", "bsvd_sgd_get", "bsvd_quantile_grid",
+           "bsvd_partition_quantile",
            "bsvd_set_owned", "bsvd_sqerr", "bsvd_loop_form",
            "bsvd_panel_launches")
 
@@ -110,6 +111,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                  ctypes.POINTER(i32)]),
         "bsvd_sgd_predict": (i32, [vp, i64, vp, vp, vp]),
         "bsvd_sgd_get": (i32, [vp, vp, vp, vp, vp]),
+        "bsvd_partition_quantile": (i32, [vp, i64, i64, i64, vp, vp, vp, i32,
+                                          i32, vp, vp]),
         "bsvd_quantile_grid": (i32, [vp, i64, i64, i64, vp, vp, i32, i32, vp,
                                      vp, vp, vp]),
         "bsvd_set_owned": (i32, [vp, i32, vp]),
@@ -227,6 +230,21 @@ def bsvd_quantile_grid(ctx, m, n, u, i, p, q, row_perm, col_perm):
         ctx, m, n, nnz, _ptr(u, np.int32, "u"), _ptr(i, np.int32, "i"), p, q,
         _ptr(row_perm, np.int32, "row_perm"),
         _ptr(col_perm, np.int32, "col_perm"), rb.ctypes.data, cb.ctypes.data)
+    _check(ctx, st)
+    return rb, cb
+
+
+def bsvd_partition_quantile(ctx, m, n, u, i, x, p, q):
+    """The activity-quantile grid and the partition on it in one call;
+    returns (row_bounds, col_bounds) as numpy."""
+    nnz = _len(u)
+    if _len(i) != nnz or _len(x) != nnz:
+        raise ValueError("u, i, x must have the same length")
+    rb = np.zeros(p + 1, np.int64)
+    cb = np.zeros(q + 1, np.int64)
+    st = load().bsvd_partition_quantile(
+        ctx, m, n, nnz, _ptr(u, np.int32, "u"), _ptr(i, np.int32, "i"),
+        _ptr(x, np.float32, "x"), p, q, rb.ctypes.data, cb.ctypes.data)
     _check(ctx, st)
     return rb, cb
 
@@ -544,6 +562,13 @@ class Context:
             cp = np.empty(n, np.int32)
         rb, cb = bsvd_quantile_grid(self.handle, m, n, u, i, p, q, rp, cp)
         return dict(row_bounds=rb, col_bounds=cb, row_perm=rp, col_perm=cp)
+
+    def partition_quantile(self, m, n, u, i, x, p, q):
+        """quantile_grid() and partition() in one call (host ratings go up
+        once); returns (row_bounds, col_bounds)."""
+        rb, cb = bsvd_partition_quantile(self.handle, m, n, u, i, x, p, q)
+        self.nblocks = p * q
+        return rb, cb
 
     def partition_diag(self, row_bounds, col_bounds, u, i, x):
         bsvd_partition_diag(self.handle, row_bounds, col_bounds, u, i, x)

@@ -132,6 +132,10 @@ struct bsvd_ctx {
   // for, the key of this and of the previous factorisation, kernel counts
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t cap = nullptr, side = nullptr, side2 = nullptr;  // capture
+  // bsvd_partition_quantile uploads x on its own stream while the grid is
+  // cut on the caller's
+  cudaStream_t up = nullptr;
+  cudaEvent_t ev_up_fork = nullptr, ev_up_join = nullptr;
   std::vector<unsigned char> gkey_now, gkey_prev, gkey_exec;
   bool graph_failed = false, capturing = false;
   std::string graph_err;     // why the graph could not be built
@@ -162,6 +166,7 @@ struct bsvd_ctx {
   DevBuf s_a, s_b, s_c, s_out, d_partials, d_rmse;
   // activity-quantile cut: counts, sort keys, running sums, perms, bounds
   DevBuf d_qcnt, d_qkeys, d_qcum, d_qperm, d_qbounds;
+  DevBuf d_qperm2;          // the columns' permutation (partition_quantile)
 
   // tracing: kernel launch count and per-phase CUDA events
   int64_t launches = 0;
@@ -564,15 +569,20 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->d_sgd_range, &c->d_sgd_blocks, &c->d_sgd_P,
                     &c->d_sgd_Q, &c->d_sgd_bu, &c->d_sgd_bi, &c->d_sgd_sum,
                     &c->d_qcnt, &c->d_qkeys, &c->d_qcum, &c->d_qperm,
+                    &c->d_qperm2,
                     &c->d_qbounds, &c->d_pbmaps, &c->d_fbmaps, &c->d_FB,
                     &c->d_lpart, &c->d_spart, &c->d_flip, &c->d_pctl,
                     &c->d_ptime, &c->d_loopctl, &c->d_finv, &c->d_chunks};
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
+  if (c->up) cudaStreamSynchronize(c->up);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->side2) cudaStreamDestroy(c->side2);
+  if (c->up) cudaStreamDestroy(c->up);
+  if (c->ev_up_fork) cudaEventDestroy(c->ev_up_fork);
+  if (c->ev_up_join) cudaEventDestroy(c->ev_up_join);
   for (DevBuf *b : bufs) b->release();
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
@@ -918,6 +928,72 @@ bsvd_status bsvd_quantile_grid(bsvd_ctx *c, int64_t m, int64_t n, int64_t nnz,
                     q, col_perm, col_bounds);
   if (s != BSVD_OK) return s;
   return read_errors(c, "quantile_grid");
+}
+
+bsvd_status bsvd_partition_quantile(bsvd_ctx *c, int64_t m, int64_t n,
+                                    int64_t nnz, const int32_t *u,
+                                    const int32_t *i, const float *x,
+                                    int32_t p, int32_t q, int64_t *row_bounds,
+                                    int64_t *col_bounds) {
+  if (!c) return BSVD_EINVAL;
+  c->err.clear();
+  if (m < 1 || n < 1 || m > INT32_MAX || n > INT32_MAX || nnz < 0 ||
+      nnz > (int64_t)UINT32_MAX)
+    return fail(c, BSVD_EINVAL, "partition_quantile: bad sizes m=%lld n=%lld "
+                "nnz=%lld", (long long)m, (long long)n, (long long)nnz);
+  if (p < 1 || q < 1 || p > m || q > n)
+    return fail(c, BSVD_EINVAL, "partition_quantile: bad grid %d x %d", p, q);
+  if (nnz > 0 && (!u || !i || !x))
+    return fail(c, BSVD_EINVAL, "partition_quantile: null rating arrays");
+  const char *what = "partition_quantile";
+  // x (host) goes up on its own stream, after whatever the caller's stream
+  // still has to do with the staging buffer, while u and i go up and the
+  // grid is cut on the caller's stream
+  const void *du = nullptr, *di = nullptr, *dx = x;
+  bool forked = false;
+  if (nnz > 0 && !is_device_ptr(x)) {
+    if (!c->up)
+      CK(cudaStreamCreateWithFlags(&c->up, cudaStreamNonBlocking), what);
+    if (!c->ev_up_fork)
+      CK(cudaEventCreateWithFlags(&c->ev_up_fork, cudaEventDisableTiming), what);
+    if (!c->ev_up_join)
+      CK(cudaEventCreateWithFlags(&c->ev_up_join, cudaEventDisableTiming), what);
+    CK(c->s_c.ensure(sizeof(float) * nnz), what);
+    CK(cudaEventRecord(c->ev_up_fork, c->st), what);
+    CK(cudaStreamWaitEvent(c->up, c->ev_up_fork, 0), what);
+    CK(cudaMemcpyAsync(c->s_c.p, x, sizeof(float) * nnz, cudaMemcpyHostToDevice,
+                       c->up), what);
+    CK(cudaEventRecord(c->ev_up_join, c->up), what);
+    dx = c->s_c.p;
+    forked = true;
+  }
+  CK(cudaMemsetAsync(c->d_err.p, 0, sizeof(int32_t), c->st), what);
+  CK(device_view(c, u, sizeof(int32_t) * nnz, c->s_a, &du), what);
+  CK(device_view(c, i, sizeof(int32_t) * nnz, c->s_b, &di), what);
+  // the permutations stay on the device (the partition copies them into
+  // the context); the bounds come to the host for the block layout
+  CK(c->d_qperm.ensure(sizeof(int32_t) * m), what);
+  CK(c->d_qperm2.ensure(sizeof(int32_t) * n), what);
+  std::vector<int64_t> rb(p + 1), cb(q + 1);
+  bsvd_status s = quantile_side(c, "partition_quantile: rows", m, nnz,
+                                (const int32_t *)du, p,
+                                c->d_qperm.as<int32_t>(), rb.data());
+  if (s == BSVD_OK)
+    s = quantile_side(c, "partition_quantile: columns", n, nnz,
+                      (const int32_t *)di, q, c->d_qperm2.as<int32_t>(),
+                      cb.data());
+  // the caller's stream takes the upload over in every case, so no later
+  // call reuses the staging buffer while it is still being written
+  if (forked) CK(cudaStreamWaitEvent(c->st, c->ev_up_join, 0), what);
+  if (s != BSVD_OK) return s;
+  s = read_errors(c, what);
+  if (s != BSVD_OK) return s;
+  if (row_bounds) std::copy(rb.begin(), rb.end(), row_bounds);
+  if (col_bounds) std::copy(cb.begin(), cb.end(), col_bounds);
+  return partition_impl(c, m, n, nnz, (const int32_t *)du, (const int32_t *)di,
+                        (const float *)dx, p, q, rb.data(), cb.data(),
+                        c->d_qperm.as<int32_t>(), c->d_qperm2.as<int32_t>(),
+                        false);
 }
 
 static bsvd_status factor_impl(bsvd_ctx *c, int32_t k, const int32_t *ks);

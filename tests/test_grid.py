@@ -75,6 +75,53 @@ def test_library_grid_both_sides_and_errors():
             ctx.quantile_grid(m, n, u, i, m + 1, 3)
 
 
+@pytest.mark.gpu
+def test_partition_quantile_matches_the_two_calls():
+    """bsvd_partition_quantile (the grid cut and the partition in one call,
+    host ratings uploaded once) gives the oracle's bounds and the same
+    counts, means and factors as bsvd_quantile_grid + bsvd_partition, from
+    host and from device inputs; a bad id is rejected."""
+    torch = pytest.importorskip("torch")
+    import paper_1907_07410_gb300 as bs
+    import synth
+    w = synth.UNEVEN
+    r = synth.generate(w)
+    _, orb = oracle.activity_quantile_cut(r.u_train, w.m, w.p)
+    _, ocb = oracle.activity_quantile_cut(r.i_train, w.n, w.q)
+
+    def run(one_call, on_device):
+        conv = (lambda a: torch.from_numpy(a).cuda()) if on_device else (lambda a: a)
+        u, i, x = conv(r.u_train), conv(r.i_train), conv(r.x_train)
+        with bs.Context() as ctx:
+            if one_call:
+                rb, cb = ctx.partition_quantile(w.m, w.n, u, i, x, w.p, w.q)
+            else:
+                kw = ctx.quantile_grid(w.m, w.n, u, i, w.p, w.q)
+                ctx.partition(w.m, w.n, u, i, x, w.p, w.q, **kw)
+                rb, cb = kw["row_bounds"], kw["col_bounds"]
+            counts, mu = ctx.block_stats()
+            assert ctx.factor(w.k) == bs.OK
+            sig = [ctx.get_block(b)["sigma"] for b in range(w.p * w.q)]
+            rm = ctx.rmse(r.u_test, r.i_test, r.x_test)
+        return rb, cb, counts, mu, sig, rm
+
+    ref = run(False, True)
+    assert np.array_equal(ref[0], orb) and np.array_equal(ref[1], ocb)
+    for on_device in (True, False):
+        got = run(True, on_device)
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+        assert np.array_equal(got[2], ref[2]) and np.array_equal(got[3], ref[3])
+        for a, b in zip(got[4], ref[4]):
+            assert np.array_equal(a, b)
+        assert got[5] == ref[5]
+    bad = r.u_train.copy()
+    bad[5] = w.m
+    with bs.Context() as ctx:
+        with pytest.raises(bs.BsvdError) as e:
+            ctx.partition_quantile(w.m, w.n, bad, r.i_train, r.x_train, w.p, w.q)
+        assert e.value.status == bs.EINVAL
+
+
 def test_oracle_cut_hand_example():
     ids = np.array([0] * 5 + [1] + [2] * 3 + [4] * 3)
     perm, bounds = oracle.activity_quantile_cut(ids, 5, 2)
