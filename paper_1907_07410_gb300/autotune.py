@@ -34,7 +34,7 @@ import numpy as np
 
 # allowed difference in held-out RMSE from the default schedule's
 RMSE_SLACK = 1e-5
-DEGREES = (6, 8, 10, 12)
+DEGREES = (4, 6, 8, 10, 12)
 OVERSAMPLES = (0, 8, 24, 48)
 
 
