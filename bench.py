@@ -638,14 +638,16 @@ def step_roofline(w, r, shapes, keff, gram_path, step_s, peaks, peak_kind):
                     "bytes"}
 
 
-def panel_roofline(w, shapes, rep, filter_ms, peaks, peak_kind):
+def panel_roofline(w, shapes, rep, filter_ms, peaks, peak_kind,
+                   oversample=0):
     """The eigen-solver's panel products G X (k_gpanel_tc): algorithmic
     bytes per product = G once (4 s^2) + the panel in and out (4 s b each),
     summed over every product of every block and divided by the products'
     own device time (the library sums each launch's span, first CTA start
     to last CTA end, with the GPU's timer). b/2 flop per byte of G: far
-    below the tensor ridge, so the bound is bandwidth."""
-    want = w.k + max(8, w.k // 2)
+    below the tensor ridge, so the bound is bandwidth. b is the subspace
+    width the schedule's oversample gives (the library's rule)."""
+    want = w.k + (oversample if oversample > 0 else max(8, w.k // 2))
     bsub = 16 if want <= 16 else (32 if want <= 32 else 64)
     pflops = pbytes = 0.0
     nprod = 0
@@ -885,7 +887,7 @@ def main():
         "converged_blocks": main_sum["converged_blocks"],
         "roofline": panel_roofline(w, shapes, main_res["report"],
                                    main_res["phases"]["eigen_filter"], peaks,
-                                   peak_kind),
+                                   peak_kind, params.get("oversample", 0)),
         "roofline_step": step_roofline(w, r, shapes, w.k, gram_path, step_s,
                                        peaks, peak_kind),
         "roofline_gram": {"kernel": GRAM_KERNELS.get(gram_path), "bound": bound,
