@@ -24,8 +24,15 @@
  *
  * Arithmetic is float64, evaluated left to right as written, one rounding
  * per operation (compile without floating-point contraction).
+ * oracle_sgd_pass_f32 is the same pass in float32, for the library's
+ * float32 form.
  */
+#include <float.h>
 #include <stdint.h>
+
+#if FLT_EVAL_METHOD != 0
+#error "float expressions must be evaluated in float"
+#endif
 
 typedef struct {
   double a_user, b_user;    /* user factors */
@@ -49,6 +56,35 @@ void oracle_sgd_pass(int64_t n, const int32_t *u, const int32_t *i,
       const double pf = p[f];
       p[f] = pf + r->a_user * (err * q[f] - r->b_user * pf);
       q[f] = q[f] + r->a_item * (err * pf - r->b_item * q[f]);
+    }
+  }
+}
+
+/*
+ * The same pass in float32: the parameters are float arrays, the rates are
+ * the float64 rates rounded to float32, and every operation rounds once to
+ * float32, in the order of oracle_sgd_pass (C evaluates float expressions
+ * in float on the targets this builds for: FLT_EVAL_METHOD 0).
+ */
+void oracle_sgd_pass_f32(int64_t n, const int32_t *u, const int32_t *i,
+                         const float *x, int32_t k, float *P, float *Q,
+                         float *bu, float *bi, const oracle_sgd_rates *r) {
+  const float a_user = (float)r->a_user, b_user = (float)r->b_user;
+  const float a_item = (float)r->a_item, b_item = (float)r->b_item;
+  const float a_ubias = (float)r->a_ubias, b_ubias = (float)r->b_ubias;
+  const float a_ibias = (float)r->a_ibias, b_ibias = (float)r->b_ibias;
+  for (int64_t t = 0; t < n; ++t) {
+    float *p = P + (int64_t)u[t] * k;
+    float *q = Q + (int64_t)i[t] * k;
+    float dot = 0.0f;
+    for (int32_t f = 0; f < k; ++f) dot = dot + p[f] * q[f];
+    const float err = x[t] - bu[u[t]] - bi[i[t]] - dot;
+    bu[u[t]] = bu[u[t]] + a_ubias * (err - b_ubias * bu[u[t]]);
+    bi[i[t]] = bi[i[t]] + a_ibias * (err - b_ibias * bi[i[t]]);
+    for (int32_t f = 0; f < k; ++f) {
+      const float pf = p[f];
+      p[f] = pf + a_user * (err * q[f] - b_user * pf);
+      q[f] = q[f] + a_item * (err * pf - b_item * q[f]);
     }
   }
 }

@@ -26,6 +26,11 @@ What it computes, with the passage each step follows:
 5. Predict (Eq. 3): y_hat = p_u . q_i + bu_u + bi_i, the dot product summed
    over f = 0 .. k-1 in order, then the biases added left to right.
 
+Precision: float64. ``train(..., dtype=np.float32)`` runs the same steps
+with float32 parameters and float32 arithmetic in each update, the
+reference for the library's float32 form; its pins compare it with the
+float64 run.
+
 Readings: see ``sgd.c`` for the update; the starting factors are inputs
 (the paper only says "random values"); biases start at zero; the RMSE of
 the stopping rule is the training RMSE, since Algorithm 1 sees only X.
@@ -75,12 +80,12 @@ def _load():
         if _lib is not None:
             return _lib
         lib = ctypes.CDLL(path)
-        f = lib.oracle_sgd_pass
-        f.restype = None
-        f.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
-                      ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
-                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                      ctypes.POINTER(_Rates)]
+        for f in (lib.oracle_sgd_pass, lib.oracle_sgd_pass_f32):
+            f.restype = None
+            f.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.POINTER(_Rates)]
         _lib = lib
     return _lib
 
@@ -135,17 +140,22 @@ def processing_order(grid, u, i) -> np.ndarray:
 
 
 def sgd_pass(u, i, x, P, Q, bu, bi, rates: Rates) -> None:
-    """One pass over ratings in the given order, in place (``sgd.c``)."""
+    """One pass over ratings in the given order, in place (``sgd.c``). The
+    parameters' dtype picks the arithmetic: all float64, or all float32
+    (the same pass with every operation rounded to float32)."""
     u = np.ascontiguousarray(u, np.int32)
     i = np.ascontiguousarray(i, np.int32)
     x = np.ascontiguousarray(x, np.float32)
+    dt = P.dtype
+    assert dt in (np.float64, np.float32)
     for a in (P, Q, bu, bi):
-        assert a.dtype == np.float64 and a.flags.c_contiguous
+        assert a.dtype == dt and a.flags.c_contiguous
     r = rates.c()
-    _load().oracle_sgd_pass(len(u), u.ctypes.data, i.ctypes.data,
-                            x.ctypes.data, P.shape[1], P.ctypes.data,
-                            Q.ctypes.data, bu.ctypes.data, bi.ctypes.data,
-                            ctypes.byref(r))
+    lib = _load()
+    f = lib.oracle_sgd_pass if dt == np.float64 else lib.oracle_sgd_pass_f32
+    f(len(u), u.ctypes.data, i.ctypes.data, x.ctypes.data, P.shape[1],
+      P.ctypes.data, Q.ctypes.data, bu.ctypes.data, bi.ctypes.data,
+      ctypes.byref(r))
 
 
 def predict(P, Q, bu, bi, u, i) -> np.ndarray:
@@ -174,22 +184,30 @@ class Trained:
 
 
 def train(grid, u, i, x, P0, Q0, steps: int, rates: Rates | None = None,
-          delta: float = DELTA) -> Trained:
+          delta: float = DELTA, dtype=np.float64) -> Trained:
     """Algorithm 1 over the grid's blocks, from factors P0 (m x k) and
-    Q0 (n x k) and zero biases, for at most `steps` epochs."""
+    Q0 (n x k) and zero biases, for at most `steps` epochs. With dtype
+    float32 the parameters are P0, Q0 rounded to float32 and every update
+    is float32 arithmetic; the RMSE (and so the stopping rule) is float64
+    over the parameters' values either way. The returned arrays are
+    float64 (exact copies of float32 ones)."""
     rates = rates or Rates()
     order = processing_order(grid, u, i)
     uo, io, xo = (np.asarray(a)[order] for a in (u, i, x))
-    P = np.array(P0, np.float64, order="C")
-    Q = np.array(Q0, np.float64, order="C")
-    bu = np.zeros(P.shape[0])
-    bi = np.zeros(Q.shape[0])
-    hist = [rmse(P, Q, bu, bi, u, i, x)]
+    P = np.array(P0, dtype, order="C")
+    Q = np.array(Q0, dtype, order="C")
+    bu = np.zeros(P.shape[0], dtype)
+    bi = np.zeros(Q.shape[0], dtype)
+
+    def wide():
+        return tuple(np.asarray(a, np.float64) for a in (P, Q, bu, bi))
+
+    hist = [rmse(*wide(), u, i, x)]
     ran = 0
     for _ in range(steps):
         sgd_pass(uo, io, xo, P, Q, bu, bi, rates)
         ran += 1
-        hist.append(rmse(P, Q, bu, bi, u, i, x))
+        hist.append(rmse(*wide(), u, i, x))
         if hist[-2] - hist[-1] < delta:
             break
-    return Trained(P, Q, bu, bi, hist, ran)
+    return Trained(*wide(), hist, ran)

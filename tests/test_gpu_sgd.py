@@ -59,7 +59,8 @@ def test_small_workload_three_epochs_bit_identical():
 
 
 @pytest.mark.parametrize("p,q,k", [(3, 2, 7), (2, 5, 1), (1, 1, 32),
-                                   (4, 4, 13), (7, 3, 5)])
+                                   (4, 4, 13), (7, 3, 5), (3, 3, 15),
+                                   (2, 3, 16)])
 def test_grid_shapes_and_ranks(p, q, k):
     r = synth.random_ratings(31, 300, 200, 6000, 0)
     ctx, hist, ran, ref = run_both(r, p, q, k, 2)

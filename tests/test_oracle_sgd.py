@@ -161,3 +161,55 @@ def test_stopping_rule():
     # delta <= 0 with descent: all steps run
     t = sgd.train(grid, u, i, x, P0, Q0, steps=5, delta=-1e9)
     assert t.steps_run == 5 and len(t.rmse) == 6
+
+
+def test_float32_pass_is_exact_where_float32_is():
+    """With power-of-two rates and values of a few significant bits, no
+    operation of two updates (one per user and item) rounds in float32, so the float32 pass must
+    equal the float64 pass (pinned above) bit for bit: a dropped term, a
+    wrong sign or a swapped operand in the float32 code would show."""
+    r = sgd.Rates(a_user=2.0 ** -4, b_user=2.0 ** -3, a_item=2.0 ** -5,
+                  b_item=2.0 ** -2, a_ubias=2.0 ** -3, b_ubias=2.0 ** -4,
+                  a_ibias=2.0 ** -2, b_ibias=2.0 ** -5)
+    P = np.array([[0.5, -0.25, 0.75], [0.125, 0.5, -0.5]])
+    Q = np.array([[-0.5, 0.25, 0.5], [0.75, -0.125, 0.25], [0.5, 0.5, 0.5]])
+    u, i, x = [0, 1], [2, 0], [4.0, 2.0]
+    P64, Q64 = P.copy(), Q.copy()
+    bu64, bi64 = np.zeros(2), np.zeros(3)
+    sgd.sgd_pass(u, i, x, P64, Q64, bu64, bi64, r)
+    P32, Q32 = P.astype(np.float32), Q.astype(np.float32)
+    bu32, bi32 = np.zeros(2, np.float32), np.zeros(3, np.float32)
+    sgd.sgd_pass(u, i, x, P32, Q32, bu32, bi32, r)
+    # the float64 results still fit in float32 exactly
+    for a in (P64, Q64, bu64, bi64):
+        assert np.array_equal(a.astype(np.float32).astype(np.float64), a)
+    assert not np.array_equal(P64, P) and not np.array_equal(bi64, 0 * bi64)
+    for a, b in ((P32, P64), (Q32, Q64), (bu32, bu64), (bi32, bi64)):
+        assert np.array_equal(a.astype(np.float64), b)
+
+
+def test_float32_training_tracks_float64():
+    """Float32 training from the same start stays within float32 rounding
+    of the float64 run: each update perturbs a parameter by about 2^-24 of
+    its size and the updates contract, so after three epochs on a few
+    thousand ratings the parameters agree to ~1e-5 and the RMSE history to
+    ~1e-6, while a mistake in the float32 pass would move them by the size
+    of an update (~1e-2)."""
+    rng = np.random.default_rng(5)
+    m, n, k = 60, 40, 6
+    u, i = np.nonzero(rng.random((m, n)) < 0.6)
+    x = rng.integers(1, 6, len(u)).astype(np.float32)
+    grid = oracle.make_grid(m, n, 3, 2)
+    P0, Q0 = rng.normal(0, 0.1, (m, k)), rng.normal(0, 0.1, (n, k))
+    t64 = sgd.train(grid, u, i, x, P0, Q0, steps=3, delta=-1e300)
+    t32 = sgd.train(grid, u, i, x, P0, Q0, steps=3, delta=-1e300,
+                    dtype=np.float32)
+    assert t32.steps_run == 3 and t32.P.dtype == np.float64
+    for a in (t32.P, t32.Q, t32.bu, t32.bi):
+        assert np.array_equal(a.astype(np.float32).astype(np.float64), a)
+    for a, b in ((t32.P, t64.P), (t32.Q, t64.Q), (t32.bu, t64.bu),
+                 (t32.bi, t64.bi)):
+        d = np.max(np.abs(a - b))
+        assert 0 < d < 2e-5
+    np.testing.assert_allclose(t32.rmse, t64.rmse, rtol=2e-6)
+    assert t32.rmse[-1] < t32.rmse[0]
