@@ -454,7 +454,9 @@ def sgd_leg(r, w, epochs=10, grids=(8, 64, 256)):
     hyper-parameters (k = 13), on the 8 x 8 grid the paper's CPU run used
     and on a finer grid (more blocks per step). The time of an epoch covers
     its schedule steps and the training-RMSE of Algorithm 1's stopping rule.
-    Beside it, one epoch of the sequential FP64 oracle on the host."""
+    Both arithmetic forms run: float64 (bit-identical to the float64
+    oracle) and float32 (bit-identical to the float32 oracle). Beside them,
+    one epoch of each sequential oracle on the host."""
     import torch
     import paper_1907_07410_gb300 as bs
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
@@ -468,34 +470,39 @@ def sgd_leg(r, w, epochs=10, grids=(8, 64, 256)):
         ctx = bs.Context()
         ctx.partition(w.m, w.n, u, i, x, g, g)
         ctx.sgd_prepare(u, i, x)
-        ctx.sgd_train(dP, dQ, max_steps=1, delta=-1e300)       # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hist, ran = ctx.sgd_train(dP, dQ, max_steps=epochs, delta=-1e300)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        yh = ctx.sgd_predict(r.u_test, r.i_test)
-        test = float(np.sqrt(np.mean((yh - r.x_test) ** 2)))
-        out["grids"].append({
-            "grid": "%dx%d" % (g, g), "s_per_epoch": dt / ran,
-            "ratings_per_s": r.u_train.size * ran / dt,
-            "train_rmse_start": float(hist[0]),
-            "train_rmse_end": float(hist[-1]), "test_rmse_end": test})
+        for prec, name in ((bs.SGD_FP64, "fp64"), (bs.SGD_FP32, "fp32")):
+            ctx.sgd_train(dP, dQ, max_steps=1, delta=-1e300,
+                          precision=prec)                       # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hist, ran = ctx.sgd_train(dP, dQ, max_steps=epochs, delta=-1e300,
+                                      precision=prec)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            yh = ctx.sgd_predict(r.u_test, r.i_test)
+            test = float(np.sqrt(np.mean((yh - r.x_test) ** 2)))
+            out["grids"].append({
+                "grid": "%dx%d" % (g, g), "precision": name,
+                "s_per_epoch": dt / ran,
+                "ratings_per_s": r.u_train.size * ran / dt,
+                "train_rmse_start": float(hist[0]),
+                "train_rmse_end": float(hist[-1]), "test_rmse_end": test})
     # the oracle: one epoch, sequential, on the host
     import oracle
     from oracle import sgd as osgd
     grid = oracle.make_grid(w.m, w.n, grids[0], grids[0])
     order = osgd.processing_order(grid, r.u_train, r.i_train)
     uo, io, xo = r.u_train[order], r.i_train[order], r.x_train[order]
-    P, Q = P0.copy(), Q0.copy()
-    bu, bi = np.zeros(w.m), np.zeros(w.n)
-    t0 = time.perf_counter()
-    osgd.sgd_pass(uo, io, xo, P, Q, bu, bi, osgd.Rates())
-    out["cpu_baseline"] = {"kind": "oracle", "cores": 1,
-                           "s_per_epoch": time.perf_counter() - t0,
-                           "sample": "one epoch of the sequential FP64 oracle "
-                                     "(C), %dx%d grid order" % (grids[0],
-                                                                grids[0])}
+    for dt, key, name in ((np.float64, "cpu_baseline", "FP64"),
+                          (np.float32, "cpu_baseline_fp32", "FP32")):
+        P, Q = P0.astype(dt), Q0.astype(dt)
+        bu, bi = np.zeros(w.m, dt), np.zeros(w.n, dt)
+        t0 = time.perf_counter()
+        osgd.sgd_pass(uo, io, xo, P, Q, bu, bi, osgd.Rates())
+        out[key] = {"kind": "oracle", "cores": 1,
+                    "s_per_epoch": time.perf_counter() - t0,
+                    "sample": "one epoch of the sequential %s oracle (C), "
+                              "%dx%d grid order" % (name, grids[0], grids[0])}
     out["paper_context"] = ("BGSVD 13.45 s/iteration and BCSVD 34.53 "
                             "s/iteration on MovieLens 1M (Tesla M40, Xeon "
                             "E5-2640 v3); real data, not comparable")

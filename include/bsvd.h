@@ -422,10 +422,24 @@ int64_t bsvd_panel_launches(const bsvd_ctx *ctx);
  *   * Epochs (Algorithm 1): up to max_steps passes over all blocks; after
  *     each, the training RMSE is measured and training stops once it
  *     improved by less than delta.
- * Arithmetic is float64 with one rounding per operation (no fused
- * multiply-add) and the dot product summed over f = 0 .. k-1 in order, so
- * results equal a sequential float64 implementation bit for bit.
+ * Arithmetic (the precision field):
+ *   * BSVD_SGD_FP64 (the default): float64 with one rounding per operation
+ *     (no fused multiply-add) and the dot product summed over f = 0 .. k-1
+ *     in order, so results equal a sequential float64 implementation bit
+ *     for bit. A block's walk is a chain of dependent float64 operations.
+ *   * BSVD_SGD_FP32: the same operations in the same order in float32 (no
+ *     fused multiply-add), on float32 copies of P0, Q0 (rounded to nearest)
+ *     and rates rounded to float32; each block stages its users' and items'
+ *     parameters in shared memory when they fit (else it works in global
+ *     memory). Results equal a sequential float32 implementation bit for
+ *     bit. The RMSE, bsvd_sgd_predict and bsvd_sgd_get see the float32
+ *     values widened to float64.
  */
+typedef enum {
+    BSVD_SGD_FP64 = 0,
+    BSVD_SGD_FP32 = 1
+} bsvd_sgd_precision;
+
 typedef struct {
     double a_user, b_user;     /* user factors p_u (Eq. 10) */
     double a_item, b_item;     /* item factors q_i (Eq. 11) */
@@ -434,13 +448,14 @@ typedef struct {
     double delta;              /* minimum RMSE improvement per epoch */
     int32_t k;                 /* latent factors, 1 .. 32 */
     int32_t max_steps;         /* STEPS of Algorithm 1, >= 0 */
+    int32_t precision;         /* bsvd_sgd_precision */
 } bsvd_sgd_params;
 
 /*
  * The experiments' values (Section 5, "Hyper-parameters", SVD model):
  * user factors a = 0.019, b = 0.019; item factors a = 0.004, b = 0.019;
  * user biases a = 0.004, b = 0.019; item biases a = 0.013, b = 0.007;
- * delta = 1e-4; k = 13; max_steps = 100.
+ * delta = 1e-4; k = 13; max_steps = 100; precision BSVD_SGD_FP64.
  */
 void bsvd_sgd_params_default(bsvd_sgd_params *prm);
 

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libbsvd.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT, ESTATE = range(7)
 FP32, TF32, BF16 = range(3)           # bsvd_precision
+SGD_FP64, SGD_FP32 = range(2)         # bsvd_sgd_precision
 STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
                 ENOTCONV: "ENOTCONV", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
 
@@ -63,7 +64,7 @@ class SgdParams(ctypes.Structure):
                 ("a_ubias", ctypes.c_double), ("b_ubias", ctypes.c_double),
                 ("a_ibias", ctypes.c_double), ("b_ibias", ctypes.c_double),
                 ("delta", ctypes.c_double), ("k", ctypes.c_int32),
-                ("max_steps", ctypes.c_int32)]
+                ("max_steps", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 _lib = None
@@ -655,8 +656,9 @@ class Context:
 
     def sgd_train(self, P0, Q0, **params):
         """Algorithm 1 from P0 (m x k), Q0 (n x k) float64; params override
-        the Section 5 defaults (a_user, ..., delta, max_steps). Returns
-        (training RMSE history, epochs run)."""
+        the Section 5 defaults (a_user, ..., delta, max_steps, precision:
+        SGD_FP64 or SGD_FP32). Returns (training RMSE history, epochs
+        run)."""
         prm = bsvd_sgd_params_default()
         prm.k = int(np.shape(P0)[1])
         for key, v in params.items():

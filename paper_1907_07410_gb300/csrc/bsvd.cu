@@ -157,8 +157,8 @@ struct bsvd_ctx {
   int64_t sgd_nnz = 0;
   int32_t sgd_k = 0;
   DevBuf d_sgd_cnt, d_sgd_off, d_sgd_key, d_sgd_src, d_sgd_u, d_sgd_i,
-      d_sgd_x, d_sgd_range, d_sgd_blocks, d_sgd_P, d_sgd_Q, d_sgd_bu,
-      d_sgd_bi, d_sgd_sum;
+      d_sgd_x, d_sgd_r, d_sgd_c, d_sgd_range, d_sgd_blocks, d_sgd_P,
+      d_sgd_Q, d_sgd_bu, d_sgd_bi, d_sgd_sum, d_sgd_P32, d_sgd_Q32;
   std::vector<int32_t> sgd_step_off;   // steps: blocks [off[s], off[s+1])
   bool any_capped = false;
 
@@ -568,6 +568,7 @@ void bsvd_destroy(bsvd_ctx *c) {
                     &c->d_sgd_src, &c->d_sgd_u, &c->d_sgd_i, &c->d_sgd_x,
                     &c->d_sgd_range, &c->d_sgd_blocks, &c->d_sgd_P,
                     &c->d_sgd_Q, &c->d_sgd_bu, &c->d_sgd_bi, &c->d_sgd_sum,
+                    &c->d_sgd_r, &c->d_sgd_c, &c->d_sgd_P32, &c->d_sgd_Q32,
                     &c->d_qcnt, &c->d_qkeys, &c->d_qcum, &c->d_qperm,
                     &c->d_qperm2,
                     &c->d_qbounds, &c->d_pbmaps, &c->d_fbmaps, &c->d_FB,
@@ -1993,6 +1994,7 @@ void bsvd_sgd_params_default(bsvd_sgd_params *prm) {
   prm->delta = 1e-4;
   prm->k = 13;
   prm->max_steps = 100;
+  prm->precision = BSVD_SGD_FP64;
 }
 
 bsvd_status bsvd_sgd_prepare(bsvd_ctx *c, int64_t nnz, const int32_t *u,
@@ -2024,12 +2026,15 @@ bsvd_status bsvd_sgd_prepare(bsvd_ctx *c, int64_t nnz, const int32_t *u,
   CK(c->d_sgd_u.ensure(sizeof(int32_t) * n1), "sgd_prepare");
   CK(c->d_sgd_i.ensure(sizeof(int32_t) * n1), "sgd_prepare");
   CK(c->d_sgd_x.ensure(sizeof(float) * n1), "sgd_prepare");
+  CK(c->d_sgd_r.ensure(sizeof(int32_t) * n1), "sgd_prepare");
+  CK(c->d_sgd_c.ensure(sizeof(int32_t) * n1), "sgd_prepare");
   CK(c->d_sgd_range.ensure(sizeof(int64_t) * 2 * nb), "sgd_prepare");
   CK(launch_sgd_order(g, nb, nnz, (const int32_t *)du, (const int32_t *)di,
                       (const float *)dx, c->d_sgd_cnt.as<unsigned long long>(),
                       c->d_sgd_off.as<int64_t>(), c->d_sgd_key.as<int64_t>(),
                       c->d_sgd_src.as<int64_t>(), c->d_sgd_u.as<int32_t>(),
                       c->d_sgd_i.as<int32_t>(), c->d_sgd_x.as<float>(),
+                      c->d_sgd_r.as<int32_t>(), c->d_sgd_c.as<int32_t>(),
                       c->d_sgd_range.as<int64_t>(), c->d_err.as<int32_t>(),
                       c->st), "sgd_prepare");
   c->launches += nnz > 0 ? 7 : 2;
@@ -2088,6 +2093,7 @@ bsvd_status bsvd_sgd_train(bsvd_ctx *c, const bsvd_sgd_params *prm,
   c->err.clear();
   if (!c->sgd_ready) return fail(c, BSVD_ESTATE, "sgd_train: no sgd_prepare");
   if (!prm || prm->k < 1 || prm->k > 32 || prm->max_steps < 0 ||
+      (prm->precision != BSVD_SGD_FP64 && prm->precision != BSVD_SGD_FP32) ||
       !(std::isfinite(prm->a_user) && std::isfinite(prm->b_user) &&
         std::isfinite(prm->a_item) && std::isfinite(prm->b_item) &&
         std::isfinite(prm->a_ubias) && std::isfinite(prm->b_ubias) &&
@@ -2112,6 +2118,41 @@ bsvd_status bsvd_sgd_train(bsvd_ctx *c, const bsvd_sgd_params *prm,
   CK(cudaMemsetAsync(c->d_sgd_bi.p, 0, sizeof(double) * c->n, c->st), "sgd_train");
   const SgdRates r{prm->a_user, prm->b_user, prm->a_item, prm->b_item,
                    prm->a_ubias, prm->b_ubias, prm->a_ibias, prm->b_ibias};
+  const bool f32 = prm->precision == BSVD_SGD_FP32;
+  const SgdRates32 r32{(float)prm->a_user,  (float)prm->b_user,
+                       (float)prm->a_item,  (float)prm->b_item,
+                       (float)prm->a_ubias, (float)prm->b_ubias,
+                       (float)prm->a_ibias, (float)prm->b_ibias};
+  size_t stage = 0;
+  if (f32) {
+    // float32 rows of k + 1 (factors, bias); the float64 arrays then hold
+    // their widened values, which the RMSE, predict and get read
+    CK(c->d_sgd_P32.ensure(sizeof(float) * (size_t)std::max<int64_t>(
+                               c->m * (k + 1), 1)), "sgd_train");
+    CK(c->d_sgd_Q32.ensure(sizeof(float) * (size_t)std::max<int64_t>(
+                               c->n * (k + 1), 1)), "sgd_train");
+    CK(launch_sgd_narrow(c->m, c->n, k, c->d_sgd_P.as<double>(),
+                         c->d_sgd_Q.as<double>(), c->d_sgd_bu.as<double>(),
+                         c->d_sgd_bi.as<double>(), c->d_sgd_P32.as<float>(),
+                         c->d_sgd_Q32.as<float>(), c->st), "sgd_train");
+    CK(launch_sgd_widen(c->m, c->n, k, c->d_sgd_P32.as<float>(),
+                        c->d_sgd_Q32.as<float>(), c->d_sgd_P.as<double>(),
+                        c->d_sgd_Q.as<double>(), c->d_sgd_bu.as<double>(),
+                        c->d_sgd_bi.as<double>(), c->st), "sgd_train");
+    c->launches += 2;
+    // stage the blocks in shared memory when the largest one fits
+    int dev = 0, optin = 0;
+    CK(cudaGetDevice(&dev), "sgd_train");
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                              dev), "sgd_train");
+    for (int32_t b = 0; b < c->nblocks; ++b) {
+      const int32_t bi = c->diag ? b : b / c->q, bj = c->diag ? b : b % c->q;
+      stage = std::max(stage, sgd_stage_bytes(c->rb[bi + 1] - c->rb[bi],
+                                              c->cb[bj + 1] - c->cb[bj], k));
+    }
+    if (stage > (size_t)optin) stage = 0;
+  }
+  const GridDesc g = c->grid();
   double prev = 0.0;
   bsvd_status s = sgd_rmse(c, &prev);
   if (s != BSVD_OK) return s;
@@ -2120,13 +2161,32 @@ bsvd_status bsvd_sgd_train(bsvd_ctx *c, const bsvd_sgd_params *prm,
   for (int32_t step = 0; step < prm->max_steps; ++step) {
     for (size_t t = 0; t + 1 < c->sgd_step_off.size(); ++t) {
       const int32_t a = c->sgd_step_off[t], b = c->sgd_step_off[t + 1];
-      CK(launch_sgd_step(b - a, c->d_sgd_blocks.as<int32_t>() + a,
-                         c->d_sgd_range.as<int64_t>(), c->d_sgd_u.as<int32_t>(),
-                         c->d_sgd_i.as<int32_t>(), c->d_sgd_x.as<float>(),
-                         c->sgd_nnz, k, c->d_sgd_P.as<double>(),
-                         c->d_sgd_Q.as<double>(), c->d_sgd_bu.as<double>(),
-                         c->d_sgd_bi.as<double>(), r, c->d_err.as<int32_t>(),
-                         c->st), "sgd_train");
+      if (f32)
+        CK(launch_sgd_step_f32(g, b - a, c->d_sgd_blocks.as<int32_t>() + a,
+                               c->d_sgd_range.as<int64_t>(),
+                               c->d_sgd_r.as<int32_t>(),
+                               c->d_sgd_c.as<int32_t>(),
+                               c->d_sgd_u.as<int32_t>(),
+                               c->d_sgd_i.as<int32_t>(),
+                               c->d_sgd_x.as<float>(), c->sgd_nnz, k,
+                               c->d_sgd_P32.as<float>(),
+                               c->d_sgd_Q32.as<float>(), r32, stage,
+                               c->d_err.as<int32_t>(), c->st), "sgd_train");
+      else
+        CK(launch_sgd_step(b - a, c->d_sgd_blocks.as<int32_t>() + a,
+                           c->d_sgd_range.as<int64_t>(),
+                           c->d_sgd_u.as<int32_t>(), c->d_sgd_i.as<int32_t>(),
+                           c->d_sgd_x.as<float>(), c->sgd_nnz, k,
+                           c->d_sgd_P.as<double>(), c->d_sgd_Q.as<double>(),
+                           c->d_sgd_bu.as<double>(), c->d_sgd_bi.as<double>(),
+                           r, c->d_err.as<int32_t>(), c->st), "sgd_train");
+      c->launches += 1;
+    }
+    if (f32) {
+      CK(launch_sgd_widen(c->m, c->n, k, c->d_sgd_P32.as<float>(),
+                          c->d_sgd_Q32.as<float>(), c->d_sgd_P.as<double>(),
+                          c->d_sgd_Q.as<double>(), c->d_sgd_bu.as<double>(),
+                          c->d_sgd_bi.as<double>(), c->st), "sgd_train");
       c->launches += 1;
     }
     ++ran;

@@ -229,15 +229,19 @@ cudaError_t launch_finalize(const BlockMeta *meta, int32_t nblocks,
 struct SgdRates {
   double a_user, b_user, a_item, b_item, a_ubias, b_ubias, a_ibias, b_ibias;
 };
+struct SgdRates32 {
+  float a_user, b_user, a_item, b_item, a_ubias, b_ubias, a_ibias, b_ibias;
+};
 
 // Epoch order of the ratings: cnt and off hold (diag ? p : q) * m (+1)
-// buckets; key, src, su, si, sx hold nnz entries; range 2 per block.
+// buckets; key, src, su, si, sx, and the local row and column sr, sc, hold
+// nnz entries; range 2 per block.
 cudaError_t launch_sgd_order(const GridDesc &g, int32_t nblocks, int64_t nnz,
                              const int32_t *u, const int32_t *i, const float *x,
                              unsigned long long *cnt, int64_t *off,
                              int64_t *key, int64_t *src, int32_t *su,
-                             int32_t *si, float *sx, int64_t *range,
-                             int32_t *err, cudaStream_t st);
+                             int32_t *si, float *sx, int32_t *sr, int32_t *sc,
+                             int64_t *range, int32_t *err, cudaStream_t st);
 // One schedule step: nb blocks (ids in `blocks`), one warp each.
 cudaError_t launch_sgd_step(int32_t nb, const int32_t *blocks,
                             const int64_t *range, const int32_t *su,
@@ -245,6 +249,32 @@ cudaError_t launch_sgd_step(int32_t nb, const int32_t *blocks,
                             int32_t k, double *P, double *Q, double *bu,
                             double *bi, const SgdRates &r, int32_t *err,
                             cudaStream_t st);
+// The float32 form: parameters as rows of k + 1 floats (k factors, then
+// the bias), P32 m rows, Q32 n rows. narrow: float64 P, Q, bu, bi -> P32,
+// Q32 (rounded to nearest); widen: back (exact).
+cudaError_t launch_sgd_narrow(int64_t m, int64_t n, int32_t k, const double *P,
+                              const double *Q, const double *bu,
+                              const double *bi, float *P32, float *Q32,
+                              cudaStream_t st);
+cudaError_t launch_sgd_widen(int64_t m, int64_t n, int32_t k, const float *P32,
+                             const float *Q32, double *P, double *Q,
+                             double *bu, double *bi, cudaStream_t st);
+// Shared memory a block of `rows` users and `cols` items stages.
+inline size_t sgd_stage_bytes(int64_t rows, int64_t cols, int32_t k) {
+  return (size_t)(rows + cols) * sizeof(float) * (size_t)(k + 2);
+}
+// One schedule step of the float32 form: nb blocks, one CTA each (its
+// first warp walks the ratings). stage_bytes > 0: every block stages its
+// rows and columns in that much shared memory (the largest block's
+// sgd_stage_bytes); 0: the blocks work in global memory.
+cudaError_t launch_sgd_step_f32(const GridDesc &g, int32_t nb,
+                                const int32_t *blocks, const int64_t *range,
+                                const int32_t *sr, const int32_t *sc,
+                                const int32_t *su, const int32_t *si,
+                                const float *sx, int64_t nnz, int32_t k,
+                                float *P32, float *Q32, const SgdRates32 &r,
+                                size_t stage_bytes, int32_t *err,
+                                cudaStream_t st);
 // Sum of squared training errors into *out (fixed order); partials holds
 // kSqerrBlocks doubles.
 cudaError_t launch_sgd_sqerr(int64_t nnz, const int32_t *u, const int32_t *i,

@@ -178,17 +178,28 @@ k_sgd_sort_big(const int64_t *__restrict__ off,
   }
 }
 
+// Gathers the ratings into epoch order. Only the first *placed entries of
+// src were written (a rating with an id out of range was counted nowhere and
+// is reported by k_sgd_count), so only those are read.
 __global__ void __launch_bounds__(256)
-k_sgd_gather(int64_t nnz, const int64_t *__restrict__ src,
+k_sgd_gather(GridDesc g, const int64_t *__restrict__ placed,
+             const int64_t *__restrict__ src,
              const int32_t *__restrict__ u, const int32_t *__restrict__ it,
              const float *__restrict__ x, int32_t *__restrict__ su,
-             int32_t *__restrict__ si, float *__restrict__ sx) {
+             int32_t *__restrict__ si, float *__restrict__ sx,
+             int32_t *__restrict__ sr, int32_t *__restrict__ sc) {
+  const int64_t nnz = *placed;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = src[t];
-    su[t] = u[s];
-    si[t] = it[s];
+    const int32_t uu = u[s], ii = it[s];
+    int32_t blk = 0, r = 0, c = 0;
+    locate(g, uu, ii, &blk, &r, &c);      // in range: checked by k_sgd_count
+    su[t] = uu;
+    si[t] = ii;
     sx[t] = x[s];
+    sr[t] = r;
+    sc[t] = c;
   }
 }
 
@@ -287,6 +298,201 @@ k_sgd_step(const int32_t *__restrict__ blocks, const int64_t *__restrict__ range
   }
 }
 
+// ---- the float32 form -----------------------------------------------------
+//
+// A block's walk is a chain of dependent operations, each rating's update
+// feeding the next rating's dot product. In float64 on GB300 one link of
+// that chain costs about as much as a whole float32 rating, so the float32
+// form runs the same operations, in the same order and with the same
+// single rounding each, in float32.
+//
+// Parameters live as rows of k + 1 floats: factors 0 .. k-1, then the bias.
+// One CTA per block of the step. When the step's blocks fit in shared
+// memory, the CTA first stages its block's rows (the users of its block row
+// and the items of its block column that have ratings in the block), the
+// first warp walks the ratings against shared memory (lane f owns factor f;
+// lane 0 stores the biases), and the CTA writes the rows back. The next
+// rating's rows are loaded one rating ahead and its ids two ahead; a row it
+// shares with the current rating is carried in registers. Otherwise the
+// warp works on the rows in global memory the same way.
+
+__global__ void __launch_bounds__(256)
+k_sgd_narrow(int64_t m, int64_t n, int32_t k, const double *__restrict__ P,
+             const double *__restrict__ Q, const double *__restrict__ bu,
+             const double *__restrict__ bi, float *__restrict__ P32,
+             float *__restrict__ Q32) {
+  const int64_t kk = k + 1, np = m * kk, total = np + n * kk;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const bool user = e < np;
+    const int64_t a = user ? e : e - np;
+    const int64_t row = a / kk, f = a - row * kk;
+    double v;
+    if (user) v = f < k ? P[row * k + f] : bu[row];
+    else v = f < k ? Q[row * k + f] : bi[row];
+    if (user) P32[a] = __double2float_rn(v);
+    else Q32[a] = __double2float_rn(v);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_sgd_widen(int64_t m, int64_t n, int32_t k, const float *__restrict__ P32,
+            const float *__restrict__ Q32, double *__restrict__ P,
+            double *__restrict__ Q, double *__restrict__ bu,
+            double *__restrict__ bi) {
+  const int64_t kk = k + 1, np = m * kk, total = np + n * kk;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const bool user = e < np;
+    const int64_t a = user ? e : e - np;
+    const int64_t row = a / kk, f = a - row * kk;
+    const double v = (double)(user ? P32[a] : Q32[a]);
+    if (user) {
+      if (f < k) P[row * k + f] = v;
+      else bu[row] = v;
+    } else {
+      if (f < k) Q[row * k + f] = v;
+      else bi[row] = v;
+    }
+  }
+}
+
+// The walk of one block's ratings [t0, t1) by one warp. Rows are
+// Pr + ru[t] * (k + 1) and Qr + ci[t] * (k + 1): shared memory with local
+// indices, or global memory with ids.
+__device__ __forceinline__ void sgd_walk_f32(
+    int64_t t0, int64_t t1, const int32_t *__restrict__ ru,
+    const int32_t *__restrict__ ci, const float *__restrict__ sx, int32_t k,
+    float *Pr, float *Qr, const SgdRates32 &r) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x;
+  const bool mine = lane < k;
+  const int64_t kk = k + 1;
+  int32_t uu = ru[t0], ii = ci[t0];
+  float xx = sx[t0];
+  const bool two = t0 + 1 < t1;
+  int32_t un = two ? ru[t0 + 1] : uu, in = two ? ci[t0 + 1] : ii;
+  float xn = two ? sx[t0 + 1] : 0.f;
+  float pf = mine ? Pr[uu * kk + lane] : 0.f;
+  float qf = mine ? Qr[ii * kk + lane] : 0.f;
+  float bu0 = Pr[uu * kk + k], bi0 = Qr[ii * kk + k];
+  for (int64_t t = t0; t < t1; ++t) {
+    // ids of rating t + 2; the rows of t + 1 unless shared with t
+    const bool more = t + 1 < t1, more2 = t + 2 < t1;
+    const int32_t u2 = more2 ? ru[t + 2] : un;
+    const int32_t i2 = more2 ? ci[t + 2] : in;
+    const float x2 = more2 ? sx[t + 2] : 0.f;
+    const bool new_u = more && un != uu, new_i = more && in != ii;
+    float pn = 0.f, qn = 0.f, bun = 0.f, bin = 0.f;
+    if (new_u) {
+      pn = mine ? Pr[un * kk + lane] : 0.f;
+      bun = Pr[un * kk + k];
+    }
+    if (new_i) {
+      qn = mine ? Qr[in * kk + lane] : 0.f;
+      bin = Qr[in * kk + k];
+    }
+    // rating t: the dot product in f order, in chunks of eight shuffles
+    const float prod = __fmul_rn(pf, qf);
+    float dot = 0.f;
+#pragma unroll
+    for (int j0 = 0; j0 < 32; j0 += 8) {
+      if (j0 < k) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __shfl_sync(kAll, prod, j0 + j);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (j0 + j < k) dot = __fadd_rn(dot, v[j]);
+      }
+    }
+    const float e = __fsub_rn(__fsub_rn(__fsub_rn(xx, bu0), bi0), dot);
+    const float bu1 = __fadd_rn(bu0, __fmul_rn(r.a_ubias, __fsub_rn(
+                                         e, __fmul_rn(r.b_ubias, bu0))));
+    const float bi1 = __fadd_rn(bi0, __fmul_rn(r.a_ibias, __fsub_rn(
+                                         e, __fmul_rn(r.b_ibias, bi0))));
+    const float p1 = __fadd_rn(pf, __fmul_rn(r.a_user, __fsub_rn(
+                                       __fmul_rn(e, qf), __fmul_rn(r.b_user, pf))));
+    const float q1 = __fadd_rn(qf, __fmul_rn(r.a_item, __fsub_rn(
+                                       __fmul_rn(e, pf), __fmul_rn(r.b_item, qf))));
+    if (mine) {
+      Pr[uu * kk + lane] = p1;
+      Qr[ii * kk + lane] = q1;
+    }
+    if (lane == 0) {
+      Pr[uu * kk + k] = bu1;
+      Qr[ii * kk + k] = bi1;
+    }
+    // every lane reads the biases lane 0 stored, at a later rating
+    __syncwarp();
+    pf = new_u ? pn : p1;
+    qf = new_i ? qn : q1;
+    bu0 = new_u ? bun : bu1;
+    bi0 = new_i ? bin : bi1;
+    uu = un;
+    ii = in;
+    xx = xn;
+    un = u2;
+    in = i2;
+    xn = x2;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_sgd_step_f32(GridDesc g, const int32_t *__restrict__ blocks,
+               const int64_t *__restrict__ range,
+               const int32_t *__restrict__ sr, const int32_t *__restrict__ sc,
+               const int32_t *__restrict__ su, const int32_t *__restrict__ si,
+               const float *__restrict__ sx, int64_t nnz, int32_t k,
+               float *P32, float *Q32, SgdRates32 r, int staged, int32_t *err) {
+  extern __shared__ float stage[];
+  const int32_t b = blocks[blockIdx.x];
+  const int64_t t0 = range[2 * b], t1 = range[2 * b + 1];
+  if (t0 < 0 || t1 > nnz || t0 > t1) {     // never expected: refuse to run
+    if (threadIdx.x == 0) atomicOr(err, kErrIndex);
+    return;
+  }
+  if (t0 == t1) return;
+  if (!staged) {
+    if (threadIdx.x < 32) sgd_walk_f32(t0, t1, su, si, sx, k, P32, Q32, r);
+    return;
+  }
+  const int32_t bi = g.diag ? b : b / g.q, bj = g.diag ? b : b % g.q;
+  const int64_t rows = g.row_bounds[bi + 1] - g.row_bounds[bi];
+  const int64_t cols = g.col_bounds[bj + 1] - g.col_bounds[bj];
+  const int64_t kk = k + 1;
+  float *Ps = stage;
+  float *Qs = Ps + rows * kk;
+  int32_t *ids = reinterpret_cast<int32_t *>(Qs + cols * kk);  // rows, cols
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // slot -> id of the users and items the block's ratings touch (-1: none)
+  for (int64_t s = tid; s < rows + cols; s += nt) ids[s] = -1;
+  __syncthreads();
+  for (int64_t t = t0 + tid; t < t1; t += nt) {
+    ids[sr[t]] = su[t];
+    ids[rows + sc[t]] = si[t];
+  }
+  __syncthreads();
+  for (int64_t e = tid; e < (rows + cols) * kk; e += nt) {
+    const int64_t s = e / kk;
+    const int32_t id = ids[s];
+    if (id >= 0)
+      stage[e] = s < rows ? P32[(int64_t)id * kk + (e - s * kk)]
+                          : Q32[(int64_t)id * kk + (e - s * kk)];
+  }
+  __syncthreads();
+  if (tid < 32) sgd_walk_f32(t0, t1, sr, sc, sx, k, Ps, Qs, r);
+  __syncthreads();
+  for (int64_t e = tid; e < (rows + cols) * kk; e += nt) {
+    const int64_t s = e / kk;
+    const int32_t id = ids[s];
+    if (id >= 0) {
+      float *dst = s < rows ? P32 : Q32;
+      dst[(int64_t)id * kk + (e - s * kk)] = stage[e];
+    }
+  }
+}
+
 // Eq. 3 in the oracle's order: (sum_f p_f q_f, in f order) + bu + bi
 __device__ __forceinline__ double sgd_eval(int32_t k, const double *P,
                                            const double *Q, const double *bu,
@@ -367,8 +573,8 @@ cudaError_t launch_sgd_order(const GridDesc &g, int32_t nblocks, int64_t nnz,
                              const int32_t *u, const int32_t *i, const float *x,
                              unsigned long long *cnt, int64_t *off,
                              int64_t *key, int64_t *src, int32_t *su,
-                             int32_t *si, float *sx, int64_t *range,
-                             int32_t *err, cudaStream_t st) {
+                             int32_t *si, float *sx, int32_t *sr, int32_t *sc,
+                             int64_t *range, int32_t *err, cudaStream_t st) {
   const int64_t nbuckets = (int64_t)(g.diag ? g.p : g.q) * g.m;
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * nbuckets,
                                   st);
@@ -391,7 +597,8 @@ cudaError_t launch_sgd_order(const GridDesc &g, int32_t nblocks, int64_t nnz,
     if (e != cudaSuccess) return e;
     k_sgd_sort_big<<<152 * 2, 1024, sizeof(unsigned long long) * kSortTile,
                      st>>>(off, cnt, key, src);
-    k_sgd_gather<<<sgd_grid(nnz), 256, 0, st>>>(nnz, src, u, i, x, su, si, sx);
+    k_sgd_gather<<<sgd_grid(nnz), 256, 0, st>>>(g, off + nbuckets, src, u, i,
+                                                x, su, si, sx, sr, sc);
   }
   k_sgd_ranges<<<(nblocks + 255) / 256, 256, 0, st>>>(g, nblocks, off, range);
   return cudaGetLastError();
@@ -406,6 +613,44 @@ cudaError_t launch_sgd_step(int32_t nb, const int32_t *blocks,
   if (nb <= 0) return cudaSuccess;
   k_sgd_step<<<nb, 32, 0, st>>>(blocks, range, su, si, sx, nnz, k, P, Q, bu,
                                 bi, r, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sgd_narrow(int64_t m, int64_t n, int32_t k, const double *P,
+                              const double *Q, const double *bu,
+                              const double *bi, float *P32, float *Q32,
+                              cudaStream_t st) {
+  k_sgd_narrow<<<sgd_grid((m + n) * (k + 1)), 256, 0, st>>>(m, n, k, P, Q, bu,
+                                                            bi, P32, Q32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sgd_widen(int64_t m, int64_t n, int32_t k, const float *P32,
+                             const float *Q32, double *P, double *Q,
+                             double *bu, double *bi, cudaStream_t st) {
+  k_sgd_widen<<<sgd_grid((m + n) * (k + 1)), 256, 0, st>>>(m, n, k, P32, Q32,
+                                                           P, Q, bu, bi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sgd_step_f32(const GridDesc &g, int32_t nb,
+                                const int32_t *blocks, const int64_t *range,
+                                const int32_t *sr, const int32_t *sc,
+                                const int32_t *su, const int32_t *si,
+                                const float *sx, int64_t nnz, int32_t k,
+                                float *P32, float *Q32, const SgdRates32 &r,
+                                size_t stage_bytes, int32_t *err,
+                                cudaStream_t st) {
+  if (nb <= 0) return cudaSuccess;
+  if (stage_bytes > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_sgd_step_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)stage_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  k_sgd_step_f32<<<nb, 256, stage_bytes, st>>>(g, blocks, range, sr, sc, su,
+                                                si, sx, nnz, k, P32, Q32, r,
+                                                stage_bytes > 0 ? 1 : 0, err);
   return cudaGetLastError();
 }
 

@@ -41,6 +41,19 @@ def test_config_layout_matches_header():
     assert bs.Config.panel_path.offset == 64 and cfg.panel_path == 0
 
 
+def test_sgd_params_layout_matches_header():
+    prm = bs.SgdParams()
+    prm.precision = 7
+    prm.max_steps = -3
+    bs.load().bsvd_sgd_params_default(ctypes.byref(prm))
+    assert prm.k == 13 and prm.max_steps == 100 and prm.a_user == 0.019
+    # the last field is written where the binding reads it
+    assert prm.precision == bs.SGD_FP64 == 0 and bs.SGD_FP32 == 1
+    # double x9, int32 x3, padded to 8
+    assert ctypes.sizeof(bs.SgdParams) == 88
+    assert bs.SgdParams.precision.offset == 80
+
+
 def test_binding_signatures_match_header_arity():
     """Every declared function has ctypes argument types, as many as the
     header's parameter list (a missing one would silently convert a pointer

@@ -18,7 +18,7 @@ from paper_1907_07410_gb300 import grid as qgrid  # noqa: E402
 
 
 def run_both(r, p, q, k, steps, delta=-1e300, grid_kw=None, rates=None,
-             seed=13, on_device=False):
+             seed=13, on_device=False, f32=False):
     P0, Q0 = synth.sgd_start(r.m, r.n, k, seed)
     grid_kw = grid_kw or {}
     ctx = bs.Context()
@@ -32,11 +32,14 @@ def run_both(r, p, q, k, steps, delta=-1e300, grid_kw=None, rates=None,
                   p, q, **gk)
     ctx.sgd_prepare(conv(r.u_train), conv(r.i_train), conv(r.x_train))
     rk = dict(vars(rates)) if rates else {}
+    if f32:
+        rk["precision"] = bs.SGD_FP32
     hist, ran = ctx.sgd_train(conv(P0), conv(Q0), max_steps=steps,
                               delta=delta, **rk)
     g = oracle.make_grid(r.m, r.n, p, q, **grid_kw)
     ref = osgd.train(g, r.u_train, r.i_train, r.x_train, P0, Q0, steps,
-                     rates=rates, delta=delta)
+                     rates=rates, delta=delta,
+                     dtype=np.float32 if f32 else np.float64)
     return ctx, hist, ran, ref
 
 
@@ -67,13 +70,51 @@ def test_grid_shapes_and_ranks(p, q, k):
     assert_same(ctx, hist, ran, ref)
 
 
-def test_quantile_grid_with_permutations_on_device_inputs():
+@pytest.mark.parametrize("f32", [False, True])
+def test_quantile_grid_with_permutations_on_device_inputs(f32):
     w = synth.UNEVEN
     r = synth.generate(w)
     kw = qgrid.quantile_grid(r.u_train, r.i_train, w.m, w.n, w.p, w.q)
     ctx, hist, ran, ref = run_both(r, w.p, w.q, osgd.K, 1, grid_kw=kw,
-                                   on_device=True)
+                                   on_device=True, f32=f32)
     assert_same(ctx, hist, ran, ref)
+
+
+# ---- the float32 form: bit-identical to the float32 oracle ----------------
+
+@pytest.mark.parametrize("p,q,k", [(3, 2, 7), (2, 5, 1), (1, 1, 32),
+                                   (4, 4, 13), (7, 3, 5), (2, 3, 16)])
+def test_float32_form_grid_shapes_and_ranks(p, q, k):
+    """Blocks small enough to stage in shared memory."""
+    r = synth.random_ratings(31, 300, 200, 6000, 0)
+    ctx, hist, ran, ref = run_both(r, p, q, k, 2, f32=True)
+    assert_same(ctx, hist, ran, ref)
+
+
+def test_float32_form_in_global_memory():
+    """One block of 3,000 users and 600 items at k = 32 needs
+    3,600 x 34 x 4 = 490 KB, more than a CTA's shared memory: the block
+    works on its rows in global memory."""
+    r = synth.random_ratings(34, 3000, 600, 30000, 0)
+    ctx, hist, ran, ref = run_both(r, 1, 1, 32, 2, f32=True)
+    assert_same(ctx, hist, ran, ref)
+    ctx, hist, ran, ref = run_both(r, 2, 2, 32, 2, f32=True)
+    assert_same(ctx, hist, ran, ref)
+
+
+def test_float32_form_medium_workload_tracks_float64():
+    """The paper's 8 x 8 grid: three epochs equal the float32 oracle bit
+    for bit, and stay within float32 rounding of the float64 form."""
+    w = synth.MEDIUM_8x8
+    r = synth.generate(w)
+    ctx, hist, ran, ref = run_both(r, w.p, w.q, osgd.K, 3, f32=True)
+    assert_same(ctx, hist, ran, ref)
+    _, hist64, _, _ = run_both(r, w.p, w.q, osgd.K, 3)
+    np.testing.assert_allclose(hist, hist64, rtol=1e-5)
+    assert hist[-1] < hist[0]
+    got = ctx.sgd_predict(r.u_test, r.i_test)
+    want = osgd.predict(ref.P, ref.Q, ref.bu, ref.bi, r.u_test, r.i_test)
+    assert np.array_equal(got, want)
 
 
 def test_medium_workload_stops_where_the_oracle_stops():
@@ -133,6 +174,10 @@ def test_block_diagonal_batch_is_one_step():
     g = oracle.make_grid(130, 80, 3, 3, row_bounds=rb, col_bounds=cb)
     ref = osgd.train(g, u, i, x, P0, Q0, 3, delta=-1e300)
     assert_same(ctx, hist, ran, ref)
+    hist, ran = ctx.sgd_train(P0, Q0, max_steps=3, delta=-1e300,
+                              precision=bs.SGD_FP32)
+    ref = osgd.train(g, u, i, x, P0, Q0, 3, delta=-1e300, dtype=np.float32)
+    assert_same(ctx, hist, ran, ref)
 
 
 def test_call_order_and_bad_arguments():
@@ -157,6 +202,9 @@ def test_call_order_and_bad_arguments():
             ctx.sgd_train(np.zeros((50, max(kk, 1))), np.zeros((40, max(kk, 1))),
                           k=kk)
         assert e.value.status == bs.EINVAL
+    with pytest.raises(bs.BsvdError) as e:
+        ctx.sgd_train(P0, Q0, precision=2)
+    assert e.value.status == bs.EINVAL
     with pytest.raises(bs.BsvdError) as e:
         ctx.sgd_predict(r.u_test, r.i_test)
     assert e.value.status == bs.ESTATE
