@@ -17,11 +17,13 @@
  *
  * Conventions shared by every call:
  *   - Ids are 0-based. A rating is observed when it is listed in the COO
- *     input. Ratings must be finite, |x| < 2^31, and a block's count times
- *     its largest |x| must stay below 2^31. Block sums are then exact for
- *     every rating that is a multiple of 2^-32; in float32 that is every
- *     value with |x| >= 2^-9. Smaller non-zero ratings are rounded to a
- *     multiple of 2^-32 before they are summed.
+ *     input. Ratings must be finite, |x| < 2^31, and the number of
+ *     ratings times the largest |x| must stay below 2^31: the block sums,
+ *     and their total (which gives an empty block's mean), are 64-bit
+ *     fixed point with 32 fraction bits (otherwise BSVD_EINVAL). Block sums
+ *     are then exact for every rating that is a multiple of 2^-32; in
+ *     float32 that is every value with |x| >= 2^-9. Smaller non-zero
+ *     ratings are rounded to a multiple of 2^-32 before they are summed.
  *   - Pointers named "host or device" may point to either kind of memory.
  *     The library asks the CUDA runtime which kind it is. Host data is
  *     copied to device buffers that the context owns; device data is used
