@@ -97,8 +97,8 @@ def fp32_alu_peak_tflops(peaks):
 
 
 def gram_flops(blocks):
-    """Gram work as the survey counts it: 2 m_b n_b s_b flop per block
-    (s = min side), both triangles of the symmetric product."""
+    """Gram work as a general product counts it: 2 m_b n_b s_b flop per
+    block (s = min side), both triangles of the symmetric product."""
     return float(sum(2.0 * L * s * s for (s, L) in blocks))
 
 

@@ -54,7 +54,7 @@ def test_step_roofline_takes_the_binding_term():
     assert out["roofline_ms"] == pytest.approx(max(out["tensor_ms"],
                                                    out["hbm_ms"]))
     assert out["frac"] == pytest.approx(out["roofline_ms"] / 1e4)
-    # bytes as the survey's step roofline counts them: 12 a training rating,
+    # bytes as the step roofline counts them: 12 a training rating,
     # 4 + 2 + 4 a dense cell (written, read by the bf16 Gram, read by the
     # projection), 12 + 8 k a query
     assert out["algorithmic_bytes"] == 12 * 1000 + 6 * 10 + 100 * (12 + 32)
