@@ -448,7 +448,7 @@ def serve_leg(rates, per_rate=None, workers=4, max_batch=64, budget=120e9):
     return out
 
 
-def sgd_leg(r, w, epochs=10, grids=(8, 64, 256)):
+def sgd_leg(r, w, epochs=10, grids=(8, 64, 256), gpu=0):
     """The paper's own method (blocked SGD, Algorithms 1-2) on the same
     matrix: `epochs` epochs from seeded starting factors with the Section 5
     hyper-parameters (k = 13), on the 8 x 8 grid the paper's CPU run used
@@ -456,7 +456,9 @@ def sgd_leg(r, w, epochs=10, grids=(8, 64, 256)):
     its schedule steps and the training-RMSE of Algorithm 1's stopping rule.
     Both arithmetic forms run: float64 (bit-identical to the float64
     oracle) and float32 (bit-identical to the float32 oracle). Beside them,
-    one epoch of each sequential oracle on the host."""
+    one epoch of each sequential oracle on the host. The SM clock is
+    sampled during each timed run: a walk of one warp per block keeps only
+    a few SMs busy."""
     import torch
     import paper_1907_07410_gb300 as bs
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
@@ -474,11 +476,14 @@ def sgd_leg(r, w, epochs=10, grids=(8, 64, 256)):
             ctx.sgd_train(dP, dQ, max_steps=1, delta=-1e300,
                           precision=prec)                       # warm-up
             torch.cuda.synchronize()
+            clocks = ClockSampler(gpu)
+            clocks.start()
             t0 = time.perf_counter()
             hist, ran = ctx.sgd_train(dP, dQ, max_steps=epochs, delta=-1e300,
                                       precision=prec)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
+            clk = clocks.stop()
             yh = ctx.sgd_predict(r.u_test, r.i_test)
             test = float(np.sqrt(np.mean((yh - r.x_test) ** 2)))
             out["grids"].append({
@@ -486,7 +491,8 @@ def sgd_leg(r, w, epochs=10, grids=(8, 64, 256)):
                 "s_per_epoch": dt / ran,
                 "ratings_per_s": r.u_train.size * ran / dt,
                 "train_rmse_start": float(hist[0]),
-                "train_rmse_end": float(hist[-1]), "test_rmse_end": test})
+                "train_rmse_end": float(hist[-1]), "test_rmse_end": test,
+                "clocks": clk})
     # the oracle: one epoch, sequential, on the host
     import oracle
     from oracle import sgd as osgd
@@ -953,7 +959,7 @@ def main():
         line["served"] = serve_leg(rates, args.serve_requests or None)
     if world == 1 and not args.no_sgd:
         wm = synth.MEDIUM
-        line["sgd"] = sgd_leg(synth.generate(wm), wm)
+        line["sgd"] = sgd_leg(synth.generate(wm), wm, gpu=local)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -110,3 +110,34 @@ def test_step_partition_picks_the_call():
     assert [c[0] for c in calls] == ["quantile", "equal"]
     w = synth.UNEVEN
     assert calls[0][1] == (w.m, w.n, "u", "i", "x", w.p, w.q)
+
+
+def test_clock_sampler_parses_nvidia_smi_lines(tmp_path, monkeypatch):
+    """The sampler reads nvidia-smi's CSV: median SM clock, the largest
+    maximum, and every throttle reason seen active; with no samples (no
+    nvidia-smi, or a run shorter than its first line) it reports None."""
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text(
+        "#!/bin/sh\n"
+        "echo '0, 1900, 2070, 900.1, 0x4, Not Active, Not Active, Not Active, Active'\n"
+        "echo '0, 2070, 2070, 910.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+        "echo '0, 2000, 2070, 905.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+        "echo 'garbage line'\n"
+        "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    c = bench.ClockSampler(0)
+    c.start()
+    import time
+    deadline = time.time() + 10
+    while time.time() < deadline:
+        if os.path.exists(c.path) and open(c.path).read().count("\n") >= 4:
+            break
+        time.sleep(0.05)
+    got = c.stop()
+    assert got == {"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "samples": 3,
+                   "reasons": ["sw_power_cap"]}
+    monkeypatch.setenv("PATH", str(tmp_path / "none"))
+    c = bench.ClockSampler(0)
+    c.start()
+    assert c.stop() is None
